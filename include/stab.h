@@ -1,0 +1,168 @@
+/*
+ * stab.h -- C ABI of the GB300 matrix-free global stability library.
+ *
+ * The library computes eigenvalues of the Jacobian J(q0) of the discretised
+ * compressible Navier-Stokes right-hand side N(q) in primitive (p, u_i, s)
+ * form (Sec. "Governing equations", Eq. navier_stokes), applied matrix-free
+ * as the epsilon-quotient of Eq. frechet, by the Cayley-transformed
+ * implicitly restarted Arnoldi method (Algorithm iram, Eq. cayley_transform)
+ * with GMRES inner solves (Sec. "Iterative solvers") and local block-Jacobi
+ * preconditioning (Sec. "Preconditioning").
+ *
+ * Conventions shared by every entry point:
+ *  - Vectors are complex128, interleaved (re, im), laid out [var][z][y][x]
+ *    with x fastest; n = nvars * nx * ny * nz, nvars = dim + 2 (p, u, v, [w], s).
+ *  - "device" pointers are CUDA global-memory addresses on the current
+ *    device (a torch tensor's data_ptr() qualifies); all device work is
+ *    ordered on the stream given to stab_create.
+ *  - Every call returns a stab_status and never aborts; the message of the
+ *    last failure is returned by stab_last_error.  A handle is used by one
+ *    host thread at a time.
+ *  - The handle owns its copies of the base state, its tables, its
+ *    workspace and its preconditioner; the caller owns every buffer it
+ *    passes in.
+ */
+#ifndef STAB_H
+#define STAB_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct stab_handle_s* stab_handle;
+
+typedef enum {
+  STAB_OK = 0,
+  STAB_ERR_INVALID_ARG = 1,   /* bad size, pointer or option */
+  STAB_ERR_OOM = 2,           /* device allocation failed */
+  STAB_ERR_CUDA = 3,          /* a CUDA runtime call failed */
+  STAB_ERR_NOT_CONVERGED = 4, /* iteration limit reached; partial results returned */
+  STAB_ERR_BREAKDOWN = 5,     /* Krylov breakdown (invariant subspace found early) */
+  STAB_ERR_NUMERIC = 6,       /* NaN / Inf met in a reduction or the Hessenberg matrix */
+  STAB_ERR_TIMEOUT = 7,       /* a bounded device-side wait ran out */
+  STAB_ERR_BUSY = 8,
+  STAB_ERR_UNSUPPORTED = 9    /* a valid option this build does not implement */
+} stab_status;
+
+/* Grid: x (and z) periodic with lengths lx (lz); y bounded on [ly0, ly1]
+ * with non-reflective boundaries (Sec. "Model problem").  stretch = 0 gives
+ * uniform y; beta > 0 places y(eta) = yc + (ly1-ly0)/2 sinh(beta(2 eta-1))/sinh(beta),
+ * eta uniform on [0, 1].  dim = 2 requires nz = 1.  Lines need nx, ny >= 6
+ * (nz >= 6 in 3-D). */
+typedef struct {
+  int dim;
+  int nx, ny, nz;
+  double lx, ly0, ly1, lz;
+  double stretch;
+} stab_grid;
+
+typedef struct {
+  double gamma;           /* ratio of specific heats, default 1.4 */
+  double sutherland_S;    /* Sutherland constant over the reference temperature, default 110.4/273.15 */
+  double bulk_visc_ratio; /* mu_v / mu, default 0 */
+  int eps_mode;           /* J v form: 0 = epsilon-quotient of Eq. frechet evaluated without
+                             cancellation (default); 2 = exact tangent (epsilon -> 0).
+                             1 (literal double quotient) returns STAB_ERR_UNSUPPORTED. */
+  double eps;             /* 0: eps = sqrt(eps_m)(1 + ||q0||_2)/||v||_2 per call; > 0: fixed */
+  int gmres_m;            /* inner GMRES restart length, default 30 */
+  int gmres_max_restarts; /* default 200 */
+  double gmres_tol;       /* inner relative residual tolerance, default 1e-10 */
+  int precond;            /* 0 none, 1 block-Jacobi */
+  int tile[3];            /* block-Jacobi tile in grid points (x, y, z), default 8 x 8 x 1 */
+  int precond_prec;       /* block-Jacobi inverse storage: 64 (FP64) or 32 (FP32), default 32 */
+  int max_restarts;       /* IRAM restart limit, default 300 */
+  unsigned long long seed;/* start vector seed when no v0 is given, default 0x5EED */
+} stab_opts;
+
+typedef struct {
+  long long jv_calls;         /* matrix-free operator applications (the paper's matvec count) */
+  long long gmres_iterations; /* inner iterations over all solves */
+  long long gmres_solves;     /* Cayley applications */
+  long long arnoldi_steps;
+  long long restarts;         /* IRAM restarts */
+  long long precond_builds;
+  double seconds_total;
+  double seconds_precond;
+} stab_stats;
+
+/* Fill *o with the defaults listed above. */
+void stab_default_opts(stab_opts* o);
+
+/* Create a handle for one problem.
+ *  base_flow : q0, FP64 [var][z][y][x] (n doubles), on the host
+ *              (base_on_device = 0) or device (1); copied.
+ *  Ma, Re, Pr: Mach, Reynolds (Re <= 0: inviscid, Re -> infinity) and Prandtl numbers,
+ *              nondimensionalised by the layer thickness, u_inf, rho_inf, T_inf.
+ *  opts      : NULL for defaults.   cuda_stream: a cudaStream_t or NULL (legacy stream).
+ * Errors: INVALID_ARG for bad sizes, OOM, CUDA; *h is NULL on failure. */
+stab_status stab_create(stab_handle* h, const double* base_flow, int base_on_device,
+                        const stab_grid* grid, double Ma, double Re, double Pr,
+                        const stab_opts* opts, void* cuda_stream);
+
+void stab_destroy(stab_handle h);
+
+/* Message of the last failed call on h (h may be NULL for stab_create failures). */
+const char* stab_last_error(stab_handle h);
+
+/* Number of complex unknowns n. */
+long long stab_size(stab_handle h);
+
+/* Jv = J(q0) v - shift v   (Eq. frechet; with shift = tau it is the Cayley
+ * right-hand side of Eq. cayley_arnoldi).  v, Jv: device complex128, n
+ * entries each, must not overlap.  The J v form follows opts.eps_mode. */
+stab_status stab_apply_J(stab_handle h, const void* v, void* Jv, double shift_re, double shift_im);
+
+/* epsilon used by the last stab_apply_J call (0 for the exact tangent).  Synchronises the stream. */
+stab_status stab_last_eps(stab_handle h, double* eps);
+
+/* Solve (J - sigma I) x = b by restarted, right-preconditioned (flexible)
+ * GMRES to ||b - (J - sigma I) x|| <= opts.gmres_tol ||b|| with x0 = 0
+ * (Sec. "Iterative solvers").  b, x: device complex128 n.  Uses the
+ * block-Jacobi preconditioner when opts.precond = 1 (built on first use for
+ * this sigma).  iters (host, may be NULL) receives the iteration count.
+ * NOT_CONVERGED if the restart limit is reached (x holds the last iterate). */
+stab_status stab_solve(stab_handle h, double sigma_re, double sigma_im, const void* b, void* x, int* iters);
+
+/* Build the block-Jacobi preconditioner for shift sigma (Sec.
+ * "Preconditioning"): one dense block per tile of opts.tile grid points with
+ * all variables, the principal submatrix of (J_tangent - sigma I) over the
+ * tile's unknowns (local order [var][lz][ly][lx]), inverted by LU with partial
+ * pivoting and stored in opts.precond_prec precision. */
+stab_status stab_precond_build(stab_handle h, double sigma_re, double sigma_im);
+
+/* z = M^{-1} q with the block-Jacobi preconditioner (built before).  Device complex128 n. */
+stab_status stab_precond_apply(stab_handle h, const void* q, void* z);
+
+/* Copy the assembled (unfactored) block of tile t, b x b complex128 row-major, to host memory
+ * `out`; assembles it on demand for sigma (diagnostics and tests). */
+stab_status stab_precond_block(stab_handle h, double sigma_re, double sigma_im, long long t, double* out);
+
+/* Orthogonalise w against the k orthonormal columns of V by classical
+ * Gram-Schmidt applied twice (CGS2): h = V^H w (both passes summed) and
+ * w <- w - V h; returns ||w|| after.  V: device complex128 n x k, column j at
+ * V + j*n; w: device complex128 n (updated in place); hcoef: host complex128 k
+ * (may be NULL); norm: host (may be NULL). */
+stab_status stab_orthogonalize(stab_handle h, const void* V, int k, void* w, double* hcoef, double* norm);
+
+/* Cayley-transformed IRAM (Algorithm iram on C = (J - sigma I)^{-1}(J - tau I),
+ * Eqs. cayley_transform and cayley_arnoldi): nev wanted Ritz values of largest
+ * |theta|, ncv Arnoldi vectors (nev < ncv <= n), Ritz estimate of Eq.
+ * ritz_estimate with tolerance tol.
+ *  v0     : device complex128 start vector or NULL (splitmix64 from opts.seed).
+ *  lambda : host complex128 nev (interleaved), eigenvalues of J, ordered by
+ *           decreasing |theta|, ties by larger Re then Im of lambda.
+ *  vecs   : device complex128 n x nev unit eigenvectors, or NULL.
+ *  resid  : host nev true residuals ||J x - lambda x|| / ||x|| (exact tangent J), or NULL.
+ *  nconv  : host, number of converged wanted pairs.   stats: may be NULL.
+ * NOT_CONVERGED if max_restarts is reached (partial results are returned). */
+stab_status stab_eigs(stab_handle h, double sigma_re, double sigma_im, double tau_re, double tau_im,
+                      int nev, int ncv, double tol, const void* v0, double* lambda, void* vecs,
+                      double* resid, int* nconv, stab_stats* stats);
+
+/* Counters accumulated over the handle's lifetime. */
+stab_status stab_get_stats(stab_handle h, stab_stats* stats);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* STAB_H */

@@ -1,0 +1,231 @@
+"""Thin ctypes binding of the C ABI declared in include/stab.h.
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library.  Device vectors are complex128 torch tensors on the GPU (their
+data_ptr() is passed through); the handle is bound to the torch stream that
+is current when it is created.  The library is loaded from this package's
+directory and a missing or unloadable library raises immediately.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libstab.so")
+
+STATUS = {0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "CUDA", 4: "NOT_CONVERGED", 5: "BREAKDOWN",
+          6: "NUMERIC", 7: "TIMEOUT", 8: "BUSY", 9: "UNSUPPORTED"}
+
+SYMBOLS = ["stab_default_opts", "stab_create", "stab_destroy", "stab_last_error", "stab_size", "stab_apply_J",
+           "stab_last_eps", "stab_solve", "stab_precond_build", "stab_precond_apply", "stab_precond_block",
+           "stab_orthogonalize", "stab_eigs", "stab_get_stats"]
+
+
+class StabError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Grid(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("lx", ctypes.c_double), ("ly0", ctypes.c_double), ("ly1", ctypes.c_double),
+                ("lz", ctypes.c_double), ("stretch", ctypes.c_double)]
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("gamma", ctypes.c_double), ("sutherland_S", ctypes.c_double), ("bulk_visc_ratio", ctypes.c_double),
+                ("eps_mode", ctypes.c_int), ("eps", ctypes.c_double), ("gmres_m", ctypes.c_int),
+                ("gmres_max_restarts", ctypes.c_int), ("gmres_tol", ctypes.c_double), ("precond", ctypes.c_int),
+                ("tile", ctypes.c_int * 3), ("precond_prec", ctypes.c_int), ("max_restarts", ctypes.c_int),
+                ("seed", ctypes.c_ulonglong)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("jv_calls", ctypes.c_longlong), ("gmres_iterations", ctypes.c_longlong),
+                ("gmres_solves", ctypes.c_longlong), ("arnoldi_steps", ctypes.c_longlong),
+                ("restarts", ctypes.c_longlong), ("precond_builds", ctypes.c_longlong),
+                ("seconds_total", ctypes.c_double), ("seconds_precond", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+
+def load():
+    """Load libstab.so (must have been built by build.build())."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"CUDA library not built: {LIB_PATH} missing (run __graft_entry__.build())")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, dp, i, d = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int, ctypes.c_double
+    L.stab_default_opts.argtypes = [ctypes.POINTER(Opts)]
+    L.stab_default_opts.restype = None
+    L.stab_create.argtypes = [ctypes.POINTER(vp), vp, i, ctypes.POINTER(Grid), d, d, d, ctypes.POINTER(Opts), vp]
+    L.stab_destroy.argtypes = [vp]
+    L.stab_destroy.restype = None
+    L.stab_last_error.argtypes = [vp]
+    L.stab_last_error.restype = ctypes.c_char_p
+    L.stab_size.argtypes = [vp]
+    L.stab_size.restype = ctypes.c_longlong
+    L.stab_apply_J.argtypes = [vp, vp, vp, d, d]
+    L.stab_last_eps.argtypes = [vp, dp]
+    L.stab_solve.argtypes = [vp, d, d, vp, vp, ctypes.POINTER(ctypes.c_int)]
+    L.stab_precond_build.argtypes = [vp, d, d]
+    L.stab_precond_apply.argtypes = [vp, vp, vp]
+    L.stab_precond_block.argtypes = [vp, d, d, ctypes.c_longlong, dp]
+    L.stab_orthogonalize.argtypes = [vp, vp, i, vp, dp, dp]
+    L.stab_eigs.argtypes = [vp, d, d, d, d, i, i, d, vp, dp, vp, dp, ctypes.POINTER(ctypes.c_int),
+                            ctypes.POINTER(Stats)]
+    L.stab_get_stats.argtypes = [vp, ctypes.POINTER(Stats)]
+    for name in SYMBOLS:
+        if name not in ("stab_default_opts", "stab_destroy", "stab_last_error", "stab_size"):
+            getattr(L, name).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def default_opts(**kw) -> Opts:
+    o = Opts()
+    load().stab_default_opts(ctypes.byref(o))
+    for k, v in kw.items():
+        if k == "tile":
+            t = list(v) + [1] * (3 - len(v))
+            o.tile[0], o.tile[1], o.tile[2] = t[:3]
+        else:
+            setattr(o, k, v)
+    return o
+
+
+def _ptr(t) -> int:
+    if t is None:
+        return None
+    if hasattr(t, "data_ptr"):
+        return t.data_ptr()
+    return int(t)
+
+
+@dataclass
+class EigResult:
+    lam: np.ndarray
+    resid: np.ndarray
+    nconv: int
+    status: int
+    stats: dict
+
+
+class Stab:
+    """One stability problem (grid, base state, flow parameters) on the GPU."""
+
+    def __init__(self, base_flow, grid, Ma: float, Re: float, Pr: float = 0.71, stream=None, **opts):
+        import torch
+        L = load()
+        self._L = L
+        self.opts = default_opts(**opts)
+        g = Grid(grid.dim, grid.nx, grid.ny, grid.nz, grid.lx, grid.ly0, grid.ly1, grid.lz, grid.stretch)
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        h = ctypes.c_void_p()
+        if isinstance(base_flow, torch.Tensor) and base_flow.is_cuda:
+            bf = base_flow.contiguous().to(torch.float64)
+            st = L.stab_create(ctypes.byref(h), bf.data_ptr(), 1, ctypes.byref(g), Ma, Re, Pr,
+                               ctypes.byref(self.opts), stream.cuda_stream)
+        else:
+            bf = np.ascontiguousarray(np.asarray(base_flow, dtype=np.float64).reshape(-1))
+            st = L.stab_create(ctypes.byref(h), bf.ctypes.data, 0, ctypes.byref(g), Ma, Re, Pr,
+                               ctypes.byref(self.opts), stream.cuda_stream)
+        if st != 0:
+            raise StabError(st, L.stab_last_error(None).decode())
+        self._h = h
+        self.n = int(L.stab_size(h))
+        self._npts_v = grid.nx * grid.ny * grid.nz
+        self._dim_v = grid.dim
+
+    def _check(self, st: int, allow=()):
+        if st != 0 and st not in allow:
+            raise StabError(st, self._L.stab_last_error(self._h).decode())
+        return st
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.stab_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def apply_J(self, v, out, shift: complex = 0.0):
+        self._check(self._L.stab_apply_J(self._h, _ptr(v), _ptr(out), complex(shift).real, complex(shift).imag))
+        return out
+
+    def last_eps(self) -> float:
+        e = ctypes.c_double()
+        self._check(self._L.stab_last_eps(self._h, ctypes.byref(e)))
+        return e.value
+
+    def solve(self, sigma: complex, b, x) -> tuple[int, int]:
+        it = ctypes.c_int()
+        st = self._check(self._L.stab_solve(self._h, complex(sigma).real, complex(sigma).imag, _ptr(b), _ptr(x),
+                                            ctypes.byref(it)), allow=(4,))
+        return st, it.value
+
+    def precond_build(self, sigma: complex):
+        self._check(self._L.stab_precond_build(self._h, complex(sigma).real, complex(sigma).imag))
+
+    def precond_apply(self, q, z):
+        self._check(self._L.stab_precond_apply(self._h, _ptr(q), _ptr(z)))
+        return z
+
+    def precond_block(self, sigma: complex, t: int) -> np.ndarray:
+        bsz = self.block_size()
+        out = np.empty(2 * bsz * bsz)
+        self._check(self._L.stab_precond_block(self._h, complex(sigma).real, complex(sigma).imag, t,
+                                               out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+        return out.view(np.complex128).reshape(bsz, bsz)
+
+    def block_size(self) -> int:
+        t = self.opts.tile
+        return (self.n // self._npts()) * t[0] * t[1] * (t[2] if self._dim() == 3 else 1)
+
+    def _npts(self):
+        return self._npts_v
+
+    def _dim(self):
+        return self._dim_v
+
+    def orthogonalize(self, V, k: int, w):
+        hc = np.zeros(2 * max(k, 1))
+        nrm = ctypes.c_double()
+        self._check(self._L.stab_orthogonalize(self._h, _ptr(V), k, _ptr(w),
+                                               hc.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                               ctypes.byref(nrm)))
+        return hc.view(np.complex128)[:k], nrm.value
+
+    def eigs(self, sigma: complex, tau: complex, nev: int, ncv: int, tol: float, v0=None, vecs=None) -> EigResult:
+        lam = np.zeros(2 * nev)
+        res = np.zeros(nev)
+        nconv = ctypes.c_int()
+        stats = Stats()
+        dp = ctypes.POINTER(ctypes.c_double)
+        st = self._check(self._L.stab_eigs(self._h, complex(sigma).real, complex(sigma).imag, complex(tau).real,
+                                           complex(tau).imag, nev, ncv, tol, _ptr(v0), lam.ctypes.data_as(dp),
+                                           _ptr(vecs), res.ctypes.data_as(dp), ctypes.byref(nconv),
+                                           ctypes.byref(stats)), allow=(4,))
+        return EigResult(lam.view(np.complex128), res, nconv.value, st, stats.as_dict())
+
+    def stats(self) -> dict:
+        s = Stats()
+        self._check(self._L.stab_get_stats(self._h, ctypes.byref(s)))
+        return s.as_dict()

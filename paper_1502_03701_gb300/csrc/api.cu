@@ -1,0 +1,169 @@
+// C ABI entry points: handle lifetime, argument checks, error reporting.
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "internal.cuh"
+
+struct stab_handle_s : StabHandle {};
+
+static thread_local std::string g_create_err;
+
+#define STAB_CUDA(h, call)                                                   \
+  do {                                                                       \
+    cudaError_t e_ = (call);                                                 \
+    if (e_ != cudaSuccess) {                                                 \
+      (h)->err = std::string(#call) + ": " + cudaGetErrorString(e_);         \
+      return e_ == cudaErrorMemoryAllocation ? STAB_ERR_OOM : STAB_ERR_CUDA; \
+    }                                                                        \
+  } while (0)
+
+extern "C" void stab_default_opts(stab_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->gamma = 1.4;
+  o->sutherland_S = 110.4 / 273.15;
+  o->bulk_visc_ratio = 0.0;
+  o->eps_mode = 0;
+  o->eps = 0.0;
+  o->gmres_m = 30;
+  o->gmres_max_restarts = 200;
+  o->gmres_tol = 1e-10;
+  o->precond = 0;
+  o->tile[0] = 8;
+  o->tile[1] = 8;
+  o->tile[2] = 1;
+  o->precond_prec = 32;
+  o->max_restarts = 300;
+  o->seed = 0x5EEDULL;
+}
+
+static void free_handle(stab_handle h) {
+  if (!h) return;
+  cudaFree(h->d_q0);
+  cudaFree(h->d_btab);
+  cudaFree(h->d_metric);
+  cudaFree(h->d_bcflags);
+  cudaFree(h->d_scratch);
+  cudaFree(h->d_red);
+  cudaFree(h->d_work);
+  cudaFree(h->d_pinv);
+  cudaFree(h->d_pblk);
+  for (int a = 0; a < 3; ++a) {
+    cudaFree(h->ax[a].tab[0]);
+    cudaFree(h->d_dmat[a]);
+  }
+  delete h;
+}
+
+extern "C" stab_status stab_create(stab_handle* out, const double* base_flow, int base_on_device,
+                                   const stab_grid* grid, double Ma, double Re, double Pr,
+                                   const stab_opts* opts, void* cuda_stream) {
+  if (!out) return STAB_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!base_flow || !grid) { g_create_err = "stab_create: null base_flow or grid"; return STAB_ERR_INVALID_ARG; }
+  const stab_grid& g = *grid;
+  if (!(g.dim == 2 || g.dim == 3) || g.nx < 6 || g.ny < 6 || (g.dim == 2 && g.nz != 1) || (g.dim == 3 && g.nz < 6)) {
+    g_create_err = "stab_create: need dim 2 (nz = 1) or 3, and nx, ny (nz in 3-D) >= 6";
+    return STAB_ERR_INVALID_ARG;
+  }
+  if (!(g.lx > 0) || !(g.ly1 > g.ly0) || (g.dim == 3 && !(g.lz > 0)) || g.stretch < 0 || !(Ma > 0) || !(Pr > 0)) {
+    g_create_err = "stab_create: invalid lengths, stretch, Mach or Prandtl number";
+    return STAB_ERR_INVALID_ARG;
+  }
+  stab_opts o;
+  if (opts) o = *opts; else stab_default_opts(&o);
+  if (o.eps_mode != 0 && o.eps_mode != 2) {
+    g_create_err = o.eps_mode == 1 ? "stab_create: eps_mode 1 (literal double quotient) is not implemented on the GPU"
+                                   : "stab_create: eps_mode must be 0 or 2";
+    return o.eps_mode == 1 ? STAB_ERR_UNSUPPORTED : STAB_ERR_INVALID_ARG;
+  }
+  if (o.gmres_m < 1 || o.gmres_m > 200 || !(o.gmres_tol > 0) || o.gmres_max_restarts < 1 || o.eps < 0 ||
+      !(o.gamma > 1) || o.sutherland_S < 0 || o.bulk_visc_ratio < 0 || o.max_restarts < 0 ||
+      (o.precond_prec != 32 && o.precond_prec != 64) || (o.precond != 0 && o.precond != 1)) {
+    g_create_err = "stab_create: invalid option value";
+    return STAB_ERR_INVALID_ARG;
+  }
+  stab_handle h = new (std::nothrow) stab_handle_s();
+  if (!h) return STAB_ERR_OOM;
+  h->dim = g.dim; h->nx = g.nx; h->ny = g.ny; h->nz = g.nz; h->nv = g.dim + 2;
+  h->npts = (long long)g.nx * g.ny * g.nz;
+  h->n = h->nv * h->npts;
+  h->lx = g.lx; h->ly0 = g.ly0; h->ly1 = g.ly1; h->lz = g.lz; h->stretch = g.stretch;
+  h->gamma = o.gamma; h->Ma = Ma; h->Re = Re; h->Pr = Pr; h->S = o.sutherland_S; h->bulk = o.bulk_visc_ratio;
+  h->R = 1.0 / (o.gamma * Ma * Ma);
+  h->cp = o.gamma * h->R / (o.gamma - 1.0);
+  h->visc = Re > 0.0;
+  h->opts = o;
+  h->stream = (cudaStream_t)cuda_stream;
+  h->last_eps_mode = -1;
+  // host copy of the base state: homogeneity test, norm, boundary flags
+  std::vector<double> q0((size_t)h->n);
+  cudaError_t e;
+  if (base_on_device) e = cudaMemcpy(q0.data(), base_flow, h->n * sizeof(double), cudaMemcpyDeviceToHost);
+  else { std::memcpy(q0.data(), base_flow, h->n * sizeof(double)); e = cudaSuccess; }
+  if (e != cudaSuccess) { g_create_err = std::string("stab_create: copy of base_flow: ") + cudaGetErrorString(e); free_handle(h); return STAB_ERR_CUDA; }
+  double nrm = 0.0;
+  bool finite = true, homog = true;
+  for (long long a = 0; a < h->n; ++a) { nrm += q0[a] * q0[a]; if (!std::isfinite(q0[a])) finite = false; }
+  for (int var = 0; var < h->nv && homog; ++var)
+    for (int k = 0; k < h->nz && homog; ++k)
+      for (int j = 0; j < h->ny && homog; ++j) {
+        const double* row = q0.data() + (long long)var * h->npts + ((long long)k * h->ny + j) * h->nx;
+        const double* ref = q0.data() + (long long)var * h->npts + (long long)j * h->nx;
+        for (int i = 0; i < h->nx; ++i) if (row[i] != ref[0]) { homog = false; break; }
+      }
+  bool positive = true;
+  for (long long a = 0; a < h->npts; ++a) if (!(q0[a] > 0)) positive = false;
+  if (!finite || !positive) { g_create_err = "stab_create: base_flow must be finite with positive pressure"; free_handle(h); return STAB_ERR_INVALID_ARG; }
+  h->q0norm = std::sqrt(nrm);
+  h->homog = homog;
+  h->nbase = homog ? h->ny : h->npts;
+  e = cudaMalloc(&h->d_q0, h->n * sizeof(double));
+  if (e == cudaSuccess) e = cudaMemcpy(h->d_q0, q0.data(), h->n * sizeof(double), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = jv_setup(h, q0.data());
+  if (e != cudaSuccess) {
+    g_create_err = std::string("stab_create: ") + cudaGetErrorString(e);
+    stab_status st = e == cudaErrorMemoryAllocation ? STAB_ERR_OOM : STAB_ERR_CUDA;
+    free_handle(h);
+    return st;
+  }
+  *out = h;
+  return STAB_OK;
+}
+
+extern "C" void stab_destroy(stab_handle h) {
+  if (!h) return;
+  cudaStreamSynchronize(h->stream);
+  free_handle(h);
+}
+
+extern "C" const char* stab_last_error(stab_handle h) { return h ? h->err.c_str() : g_create_err.c_str(); }
+
+extern "C" long long stab_size(stab_handle h) { return h ? h->n : 0; }
+
+extern "C" stab_status stab_apply_J(stab_handle h, const void* v, void* Jv, double shift_re, double shift_im) {
+  if (!h) return STAB_ERR_INVALID_ARG;
+  if (!v || !Jv) { h->err = "stab_apply_J: null vector"; return STAB_ERR_INVALID_ARG; }
+  const char* a = (const char*)v;
+  const char* b = (const char*)Jv;
+  const long long bytes = h->n * (long long)sizeof(double2);
+  if (a < b + bytes && b < a + bytes) { h->err = "stab_apply_J: v and Jv overlap"; return STAB_ERR_INVALID_ARG; }
+  STAB_CUDA(h, jv_apply(h, (const double2*)v, (double2*)Jv, make_double2(shift_re, shift_im), h->opts.eps_mode));
+  return STAB_OK;
+}
+
+extern "C" stab_status stab_last_eps(stab_handle h, double* eps) {
+  if (!h || !eps) return STAB_ERR_INVALID_ARG;
+  STAB_CUDA(h, cudaMemcpyAsync(eps, h->d_eps, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  STAB_CUDA(h, cudaStreamSynchronize(h->stream));
+  return STAB_OK;
+}
+
+extern "C" stab_status stab_get_stats(stab_handle h, stab_stats* s) {
+  if (!h || !s) return STAB_ERR_INVALID_ARG;
+  *s = h->stats;
+  return STAB_OK;
+}

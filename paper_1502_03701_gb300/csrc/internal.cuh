@@ -1,0 +1,109 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/stab.h"
+
+#define STAB_MAX_DIM 3
+#define STAB_MAX_JOBS 16
+
+// ---------------------------------------------------------------------------
+// Compact-scheme line solve tables for one axis (device pointers).
+// Kind 0 = first derivative, kind 1 = second derivative.  The implicit
+// tridiagonal system is solved as a forward sweep g_t = r_t - l_t g_{t-1}
+// followed by a backward sweep x_t = g_t dinv_t - m_t x_{t+1}: Thomas
+// elimination for bounded lines, the two first-order factors of the
+// circulant matrix for periodic lines.
+// ---------------------------------------------------------------------------
+struct AxisTables {
+  int n;
+  int periodic;
+  double h;
+  int K[2];             // warm-up length of a chunked sweep (influence decays below 2^-56)
+  double* tab[2];       // device: [l(n), dinv(n), m(n)] per kind
+};
+
+struct LineJob {
+  const double2* in;
+  double2* out1;  // first derivative (nullable)
+  double2* out2;  // second derivative (nullable)
+};
+
+// Scratch / base-table slot layout for a problem of dimension D.
+// Field f: 0 = p, 1..D = u_i, D+1 = s, D+2 = T.   Second-derivative field g:
+// 0..D-1 = u_i, D = T.   mix[i][k] = d/dx_i d/dx_k u_k (i != k).
+struct Slots {
+  int Tw;
+  int d1[3][6];
+  int d2[3][4];
+  int mix[3][3];
+  int count;
+};
+
+struct StabHandle {
+  // problem
+  int dim, nx, ny, nz, nv;
+  long long npts, n;
+  double lx, ly0, ly1, lz, stretch;
+  double gamma, Ma, Re, Pr, S, bulk;
+  double R, cp;
+  bool visc;
+  bool homog;        // base state depends on y only
+  long long nbase;   // ny if homog else npts
+  double q0norm;
+  stab_opts opts;
+  cudaStream_t stream;
+  Slots slots;
+  AxisTables ax[3];
+  // device memory
+  double* d_q0;          // base state, n doubles
+  double* d_btab;        // base tables (see jv.cu)
+  double* d_metric;      // eta_y[ny], eta_yy[ny]
+  unsigned char* d_bcflags;  // [2][nz*nx]
+  double2* d_scratch;    // slots.count * npts complex
+  double* d_red;         // reduction partials (red_blocks) + scalars
+  int red_blocks;
+  double* d_eps;         // scalar: epsilon of the last J v
+  int last_eps_mode;
+  // Krylov workspace (allocated on demand)
+  double2* d_work;
+  size_t work_elems;
+  // block-Jacobi preconditioner
+  void* d_pinv;          // inverses, FP64 or FP32 complex
+  double2* d_pblk;       // assembled blocks (FP64) scratch for the build
+  long long ntiles, bsize;
+  double psigma_re, psigma_im;
+  bool pvalid;
+  int pprec;
+  double* d_dmat[3];     // dense 1-D derivative matrices [kind][n*n] per axis (assembly)
+  // statistics
+  stab_stats stats;
+  std::string err;
+};
+
+// jv.cu
+cudaError_t jv_setup(StabHandle* h, const double* q0_host);
+cudaError_t jv_apply(StabHandle* h, const double2* v, double2* out, double2 shift, int eps_mode);
+cudaError_t launch_norm2(StabHandle* h, const double2* v, long long n, double* d_out, int mode);
+
+// krylov.cu
+cudaError_t kry_dot_batch(StabHandle* h, const double2* V, int k, long long n, const double2* w, double2* d_h);
+cudaError_t kry_gemv_sub(StabHandle* h, const double2* V, int k, long long n, const double2* d_h, double2* w);
+cudaError_t kry_gemv_add(StabHandle* h, const double2* V, int k, long long n, const double2* d_y, double2* x);
+cudaError_t kry_cgs2(StabHandle* h, const double2* V, int k, long long n, double2* w, double2* d_h, double* d_norm);
+cudaError_t kry_scale(StabHandle* h, double2* x, long long n, const double* d_norm, double2* out_or_null);
+cudaError_t kry_axpby(StabHandle* h, double2 a, const double2* x, double2 b, double2* y, long long n);
+cudaError_t kry_copy(StabHandle* h, const double2* x, double2* y, long long n);
+cudaError_t kry_update_basis(StabHandle* h, double2* V, int m, int k, long long n, const double2* d_Q, double2* tmp);
+
+// precond.cu
+cudaError_t pc_build(StabHandle* h, double2 sigma);
+cudaError_t pc_apply(StabHandle* h, const double2* q, double2* z);
+cudaError_t pc_block(StabHandle* h, double2 sigma, long long t, double2* d_out);
+
+// host dense helpers (hessenberg.cu)
+int hess_eig(int m, const double2* H, int ldh, double2* theta, double2* Y);  // returns 0 on success

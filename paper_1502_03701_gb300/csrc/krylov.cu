@@ -1,0 +1,212 @@
+// Krylov kernels: batched complex dot products (V^H w) with a fixed-order
+// two-stage reduction, V h updates, CGS2 (classical Gram-Schmidt twice), the
+// tall-skinny basis product V Q of the implicit restart, and vector helpers.
+// Vectors are complex128 (double2); a basis V of k vectors stores column j at
+// V + j*n.
+#include "internal.cuh"
+
+namespace {
+
+constexpr int kThreads = 256;
+
+__device__ __forceinline__ double warp_sum(double x) {
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  return x;
+}
+
+// partial[b * k + j] = sum over this block's rows of conj(V_j[i]) w[i]
+__global__ void __launch_bounds__(kThreads) k_dot_partial(const double2* __restrict__ V, int k, long long n,
+                                                         const double2* __restrict__ w, double2* partial) {
+  __shared__ double red[2][kThreads / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int j = 0; j < k; ++j) {
+    const double2* Vj = V + (long long)j * n;
+    double sr = 0.0, si = 0.0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+      double2 a = Vj[i], b = w[i];
+      sr = fma(a.x, b.x, fma(a.y, b.y, sr));   // Re(conj(a) b)
+      si = fma(a.x, b.y, fma(-a.y, b.x, si));  // Im(conj(a) b)
+    }
+    sr = warp_sum(sr);
+    si = warp_sum(si);
+    if (lane == 0) { red[0][wid] = sr; red[1][wid] = si; }
+    __syncthreads();
+    if (wid == 0) {
+      double tr = lane < kThreads / 32 ? red[0][lane] : 0.0;
+      double ti = lane < kThreads / 32 ? red[1][lane] : 0.0;
+      tr = warp_sum(tr);
+      ti = warp_sum(ti);
+      if (lane == 0) partial[(long long)blockIdx.x * k + j] = make_double2(tr, ti);
+    }
+    __syncthreads();
+  }
+}
+
+// out[j] (+)= sum_b partial[b * k + j], fixed order; one warp per column
+__global__ void k_dot_final(const double2* partial, int nb, int k, double2* out, int accumulate) {
+  const int j = blockIdx.x;
+  double sr = 0.0, si = 0.0;
+  for (int b = threadIdx.x; b < nb; b += 32) {
+    double2 p = partial[(long long)b * k + j];
+    sr += p.x;
+    si += p.y;
+  }
+  sr = warp_sum(sr);
+  si = warp_sum(si);
+  if (threadIdx.x == 0) {
+    if (accumulate) { out[j].x += sr; out[j].y += si; }
+    else out[j] = make_double2(sr, si);
+  }
+}
+
+// w[i] -= sum_j V_j[i] h[j]   (sign = -1)   or   x[i] += sum_j V_j[i] y[j]   (sign = +1)
+__global__ void __launch_bounds__(kThreads) k_gemv(const double2* __restrict__ V, int k, long long n,
+                                                  const double2* __restrict__ h, double2* x, double sign) {
+  extern __shared__ double2 hs[];
+  for (int j = threadIdx.x; j < k; j += blockDim.x) hs[j] = h[j];
+  __syncthreads();
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    double ar = 0.0, ai = 0.0;
+    for (int j = 0; j < k; ++j) {
+      double2 a = V[(long long)j * n + i], c = hs[j];
+      ar = fma(a.x, c.x, fma(-a.y, c.y, ar));
+      ai = fma(a.x, c.y, fma(a.y, c.x, ai));
+    }
+    double2 xv = x[i];
+    x[i] = make_double2(fma(sign, ar, xv.x), fma(sign, ai, xv.y));
+  }
+}
+
+// x = x / *d_norm  (into out if given)
+__global__ void k_scale_inv(double2* x, long long n, const double* d_norm, double2* out) {
+  const double s = 1.0 / *d_norm;
+  double2* o = out ? out : x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    double2 v = x[i];
+    o[i] = make_double2(v.x * s, v.y * s);
+  }
+}
+
+// y = a x + b y (complex a, b)
+__global__ void k_axpby(double2 a, const double2* x, double2 b, double2* y, long long n) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    double2 xv = x[i], yv = y[i];
+    y[i] = make_double2(a.x * xv.x - a.y * xv.y + b.x * yv.x - b.y * yv.y,
+                        a.x * xv.y + a.y * xv.x + b.x * yv.y + b.y * yv.x);
+  }
+}
+
+// tmp_j[i] = sum_l V_l[i] Q[l + j*m] for j < kk (Q column-major m x kk).  A
+// block stages its rows of V (rows x m) in shared memory once.
+constexpr int kVqRows = 64;
+__global__ void __launch_bounds__(kVqRows) k_vq(const double2* __restrict__ V, int m, long long n,
+                                               const double2* __restrict__ Q, int kk, double2* tmp) {
+  extern __shared__ double2 vs[];  // [m][kVqRows]
+  const long long i0 = (long long)blockIdx.x * kVqRows;
+  const long long i = i0 + threadIdx.x;
+  for (int l = 0; l < m; ++l) vs[l * kVqRows + threadIdx.x] = i < n ? V[(long long)l * n + i] : make_double2(0.0, 0.0);
+  __syncthreads();
+  if (i >= n) return;
+  for (int j = 0; j < kk; ++j) {
+    double ar = 0.0, ai = 0.0;
+    for (int l = 0; l < m; ++l) {
+      double2 a = vs[l * kVqRows + threadIdx.x], q = __ldg(&Q[(long long)j * m + l]);
+      ar = fma(a.x, q.x, fma(-a.y, q.y, ar));
+      ai = fma(a.x, q.y, fma(a.y, q.x, ai));
+    }
+    tmp[(long long)j * n + i] = make_double2(ar, ai);
+  }
+}
+
+int red_blocks(long long n) {
+  long long b = (n + kThreads - 1) / kThreads;
+  if (b > 152 * 4) b = 152 * 4;
+  return (int)(b < 1 ? 1 : b);
+}
+
+int grid_n(long long n) {
+  long long b = (n + kThreads - 1) / kThreads;
+  if (b > 152 * 16) b = 152 * 16;
+  return (int)(b < 1 ? 1 : b);
+}
+
+}  // namespace
+
+// h[0..k) = V^H w  (d_h device)
+cudaError_t kry_dot_batch(StabHandle* h, const double2* V, int k, long long n, const double2* w, double2* d_h) {
+  if (k <= 0) return cudaSuccess;
+  const int nb = red_blocks(n);
+  double2* partial = (double2*)h->d_red;  // needs nb * k complex: checked by the caller's workspace
+  (void)partial;
+  return cudaErrorNotSupported;
+}
+
+static cudaError_t dot_into(StabHandle* h, const double2* V, int k, long long n, const double2* w, double2* d_h,
+                            double2* partial, int accumulate) {
+  const int nb = red_blocks(n);
+  k_dot_partial<<<nb, kThreads, 0, h->stream>>>(V, k, n, w, partial);
+  k_dot_final<<<k, 32, 0, h->stream>>>(partial, nb, k, d_h, accumulate);
+  return cudaGetLastError();
+}
+
+cudaError_t kry_gemv_sub(StabHandle* h, const double2* V, int k, long long n, const double2* d_h, double2* w) {
+  if (k <= 0) return cudaSuccess;
+  k_gemv<<<grid_n(n), kThreads, k * sizeof(double2), h->stream>>>(V, k, n, d_h, w, -1.0);
+  return cudaGetLastError();
+}
+
+cudaError_t kry_gemv_add(StabHandle* h, const double2* V, int k, long long n, const double2* d_y, double2* x) {
+  if (k <= 0) return cudaSuccess;
+  k_gemv<<<grid_n(n), kThreads, k * sizeof(double2), h->stream>>>(V, k, n, d_y, x, 1.0);
+  return cudaGetLastError();
+}
+
+// CGS2: h = V^H w; w -= V h; h2 = V^H w; w -= V h2; h += h2; *d_norm = ||w||.
+// d_h must hold 2k complex (second half is scratch); the partials live in the
+// Krylov workspace provided by the caller through h->d_work tail.
+cudaError_t kry_cgs2_ws(StabHandle* h, const double2* V, int k, long long n, double2* w, double2* d_h, double* d_norm,
+                        double2* partial) {
+  cudaError_t e;
+  if (k > 0) {
+    if ((e = dot_into(h, V, k, n, w, d_h, partial, 0)) != cudaSuccess) return e;
+    if ((e = kry_gemv_sub(h, V, k, n, d_h, w)) != cudaSuccess) return e;
+    if ((e = dot_into(h, V, k, n, w, d_h + k, partial, 0)) != cudaSuccess) return e;
+    if ((e = kry_gemv_sub(h, V, k, n, d_h + k, w)) != cudaSuccess) return e;
+    k_axpby<<<1, 64, 0, h->stream>>>(make_double2(1.0, 0.0), d_h + k, make_double2(1.0, 0.0), d_h, k);
+  }
+  return launch_norm2(h, w, n, d_norm, 1);
+}
+
+cudaError_t kry_cgs2(StabHandle* h, const double2* V, int k, long long n, double2* w, double2* d_h, double* d_norm) {
+  (void)h; (void)V; (void)k; (void)n; (void)w; (void)d_h; (void)d_norm;
+  return cudaErrorNotSupported;
+}
+
+cudaError_t kry_scale(StabHandle* h, double2* x, long long n, const double* d_norm, double2* out) {
+  k_scale_inv<<<grid_n(n), kThreads, 0, h->stream>>>(x, n, d_norm, out);
+  return cudaGetLastError();
+}
+
+cudaError_t kry_axpby(StabHandle* h, double2 a, const double2* x, double2 b, double2* y, long long n) {
+  k_axpby<<<grid_n(n), kThreads, 0, h->stream>>>(a, x, b, y, n);
+  return cudaGetLastError();
+}
+
+cudaError_t kry_copy(StabHandle* h, const double2* x, double2* y, long long n) {
+  return cudaMemcpyAsync(y, x, n * sizeof(double2), cudaMemcpyDeviceToDevice, h->stream);
+}
+
+// tmp[:, 0:kk] = V[:, 0:m] Q  (Q device, column-major m x kk)
+cudaError_t kry_update_basis(StabHandle* h, double2* V, int m, int kk, long long n, const double2* d_Q, double2* tmp) {
+  const size_t smem = (size_t)m * kVqRows * sizeof(double2);
+  if (smem > 200 * 1024) return cudaErrorInvalidValue;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_vq, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr = true;
+  }
+  k_vq<<<(unsigned)((n + kVqRows - 1) / kVqRows), kVqRows, smem, h->stream>>>(V, m, n, d_Q, kk, tmp);
+  return cudaGetLastError();
+}
+
+int kry_partial_elems(long long n, int k) { return red_blocks(n) * (k > 0 ? k : 1); }
