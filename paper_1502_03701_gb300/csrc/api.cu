@@ -48,9 +48,11 @@ static void free_handle(stab_handle h) {
   cudaFree(h->d_bcflags);
   cudaFree(h->d_scratch);
   cudaFree(h->d_red);
-  cudaFree(h->d_work);
+  cudaFree(h->d_gm);
+  cudaFree(h->d_ir);
   cudaFree(h->d_pinv);
   cudaFree(h->d_pblk);
+  cudaFree(h->d_coef);
   for (int a = 0; a < 3; ++a) {
     cudaFree(h->ax[a].tab[0]);
     cudaFree(h->d_dmat[a]);

@@ -69,9 +69,11 @@ struct StabHandle {
   int red_blocks;
   double* d_eps;         // scalar: epsilon of the last J v
   int last_eps_mode;
-  // Krylov workspace (allocated on demand)
-  double2* d_work;
-  size_t work_elems;
+  // Krylov workspace (allocated on demand, grown as needed)
+  double2* d_gm;   // GMRES
+  size_t gm_elems;
+  double2* d_ir;   // IRAM
+  size_t ir_elems;
   // block-Jacobi preconditioner
   void* d_pinv;          // inverses, FP64 or FP32 complex
   double2* d_pblk;       // assembled blocks (FP64) scratch for the build
@@ -80,6 +82,8 @@ struct StabHandle {
   bool pvalid;
   int pprec;
   double* d_dmat[3];     // dense 1-D derivative matrices [kind][n*n] per axis (assembly)
+  double* d_coef;        // per-row tangent coefficients of the pointwise map (y-only base)
+  bool force_dn_path;    // use the full FP64 difference-number pointwise kernel
   // statistics
   stab_stats stats;
   std::string err;
@@ -89,21 +93,23 @@ struct StabHandle {
 cudaError_t jv_setup(StabHandle* h, const double* q0_host);
 cudaError_t jv_apply(StabHandle* h, const double2* v, double2* out, double2 shift, int eps_mode);
 cudaError_t launch_norm2(StabHandle* h, const double2* v, long long n, double* d_out, int mode);
+cudaError_t jv_derivative_matrices(StabHandle* h, int axis, double2* work, double2* out1, double2* out2);
 
 // krylov.cu
-cudaError_t kry_dot_batch(StabHandle* h, const double2* V, int k, long long n, const double2* w, double2* d_h);
+cudaError_t kry_dot(StabHandle* h, const double2* V, int k, long long n, const double2* w, double2* d_h,
+                    double2* partial, int accumulate);
 cudaError_t kry_gemv_sub(StabHandle* h, const double2* V, int k, long long n, const double2* d_h, double2* w);
 cudaError_t kry_gemv_add(StabHandle* h, const double2* V, int k, long long n, const double2* d_y, double2* x);
-cudaError_t kry_cgs2(StabHandle* h, const double2* V, int k, long long n, double2* w, double2* d_h, double* d_norm);
+cudaError_t kry_cgs2(StabHandle* h, const double2* V, int k, long long n, double2* w, double2* d_h2k, double* d_norm,
+                     double2* partial);
 cudaError_t kry_scale(StabHandle* h, double2* x, long long n, const double* d_norm, double2* out_or_null);
 cudaError_t kry_axpby(StabHandle* h, double2 a, const double2* x, double2 b, double2* y, long long n);
 cudaError_t kry_copy(StabHandle* h, const double2* x, double2* y, long long n);
-cudaError_t kry_update_basis(StabHandle* h, double2* V, int m, int k, long long n, const double2* d_Q, double2* tmp);
+cudaError_t kry_update_basis(StabHandle* h, double2* V, int m, int kk, long long n, const double2* d_Q, double2* tmp);
+int kry_partial_elems(long long n, int k);
 
 // precond.cu
 cudaError_t pc_build(StabHandle* h, double2 sigma);
 cudaError_t pc_apply(StabHandle* h, const double2* q, double2* z);
 cudaError_t pc_block(StabHandle* h, double2 sigma, long long t, double2* d_out);
 
-// host dense helpers (hessenberg.cu)
-int hess_eig(int m, const double2* H, int ldh, double2* theta, double2* Y);  // returns 0 on success

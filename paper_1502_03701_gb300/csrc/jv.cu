@@ -17,66 +17,16 @@
 
 #include "internal.cuh"
 
+#include "pointwise.cuh"
+
+using pw::bt_count;
+using pw::bt_d1;
+using pw::bt_d2;
+using pw::bt_extra;
+using pw::bt_mix;
+using pw::bt_val;
+
 namespace {
-
-// ---------------------------------------------------------------------------
-// Difference numbers: a = base value, w = (perturbed - base)/eps.  Every
-// operation below is an exact identity for the scaled difference, so the
-// quotient is formed without subtracting nearly equal numbers.
-// ---------------------------------------------------------------------------
-struct DN {
-  double a, w;
-};
-__device__ __forceinline__ DN dn(double a, double w) { return DN{a, w}; }
-__device__ __forceinline__ DN operator+(DN x, DN y) { return dn(x.a + y.a, x.w + y.w); }
-__device__ __forceinline__ DN operator-(DN x, DN y) { return dn(x.a - y.a, x.w - y.w); }
-__device__ __forceinline__ DN operator-(DN x) { return dn(-x.a, -x.w); }
-__device__ __forceinline__ DN operator*(double c, DN x) { return dn(c * x.a, c * x.w); }
-__device__ __forceinline__ DN add(DN x, double c) { return dn(x.a + c, x.w); }
-// (a1 + e w1)(a2 + e w2) - a1 a2 = e [a1 w2 + w1 (a2 + e w2)]
-__device__ __forceinline__ DN mul(DN x, DN y, double e) {
-  return dn(x.a * y.a, fma(x.a, y.w, x.w * fma(e, y.w, y.a)));
-}
-// 1/(a + e w) - 1/a = -e w / (a (a + e w))
-__device__ __forceinline__ DN rcp(DN x, double e) {
-  double inv = 1.0 / x.a;
-  return dn(inv, -x.w / (x.a * fma(e, x.w, x.a)));
-}
-// sqrt(a + e w) - sqrt(a) = e w / (sqrt(a + e w) + sqrt(a))
-__device__ __forceinline__ DN dsqrt(DN x, double e) {
-  double s = sqrt(x.a);
-  return dn(s, x.w / (sqrt(fma(e, x.w, x.a)) + s));
-}
-// expm1(z)/z and log1p(z)/z with their limits at z = 0
-__device__ __forceinline__ double expm1_over(double z) { return z == 0.0 ? 1.0 : expm1(z) / z; }
-__device__ __forceinline__ double log1p_over(double z) { return z == 0.0 ? 1.0 : log1p(z) / z; }
-
-// Scaled differences of the closure rho(p, s) = (p/p_ref)^{1/gamma} e^{-s/c_p}
-// and T(p, s) = (p/p_ref)^{(gamma-1)/gamma} e^{s/c_p}:
-//   rho(q0 + e w)/rho0 = exp(x_rho),  x_rho = (1/gamma) log1p(e wp/p0) - e ws/c_p.
-struct ClosureK {
-  double ig, omig, icp;  // 1/gamma, 1 - 1/gamma, 1/c_p
-};
-__device__ __forceinline__ void closure_w(const ClosureK& C, double p0, double rho0, double T0, double wp,
-                                          double ws, double e, double* wrho, double* wT) {
-  double q = wp / p0;
-  double lq = q * log1p_over(e * q);
-  double xr = C.ig * lq - ws * C.icp;
-  double xt = C.omig * lq + ws * C.icp;
-  if (wrho) *wrho = rho0 * expm1_over(e * xr) * xr;
-  if (wT) *wT = T0 * expm1_over(e * xt) * xt;
-}
-
-// ---------------------------------------------------------------------------
-// Base-table layout (real arrays of length nbase, physical derivatives).
-// ---------------------------------------------------------------------------
-__host__ __device__ __forceinline__ int bt_val(int D, int f) { (void)D; return f; }  // p,u..,s,T,rho
-__host__ __device__ __forceinline__ int bt_d1(int D, int ax, int f) { return (D + 4) + ax * (D + 3) + f; }
-__host__ __device__ __forceinline__ int bt_d2(int D, int ax, int g) { return (D + 4) + D * (D + 3) + ax * (D + 1) + g; }
-__host__ __device__ __forceinline__ int bt_mix(int D, int i, int k) {
-  return (D + 4) + D * (D + 3) + D * (D + 1) + i * D + k;
-}
-__host__ __device__ __forceinline__ int bt_count(int D) { return (D + 4) + D * (D + 3) + D * (D + 1) + D * D; }
 
 // ---------------------------------------------------------------------------
 // Line pass: compact derivatives along one axis for a batch of fields.
@@ -105,101 +55,130 @@ __device__ __forceinline__ long long line_base(const PassParams& P, long long l)
   return l;
 }
 
-__device__ __forceinline__ int wrapi(int t, int n) {
-  int r = t % n;
-  return r < 0 ? r + n : r;
+// t mod n for t within a few periods of [0, n) (no integer division)
+__device__ __forceinline__ int wrap_small(int t, int n) {
+  while (t < 0) t += n;
+  while (t >= n) t -= n;
+  return t;
 }
 
-__device__ __forceinline__ double2 d2sub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
-__device__ __forceinline__ double2 d2lin(double c1, double2 a, double c2, double2 b) {
-  return make_double2(c1 * a.x + c2 * b.x, c1 * a.y + c2 * b.y);
-}
+// shared-memory index of line point t: one pad double after every 32-point
+// chunk so that the chunk starts fall in different banks
+__device__ __forceinline__ int sidx(int t) { return t + (t >> 5); }
 
-// right-hand side B f of the compact scheme at point t
-__device__ double2 stencil_rhs(const PassParams& P, const double2* F, int L, int lt, int t, int kind) {
+// right-hand side (B f)_t of the compact scheme for one real component
+__device__ __forceinline__ double stencil_rhs(const PassParams& P, const double* fl, int t, int kind) {
   const int n = P.n;
-  auto f = [&](int s) { return F[(P.periodic ? wrapi(s, n) : s) * L + lt]; };
+  auto f = [&](int q) { return fl[sidx(q)]; };
   const double h = P.h;
   if (!P.periodic && (t < 2 || t > n - 3)) {
     if (kind == 0) {
-      if (t == 0) { double2 a = f(0), b = f(1), c = f(2); return make_double2((-2.5 * a.x + 2.0 * b.x + 0.5 * c.x) / h, (-2.5 * a.y + 2.0 * b.y + 0.5 * c.y) / h); }
-      if (t == n - 1) { double2 a = f(n - 1), b = f(n - 2), c = f(n - 3); return make_double2((2.5 * a.x - 2.0 * b.x - 0.5 * c.x) / h, (2.5 * a.y - 2.0 * b.y - 0.5 * c.y) / h); }
-      double2 d = d2sub(f(t + 1), f(t - 1));
-      return make_double2(0.75 * d.x / h, 0.75 * d.y / h);
-    } else {
-      const double ih2 = 1.0 / (h * h);
-      if (t == 0 || t == n - 1) {
-        int s = t == 0 ? 1 : -1;
-        double2 a = f(t), b = f(t + s), c = f(t + 2 * s), d = f(t + 3 * s);
-        return make_double2((13.0 * a.x - 27.0 * b.x + 15.0 * c.x - d.x) * ih2, (13.0 * a.y - 27.0 * b.y + 15.0 * c.y - d.y) * ih2);
-      }
-      double2 a = f(t - 1), b = f(t), c = f(t + 1);
-      return make_double2(1.2 * (c.x - 2.0 * b.x + a.x) * ih2, 1.2 * (c.y - 2.0 * b.y + a.y) * ih2);
+      if (t == 0) return (-2.5 * f(0) + 2.0 * f(1) + 0.5 * f(2)) / h;
+      if (t == n - 1) return (2.5 * f(n - 1) - 2.0 * f(n - 2) - 0.5 * f(n - 3)) / h;
+      return 0.75 * (f(t + 1) - f(t - 1)) / h;
     }
+    const double ih2 = 1.0 / (h * h);
+    if (t == 0) return (13.0 * f(0) - 27.0 * f(1) + 15.0 * f(2) - f(3)) * ih2;
+    if (t == n - 1) return (13.0 * f(n - 1) - 27.0 * f(n - 2) + 15.0 * f(n - 3) - f(n - 4)) * ih2;
+    return 1.2 * (f(t + 1) - 2.0 * f(t) + f(t - 1)) * ih2;
   }
-  double2 fm2 = f(t - 2), fm1 = f(t - 1), fp1 = f(t + 1), fp2 = f(t + 2);
-  if (kind == 0) return d2lin(P.c1[0], d2sub(fp1, fm1), P.c2[0], d2sub(fp2, fm2));
-  double2 f0 = f(t);
-  double2 s1 = make_double2(fp1.x - 2.0 * f0.x + fm1.x, fp1.y - 2.0 * f0.y + fm1.y);
-  double2 s2 = make_double2(fp2.x - 2.0 * f0.x + fm2.x, fp2.y - 2.0 * f0.y + fm2.y);
-  return d2lin(P.c1[1], s1, P.c2[1], s2);
+  int tm2 = t - 2, tm1 = t - 1, tp1 = t + 1, tp2 = t + 2;
+  if (P.periodic) { tm2 = wrap_small(tm2, n); tm1 = wrap_small(tm1, n); tp1 = wrap_small(tp1, n); tp2 = wrap_small(tp2, n); }
+  if (kind == 0) return fma(P.c1[0], f(tp1) - f(tm1), P.c2[0] * (f(tp2) - f(tm2)));
+  const double f0 = f(t);
+  return fma(P.c1[1], f(tp1) - 2.0 * f0 + f(tm1), P.c2[1] * (f(tp2) - 2.0 * f0 + f(tm2)));
 }
 
+// Shared memory (doubles): R[kind][comp][lt][LS], then F[comp][lt][LS]
+// aliased by G[kind][comp][lt][LS] once R is complete; LS = padded line
+// stride (33 doubles per 32-point chunk, plus one).
 __global__ void k_line_pass(const PassParams P) {
-  extern __shared__ double2 sm[];
+  extern __shared__ double sm[];
   const LineJob J = P.job[blockIdx.y];
   const int n = P.n, L = P.L;
-  double2* F = sm;
-  double2* G[2] = {sm + (size_t)n * L, sm + (size_t)2 * n * L};
+  const int LS = 33 * P.nchunks + 1;
+  const size_t plane = (size_t)L * LS;  // one (kind, comp) or (comp) plane
+  double* R = sm;                      // 4 planes
+  double* F = sm + 4 * plane;          // 2 planes
+  double* G = sm + 4 * plane;          // 4 planes (after R is built)
   const long long l0 = (long long)blockIdx.x * L;
+  const bool need2 = J.out2 != nullptr;
 
   for (int idx = threadIdx.x; idx < n * L; idx += blockDim.x) {
     int lt, t;
-    if (P.axis == 0) { lt = idx / n; t = idx % n; } else { t = idx / L; lt = idx % L; }
-    long long l = l0 + lt;
+    if (P.axis == 0) { lt = idx / n; t = idx - lt * n; } else { t = idx / L; lt = idx - t * L; }
+    const long long l = l0 + lt;
     double2 val = make_double2(0.0, 0.0);
     if (l < P.nlines) val = J.in[line_base(P, l) + (long long)t * P.stride];
-    F[t * L + lt] = val;
+    F[(size_t)lt * LS + sidx(t)] = val.x;
+    F[plane + (size_t)lt * LS + sidx(t)] = val.y;
   }
   __syncthreads();
-
+  // compact right-hand sides, all points in parallel
+  const int nk = need2 ? 2 : 1;
+  for (int idx = threadIdx.x; idx < nk * 2 * L * n; idx += blockDim.x) {
+    const int t = idx % n;
+    const int rest = idx / n;
+    const int lt = rest % L, comp = (rest / L) & 1, kind = rest / (2 * L);
+    R[((size_t)(kind * 2 + comp) * L + lt) * LS + sidx(t)] = stencil_rhs(P, F + (size_t)comp * plane + (size_t)lt * LS, t, kind);
+  }
+  __syncthreads();
+  // thread -> (chunk, line, comp, kind); x lines: chunk fastest, strided
+  // lines: line fastest (neighbouring lines are neighbouring addresses)
   const int per = L * P.nchunks;
-  const int kind = threadIdx.x / per;
-  const int rem = threadIdx.x % per;
-  const int lt = rem % L, ch = rem / L;
+  const int ch = P.axis == 0 ? threadIdx.x % P.nchunks : (threadIdx.x / L) % P.nchunks;
+  const int lt = P.axis == 0 ? (threadIdx.x / P.nchunks) % L : threadIdx.x % L;
+  const int comp = (threadIdx.x / per) & 1;
+  const int kind = threadIdx.x / (2 * per);
   double2* out = kind == 0 ? J.out1 : J.out2;
-  const bool active = kind < 2 && out != nullptr && (l0 + lt) < P.nlines;
+  const bool active = kind < nk && out != nullptr && (l0 + lt) < P.nlines;
   const int t0 = ch * P.C, t1 = min(n, t0 + P.C);
-  const double* tl = P.tab[kind < 2 ? kind : 0];
+  const int kk = kind < 2 ? kind : 0;
+  const double* tl = P.tab[kk];
   const double* tdinv = tl + n;
   const double* tm = tl + 2 * n;
-  const int K = P.K[kind < 2 ? kind : 0];
-  double2* Gk = G[kind < 2 ? kind : 0];
-
+  const int K = P.K[kk];
+  const double* Rk = R + ((size_t)(kk * 2 + comp) * L + lt) * LS;
+  double* Gk = G + ((size_t)(kk * 2 + comp) * L + lt) * LS;
+  // forward sweep (reads R only; F is dead, so G may overwrite it)
   if (active) {
-    int ts = P.periodic ? t0 - K : ((t0 - K < 8) ? 0 : t0 - K);
-    double2 g = make_double2(0.0, 0.0);
-    for (int t = ts; t < t1; ++t) {
-      int tt = P.periodic ? wrapi(t, n) : t;
-      double2 r = stencil_rhs(P, F, L, lt, tt, kind);
-      double lv = __ldg(tl + tt);
-      g.x = fma(-lv, g.x, r.x);
-      g.y = fma(-lv, g.y, r.y);
-      if (t >= t0) Gk[tt * L + lt] = g;
+    double g = 0.0;
+    if (P.periodic) {
+      const double lv = __ldg(tl);
+      int tt = wrap_small(t0 - K, n);
+      for (int s = t0 - K; s < t1; ++s) {
+        g = fma(-lv, g, Rk[sidx(tt)]);
+        if (s >= t0) Gk[sidx(tt)] = g;
+        if (++tt == n) tt = 0;
+      }
+    } else {
+      const int ts = (t0 - K < 8) ? 0 : t0 - K;
+      for (int t = ts; t < t1; ++t) {
+        g = fma(-__ldg(tl + t), g, Rk[sidx(t)]);
+        if (t >= t0) Gk[sidx(t)] = g;
+      }
     }
   }
   __syncthreads();
   if (active) {
-    int te = P.periodic ? t1 - 1 + K : ((t1 - 1 + K > n - 9) ? n - 1 : t1 - 1 + K);
-    double2 x = make_double2(0.0, 0.0);
+    double x = 0.0;
     const long long base = line_base(P, l0 + lt);
-    for (int t = te; t >= t0; --t) {
-      int tt = P.periodic ? wrapi(t, n) : t;
-      double2 gg = Gk[tt * L + lt];
-      double di = __ldg(tdinv + tt), mm = __ldg(tm + tt);
-      x.x = fma(gg.x, di, -mm * x.x);
-      x.y = fma(gg.y, di, -mm * x.y);
-      if (t < t1) out[base + (long long)tt * P.stride] = x;
+    double* o = (double*)out + comp;
+    if (P.periodic) {
+      const double di = __ldg(tdinv), mm = __ldg(tm);
+      int te = t1 - 1 + K;
+      int tt = wrap_small(te, n);
+      for (int s = te; s >= t0; --s) {
+        x = fma(Gk[sidx(tt)], di, -mm * x);
+        if (s < t1) o[2 * (base + (long long)tt * P.stride)] = x;
+        if (--tt < 0) tt = n - 1;
+      }
+    } else {
+      const int te = (t1 - 1 + K > n - 9) ? n - 1 : t1 - 1 + K;
+      for (int t = te; t >= t0; --t) {
+        x = fma(Gk[sidx(t)], __ldg(tdinv + t), -__ldg(tm + t) * x);
+        if (t < t1) o[2 * (base + (long long)t * P.stride)] = x;
+      }
     }
   }
 }
@@ -255,8 +234,8 @@ struct PointParams {
   const double2* v;
   const double2* scratch;
   long long npts;
-  int nx, ny, nz, D;
-  int homog, visc;
+  int nx, ny, nz;
+  int homog;
   int s_Tw;
   int s_d1[3][6], s_d2[3][4], s_mix[3][3];
   const double* btab;
@@ -267,197 +246,213 @@ struct PointParams {
   const double* eps;
   double2* out;
   double2 shift;
-  double gamma, R, cp, Pr, S, Re, bulk;
-  ClosureK C;
+  pw::Phys phys;
 };
 
 __global__ void k_temperature(const PointParams P, double2* Tw) {
-  const int D = P.D;
+  const int D = P.nz > 1 ? 3 : 2;
   const double e = *P.eps;
   for (long long pt = (long long)blockIdx.x * blockDim.x + threadIdx.x; pt < P.npts; pt += (long long)gridDim.x * blockDim.x) {
     int j = (int)((pt / P.nx) % P.ny);
     long long b = P.homog ? j : pt;
-    double p0 = P.btab[bt_val(D, 0) * P.nbase + b];
+    double ip0 = P.btab[bt_extra(D, pw::X_IP) * P.nbase + b];
     double T0 = P.btab[bt_val(D, D + 2) * P.nbase + b];
     double2 wp = P.v[pt], ws = P.v[(long long)(D + 1) * P.npts + pt];
-    double t0, t1;
-    closure_w(P.C, p0, 0.0, T0, wp.x, ws.x, e, nullptr, &t0);
-    closure_w(P.C, p0, 0.0, T0, wp.y, ws.y, e, nullptr, &t1);
+    double t0 = pw::closure_T_w(P.phys.C, T0, pw::closure_lq(wp.x, ip0, e), ws.x, e);
+    double t1 = pw::closure_T_w(P.phys.C, T0, pw::closure_lq(wp.y, ip0, e), ws.y, e);
     Tw[pt] = make_double2(t0, t1);
   }
 }
 
 template <int D>
-__device__ void point_rhs(const PointParams& P, long long pt, int i, int j, int k, int part, double e, double* res) {
-  const long long b = P.homog ? j : pt;
-  const double* BT = P.btab;
-  const long long NB = P.nbase;
-  auto B = [&](int slot) { return BT[(long long)slot * NB + b]; };
-  auto Wv = [&](const double2* f) { double2 z = f[pt]; return part ? z.y : z.x; };
-  auto S_ = [&](int slot) { return P.scratch + (long long)slot * P.npts; };
-  const double ey = P.eta_y[j], eyy = P.eta_yy[j];
-  const int Y = 1;
-
-  DN p = dn(B(bt_val(D, 0)), Wv(P.v));
-  DN u[D];
+__global__ void __launch_bounds__(128) k_point(const PointParams P) {
+  const double e = *P.eps;
+  const bool visc = P.phys.visc;
+  for (long long pt = (long long)blockIdx.x * blockDim.x + threadIdx.x; pt < P.npts; pt += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(pt % P.nx);
+    const int j = (int)((pt / P.nx) % P.ny);
+    const int k = (int)(pt / ((long long)P.nx * P.ny));
+    const long long b = P.homog ? j : pt;
+    const double ey = P.eta_y[j], eyy = P.eta_yy[j];
+    const bool bc_row = (j == 0 || j == P.ny - 1);
+    const unsigned fl = bc_row ? P.bcflags[(j == P.ny - 1 ? (long long)P.nx * P.nz : 0) + (long long)k * P.nx + i] : 0u;
+    auto B = [&](int slot) { return P.btab[(long long)slot * P.nbase + b]; };
+    auto S = [&](int slot) { return P.scratch[(long long)slot * P.npts + pt]; };
+#pragma unroll 1
+    for (int part = 0; part < 2; ++part) {
+      auto pick = [&](double2 z) { return part ? z.y : z.x; };
+      pw::WIn<D> W;
 #pragma unroll
-  for (int a = 0; a < D; ++a) u[a] = dn(B(bt_val(D, 1 + a)), Wv(P.v + (long long)(1 + a) * P.npts));
-  DN s = dn(B(bt_val(D, D + 1)), Wv(P.v + (long long)(D + 1) * P.npts));
-  const double T0 = B(bt_val(D, D + 2)), rho0 = B(bt_val(D, D + 3));
-  double wrho;
-  closure_w(P.C, p.a, rho0, T0, p.w, s.w, e, &wrho, nullptr);
-  DN rho = dn(rho0, wrho);
-
-  auto D1 = [&](int ax, int f) {
-    double w = Wv(S_(P.s_d1[ax][f]));
-    if (ax == Y) w *= ey;
-    return dn(B(bt_d1(D, ax, f)), w);
-  };
-  DN dp[D], ds[D], du[D][D];
+      for (int f = 0; f < D + 2; ++f) W.v[f] = pick(P.v[(long long)f * P.npts + pt]);
+      W.v[D + 2] = visc ? pick(S(P.s_Tw)) : 0.0;
 #pragma unroll
-  for (int a = 0; a < D; ++a) {
-    dp[a] = D1(a, 0);
-    ds[a] = D1(a, D + 1);
+      for (int ax = 0; ax < D; ++ax) {
+        const double sc = ax == 1 ? ey : 1.0;
 #pragma unroll
-    for (int c = 0; c < D; ++c) du[c][a] = D1(a, 1 + c);
-  }
-  DN div = du[0][0];
-#pragma unroll
-  for (int a = 1; a < D; ++a) div = div + du[a][a];
-
-  DN heat = dn(0.0, 0.0), Phi = dn(0.0, 0.0);
-  DN vis[D];
-#pragma unroll
-  for (int a = 0; a < D; ++a) vis[a] = dn(0.0, 0.0);
-  if (P.visc) {
-    DN T = dn(T0, Wv(P.scratch + (long long)P.s_Tw * P.npts));
-    DN dT[D];
-#pragma unroll
-    for (int a = 0; a < D; ++a) dT[a] = D1(a, D + 2);
-    auto D2 = [&](int ax, int g, int f) {
-      double w = Wv(S_(P.s_d2[ax][g]));
-      if (ax == Y) w = fma(w, ey * ey, Wv(S_(P.s_d1[ax][f])) * eyy);
-      return dn(B(bt_d2(D, ax, g)), w);
-    };
-    auto MX = [&](int a, int c) {
-      double w = Wv(S_(P.s_mix[a][c]));
-      if (a == Y || c == Y) w *= ey;
-      return dn(B(bt_mix(D, a, c)), w);
-    };
-    // Sutherland: mu = (1+S)/Re T^{3/2}/(T+S);  dmu/dT = mu (3/(2T) - 1/(T+S))
-    DN sqT = dsqrt(T, e);
-    DN rTS = rcp(add(T, P.S), e);
-    DN mu = ((1.0 + P.S) / P.Re) * mul(mul(T, sqT, e), rTS, e);
-    DN dmu = mul(mu, 1.5 * rcp(T, e) - rTS, e);
-    const double kl = P.cp / P.Pr;
-    DN lam = kl * mu, dlam = kl * dmu;
-    DN muv = P.bulk * mu, dmuv = P.bulk * dmu;
-    DN lapT = dn(0.0, 0.0), gT2 = dn(0.0, 0.0);
-#pragma unroll
-    for (int a = 0; a < D; ++a) {
-      lapT = lapT + D2(a, D, D + 2);
-      gT2 = gT2 + mul(dT[a], dT[a], e);
-    }
-    heat = mul(lam, lapT, e) + mul(dlam, gT2, e);
-    DN SS = dn(0.0, 0.0);
-#pragma unroll
-    for (int a = 0; a < D; ++a)
-#pragma unroll
-      for (int c = 0; c < D; ++c) {
-        DN sij = 0.5 * (du[a][c] + du[c][a]);
-        SS = SS + mul(sij, sij, e);
+        for (int f = 0; f < D + 3; ++f) W.d1[ax][f] = (f < D + 2 || visc) ? pick(S(P.s_d1[ax][f])) * sc : 0.0;
       }
-    DN div2 = mul(div, div, e);
-    Phi = 2.0 * mul(mu, SS - (1.0 / 3.0) * div2, e) + mul(muv, div2, e);
+      if (visc) {
 #pragma unroll
-    for (int a = 0; a < D; ++a) {
-      DN lap = dn(0.0, 0.0), ddiv = dn(0.0, 0.0), cross = dn(0.0, 0.0);
+        for (int ax = 0; ax < D; ++ax)
 #pragma unroll
-      for (int c = 0; c < D; ++c) {
-        DN d2ac = D2(c, a, 1 + a);  // d^2 u_a / dx_c^2
-        lap = lap + d2ac;
-        ddiv = ddiv + (c == a ? d2ac : MX(a, c));
-        cross = cross + mul(mul(dmu, dT[c], e), du[a][c] + du[c][a], e);
+          for (int g = 0; g < D + 1; ++g) {
+            double w = pick(S(P.s_d2[ax][g]));
+            if (ax == 1) w = fma(w, ey * ey, pick(S(P.s_d1[1][g < D ? 1 + g : D + 2])) * eyy);
+            W.d2[ax][g] = w;
+          }
+#pragma unroll
+        for (int a = 0; a < D; ++a)
+#pragma unroll
+          for (int c = 0; c < D; ++c)
+            W.mix[a][c] = a == c ? 0.0 : pick(S(P.s_mix[a][c])) * ((a == 1 || c == 1) ? ey : 1.0);
       }
-      vis[a] = mul(mu, lap + (1.0 / 3.0) * ddiv, e) + mul(muv, ddiv, e) + cross +
-               mul(mul(dmuv - (2.0 / 3.0) * dmu, dT[a], e), div, e);
+      double res[D + 2];
+      pw::rhs_diff<D>(P.phys, B, W, e, bc_row, fl, res);
+#pragma unroll
+      for (int a = 0; a < D + 2; ++a) {
+        const long long o = (long long)a * P.npts + pt;
+        double2 vv = P.v[o];
+        double sv = part ? (P.shift.x * vv.y + P.shift.y * vv.x) : (P.shift.x * vv.x - P.shift.y * vv.y);
+        double r = res[a] - sv;
+        if (part) P.out[o].y = r; else P.out[o].x = r;
+      }
     }
   }
+}
 
-  // y-direction inviscid terms, replaced at the non-reflective boundaries
-  DN Yp, Yv;
-  bool dropc = false;
-  if (j == 0 || j == P.ny - 1) {
-    unsigned char fl = P.bcflags[(j == P.ny - 1 ? (long long)P.nx * P.nz : 0) + (long long)k * P.nx + i];
-    DN c = dsqrt(P.gamma * mul(p, rcp(rho, e), e), e);
-    DN rc = mul(rho, c, e);
-    DN rcv = mul(rc, du[Y][Y], e);
-    DN Xp = 0.5 * mul(u[Y] + c, dp[Y] + rcv, e);
-    DN Xm = 0.5 * mul(u[Y] - c, dp[Y] - rcv, e);
-    if (fl & 1) Xp = dn(0.0, 0.0);
-    if (fl & 2) Xm = dn(0.0, 0.0);
-    dropc = (fl & 4) != 0;
-    Yp = -(Xp + Xm);
-    Yv = -mul(Xp - Xm, rcp(rc, e), e);
-  } else {
-    Yp = -(mul(u[Y], dp[Y], e) + P.gamma * mul(p, du[Y][Y], e));
-    Yv = -(mul(u[Y], du[Y][Y], e) + mul(dp[Y], rcp(rho, e), e));
-  }
-  DN src = heat + Phi;
-  DN pt_ = Yp;
-#pragma unroll
-  for (int a = 0; a < D; ++a)
-    if (a != Y) pt_ = pt_ - (mul(u[a], dp[a], e) + P.gamma * mul(p, du[a][a], e));
-  pt_ = pt_ + (P.gamma - 1.0) * src;
-  res[0] = pt_.w;
-  DN irho = rcp(rho, e);
-#pragma unroll
-  for (int c = 0; c < D; ++c) {
-    DN r = dn(0.0, 0.0);
-    if (c == Y) {
-      r = Yv;
-#pragma unroll
-      for (int a = 0; a < D; ++a)
-        if (a != Y) r = r - mul(u[a], du[c][a], e);
-    } else {
-#pragma unroll
-      for (int a = 0; a < D; ++a) {
-        if (a == Y && dropc) continue;
-        r = r - mul(u[a], du[c][a], e);
-      }
-      r = r - mul(dp[c], irho, e);
-    }
-    r = r + mul(vis[c], irho, e);
-    res[1 + c] = r.w;
-  }
-  DN st = dn(0.0, 0.0);
-#pragma unroll
-  for (int a = 0; a < D; ++a) {
-    if (a == Y && dropc) continue;
-    st = st - mul(u[a], ds[a], e);
-  }
-  st = st + mul(P.R * rcp(p, e), src, e);
-  res[D + 1] = st.w;
+// ---------------------------------------------------------------------------
+// Fast pointwise path for a base state that depends on y only.  The map from
+// the scaled perturbation inputs (values and derivatives at a point) to the
+// tendencies is, to first order, linear with coefficients that depend on the
+// row only: C_j (D+2 x NW), tabulated once by feeding unit inputs through the
+// FP64 tangent.  J v at a point is then C_j w in FP64; for eps > 0 the
+// remaining O(eps) part of the quotient is added, evaluated in FP32.
+// ---------------------------------------------------------------------------
+template <int D, class V>
+__device__ __forceinline__ void set_input(pw::WIn<D, V>& W, int idx, V val) {
+  if (idx < D + 3) { W.v[idx] = val; return; }
+  idx -= D + 3;
+  if (idx < D * (D + 3)) { W.d1[idx / (D + 3)][idx % (D + 3)] = val; return; }
+  idx -= D * (D + 3);
+  if (idx < D * (D + 1)) { W.d2[idx / (D + 1)][idx % (D + 1)] = val; return; }
+  idx -= D * (D + 1);
+  W.mix[idx / D][idx % D] = val;
 }
 
 template <int D>
-__global__ void __launch_bounds__(128) k_point(const PointParams P) {
-  const double e = *P.eps;
-  for (long long pt = (long long)blockIdx.x * blockDim.x + threadIdx.x; pt < P.npts; pt += (long long)gridDim.x * blockDim.x) {
-    int i = (int)(pt % P.nx);
-    int j = (int)((pt / P.nx) % P.ny);
-    int k = (int)(pt / ((long long)P.nx * P.ny));
-    double r0[D + 2], r1[D + 2];
-    point_rhs<D>(P, pt, i, j, k, 0, e, r0);
-    point_rhs<D>(P, pt, i, j, k, 1, e, r1);
+__global__ void k_coeffs(const PointParams P, double* coef) {
+  constexpr int NW = pw::nw_inputs(D);
+  const int j = blockIdx.x, k = threadIdx.x;
+  if (k >= NW) return;
+  pw::WIn<D> W;
 #pragma unroll
-    for (int a = 0; a < D + 2; ++a) {
-      long long o = (long long)a * P.npts + pt;
-      double2 vv = P.v[o];
-      // out = J v - shift v
-      double2 r = make_double2(r0[a] - (P.shift.x * vv.x - P.shift.y * vv.y), r1[a] - (P.shift.x * vv.y + P.shift.y * vv.x));
-      P.out[o] = r;
+  for (int q = 0; q < NW; ++q) set_input<D, double>(W, q, q == k ? 1.0 : 0.0);
+  auto B = [&](int slot) { return P.btab[(long long)slot * P.nbase + j]; };
+  const bool bc_row = (j == 0 || j == P.ny - 1);
+  const unsigned fl = bc_row ? P.bcflags[(j == P.ny - 1 ? (long long)P.nx * P.nz : 0)] : 0u;
+  double res[D + 2];
+  pw::rhs_diff<D>(P.phys, B, W, 0.0, bc_row, fl, res);
+  for (int a = 0; a < D + 2; ++a) coef[((long long)j * (D + 2) + a) * NW + k] = res[a];
+}
+
+template <int D>
+__global__ void __launch_bounds__(128) k_point_fast(const PointParams P, const double* __restrict__ coef) {
+  constexpr int NW = pw::nw_inputs(D);
+  const double e = *P.eps;
+  const bool visc = P.phys.visc;
+  for (long long pt = (long long)blockIdx.x * blockDim.x + threadIdx.x; pt < P.npts; pt += (long long)gridDim.x * blockDim.x) {
+    const int j = (int)((pt / P.nx) % P.ny);
+    const double ey = P.eta_y[j], eyy = P.eta_yy[j];
+    const bool bc_row = (j == 0 || j == P.ny - 1);
+    const unsigned fl = bc_row ? P.bcflags[(j == P.ny - 1 ? (long long)P.nx * P.nz : 0)] : 0u;
+    const double* C = coef + (long long)j * (D + 2) * NW;
+    auto S = [&](int slot) { return P.scratch[(long long)slot * P.npts + pt]; };
+#pragma unroll 1
+    for (int part = 0; part < 2; ++part) {
+      auto pick = [&](double2 z) { return part ? z.y : z.x; };
+      double w[NW];
+#pragma unroll
+      for (int f = 0; f < D + 2; ++f) w[f] = pick(P.v[(long long)f * P.npts + pt]);
+      w[D + 2] = visc ? pick(S(P.s_Tw)) : 0.0;
+#pragma unroll
+      for (int ax = 0; ax < D; ++ax) {
+        const double sc = ax == 1 ? ey : 1.0;
+#pragma unroll
+        for (int f = 0; f < D + 3; ++f) w[D + 3 + ax * (D + 3) + f] = (f < D + 2 || visc) ? pick(S(P.s_d1[ax][f])) * sc : 0.0;
+      }
+      constexpr int o2 = (D + 3) + D * (D + 3), om = o2 + D * (D + 1);
+#pragma unroll
+      for (int ax = 0; ax < D; ++ax)
+#pragma unroll
+        for (int g = 0; g < D + 1; ++g) {
+          double v = 0.0;
+          if (visc) {
+            v = pick(S(P.s_d2[ax][g]));
+            if (ax == 1) v = fma(v, ey * ey, pick(S(P.s_d1[1][g < D ? 1 + g : D + 2])) * eyy);
+          }
+          w[o2 + ax * (D + 1) + g] = v;
+        }
+#pragma unroll
+      for (int a = 0; a < D; ++a)
+#pragma unroll
+        for (int c = 0; c < D; ++c)
+          w[om + a * D + c] = (visc && a != c) ? pick(S(P.s_mix[a][c])) * ((a == 1 || c == 1) ? ey : 1.0) : 0.0;
+      double res[D + 2];
+#pragma unroll
+      for (int a = 0; a < D + 2; ++a) {
+        double acc = 0.0;
+#pragma unroll
+        for (int q = 0; q < NW; ++q) acc = fma(__ldg(C + a * NW + q), w[q], acc);
+        res[a] = acc;
+      }
+      if (e != 0.0) {  // O(eps) remainder of the quotient, FP32
+        pw::WIn<D, float> Wf;
+#pragma unroll
+        for (int q = 0; q < NW; ++q) set_input<D, float>(Wf, q, (float)w[q]);
+        auto B = [&](int slot) { return P.btab[(long long)slot * P.nbase + j]; };
+        pw::DN3 o[D + 2];
+        pw::rhs_num<D, pw::DN3>(P.phys, B, Wf, e, bc_row, fl, o);
+#pragma unroll
+        for (int a = 0; a < D + 2; ++a) res[a] += (double)o[a].w2;
+      }
+#pragma unroll
+      for (int a = 0; a < D + 2; ++a) {
+        const long long o = (long long)a * P.npts + pt;
+        double2 vv = P.v[o];
+        double sv = part ? (P.shift.x * vv.y + P.shift.y * vv.x) : (P.shift.x * vv.x - P.shift.y * vv.y);
+        double r = res[a] - sv;
+        if (part) P.out[o].y = r; else P.out[o].x = r;
+      }
     }
+  }
+}
+
+// T's scaled difference split the same way: FP64 first order + FP32 rest
+__global__ void k_temperature_fast(const PointParams P, double2* Tw) {
+  const int D = P.nz > 1 ? 3 : 2;
+  const double e = *P.eps;
+  const float ef = (float)e;
+  const pw::ClosureK C = P.phys.C;
+  for (long long pt = (long long)blockIdx.x * blockDim.x + threadIdx.x; pt < P.npts; pt += (long long)gridDim.x * blockDim.x) {
+    const int j = (int)((pt / P.nx) % P.ny);
+    const double ip0 = P.btab[pw::bt_extra(D, pw::X_IP) * P.nbase + j];
+    const double T0 = P.btab[pw::bt_val(D, D + 2) * P.nbase + j];
+    const double2 wp = P.v[pt], ws = P.v[(long long)(D + 1) * P.npts + pt];
+    double t[2];
+#pragma unroll
+    for (int part = 0; part < 2; ++part) {
+      const double q = (part ? wp.y : wp.x) * ip0, s = part ? ws.y : ws.x;
+      const double X1 = fma(C.omig, q, s * C.icp);
+      double r = T0 * X1;
+      if (e != 0.0) {
+        const float qf = (float)q;
+        const float X2 = (float)C.omig * qf * pw::log1p_m1_over_f(ef * qf);
+        const float X = (float)X1 + X2;
+        r += (double)((float)T0 * fmaf(X, pw::expm1_m1_over_f(ef * X), X2));
+      }
+      t[part] = r;
+    }
+    Tw[pt] = make_double2(t[0], t[1]);
   }
 }
 
@@ -481,7 +476,7 @@ struct PackParams {
   int s_Tw, s_d1[3][6], s_d2[3][4], s_mix[3][3];
   const double* eta_y;
   const double* eta_yy;
-  double pref, igam, icp, R;
+  double pref, igam, icp, R, gam, S;
 };
 
 __global__ void k_pack_base(const PackParams P) {
@@ -495,8 +490,18 @@ __global__ void k_pack_base(const PackParams P) {
     for (int f = 0; f < D + 2; ++f) out(bt_val(D, f), P.q0[(long long)f * P.npts + pt]);
     double p = P.q0[pt], s = P.q0[(long long)(D + 1) * P.npts + pt];
     double rho = pow(p / P.pref, P.igam) * exp(-s * P.icp);
-    out(bt_val(D, D + 2), p / (rho * P.R));
+    const double T = p / (rho * P.R);
+    out(bt_val(D, D + 2), T);
     out(bt_val(D, D + 3), rho);
+    const double c = sqrt(P.gam * p / rho);
+    out(bt_extra(D, pw::X_IRHO), 1.0 / rho);
+    out(bt_extra(D, pw::X_IP), 1.0 / p);
+    out(bt_extra(D, pw::X_IT), 1.0 / T);
+    out(bt_extra(D, pw::X_SQT), sqrt(T));
+    out(bt_extra(D, pw::X_ITS), 1.0 / (T + P.S));
+    out(bt_extra(D, pw::X_C), c);
+    out(bt_extra(D, pw::X_RC), rho * c);
+    out(bt_extra(D, pw::X_IRC), 1.0 / (rho * c));
     for (int ax = 0; ax < D; ++ax) {
       for (int f = 0; f < D + 3; ++f) {
         double v = 0.0;
@@ -528,6 +533,22 @@ __global__ void k_pack_base(const PackParams P) {
 // ---------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------
+pw::Phys phys_of(const StabHandle* h) {
+  pw::Phys p;
+  p.gamma = h->gamma;
+  p.R = h->R;
+  p.cp = h->cp;
+  p.Pr = h->Pr;
+  p.S = h->S;
+  p.Re = h->Re;
+  p.bulk = h->bulk;
+  p.C.ig = 1.0 / h->gamma;
+  p.C.omig = 1.0 - 1.0 / h->gamma;
+  p.C.icp = 1.0 / h->cp;
+  p.visc = h->visc;
+  return p;
+}
+
 static void fill_axis_tables(AxisTables& A, std::vector<double>& host) {
   const int n = A.n;
   host.assign((size_t)6 * n, 0.0);
@@ -584,7 +605,8 @@ static void make_slots(StabHandle* h) {
   S.count = c;
 }
 
-static cudaError_t run_pass(StabHandle* h, int axis, const PassParams& base_params, const std::vector<LineJob>& jobs) {
+static cudaError_t run_pass(StabHandle* h, int axis, const PassParams& base_params, const std::vector<LineJob>& jobs,
+                            long long contiguous_lines = -1) {
   if (jobs.empty()) return cudaSuccess;
   PassParams P = base_params;
   const AxisTables& A = h->ax[axis];
@@ -600,22 +622,33 @@ static cudaError_t run_pass(StabHandle* h, int axis, const PassParams& base_para
   P.K[1] = A.K[1];
   P.stride = axis == 0 ? 1 : axis == 1 ? h->nx : (long long)h->nx * h->ny;
   P.nlines = h->npts / A.n;
+  if (contiguous_lines >= 0) {  // lines stored back to back (line l at l * n), this axis's scheme
+    P.axis = 0;
+    P.nx = A.n;
+    P.stride = 1;
+    P.nlines = contiguous_lines;
+  }
   // interior weights: first (a/2h, b/4h), second (a/h^2, b/4h^2)
   P.c1[0] = (14.0 / 9.0) / (2.0 * A.h);
   P.c2[0] = (1.0 / 9.0) / (4.0 * A.h);
   P.c1[1] = (12.0 / 11.0) / (A.h * A.h);
   P.c2[1] = (3.0 / 11.0) / (4.0 * A.h * A.h);
   const int n = A.n;
-  int L = (int)(98304 / (3 * 16 * (long long)n));
+  // chunks of 32 points (at most 64 per line: n <= 2048); lines per CTA so
+  // that 8 planes of L x n doubles stay near 96 KB (two CTAs per SM)
+  P.C = 32;
+  P.nchunks = (n + P.C - 1) / P.C;
+  if (P.nchunks > 64 || n > 2048) return cudaErrorInvalidValue;
+  const long long LS = 33LL * P.nchunks + 1;
+  int L = (int)(98304 / (8 * 8 * LS));
+  const int maxL = 1024 / (4 * P.nchunks);
+  if (L > maxL) L = maxL;
   if (L > 32) L = 32;
   if (L < 1) L = 1;
   P.L = L;
-  P.C = 64;
-  P.nchunks = (n + P.C - 1) / P.C;
-  int threads = 2 * L * P.nchunks;
+  int threads = 4 * L * P.nchunks;
   threads = ((threads + 31) / 32) * 32;
-  size_t smem = (size_t)3 * n * L * sizeof(double2);
-  if (smem > 200 * 1024) return cudaErrorInvalidValue;  // lines longer than 4266 points
+  size_t smem = (size_t)8 * LS * L * sizeof(double);
   static bool attr_set = false;
   if (!attr_set) {
     cudaFuncSetAttribute(k_line_pass, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
@@ -690,9 +723,7 @@ static PointParams point_params(StabHandle* h, const double2* v) {
   P.nx = h->nx;
   P.ny = h->ny;
   P.nz = h->nz;
-  P.D = h->dim;
   P.homog = h->homog;
-  P.visc = h->visc;
   P.s_Tw = h->slots.Tw;
   for (int a = 0; a < 3; ++a) {
     for (int f = 0; f < 6; ++f) P.s_d1[a][f] = h->slots.d1[a][f];
@@ -705,16 +736,7 @@ static PointParams point_params(StabHandle* h, const double2* v) {
   P.eta_yy = h->d_metric + h->ny;
   P.bcflags = h->d_bcflags;
   P.eps = h->d_eps;
-  P.gamma = h->gamma;
-  P.R = h->R;
-  P.cp = h->cp;
-  P.Pr = h->Pr;
-  P.S = h->S;
-  P.Re = h->Re;
-  P.bulk = h->bulk;
-  P.C.ig = 1.0 / h->gamma;
-  P.C.omig = 1.0 - 1.0 / h->gamma;
-  P.C.icp = 1.0 / h->cp;
+  P.phys = phys_of(h);
   return P;
 }
 
@@ -726,8 +748,12 @@ static int grid_for(long long n, int threads) {
 }
 
 cudaError_t launch_norm2(StabHandle* h, const double2* v, long long n, double* d_out, int mode) {
-  k_norm2_partial<<<h->red_blocks, 256, 0, h->stream>>>(v, n, h->d_red);
-  k_norm2_final<<<1, 32, 0, h->stream>>>(h->d_red, h->red_blocks, d_out, mode, h->q0norm, h->opts.eps);
+  // block count depends on n only, so the summation order is reproducible
+  long long nb = (n + 1023) / 1024;
+  if (nb > h->red_blocks) nb = h->red_blocks;
+  if (nb < 1) nb = 1;
+  k_norm2_partial<<<(int)nb, 256, 0, h->stream>>>(v, n, h->d_red);
+  k_norm2_final<<<1, 32, 0, h->stream>>>(h->d_red, (int)nb, d_out, mode, h->q0norm, h->opts.eps);
   return cudaGetLastError();
 }
 
@@ -833,11 +859,36 @@ cudaError_t jv_setup(StabHandle* h, const double* q0_host) {
   K.igam = 1.0 / h->gamma;
   K.icp = 1.0 / h->cp;
   K.R = h->R;
+  K.gam = h->gamma;
+  K.S = h->S;
   k_pack_base<<<grid_for(h->nbase, thr), thr, 0, h->stream>>>(K);
   if ((err = cudaGetLastError()) != cudaSuccess) return err;
+  if (h->homog) {
+    const int nw = pw::nw_inputs(D);
+    if ((err = cudaMalloc(&h->d_coef, (size_t)h->ny * (D + 2) * nw * sizeof(double))) != cudaSuccess) return err;
+    PointParams PP = point_params(h, nullptr);
+    if (D == 2) k_coeffs<2><<<h->ny, 32, 0, h->stream>>>(PP, h->d_coef);
+    else k_coeffs<3><<<h->ny, 64, 0, h->stream>>>(PP, h->d_coef);
+    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+  }
   if ((err = cudaStreamSynchronize(h->stream)) != cudaSuccess) return err;
   cudaFree(bv);
   return cudaSuccess;
+}
+
+// Dense 1-D derivative matrices of an axis, column-major: out1[l * n + t] =
+// (D e_l)_t and out2 likewise for the second derivative, computed by the
+// same line sweeps as the operator.
+cudaError_t jv_derivative_matrices(StabHandle* h, int axis, double2* work, double2* out1, double2* out2) {
+  const int n = h->ax[axis].n;
+  std::vector<double2> eye((size_t)n * n, make_double2(0.0, 0.0));
+  for (int l = 0; l < n; ++l) eye[(size_t)l * n + l] = make_double2(1.0, 0.0);
+  cudaError_t e = cudaMemcpyAsync(work, eye.data(), eye.size() * sizeof(double2), cudaMemcpyHostToDevice, h->stream);
+  if (e != cudaSuccess) return e;
+  std::vector<LineJob> jobs{LineJob{work, out1, out2}};
+  PassParams P{};
+  if ((e = run_pass(h, axis, P, jobs, n)) != cudaSuccess) return e;
+  return cudaStreamSynchronize(h->stream);  // eye must outlive the copy
 }
 
 cudaError_t jv_apply(StabHandle* h, const double2* v, double2* out, double2 shift, int eps_mode) {
@@ -853,14 +904,23 @@ cudaError_t jv_apply(StabHandle* h, const double2* v, double2* out, double2 shif
   P.shift = shift;
   double2* Tw = h->d_scratch + (long long)h->slots.Tw * h->npts;
   const int thr = 128;
-  if (h->visc) k_temperature<<<grid_for(h->npts, thr), thr, 0, h->stream>>>(P, Tw);
+  const bool fast = h->homog && h->d_coef && !h->force_dn_path;
+  if (h->visc) {
+    if (fast) k_temperature_fast<<<grid_for(h->npts, thr), thr, 0, h->stream>>>(P, Tw);
+    else k_temperature<<<grid_for(h->npts, thr), thr, 0, h->stream>>>(P, Tw);
+  }
   const int D = h->dim;
   const double2* src[6];
   for (int f = 0; f < D + 2; ++f) src[f] = v + (long long)f * h->npts;
   src[D + 2] = Tw;
   if ((err = run_derivatives(h, src)) != cudaSuccess) return err;
-  if (D == 2) k_point<2><<<grid_for(h->npts, thr), thr, 0, h->stream>>>(P);
-  else k_point<3><<<grid_for(h->npts, thr), thr, 0, h->stream>>>(P);
+  if (fast) {
+    if (D == 2) k_point_fast<2><<<grid_for(h->npts, thr), thr, 0, h->stream>>>(P, h->d_coef);
+    else k_point_fast<3><<<grid_for(h->npts, thr), thr, 0, h->stream>>>(P, h->d_coef);
+  } else {
+    if (D == 2) k_point<2><<<grid_for(h->npts, thr), thr, 0, h->stream>>>(P);
+    else k_point<3><<<grid_for(h->npts, thr), thr, 0, h->stream>>>(P);
+  }
   h->stats.jv_calls++;
   return cudaGetLastError();
 }

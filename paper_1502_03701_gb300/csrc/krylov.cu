@@ -132,16 +132,7 @@ int grid_n(long long n) {
 
 }  // namespace
 
-// h[0..k) = V^H w  (d_h device)
-cudaError_t kry_dot_batch(StabHandle* h, const double2* V, int k, long long n, const double2* w, double2* d_h) {
-  if (k <= 0) return cudaSuccess;
-  const int nb = red_blocks(n);
-  double2* partial = (double2*)h->d_red;  // needs nb * k complex: checked by the caller's workspace
-  (void)partial;
-  return cudaErrorNotSupported;
-}
-
-static cudaError_t dot_into(StabHandle* h, const double2* V, int k, long long n, const double2* w, double2* d_h,
+cudaError_t kry_dot(StabHandle* h, const double2* V, int k, long long n, const double2* w, double2* d_h,
                             double2* partial, int accumulate) {
   const int nb = red_blocks(n);
   k_dot_partial<<<nb, kThreads, 0, h->stream>>>(V, k, n, w, partial);
@@ -164,22 +155,17 @@ cudaError_t kry_gemv_add(StabHandle* h, const double2* V, int k, long long n, co
 // CGS2: h = V^H w; w -= V h; h2 = V^H w; w -= V h2; h += h2; *d_norm = ||w||.
 // d_h must hold 2k complex (second half is scratch); the partials live in the
 // Krylov workspace provided by the caller through h->d_work tail.
-cudaError_t kry_cgs2_ws(StabHandle* h, const double2* V, int k, long long n, double2* w, double2* d_h, double* d_norm,
+cudaError_t kry_cgs2(StabHandle* h, const double2* V, int k, long long n, double2* w, double2* d_h, double* d_norm,
                         double2* partial) {
   cudaError_t e;
   if (k > 0) {
-    if ((e = dot_into(h, V, k, n, w, d_h, partial, 0)) != cudaSuccess) return e;
+    if ((e = kry_dot(h, V, k, n, w, d_h, partial, 0)) != cudaSuccess) return e;
     if ((e = kry_gemv_sub(h, V, k, n, d_h, w)) != cudaSuccess) return e;
-    if ((e = dot_into(h, V, k, n, w, d_h + k, partial, 0)) != cudaSuccess) return e;
+    if ((e = kry_dot(h, V, k, n, w, d_h + k, partial, 0)) != cudaSuccess) return e;
     if ((e = kry_gemv_sub(h, V, k, n, d_h + k, w)) != cudaSuccess) return e;
     k_axpby<<<1, 64, 0, h->stream>>>(make_double2(1.0, 0.0), d_h + k, make_double2(1.0, 0.0), d_h, k);
   }
   return launch_norm2(h, w, n, d_norm, 1);
-}
-
-cudaError_t kry_cgs2(StabHandle* h, const double2* V, int k, long long n, double2* w, double2* d_h, double* d_norm) {
-  (void)h; (void)V; (void)k; (void)n; (void)w; (void)d_h; (void)d_norm;
-  return cudaErrorNotSupported;
 }
 
 cudaError_t kry_scale(StabHandle* h, double2* x, long long n, const double* d_norm, double2* out) {

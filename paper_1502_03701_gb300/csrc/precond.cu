@@ -1,0 +1,451 @@
+// Local block-Jacobi preconditioner (Sec. "Preconditioning"): one dense
+// block per tile of tx x ty (x tz) grid points with all variables, equal to
+// the principal submatrix of (J - sigma I) over the tile's unknowns, J the
+// exact tangent.  The block is assembled from the linearised pointwise
+// operator fed with unit perturbations: a perturbation at tile point q only
+// reaches tile point p through the entries of the dense 1-D derivative
+// matrices (A^{-1} B of the compact schemes) that couple q and p, so the
+// restriction to the tile is exact.  Blocks are inverted by Gauss-Jordan
+// elimination with partial pivoting (first row of maximum modulus) and
+// applied as a batched block matrix-vector product.
+// Local unknown order inside a tile: [var][lz][ly][lx], lx fastest.
+#include <cstring>
+#include <vector>
+
+#include "internal.cuh"
+#include "pointwise.cuh"
+
+pw::Phys phys_of(const StabHandle* h);
+
+namespace {
+
+struct AsmParams {
+  int nx, ny, nz, tx, ty, tz, ntx, nty, ntpts, bsz;
+  long long npts, nbase, tile0;
+  int homog;
+  const double* btab;
+  const double* eta_y;
+  const double* eta_yy;
+  const unsigned char* bcflags;
+  const double2* Dm1[3];  // [l * n + t] = (D e_l)_t: first-derivative matrix of axis a, column-major
+  const double2* Dm2[3];
+  int nax[3];
+  pw::Phys phys;
+  double2 sigma;
+  double2* out;  // [tile - tile0][row][col]
+};
+
+template <int D>
+__global__ void __launch_bounds__(128) k_assemble(const AsmParams P) {
+  const long long tile = P.tile0 + blockIdx.x;
+  const int tX = (int)(tile % P.ntx);
+  const int tY = (int)((tile / P.ntx) % P.nty);
+  const int tZ = (int)(tile / ((long long)P.ntx * P.nty));
+  const int x0 = tX * P.tx, y0 = tY * P.ty, z0 = tZ * P.tz;
+  const int T = P.ntpts, bsz = P.bsz;
+  double2* blk = P.out + (long long)blockIdx.x * bsz * bsz;
+  const double ig = P.phys.C.ig;
+  for (long long idx = threadIdx.x; idx < (long long)bsz * T; idx += blockDim.x) {
+    const int col = (int)(idx / T), pp = (int)(idx % T);
+    const int beta = col / T, q = col % T;
+    const int qx = q % P.tx, qy = (q / P.tx) % P.ty, qz = q / (P.tx * P.ty);
+    const int px = pp % P.tx, py = (pp / P.tx) % P.ty, pz = pp / (P.tx * P.ty);
+    const int gq[3] = {x0 + qx, y0 + qy, z0 + qz};
+    const int gp[3] = {x0 + px, y0 + py, z0 + pz};
+    const long long ptp = ((long long)gp[2] * P.ny + gp[1]) * P.nx + gp[0];
+    const long long ptq = ((long long)gq[2] * P.ny + gq[1]) * P.nx + gq[0];
+    const long long bp = P.homog ? gp[1] : ptp, bq = P.homog ? gq[1] : ptq;
+    // field values at q of the unit perturbation (fields 0..D+1 = variables, D+2 = T)
+    double fq[D + 3];
+#pragma unroll
+    for (int f = 0; f < D + 2; ++f) fq[f] = f == beta ? 1.0 : 0.0;
+    {
+      const double T0 = P.btab[(long long)pw::bt_val(D, D + 2) * P.nbase + bq];
+      const double ip0 = P.btab[(long long)pw::bt_extra(D, pw::X_IP) * P.nbase + bq];
+      fq[D + 2] = beta == 0 ? T0 * (1.0 - ig) * ip0 : (beta == D + 1 ? T0 * P.phys.C.icp : 0.0);
+    }
+    const double ey = P.eta_y[gp[1]], eyy = P.eta_yy[gp[1]];
+    bool same[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) same[a] = gp[a] == gq[a];
+    auto d1c = [&](int a) { return P.Dm1[a][(long long)gq[a] * P.nax[a] + gp[a]].x; };  // D[p][q]
+    auto d2c = [&](int a) { return P.Dm2[a][(long long)gq[a] * P.nax[a] + gp[a]].x; };
+    pw::WIn<D> W;
+    const bool at_q = same[0] && same[1] && same[2];
+#pragma unroll
+    for (int f = 0; f < D + 3; ++f) W.v[f] = at_q ? fq[f] : 0.0;
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      bool line = true;  // p and q differ only along axis a
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+        if (c != a && !same[c]) line = false;
+      const double c1 = line ? d1c(a) * (a == 1 ? ey : 1.0) : 0.0;
+      double c2 = 0.0;
+      if (line) c2 = a == 1 ? fma(d2c(a), ey * ey, d1c(a) * eyy) : d2c(a);
+#pragma unroll
+      for (int f = 0; f < D + 3; ++f) W.d1[a][f] = c1 * fq[f];
+#pragma unroll
+      for (int g = 0; g < D + 1; ++g) W.d2[a][g] = c2 * fq[g < D ? 1 + g : D + 2];
+    }
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+#pragma unroll
+      for (int c = 0; c < D; ++c) {
+        double w = 0.0;
+        if (a != c) {
+          bool plane = true;  // p and q differ only along axes a and c
+#pragma unroll
+          for (int o = 0; o < 3; ++o)
+            if (o != a && o != c && !same[o]) plane = false;
+          if (plane) w = d1c(a) * d1c(c) * ((a == 1 || c == 1) ? ey : 1.0) * fq[1 + c];
+        }
+        W.mix[a][c] = w;
+      }
+    auto B = [&](int slot) { return P.btab[(long long)slot * P.nbase + bp]; };
+    const bool bc_row = gp[1] == 0 || gp[1] == P.ny - 1;
+    const unsigned fl =
+        bc_row ? P.bcflags[(gp[1] == P.ny - 1 ? (long long)P.nx * P.nz : 0) + (long long)gp[2] * P.nx + gp[0]] : 0u;
+    double res[D + 2];
+    pw::rhs_diff<D>(P.phys, B, W, 0.0, bc_row, fl, res);
+#pragma unroll
+    for (int a = 0; a < D + 2; ++a) {
+      const int row = a * T + pp;
+      double2 val = make_double2(res[a], 0.0);
+      if (row == col) { val.x -= P.sigma.x; val.y -= P.sigma.y; }
+      blk[(long long)row * bsz + col] = val;
+    }
+  }
+}
+
+template <class R>
+struct C2 {
+  R x, y;
+};
+
+__global__ void k_to_float(const double2* in, float2* out, long long count) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (long long)gridDim.x * blockDim.x) {
+    double2 v = in[i];
+    out[i] = make_float2((float)v.x, (float)v.y);
+  }
+}
+
+// In-place Gauss-Jordan inversion with partial pivoting of one b x b complex
+// block per CTA (row-major).  Threads own columns; rows are swept in order.
+template <class R>
+__global__ void k_gauss_jordan(C2<R>* A, int b, int* info) {
+  extern __shared__ unsigned char smraw[];
+  C2<R>* prow = (C2<R>*)smraw;
+  C2<R>* pcol = prow + b;
+  int* perm = (int*)(pcol + b);
+  __shared__ double rv[32];
+  __shared__ int ri[32];
+  __shared__ int s_piv;
+  C2<R>* M = A + (long long)blockIdx.x * b * b;
+  const int nthr = blockDim.x, lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int bad = 0;
+  for (int k = 0; k < b; ++k) {
+    // pivot: first row i >= k of maximum |A[i][k]|
+    double best = -1.0;
+    int bi = b;
+    for (int i = k + threadIdx.x; i < b; i += nthr) {
+      C2<R> v = M[(long long)i * b + k];
+      double m = (double)v.x * v.x + (double)v.y * v.y;
+      if (m > best) { best = m; bi = i; }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      double ob = __shfl_xor_sync(0xffffffffu, best, o);
+      int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+    }
+    if (lane == 0) { rv[wid] = best; ri[wid] = bi; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double bb = -1.0;
+      int bbi = b;
+      for (int w = 0; w < (nthr + 31) / 32; ++w)
+        if (rv[w] > bb || (rv[w] == bb && ri[w] < bbi)) { bb = rv[w]; bbi = ri[w]; }
+      if (!(bb > 0.0)) { bad = k + 1; bbi = k; }
+      s_piv = bbi;
+      perm[k] = bbi;
+    }
+    __syncthreads();
+    const int p = s_piv;
+    for (int j = threadIdx.x; j < b; j += nthr) {
+      C2<R> a = M[(long long)k * b + j], c = M[(long long)p * b + j];
+      if (p != k) { M[(long long)k * b + j] = c; M[(long long)p * b + j] = a; }
+      prow[j] = p != k ? c : a;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < b; i += nthr) pcol[i] = M[(long long)i * b + k];
+    __syncthreads();
+    C2<R> pv = prow[k];
+    R den = pv.x * pv.x + pv.y * pv.y;
+    if (!(den > (R)0)) den = (R)1;
+    const C2<R> inv = {pv.x / den, -pv.y / den};
+    for (int j = threadIdx.x; j < b; j += nthr) {
+      const C2<R> pj = prow[j];
+      const C2<R> s = {pj.x * inv.x - pj.y * inv.y, pj.x * inv.y + pj.y * inv.x};  // prow[j] / pivot
+      for (int i = 0; i < b; ++i) {
+        C2<R>* a = &M[(long long)i * b + j];
+        const C2<R> ci = pcol[i];
+        if (i == k) {
+          *a = j == k ? inv : s;
+        } else if (j == k) {
+          *a = C2<R>{-(ci.x * inv.x - ci.y * inv.y), -(ci.x * inv.y + ci.y * inv.x)};
+        } else {
+          C2<R> v = *a;
+          v.x -= ci.x * s.x - ci.y * s.y;
+          v.y -= ci.x * s.y + ci.y * s.x;
+          *a = v;
+        }
+      }
+    }
+    __syncthreads();
+  }
+  // undo the row interchanges: swap columns in reverse order
+  for (int k = b - 1; k >= 0; --k) {
+    const int p = perm[k];
+    if (p != k)
+      for (int i = threadIdx.x; i < b; i += nthr) {
+        C2<R> t = M[(long long)i * b + k];
+        M[(long long)i * b + k] = M[(long long)i * b + p];
+        M[(long long)i * b + p] = t;
+      }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0 && bad) atomicMax(info, 1);
+}
+
+struct ApplyParams {
+  const double2* q;
+  double2* z;
+  const void* inv;
+  int nx, ny, tx, ty, tz, ntx, nty, ntpts, bsz;
+  long long npts;
+};
+
+__device__ __forceinline__ long long tile_dof(const ApplyParams& P, long long tile, int r) {
+  const int tX = (int)(tile % P.ntx), tY = (int)((tile / P.ntx) % P.nty), tZ = (int)(tile / ((long long)P.ntx * P.nty));
+  const int var = r / P.ntpts, pp = r % P.ntpts;
+  const int px = pp % P.tx, py = (pp / P.tx) % P.ty, pz = pp / (P.tx * P.ty);
+  return (long long)var * P.npts + ((long long)(tZ * P.tz + pz) * P.ny + (tY * P.ty + py)) * P.nx + tX * P.tx + px;
+}
+
+// z_tile = Minv_tile q_tile; one CTA per tile, one warp per row at a time
+template <class R>
+__global__ void k_apply(const ApplyParams P) {
+  extern __shared__ unsigned char smraw[];
+  C2<R>* qs = (C2<R>*)smraw;
+  const long long tile = blockIdx.x;
+  const C2<R>* M = (const C2<R>*)P.inv + (long long)tile * P.bsz * P.bsz;
+  for (int r = threadIdx.x; r < P.bsz; r += blockDim.x) {
+    double2 v = P.q[tile_dof(P, tile, r)];
+    qs[r] = C2<R>{(R)v.x, (R)v.y};
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int r = wid; r < P.bsz; r += nw) {
+    const C2<R>* row = M + (long long)r * P.bsz;
+    R ar = 0, ai = 0;
+    for (int c = lane; c < P.bsz; c += 32) {
+      C2<R> m = row[c], x = qs[c];
+      ar += m.x * x.x - m.y * x.y;
+      ai += m.x * x.y + m.y * x.x;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      ar += __shfl_xor_sync(0xffffffffu, ar, o);
+      ai += __shfl_xor_sync(0xffffffffu, ai, o);
+    }
+    if (lane == 0) P.z[tile_dof(P, tile, r)] = make_double2((double)ar, (double)ai);
+  }
+}
+
+struct Geo {
+  int tx, ty, tz, ntx, nty, ntz, ntpts, bsz;
+  long long ntiles;
+};
+
+bool tile_geo(StabHandle* h, Geo& g) {
+  g.tx = h->opts.tile[0];
+  g.ty = h->opts.tile[1];
+  g.tz = h->dim == 3 ? h->opts.tile[2] : 1;
+  if (g.tx < 1 || g.ty < 1 || g.tz < 1 || h->nx % g.tx || h->ny % g.ty || h->nz % g.tz) return false;
+  g.ntx = h->nx / g.tx;
+  g.nty = h->ny / g.ty;
+  g.ntz = h->nz / g.tz;
+  g.ntpts = g.tx * g.ty * g.tz;
+  g.bsz = h->nv * g.ntpts;
+  g.ntiles = (long long)g.ntx * g.nty * g.ntz;
+  return g.bsz <= 1024;
+}
+
+cudaError_t ensure_dmats(StabHandle* h) {
+  cudaError_t e;
+  for (int a = 0; a < h->dim; ++a) {
+    if (h->d_dmat[a]) continue;
+    const int n = h->ax[a].n;
+    double2* buf;
+    if ((e = cudaMalloc(&buf, (size_t)3 * n * n * sizeof(double2))) != cudaSuccess) return e;
+    // [D1 | D2 | work]
+    if ((e = jv_derivative_matrices(h, a, buf + (size_t)2 * n * n, buf, buf + (size_t)n * n)) != cudaSuccess) {
+      cudaFree(buf);
+      return e;
+    }
+    h->d_dmat[a] = (double*)buf;
+  }
+  return cudaSuccess;
+}
+
+AsmParams asm_params(StabHandle* h, const Geo& g, double2 sigma) {
+  AsmParams P{};
+  P.nx = h->nx; P.ny = h->ny; P.nz = h->nz;
+  P.tx = g.tx; P.ty = g.ty; P.tz = g.tz; P.ntx = g.ntx; P.nty = g.nty; P.ntpts = g.ntpts; P.bsz = g.bsz;
+  P.npts = h->npts; P.nbase = h->nbase; P.homog = h->homog;
+  P.btab = h->d_btab;
+  P.eta_y = h->d_metric;
+  P.eta_yy = h->d_metric + h->ny;
+  P.bcflags = h->d_bcflags;
+  for (int a = 0; a < 3; ++a) {
+    P.nax[a] = h->ax[a].n;
+    const int n = h->ax[a].n;
+    P.Dm1[a] = a < h->dim ? (const double2*)h->d_dmat[a] : nullptr;
+    P.Dm2[a] = a < h->dim ? (const double2*)h->d_dmat[a] + (size_t)n * n : nullptr;
+  }
+  if (h->dim == 2) { P.Dm1[2] = P.Dm1[0]; P.Dm2[2] = P.Dm2[0]; P.nax[2] = 1; }
+  P.phys = phys_of(h);
+  P.sigma = sigma;
+  return P;
+}
+
+int gj_threads(int b) {
+  int t = b < 512 ? b : 512;
+  return ((t + 31) / 32) * 32;  // whole warps: the pivot search reduces with full-warp shuffles
+}
+
+cudaError_t launch_assemble(StabHandle* h, AsmParams& P, long long ntile_batch) {
+  if (h->dim == 2) k_assemble<2><<<(unsigned)ntile_batch, 128, 0, h->stream>>>(P);
+  else k_assemble<3><<<(unsigned)ntile_batch, 128, 0, h->stream>>>(P);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t pc_block(StabHandle* h, double2 sigma, long long t, double2* d_out) {
+  Geo g;
+  if (!tile_geo(h, g) || t < 0 || t >= g.ntiles) return cudaErrorInvalidValue;
+  cudaError_t e;
+  if ((e = ensure_dmats(h)) != cudaSuccess) return e;
+  AsmParams P = asm_params(h, g, sigma);
+  P.tile0 = t;
+  P.out = d_out;
+  return launch_assemble(h, P, 1);
+}
+
+cudaError_t pc_build(StabHandle* h, double2 sigma) {
+  Geo g;
+  if (!tile_geo(h, g)) return cudaErrorInvalidValue;
+  cudaError_t e;
+  if ((e = ensure_dmats(h)) != cudaSuccess) return e;
+  const int prec = h->opts.precond_prec;
+  const size_t esz = prec == 64 ? sizeof(double2) : sizeof(float2);
+  const size_t bb = (size_t)g.bsz * g.bsz;
+  if (!h->d_pinv || h->ntiles != g.ntiles || h->bsize != g.bsz || h->pprec != prec) {
+    cudaFree(h->d_pinv);
+    h->d_pinv = nullptr;
+    if ((e = cudaMalloc(&h->d_pinv, bb * g.ntiles * esz)) != cudaSuccess) return e;
+    h->ntiles = g.ntiles;
+    h->bsize = g.bsz;
+    h->pprec = prec;
+  }
+  h->pvalid = false;
+  // FP64 assembly in batches of at most ~1 GiB (directly into the inverse storage when FP64)
+  long long batch = (long long)((1ull << 30) / (bb * sizeof(double2)));
+  if (batch < 1) batch = 1;
+  if (batch > g.ntiles) batch = g.ntiles;
+  if (prec == 32 && !h->d_pblk) {
+    if ((e = cudaMalloc(&h->d_pblk, bb * batch * sizeof(double2))) != cudaSuccess) return e;
+  }
+  int* d_info;
+  if ((e = cudaMalloc(&d_info, sizeof(int))) != cudaSuccess) return e;
+  cudaMemsetAsync(d_info, 0, sizeof(int), h->stream);
+  AsmParams P = asm_params(h, g, sigma);
+  const size_t smem = (size_t)2 * g.bsz * esz + g.bsz * sizeof(int);
+  for (long long t0 = 0; t0 < g.ntiles; t0 += batch) {
+    const long long nb = std::min(batch, g.ntiles - t0);
+    P.tile0 = t0;
+    if (prec == 64) {
+      P.out = (double2*)h->d_pinv + bb * t0;
+      if ((e = launch_assemble(h, P, nb)) != cudaSuccess) break;
+      k_gauss_jordan<double><<<(unsigned)nb, gj_threads(g.bsz), smem, h->stream>>>(
+          (C2<double>*)P.out, g.bsz, d_info);
+    } else {
+      P.out = h->d_pblk;
+      if ((e = launch_assemble(h, P, nb)) != cudaSuccess) break;
+      float2* dst = (float2*)h->d_pinv + bb * t0;
+      k_to_float<<<1024, 256, 0, h->stream>>>(h->d_pblk, dst, (long long)(bb * nb));
+      k_gauss_jordan<float><<<(unsigned)nb, gj_threads(g.bsz), smem, h->stream>>>((C2<float>*)dst, g.bsz, d_info);
+    }
+    if ((e = cudaGetLastError()) != cudaSuccess) break;
+  }
+  int info = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&info, d_info, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  cudaFree(d_info);
+  if (e != cudaSuccess) return e;
+  if (info) return cudaErrorInvalidValue;  // a singular block
+  h->pvalid = true;
+  h->psigma_re = sigma.x;
+  h->psigma_im = sigma.y;
+  h->stats.precond_builds++;
+  return cudaSuccess;
+}
+
+cudaError_t pc_apply(StabHandle* h, const double2* q, double2* z) {
+  if (!h->pvalid) return cudaErrorInvalidValue;
+  Geo g;
+  tile_geo(h, g);
+  ApplyParams P{};
+  P.q = q; P.z = z; P.inv = h->d_pinv;
+  P.nx = h->nx; P.ny = h->ny; P.tx = g.tx; P.ty = g.ty; P.tz = g.tz; P.ntx = g.ntx; P.nty = g.nty;
+  P.ntpts = g.ntpts; P.bsz = g.bsz; P.npts = h->npts;
+  if (h->pprec == 64) k_apply<double><<<(unsigned)g.ntiles, 256, g.bsz * sizeof(double2), h->stream>>>(P);
+  else k_apply<float><<<(unsigned)g.ntiles, 256, g.bsz * sizeof(float2), h->stream>>>(P);
+  return cudaGetLastError();
+}
+
+extern "C" stab_status stab_precond_build(stab_handle hh, double sr, double si) {
+  StabHandle* h = (StabHandle*)hh;
+  if (!h) return STAB_ERR_INVALID_ARG;
+  Geo g;
+  if (!tile_geo(h, g)) { h->err = "stab_precond_build: tile must divide the grid and give blocks of at most 1024 unknowns"; return STAB_ERR_INVALID_ARG; }
+  cudaError_t e = pc_build(h, make_double2(sr, si));
+  if (e == cudaErrorInvalidValue) { h->err = "stab_precond_build: singular block"; return STAB_ERR_NUMERIC; }
+  if (e != cudaSuccess) { h->err = std::string("stab_precond_build: ") + cudaGetErrorString(e); return e == cudaErrorMemoryAllocation ? STAB_ERR_OOM : STAB_ERR_CUDA; }
+  return STAB_OK;
+}
+
+extern "C" stab_status stab_precond_apply(stab_handle hh, const void* q, void* z) {
+  StabHandle* h = (StabHandle*)hh;
+  if (!h) return STAB_ERR_INVALID_ARG;
+  if (!q || !z || q == z) { h->err = "stab_precond_apply: bad vectors"; return STAB_ERR_INVALID_ARG; }
+  if (!h->pvalid) { h->err = "stab_precond_apply: preconditioner not built"; return STAB_ERR_INVALID_ARG; }
+  cudaError_t e = pc_apply(h, (const double2*)q, (double2*)z);
+  if (e != cudaSuccess) { h->err = std::string("stab_precond_apply: ") + cudaGetErrorString(e); return STAB_ERR_CUDA; }
+  return STAB_OK;
+}
+
+extern "C" stab_status stab_precond_block(stab_handle hh, double sr, double si, long long t, double* out) {
+  StabHandle* h = (StabHandle*)hh;
+  if (!h) return STAB_ERR_INVALID_ARG;
+  Geo g;
+  if (!out || !tile_geo(h, g) || t < 0 || t >= g.ntiles) { h->err = "stab_precond_block: bad tile or output"; return STAB_ERR_INVALID_ARG; }
+  double2* d;
+  cudaError_t e = cudaMalloc(&d, (size_t)g.bsz * g.bsz * sizeof(double2));
+  if (e == cudaSuccess) e = pc_block(h, make_double2(sr, si), t, d);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(out, d, (size_t)g.bsz * g.bsz * sizeof(double2), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  cudaFree(d);
+  if (e != cudaSuccess) { h->err = std::string("stab_precond_block: ") + cudaGetErrorString(e); return STAB_ERR_CUDA; }
+  return STAB_OK;
+}

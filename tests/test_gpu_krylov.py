@@ -1,0 +1,118 @@
+"""GPU parity of the Krylov layer through the C ABI: CGS2 (Sec. Krylov
+methods), GMRES (Sec. Iterative solvers) and Cayley-IRAM (Algorithm iram),
+against the oracle and dense LAPACK."""
+import json
+import os
+
+import numpy as np
+import pytest
+import scipy.linalg as sla
+
+import stab_inputs as si
+from gpu_util import rel_err
+
+pytestmark = pytest.mark.gpu
+GOLD = os.path.join(os.path.dirname(__file__), "golden", "c1_dense_eigs.json")
+
+
+def _stab(nx, ny, **opts):
+    from paper_1502_03701_gb300 import Stab
+    g, f = si.mixing_layer_2d(nx, ny)
+    q0 = si.tanh_base_flow(g, f)
+    return Stab(q0, g, f.Ma, f.Re, f.Pr, **opts), g, f, q0
+
+
+def test_cgs2_matches_oracle(orc):
+    import torch
+    S, g, f, q0 = _stab(16, 24)
+    n = g.n
+    rng = np.random.default_rng(3)
+    for k in (0, 1, 7, 33):
+        Vh = np.linalg.qr(rng.standard_normal((n, max(k, 1))) + 1j * rng.standard_normal((n, max(k, 1))))[0][:, :k]
+        w = si.random_complex(40 + k, n)
+        V = torch.from_numpy(np.ascontiguousarray(Vh.T)).cuda()  # column j contiguous
+        wd = torch.from_numpy(w.copy()).cuda()
+        h, nrm = S.orthogonalize(V, k, wd)
+        if k:
+            href, wref = orc.krylov.cgs2(Vh, w)
+            assert np.abs(h - href).max() < 1e-13 * np.abs(href).max()
+        else:
+            wref = w
+        assert rel_err(wd.cpu().numpy(), wref) < 1e-13
+        assert abs(nrm - np.linalg.norm(wref)) < 1e-13 * nrm
+        if k:
+            assert np.abs(Vh.conj().T @ wd.cpu().numpy()).max() < 1e-13 * nrm
+    S.close()
+
+
+@pytest.mark.parametrize("sigma", [0.25, 0.1 + 0.3j])
+def test_gmres_solution_against_dense_solve(orc, sigma):
+    import torch
+    S, g, f, q0 = _stab(8, 16, eps_mode=2, gmres_m=40, gmres_tol=1e-12, gmres_max_restarts=400)
+    J = orc.core.dense_jacobian(orc.Problem.from_inputs(g, f), q0)
+    A = J - sigma * np.eye(g.n)
+    b = si.random_complex(77, g.n)
+    x = torch.zeros(g.n, dtype=torch.complex128, device="cuda")
+    st, iters = S.solve(sigma, torch.from_numpy(b).cuda(), x)
+    assert st == 0 and iters > 0
+    xh = x.cpu().numpy()
+    assert np.linalg.norm(b - A @ xh) <= 1.05e-12 * np.linalg.norm(b)
+    ref = sla.solve(A, b)
+    assert rel_err(xh, ref) < 1e-7  # conditioning of J - sigma I times the tolerance
+    S.close()
+
+
+def test_eigs_match_dense_lapack_tiny(orc):
+    """8 x 16 layer, real pole near the Kelvin-Helmholtz mode: the two wanted
+    Ritz values (the double eigenvalue of the +-alpha pair) match dense LAPACK
+    eigenvalues of J to 1e-8 relative with true residuals below 1e-8."""
+    S, g, f, q0 = _stab(8, 16, eps_mode=2, gmres_m=30, gmres_tol=1e-12, gmres_max_restarts=400)
+    J = orc.core.dense_jacobian(orc.Problem.from_inputs(g, f), q0)
+    lam_all = sla.eigvals(J)
+    r = S.eigs(0.25, -1.0, nev=2, ncv=12, tol=1e-11, v0=None)
+    assert r.status == 0 and r.nconv == 2
+    for l in r.lam:
+        assert np.abs(lam_all - l).min() < 1e-8 * abs(l)
+    ref, _ = orc.stability.dense_reference(J, 0.25, -1.0, 2)
+    for l in ref:
+        assert np.abs(r.lam - l).min() < 1e-8 * abs(l)
+    assert r.resid.max() < 1e-8
+    assert r.stats["jv_calls"] > 0 and r.stats["gmres_solves"] > 0
+    S.close()
+
+
+def test_eigs_small_layer_against_stored_dense_eigenvalues():
+    """32 x 64 layer (8,192 unknowns), sigma = 0.25, tau = -1: eigenvalues
+    against the stored dense LAPACK values written by the oracle."""
+    import torch
+    gold = json.load(open(GOLD))
+    ref = [complex(*l) for l in gold["sets"][1]["lambda"]]
+    S, g, f, q0 = _stab(32, 64, eps_mode=2, gmres_m=30, gmres_tol=1e-12, gmres_max_restarts=2000)
+    v0 = torch.from_numpy(si.start_vector(0x5EED, g.n)).cuda()
+    r = S.eigs(0.25, -1.0, nev=2, ncv=12, tol=1e-10, v0=v0)
+    assert r.status == 0 and r.nconv == 2
+    for l in r.lam:
+        assert np.abs(np.array(ref) - l).min() < 1e-8 * abs(l)
+    assert r.resid.max() < 1e-8
+    S.close()
+
+
+def test_eigs_eps_mode_offset_is_small(orc):
+    """With the epsilon-quotient (eps ~ 1e-7 per unit vector) the eigenvalues
+    move from the tangent ones by O(eps); both are reported."""
+    S0, g, f, q0 = _stab(8, 16, eps_mode=2, gmres_tol=1e-12, gmres_max_restarts=400)
+    S1, _, _, _ = _stab(8, 16, eps_mode=0, gmres_tol=1e-12, gmres_max_restarts=400)
+    a = S0.eigs(0.25, -1.0, nev=2, ncv=12, tol=1e-11)
+    b = S1.eigs(0.25, -1.0, nev=2, ncv=12, tol=1e-11)
+    assert a.nconv == 2 and b.nconv == 2
+    assert np.abs(np.sort_complex(a.lam) - np.sort_complex(b.lam)).max() < 1e-5
+    S0.close()
+    S1.close()
+
+
+def test_eigs_rejects_bad_arguments():
+    from paper_1502_03701_gb300 import StabError
+    S, g, f, q0 = _stab(8, 16)
+    with pytest.raises(StabError, match="INVALID_ARG"):
+        S.eigs(0.25, -1.0, nev=5, ncv=5, tol=1e-8)
+    S.close()
