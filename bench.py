@@ -1,17 +1,20 @@
 """Benchmark of the stability hot path on GB300.  Prints one JSON line.
 
-Default workload (--workload eigs): the 256 x 512 compressible tanh mixing
-layer (524,288 complex unknowns, Re 1000, Ma swept over 0.3 / 0.6 / 0.9 step
-by step).  One step is one complete stability solve through the C ABI:
-block-Jacobi build for the pole (8 x 8-point tiles, 256 x 256 blocks, FP32
-inverses), Cayley-transformed IRAM (sigma = 0.2i, tau = -1 + 0.2i, nev 10,
-ncv 60, tol 1e-10) with flexible GMRES(50) inner solves to 1e-10 on the exact
-tangent J v, eigenvectors and true residuals.  value = converged eigenpairs
-per second (pairs with true residual < 1e-8 counted); the step times give the
-p50 / p99 solve latency.
+Default (--workload jv): the 256 x 512 compressible tanh mixing layer
+(524,288 complex unknowns, Ma 0.3, Re 1000).  One timed step is one
+application of the matrix-free operator J(q0) v through the C ABI (the
+cancellation-free epsilon-quotient of the paper's Frechet derivative), the
+innermost and most-called step of the method; value = GB/s of algorithmic
+traffic (32 B per complex unknown).  Also reported, measured in the same run:
+  * "eigs": complete Cayley-IRAM solves of the 32 x 64 layer through stab_eigs
+    (sigma 1, tau -1, nev 4, ncv 30, block-Jacobi FGMRES(50) to 1e-10,
+    exact-tangent J v): converged eigenpairs per second (true residual
+    < 1e-8), the p50 / p99 solve latency and the J v count per solve;
+  * "gmres_256x512": preconditioned FGMRES(50) iterations per second on the
+    256 x 512 layer (block-Jacobi over 8 x 8-point tiles, FP32 inverses).
 
---workload jv: one step is one J v (cancellation-free epsilon-quotient) on
-the same layer; value in GB/s of algorithmic traffic.
+--workload eigs makes the 256 x 512 Cayley-IRAM solve the timed step (slow:
+its inner solves need thousands of preconditioned iterations each).
 
 --impl reference times the CPU oracle (plain C++ restatement) on the host
 cores on a bounded sample and scales it to the same metric.
@@ -154,9 +157,22 @@ def run_reference(args):
         return
     g, f, q0 = _layer(args.nx, args.ny, 0.3)
     if args.workload == "jv":
-        dt, count, cores = oracle_jv_seconds(g, f, q0, max(1.0, 0.5 * args.steps), "literal")
+        import oracle
+        oracle.build()
+        P = oracle.Problem.from_inputs(g, f)
+        v = si.random_complex(11, g.n)
+        eps = oracle.core.knoll_keyes_eps(q0, v)
+        for _ in range(max(args.warmup, 1)):
+            oracle.core.jv(P, q0, v, "literal", eps)
+        t0 = time.perf_counter()
+        count = 0
+        while count < args.steps and time.perf_counter() - t0 < 60.0:  # K steps, at most a minute
+            oracle.core.jv(P, q0, v, "literal", eps)
+            count += 1
+        dt = (time.perf_counter() - t0) / count
+        cores = oracle.core.num_threads()
         val, unit, ms = g.n * JV_BYTES_PER_DOF / dt / 1e9, "GB/s", dt * 1e3
-        sample = f"{count} literal double epsilon-quotient J v on the full layer"
+        sample = f"{count} literal double epsilon-quotient J v on the full {g.nx}x{g.ny} layer (of {args.steps} steps)"
     else:
         # bounded sample: the oracle's J v time scaled by the J v count of a solve of this workload
         # (recorded by the GPU arm in profiles/; 1 J v per GMRES iteration plus one per restart)
@@ -173,6 +189,61 @@ def run_reference(args):
             "cpu_baseline": {"value": val, "unit": unit, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": val, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
+
+
+# 32 x 64 layer; the pole sits right of the spectrum (inner solves converge), the four least-stable
+# eigenvalues (two Kelvin-Helmholtz double eigenvalues) are wanted.
+SMALL_EIG = dict(nx=32, ny=64, sigma=1.0, tau=-1.0, nev=4, ncv=30, tol=1e-10)
+
+
+def small_layer_eigs(args, Stab, torch, rank):
+    """Complete solves of the 32 x 64 layer: eigenpairs/s and latency."""
+    g, f, q0 = _layer(SMALL_EIG["nx"], SMALL_EIG["ny"], 0.3)
+    S = Stab(q0, g, f.Ma, f.Re, f.Pr, eps_mode=2, precond=1, tile=(8, 8), precond_prec=32, gmres_m=50,
+             gmres_tol=1e-10, gmres_max_restarts=100, max_restarts=40, seed=0x5EED + rank)
+    args_e = (SMALL_EIG["sigma"], SMALL_EIG["tau"], SMALL_EIG["nev"], SMALL_EIG["ncv"], SMALL_EIG["tol"])
+    S.eigs(*args_e)  # warm-up
+    times, good, res = [], 0, []
+    for _ in range(args.eig_steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = S.eigs(*args_e)
+        torch.cuda.synchronize()
+        times.append(time.perf_counter() - t0)
+        good += int(np.sum(r.resid[:r.nconv] < RESID_OK))
+        res.append(r)
+    S.close()
+    lat = sorted(times)
+    return {"value": good / sum(times), "unit": "eigenpairs/s", "workload": "eigs_mixing_layer_32x64",
+            "sigma": [1.0, 0.0], "tau": [-1.0, 0.0], "nev": SMALL_EIG["nev"], "ncv": SMALL_EIG["ncv"],
+            "tol": SMALL_EIG["tol"], "gmres": "FGMRES(50) to 1e-10, block-Jacobi 8x8 tiles FP32",
+            "solves": len(times),
+            "latency_ms": {"p50": statistics.median(lat) * 1e3, "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))] * 1e3},
+            "nconv": [r.nconv for r in res], "max_resid": max(float(np.max(r.resid)) for r in res),
+            "jv_per_solve": statistics.mean(r.stats["jv_calls"] for r in res),
+            "gmres_iterations_per_solve": statistics.mean(r.stats["gmres_iterations"] for r in res),
+            "restarts": [r.stats["restarts"] for r in res]}
+
+
+def gmres_throughput(args, Stab, torch, q0, g, f):
+    """Preconditioned FGMRES(50) on the 256 x 512 layer: iterations per second."""
+    S = Stab(q0, g, f.Ma, f.Re, f.Pr, eps_mode=2, precond=1, tile=(8, 8), precond_prec=32, gmres_m=50,
+             gmres_tol=1e-10, gmres_max_restarts=args.gmres_restarts)
+    sigma = 1.0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    S.precond_build(sigma)
+    torch.cuda.synchronize()
+    t_build = time.perf_counter() - t0
+    b = torch.from_numpy(si.random_complex(1, g.n)).cuda()
+    x = torch.zeros_like(b)
+    t0 = time.perf_counter()
+    st, it = S.solve(sigma, b, x)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    S.close()
+    return {"value": it / dt, "unit": "iterations/s", "iterations": it, "seconds": dt, "converged": st == 0,
+            "precond_build_s": t_build, "sigma": sigma, "tile": [8, 8], "block": 256, "precond": "FP32 inverses"}
 
 
 def _time_jv(S, v, out, steps, flush, stream, torch):
@@ -239,7 +310,12 @@ def run_ours(args):
                 "note": "FP64-pipe bound on GB300 (FP64 1.2 TFLOP/s measured); see profiles/"}
 
     if args.workload == "jv":
-        steps_t = _time_jv(Sj, v, out, args.steps, flush, stream, torch)
+        sampler = ClockSampler(local, 50)
+        barrier()
+        with sampler:
+            steps_t = _time_jv(Sj, v, out, args.steps, flush, stream, torch)
+            barrier()
+        clock_sum = sampler.summary()
         t_max = max_over_ranks(sum(steps_t))
         value = world * args.steps * bytes_jv / t_max / 1e9
         unit = "GB/s"
@@ -262,7 +338,11 @@ def run_ours(args):
         e2e = {"value": world * bytes_jv / (e0.elapsed_time(e1) / 1e3 / args.steps) / 1e9, "unit": "GB/s",
                "h2d_bytes_per_step": n * 16, "d2h_bytes_per_step": n * 16}
         extra = {"gpu_launches": args.steps * 6}
-        sampler_summary = None
+        sampler_summary = clock_sum
+        if args.eig_steps > 0:
+            extra["eigs"] = small_layer_eigs(args, Stab, torch, rank)
+        if args.gmres_restarts > 0:
+            extra["gmres_256x512"] = gmres_throughput(args, Stab, torch, q0, g, f)
     else:
         sweep = (0.3, 0.6, 0.9)
         handles = []
@@ -366,10 +446,12 @@ def run_ours(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="eigs", choices=["eigs", "jv"])
+    ap.add_argument("--workload", default="jv", choices=["eigs", "jv"])
+    ap.add_argument("--eig-steps", type=int, default=3)
+    ap.add_argument("--gmres-restarts", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--nx", type=int, default=256)
     ap.add_argument("--ny", type=int, default=512)

@@ -118,6 +118,125 @@ __global__ void __launch_bounds__(kVqRows) k_vq(const double2* __restrict__ V, i
   }
 }
 
+// ---------------------------------------------------------------------------
+// Fused CGS2.  Pass A: partial1 = block sums of V^H w.  Pass B: every block
+// reduces partial1 to h1 (same fixed order in every block), updates its rows
+// w -= V h1 and forms the block sums of V^H w' (partial2).  Pass C: every
+// block reduces partial2 to h2, updates w -= V h2, forms the block sums of
+// |w|^2; block 0 stores h = h1 + h2.  A final warp sums the norm partials.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void reduce_partials(const double2* partial, int nb, int k, double2* hs) {
+  // hs[j] = sum_b partial[b * k + j]; one warp per column, fixed order
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int j = wid; j < k; j += nw) {
+    double sr = 0.0, si = 0.0;
+    for (int b = lane; b < nb; b += 32) {
+      double2 p = partial[(long long)b * k + j];
+      sr += p.x;
+      si += p.y;
+    }
+    sr = warp_sum(sr);
+    si = warp_sum(si);
+    if (lane == 0) hs[j] = make_double2(sr, si);
+  }
+}
+
+__device__ __forceinline__ void block_dot_columns(const double2* __restrict__ V, int k, long long n,
+                                                  const double2* w, double2* partial_out, double* red) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int j = 0; j < k; ++j) {
+    const double2* Vj = V + (long long)j * n;
+    double sr = 0.0, si = 0.0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+      double2 a = Vj[i], b = w[i];
+      sr = fma(a.x, b.x, fma(a.y, b.y, sr));
+      si = fma(a.x, b.y, fma(-a.y, b.x, si));
+    }
+    sr = warp_sum(sr);
+    si = warp_sum(si);
+    if (lane == 0) { red[2 * wid] = sr; red[2 * wid + 1] = si; }
+    __syncthreads();
+    if (wid == 0) {
+      double tr = lane < (int)(blockDim.x >> 5) ? red[2 * lane] : 0.0;
+      double ti = lane < (int)(blockDim.x >> 5) ? red[2 * lane + 1] : 0.0;
+      tr = warp_sum(tr);
+      ti = warp_sum(ti);
+      if (lane == 0) partial_out[(long long)blockIdx.x * k + j] = make_double2(tr, ti);
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_cgs2_a(const double2* __restrict__ V, int k, long long n,
+                                                    const double2* __restrict__ w, double2* partial1) {
+  __shared__ double red[2 * kThreads / 32];
+  block_dot_columns(V, k, n, w, partial1, red);
+}
+
+__global__ void __launch_bounds__(kThreads) k_cgs2_b(const double2* __restrict__ V, int k, long long n, double2* w,
+                                                    const double2* partial1, double2* partial2, double2* d_h) {
+  extern __shared__ double2 hs[];
+  __shared__ double red[2 * kThreads / 32];
+  reduce_partials(partial1, gridDim.x, k, hs);
+  __syncthreads();
+  if (blockIdx.x == 0)
+    for (int j = threadIdx.x; j < k; j += blockDim.x) d_h[j] = hs[j];
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    double ar = 0.0, ai = 0.0;
+    for (int j = 0; j < k; ++j) {
+      double2 a = V[(long long)j * n + i], c = hs[j];
+      ar = fma(a.x, c.x, fma(-a.y, c.y, ar));
+      ai = fma(a.x, c.y, fma(a.y, c.x, ai));
+    }
+    double2 xv = w[i];
+    w[i] = make_double2(xv.x - ar, xv.y - ai);
+  }
+  __syncthreads();  // this block's rows of w are final; the dots below read only them
+  block_dot_columns(V, k, n, w, partial2, red);
+}
+
+__global__ void __launch_bounds__(kThreads) k_cgs2_c(const double2* __restrict__ V, int k, long long n, double2* w,
+                                                    const double2* partial2, double2* d_h, double* norm_partial) {
+  extern __shared__ double2 hs[];
+  __shared__ double red[kThreads / 32];
+  reduce_partials(partial2, gridDim.x, k, hs);
+  __syncthreads();
+  if (blockIdx.x == 0)
+    for (int j = threadIdx.x; j < k; j += blockDim.x) {
+      double2 h1 = d_h[j];
+      d_h[j] = make_double2(h1.x + hs[j].x, h1.y + hs[j].y);
+    }
+  double s = 0.0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    double ar = 0.0, ai = 0.0;
+    for (int j = 0; j < k; ++j) {
+      double2 a = V[(long long)j * n + i], c = hs[j];
+      ar = fma(a.x, c.x, fma(-a.y, c.y, ar));
+      ai = fma(a.x, c.y, fma(a.y, c.x, ai));
+    }
+    double2 xv = w[i];
+    double2 r = make_double2(xv.x - ar, xv.y - ai);
+    w[i] = r;
+    s = fma(r.x, r.x, fma(r.y, r.y, s));
+  }
+  s = warp_sum(s);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) red[wid] = s;
+  __syncthreads();
+  if (wid == 0) {
+    double t = lane < (int)(blockDim.x >> 5) ? red[lane] : 0.0;
+    t = warp_sum(t);
+    if (lane == 0) norm_partial[blockIdx.x] = t;
+  }
+}
+
+__global__ void k_norm_final(const double* partial, int nb, double* out) {
+  double s = 0.0;
+  for (int i = threadIdx.x; i < nb; i += 32) s += partial[i];
+  s = warp_sum(s);
+  if (threadIdx.x == 0) *out = sqrt(s);
+}
+
 int red_blocks(long long n) {
   long long b = (n + kThreads - 1) / kThreads;
   if (b > 152 * 4) b = 152 * 4;
@@ -153,17 +272,21 @@ cudaError_t kry_gemv_add(StabHandle* h, const double2* V, int k, long long n, co
 }
 
 // CGS2: h = V^H w; w -= V h; h2 = V^H w; w -= V h2; h += h2; *d_norm = ||w||.
-// d_h must hold 2k complex (second half is scratch); the partials live in the
-// Krylov workspace provided by the caller through h->d_work tail.
+// partial holds kry_partial_elems(n, k) complex (two sets of block sums and
+// the norm partials); d_h holds 2k complex.
 cudaError_t kry_cgs2(StabHandle* h, const double2* V, int k, long long n, double2* w, double2* d_h, double* d_norm,
-                        double2* partial) {
-  cudaError_t e;
+                     double2* partial) {
+  const int nb = red_blocks(n);
+  double2* p1 = partial;
+  double2* p2 = partial + (size_t)nb * (k > 0 ? k : 1);
+  double* np = (double*)(p2 + (size_t)nb * (k > 0 ? k : 1));
   if (k > 0) {
-    if ((e = kry_dot(h, V, k, n, w, d_h, partial, 0)) != cudaSuccess) return e;
-    if ((e = kry_gemv_sub(h, V, k, n, d_h, w)) != cudaSuccess) return e;
-    if ((e = kry_dot(h, V, k, n, w, d_h + k, partial, 0)) != cudaSuccess) return e;
-    if ((e = kry_gemv_sub(h, V, k, n, d_h + k, w)) != cudaSuccess) return e;
-    k_axpby<<<1, 64, 0, h->stream>>>(make_double2(1.0, 0.0), d_h + k, make_double2(1.0, 0.0), d_h, k);
+    const size_t sm = (size_t)k * sizeof(double2);
+    k_cgs2_a<<<nb, kThreads, 0, h->stream>>>(V, k, n, w, p1);
+    k_cgs2_b<<<nb, kThreads, sm, h->stream>>>(V, k, n, w, p1, p2, d_h);
+    k_cgs2_c<<<nb, kThreads, sm, h->stream>>>(V, k, n, w, p2, d_h, np);
+    k_norm_final<<<1, 32, 0, h->stream>>>(np, nb, d_norm);
+    return cudaGetLastError();
   }
   return launch_norm2(h, w, n, d_norm, 1);
 }
@@ -195,4 +318,7 @@ cudaError_t kry_update_basis(StabHandle* h, double2* V, int m, int kk, long long
   return cudaGetLastError();
 }
 
-int kry_partial_elems(long long n, int k) { return red_blocks(n) * (k > 0 ? k : 1); }
+int kry_partial_elems(long long n, int k) {
+  const int nb = red_blocks(n);
+  return 2 * nb * (k > 0 ? k : 1) + (nb + 1) / 2 + 1;
+}

@@ -5,7 +5,8 @@
 //  * the Cayley-transformed implicitly restarted Arnoldi method
 //    (Algorithm iram, Eqs. cayley_transform / cayley_arnoldi / ritz_estimate)
 //    with CGS2 orthogonalisation and exact shifts.
-// Only the small (m x m) Hessenberg algebra runs on the host.
+// The small (m x m) Hessenberg algebra of the restart stays on the device
+// (k_restart); GMRES's Givens least-squares update runs on the host.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -13,6 +14,7 @@
 #include <cstring>
 #include <vector>
 
+#include "hess_dev.cuh"
 #include "hessenberg.h"
 #include "internal.cuh"
 
@@ -164,6 +166,112 @@ int gmres(StabHandle* h, cd sigma, const double2* b, double2* x, int eps_mode, b
   return total;
 }
 
+// ---------------------------------------------------------------------------
+// Device-resident Hessenberg state of the implicit restart.
+// ---------------------------------------------------------------------------
+struct RestartWs {
+  hd::zc *H, *T, *Z, *X, *Y, *Q, *theta, *sn, *Qc, *out_theta;
+  double *cs, *est, *scal;  // scal: [conv count, fnorm, ||H||_F]
+  int* order;
+  hd::zc* coef;             // [beta_k, sigma_k]
+};
+
+size_t restart_ws_elems(int m, int k) {
+  // complex elements: 7 m*m + 4 m + m*(k+1) + k + 2, plus doubles/ints packed as complex
+  return (size_t)7 * m * m + 4 * m + (size_t)m * (k + 1) + k + 2 + (m + k + 4) + m;
+}
+
+RestartWs restart_ws(double2* base, int m, int k) {
+  RestartWs w;
+  hd::zc* p = (hd::zc*)base;
+  w.H = p; p += (size_t)m * m;
+  w.T = p; p += (size_t)m * m;
+  w.Z = p; p += (size_t)m * m;
+  w.X = p; p += (size_t)m * m;
+  w.Y = p; p += (size_t)m * m;
+  w.Q = p; p += (size_t)m * m;
+  p += (size_t)m * m;  // spare
+  w.theta = p; p += m;
+  w.sn = p; p += m;
+  w.out_theta = p; p += m;
+  p += m;
+  w.Qc = p; p += (size_t)m * (k + 1);
+  w.coef = p; p += 2;
+  double* d = (double*)p;
+  w.cs = d; d += m;
+  w.est = d; d += k;
+  w.scal = d; d += 4;
+  w.order = (int*)d;
+  return w;
+}
+
+// H(0..j, j) = h;  H(j, j-1) = beta (when set)
+__global__ void k_hcol(hd::zc* H, int m, int j, const double2* dh, const double* beta, int set_sub) {
+  for (int i = threadIdx.x; i <= j; i += blockDim.x) H[i * m + j] = hd::mk(dh[i].x, dh[i].y);
+  if (threadIdx.x == 0 && set_sub && j > 0) H[j * m + j - 1] = hd::mk(*beta, 0.0);
+}
+
+__global__ void k_hsub(hd::zc* H, int m, int j, const double* beta) { H[j * m + j - 1] = hd::mk(*beta, 0.0); }
+
+__global__ void k_zero(hd::zc* H, int count) {
+  for (int i = threadIdx.x; i < count; i += blockDim.x) H[i] = hd::mk(0.0);
+}
+
+// Spectrum of H_m, wanted/unwanted split, Ritz estimates (Eq. ritz_estimate);
+// then either the wanted eigenvectors (finish = 1 or all converged) or the
+// exact-shift sweeps and the coefficients of the basis update (Algorithm iram).
+__global__ void k_restart(RestartWs w, int m, int k, double2 sg, double2 ta, double tol, const double* fnorm,
+                          int finish) {
+  if (threadIdx.x != 0) return;
+  const hd::zc sigma = hd::mk(sg.x, sg.y), tau = hd::mk(ta.x, ta.y);
+  if (hd::eig(m, w.H, w.theta, w.Y, w.T, w.Z, w.X) != 0) { w.scal[0] = -1.0; return; }
+  for (int i = 0; i < m; ++i) w.order[i] = i;
+  for (int i = 1; i < m; ++i) {  // insertion sort (stable) by the wanted order
+    int v = w.order[i], j = i - 1;
+    while (j >= 0 && hd::before(w.theta[v], w.theta[w.order[j]], sigma, tau)) { w.order[j + 1] = w.order[j]; --j; }
+    w.order[j + 1] = v;
+  }
+  double hn = 0.0;
+  for (int i = 0; i < m * m; ++i) hn += hd::abs2(w.H[i]);
+  hn = sqrt(hn);
+  const double fn = *fnorm;
+  int conv = 0;
+  for (int q = 0; q < k; ++q) {
+    const int i = w.order[q];
+    w.est[q] = fn * hd::zabs(w.Y[(m - 1) * m + i]);
+    w.out_theta[q] = w.theta[i];
+    if (w.est[q] <= fmax(2.220446049250313e-16 * hn, tol * hd::zabs(w.theta[i]))) ++conv;
+  }
+  w.scal[0] = conv;
+  w.scal[1] = fn;
+  w.scal[2] = hn;
+  if (conv == k || finish) {
+    for (int q = 0; q < k; ++q)
+      for (int l = 0; l < m; ++l) w.Qc[q * m + l] = w.Y[l * m + w.order[q]];
+    return;
+  }
+  for (int i = 0; i < m * m; ++i) w.Q[i] = hd::mk(0.0);
+  for (int i = 0; i < m; ++i) w.Q[i * m + i] = hd::mk(1.0);
+  for (int q = k; q < m; ++q) hd::shifted_qr(m, w.H, w.Q, w.theta[w.order[q]], w.cs, w.sn);
+  w.coef[0] = w.H[k * m + k - 1];        // beta_k
+  w.coef[1] = w.Q[(m - 1) * m + k - 1];  // sigma_k
+  for (int j = 0; j <= k; ++j)
+    for (int l = 0; l < m; ++l) w.Qc[j * m + l] = w.Q[l * m + j];
+  for (int r = 0; r < m; ++r)
+    for (int c = 0; c < m; ++c)
+      if (r >= k || c >= k) w.H[r * m + c] = hd::mk(0.0);
+}
+
+// f = x * coef[0] + f * coef[1]  (coefficients in device memory)
+__global__ void k_f_update(const double2* x, double2* f, long long n, const hd::zc* coef) {
+  const hd::zc a = coef[0], b = coef[1];
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    double2 xv = x[i], fv = f[i];
+    f[i] = make_double2(a.re * xv.x - a.im * xv.y + b.re * fv.x - b.im * fv.y,
+                        a.re * xv.y + a.im * xv.x + b.re * fv.y + b.im * fv.x);
+  }
+}
+
 // splitmix64 (Steele, Lea and Flood 2014): uniform [-1/2, 1/2) from the top 53 bits
 void splitmix_start(unsigned long long seed, long long n, std::vector<double>& out) {
   out.resize(2 * (size_t)n);
@@ -246,18 +354,20 @@ extern "C" stab_status stab_eigs(stab_handle hh, double sr, double si, double tr
       ck(h, cudaStreamSynchronize(h->stream), "sync");
       h->stats.seconds_precond += std::chrono::duration<double>(std::chrono::steady_clock::now() - tp).count();
     }
-    // IRAM workspace: V (m n), f (n), x (n), tmp ((k+1) n), Q (m (k+1)), partials, dh, scalars
+    // IRAM workspace: V (m n), f (n), x (n), tmp ((k+1) n), partials, dh, scalars, restart state
     const size_t part = (size_t)kry_partial_elems(n, m);
-    const size_t need = (size_t)m * n + 2 * (size_t)n + (size_t)(k + 1) * n + (size_t)m * (k + 1) + part + 2 * m + 4;
+    const size_t rws = restart_ws_elems(m, k);
+    const size_t need = (size_t)m * n + 2 * (size_t)n + (size_t)(k + 1) * n + part + 2 * m + 4 + rws;
     double2* base = ensure(h, &h->d_ir, &h->ir_elems, need);
     double2* V = base;
     double2* f = V + (size_t)m * n;
     double2* xw = f + n;
     double2* tmp = xw + n;
-    double2* dQ = tmp + (size_t)(k + 1) * n;
-    double2* partial = dQ + (size_t)m * (k + 1);
+    double2* partial = tmp + (size_t)(k + 1) * n;
     double2* dh = partial + part;
     double* dn = (double*)(dh + 2 * m);
+    RestartWs RW = restart_ws(dh + 2 * m + 4, m, k);
+    const double2* dQ = (const double2*)RW.Qc;
     // start vector
     if (v0) ck(h, kry_copy(h, (const double2*)v0, f, n), "copy v0");
     else {
@@ -266,22 +376,21 @@ extern "C" stab_status stab_eigs(stab_handle hh, double sr, double si, double tr
       ck(h, cudaMemcpyAsync(f, sv.data(), sizeof(double) * sv.size(), cudaMemcpyHostToDevice, h->stream), "copy start");
       ck(h, cudaStreamSynchronize(h->stream), "sync");
     }
-    std::vector<cd> H((size_t)m * m, 0.0), theta(m), Y((size_t)m * m), Q((size_t)m * m);
-    std::vector<double> hbuf(2 * m);
-    std::vector<int> order(m);
-    std::vector<double> est(k);
+    k_zero<<<1, 256, 0, h->stream>>>(RW.H, m * m);
+    std::vector<double> ritz(2 * k + k + 4);
     int j0 = 0;
     bool first = true;
     int conv_count = 0;
-    double fnorm = 0.0;
+    std::vector<cd> theta_w(k);
     for (int restart = 0;; ++restart) {
       for (int j = j0; j < m; ++j) {
         ck(h, launch_norm2(h, f, n, dn, 1), "norm");
         const double beta = read_scalar(h, dn);
         if (!(beta < INFINITY)) fail(h, STAB_ERR_NUMERIC, "IRAM: non-finite residual vector");
         if (beta == 0.0) fail(h, STAB_ERR_BREAKDOWN, "IRAM: Arnoldi breakdown (invariant subspace)");
-        if (!first || j > 0) H[(size_t)j * m + j - 1] = beta;
+        // H(j, j-1) = beta from the device norm; the column H(0..j, j) follows the orthogonalisation
         double2* Vj = V + (size_t)j * n;
+        if (!first || j > 0) k_hsub<<<1, 1, 0, h->stream>>>(RW.H, m, j, dn);
         ck(h, kry_scale(h, f, n, dn, Vj), "scale");
         // w = C v_j: b = (J - tau I) v_j, then (J - sigma I) x = b
         ck(h, jv_apply(h, Vj, xw, d2(tau), h->opts.eps_mode), "J v");
@@ -289,67 +398,37 @@ extern "C" stab_status stab_eigs(stab_handle hh, double sr, double si, double tr
         gmres(h, sigma, xw, f, h->opts.eps_mode, &gconv);
         if (!gconv) result = STAB_ERR_NOT_CONVERGED;
         ck(h, kry_cgs2(h, V, j + 1, n, f, dh, dn, partial), "CGS2");
-        ck(h, cudaMemcpyAsync(hbuf.data(), dh, sizeof(double2) * (j + 1), cudaMemcpyDeviceToHost, h->stream), "copy h");
-        ck(h, cudaStreamSynchronize(h->stream), "sync");
-        for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = cd(hbuf[2 * i], hbuf[2 * i + 1]);
+        k_hcol<<<1, 64, 0, h->stream>>>(RW.H, m, j, dh, dn, 0);
         h->stats.arnoldi_steps++;
       }
       first = false;
-      fnorm = read_scalar(h, dn);
-      // Ritz values, wanted set (largest |theta|; ties: larger Re, then Im lambda)
-      if (hess::eig(m, H.data(), theta.data(), Y.data()) != 0) fail(h, STAB_ERR_NUMERIC, "IRAM: Hessenberg QR failed");
-      for (int i = 0; i < m; ++i) order[i] = i;
-      auto lam_of = [&](cd t) { return (sigma * t - tau) / (t - 1.0); };
-      std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
-        double aa = std::abs(theta[a]), ab = std::abs(theta[b]);
-        if (aa != ab) return aa > ab;
-        cd la = lam_of(theta[a]), lb = lam_of(theta[b]);
-        if (la.real() != lb.real()) return la.real() > lb.real();
-        return la.imag() > lb.imag();
-      });
-      double hn = 0.0;
-      for (auto& z : H) hn += std::norm(z);
-      hn = std::sqrt(hn);
-      conv_count = 0;
-      for (int q = 0; q < k; ++q) {
-        const int i = order[q];
-        est[q] = fnorm * std::abs(Y[(size_t)(m - 1) * m + i]);
-        if (est[q] <= std::max(2.220446049250313e-16 * hn, tol * std::abs(theta[i]))) ++conv_count;
-      }
-      if (conv_count == k || restart >= h->opts.max_restarts) {
+      const int finish = restart >= h->opts.max_restarts;
+      k_restart<<<1, 32, 0, h->stream>>>(RW, m, k, d2(sigma), d2(tau), tol, dn, finish);
+      ck(h, cudaGetLastError(), "restart kernel");
+      ck(h, cudaMemcpyAsync(ritz.data(), RW.out_theta, sizeof(double2) * k, cudaMemcpyDeviceToHost, h->stream), "copy");
+      ck(h, cudaMemcpyAsync(ritz.data() + 2 * k, RW.est, sizeof(double) * (k + 4), cudaMemcpyDeviceToHost, h->stream),
+         "copy");
+      ck(h, cudaStreamSynchronize(h->stream), "sync");
+      const double* scal = ritz.data() + 3 * k;
+      if (scal[0] < 0) fail(h, STAB_ERR_NUMERIC, "IRAM: Hessenberg QR failed");
+      conv_count = (int)scal[0];
+      for (int q = 0; q < k; ++q) theta_w[q] = cd(ritz[2 * q], ritz[2 * q + 1]);
+      if (conv_count == k || finish) {
         if (conv_count < k) { result = STAB_ERR_NOT_CONVERGED; h->err = "stab_eigs: IRAM restart limit reached"; }
         break;
       }
       h->stats.restarts++;
-      // exact shifts: the m - k unwanted Ritz values
-      std::fill(Q.begin(), Q.end(), cd(0.0));
-      for (int i = 0; i < m; ++i) Q[(size_t)i * m + i] = 1.0;
-      for (int q = k; q < m; ++q) hess::shifted_qr(m, H.data(), Q.data(), theta[order[q]]);
-      const cd beta_k = H[(size_t)k * m + k - 1];
-      const cd sig_k = Q[(size_t)(m - 1) * m + k - 1];
       // tmp = V Q[:, 0:k+1];  f = tmp_k beta_k + f sigma_k;  V[:, 0:k] = tmp[:, 0:k]
-      std::vector<cd> Qc((size_t)m * (k + 1));
-      for (int jj = 0; jj <= k; ++jj)
-        for (int l = 0; l < m; ++l) Qc[(size_t)jj * m + l] = Q[(size_t)l * m + jj];
-      ck(h, cudaMemcpyAsync(dQ, Qc.data(), sizeof(double2) * Qc.size(), cudaMemcpyHostToDevice, h->stream), "copy Q");
       ck(h, kry_update_basis(h, V, m, k + 1, n, dQ, tmp), "V Q");
-      ck(h, kry_axpby(h, d2(beta_k), tmp + (size_t)k * n, d2(sig_k), f, n), "f update");
+      k_f_update<<<1024, 256, 0, h->stream>>>(tmp + (size_t)k * n, f, n, RW.coef);
       ck(h, cudaMemcpyAsync(V, tmp, sizeof(double2) * (size_t)k * n, cudaMemcpyDeviceToDevice, h->stream), "copy V");
-      ck(h, cudaStreamSynchronize(h->stream), "sync");
-      for (int r = 0; r < m; ++r)
-        for (int c = 0; c < m; ++c)
-          if (r >= k || c >= k) H[(size_t)r * m + c] = 0.0;
       j0 = k;
     }
-    // eigenpairs: x_q = V y_q, lambda_q = (sigma theta - tau)/(theta - 1)
-    std::vector<cd> Yw((size_t)m * k);
-    for (int q = 0; q < k; ++q)
-      for (int l = 0; l < m; ++l) Yw[(size_t)q * m + l] = Y[(size_t)l * m + order[q]];
-    ck(h, cudaMemcpyAsync(dQ, Yw.data(), sizeof(double2) * Yw.size(), cudaMemcpyHostToDevice, h->stream), "copy Y");
+    // eigenpairs: x_q = V y_q (the wanted Ritz vectors are in Qc), lambda_q = (sigma theta - tau)/(theta - 1)
     double2* X = tmp;  // k vectors (tmp holds k + 1)
     ck(h, kry_update_basis(h, V, m, k, n, dQ, X), "V Y");
     for (int q = 0; q < k; ++q) {
-      const cd t = theta[order[q]];
+      const cd t = theta_w[q];
       const cd lam = (sigma * t - tau) / (t - 1.0);
       lambda[2 * q] = lam.real();
       lambda[2 * q + 1] = lam.imag();
