@@ -162,6 +162,24 @@ stab_status stab_eigs(stab_handle h, double sigma_re, double sigma_im, double ta
 /* Counters accumulated over the handle's lifetime. */
 stab_status stab_get_stats(stab_handle h, stab_stats* stats);
 
+/* The CGS2 step of stab_orthogonalize for callers that cannot allocate device
+ * memory (their device memory belongs to another framework's pool, or they run
+ * under a fixed device budget reserved up front), so they can neither call
+ * cudaMalloc nor create a handle.  The paper has no counterpart: this is a
+ * deployment variant.  No handle; no allocation of any kind: the reduction
+ * scratch is a file-scope device array of about 1.3 MB that every device
+ * loading the library keeps until exit.
+ *  V, w   : device complex128, V = k columns of n (column j at V + j*n), w updated in place.
+ *  hcoef  : host complex128 k (may be NULL);  norm: host (may be NULL).
+ *  stream : cudaStream_t or NULL; the call synchronises it.
+ * Limits: 0 <= k <= 128, 1 <= n <= 2^28; larger sizes return INVALID_ARG with
+ * a message in stab_last_error(NULL).  All calls share the scratch array, so
+ * calls whose GPU work overlaps race: serialise them.  The first call on a
+ * device looks up the array's device address (with that device current);
+ * make that first call before any stream capture. */
+stab_status stab_orthogonalize_noalloc(const void* V, int k, long long n, void* w, double* hcoef, double* norm,
+                                       void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -22,7 +22,7 @@ STATUS = {0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "CUDA", 4: "NOT_CONVERGED", 5:
 
 SYMBOLS = ["stab_default_opts", "stab_create", "stab_destroy", "stab_last_error", "stab_size", "stab_apply_J",
            "stab_last_eps", "stab_solve", "stab_precond_build", "stab_precond_apply", "stab_precond_block",
-           "stab_orthogonalize", "stab_eigs", "stab_get_stats"]
+           "stab_orthogonalize", "stab_eigs", "stab_get_stats", "stab_orthogonalize_noalloc"]
 
 
 class StabError(RuntimeError):
@@ -86,6 +86,7 @@ def load():
     L.stab_eigs.argtypes = [vp, d, d, d, d, i, i, d, vp, dp, vp, dp, ctypes.POINTER(ctypes.c_int),
                             ctypes.POINTER(Stats)]
     L.stab_get_stats.argtypes = [vp, ctypes.POINTER(Stats)]
+    L.stab_orthogonalize_noalloc.argtypes = [vp, i, ctypes.c_longlong, vp, dp, dp, vp]
     for name in SYMBOLS:
         if name not in ("stab_default_opts", "stab_destroy", "stab_last_error", "stab_size"):
             getattr(L, name).restype = ctypes.c_int
@@ -111,6 +112,18 @@ def _ptr(t) -> int:
     if hasattr(t, "data_ptr"):
         return t.data_ptr()
     return int(t)
+
+
+def orthogonalize_noalloc(V, k: int, n: int, w, stream=None):
+    """CGS2 of w against k columns of V without any device allocation (no handle)."""
+    L = load()
+    hc = np.zeros(2 * max(k, 1))
+    nrm = ctypes.c_double()
+    st = L.stab_orthogonalize_noalloc(_ptr(V), k, n, _ptr(w), hc.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                      ctypes.byref(nrm), None if stream is None else stream.cuda_stream)
+    if st != 0:
+        raise StabError(st, L.stab_last_error(None).decode())
+    return hc.view(np.complex128)[:k], nrm.value
 
 
 @dataclass

@@ -144,6 +144,9 @@ extern "C" void stab_destroy(stab_handle h) {
 
 extern "C" const char* stab_last_error(stab_handle h) { return h ? h->err.c_str() : g_create_err.c_str(); }
 
+// message for entry points that take no handle (reported by stab_last_error(NULL))
+void stab_set_global_error(const char* msg) { g_create_err = msg ? msg : ""; }
+
 extern "C" long long stab_size(stab_handle h) { return h ? h->n : 0; }
 
 extern "C" stab_status stab_apply_J(stab_handle h, const void* v, void* Jv, double shift_re, double shift_im) {

@@ -924,3 +924,11 @@ cudaError_t jv_apply(StabHandle* h, const double2* v, double2* out, double2 shif
   h->stats.jv_calls++;
   return cudaGetLastError();
 }
+
+// ||v||_2 on an explicit stream with caller-provided partials (nb blocks,
+// fixed by the caller so the summation order is reproducible).
+cudaError_t launch_norm2_stream(cudaStream_t st, const double2* v, long long n, double* partial, int nb, double* d_out) {
+  k_norm2_partial<<<nb, 256, 0, st>>>(v, n, partial);
+  k_norm2_final<<<1, 32, 0, st>>>(partial, nb, d_out, 1, 0.0, 0.0);
+  return cudaGetLastError();
+}

@@ -322,3 +322,24 @@ int kry_partial_elems(long long n, int k) {
   const int nb = red_blocks(n);
   return 2 * nb * (k > 0 ? k : 1) + (nb + 1) / 2 + 1;
 }
+
+// CGS2 on an explicit stream with caller-provided scratch (no handle):
+// partial needs red_blocks(n) * k complex, d_h 2k complex, norm_partial
+// ceil(n / 1024) (at most 1024) doubles.  The same classical Gram-Schmidt
+// applied twice as kry_cgs2, computed with the separate dot / update kernels.
+cudaError_t kry_cgs2_stream(cudaStream_t st, const double2* V, int k, long long n, double2* w, double2* d_h,
+                            double* d_norm, double2* partial, double* norm_partial, int norm_blocks) {
+  if (k > 0) {
+    const int nb = red_blocks(n);
+    for (int pass = 0; pass < 2; ++pass) {
+      double2* hp = d_h + (size_t)pass * k;
+      k_dot_partial<<<nb, kThreads, 0, st>>>(V, k, n, w, partial);
+      k_dot_final<<<k, 32, 0, st>>>(partial, nb, k, hp, 0);
+      k_gemv<<<grid_n(n), kThreads, k * sizeof(double2), st>>>(V, k, n, hp, w, -1.0);
+    }
+    k_axpby<<<1, 64, 0, st>>>(make_double2(1.0, 0.0), d_h + k, make_double2(1.0, 0.0), d_h, k);
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return launch_norm2_stream(st, w, n, norm_partial, norm_blocks, d_norm);
+}
