@@ -2,6 +2,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 
@@ -53,6 +54,8 @@ static void free_handle(stab_handle h) {
   cudaFree(h->d_pinv);
   cudaFree(h->d_pblk);
   cudaFree(h->d_coef);
+  cudaFree(h->d_coef_f);
+  cudaFree(h->d_btab_f);
   for (int a = 0; a < 3; ++a) {
     cudaFree(h->ax[a].tab[0]);
     cudaFree(h->d_dmat[a]);

@@ -184,6 +184,47 @@ __global__ void k_line_pass(const PassParams P) {
 }
 
 // ---------------------------------------------------------------------------
+// Conversions between double and FP32 (pairs) with integer operations only,
+// so that the FP32 remainder of the pointwise kernel spends no FP64-pipe
+// cycles on conversions.
+// ---------------------------------------------------------------------------
+struct ffn {
+  float hi, lo;
+};
+
+// Exact split of a double into an FP32 pair with integer operations only
+// (no FP64-pipe conversions): hi keeps the top 24 significant bits, lo the
+// next bits rounded to 24 (|d - hi - lo| <= 2^-47 |d|).  Values below 2^-74
+// keep hi only; values outside the FP32 range saturate.
+__device__ __forceinline__ ffn ff_split(double d) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+  const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+  const int e = (int)((b >> 52) & 0x7FF);
+  const int ef = e - 1023 + 127;
+  if (ef <= 0) return ffn{0.0f, 0.0f};
+  if (ef >= 255) return ffn{__uint_as_float(sign | 0x7F800000u), 0.0f};
+  const unsigned long long mant = b & 0xFFFFFFFFFFFFFull;
+  const float hi = __uint_as_float(sign | ((unsigned)ef << 23) | (unsigned)(mant >> 29));
+  float lo = 0.0f;
+  const unsigned mlo = (unsigned)(mant & 0x1FFFFFFFu);
+  if (mlo != 0u && e >= 949) {
+    lo = __uint2float_rn(mlo) * __uint_as_float((unsigned)(e - 948) << 23);
+    if (sign) lo = -lo;
+  }
+  return ffn{hi, lo};
+}
+// float -> double exactly, with integer operations
+__device__ __forceinline__ double f2d_exact(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned ex = (u >> 23) & 0xFF;
+  if (ex == 0) return 0.0;  // zero (FP32 denormals do not occur here)
+  const unsigned long long b = ((unsigned long long)(u & 0x80000000u) << 32) |
+                               ((unsigned long long)(ex - 127 + 1023) << 52) |
+                               ((unsigned long long)(u & 0x7FFFFFu) << 29);
+  return __longlong_as_double((long long)b);
+}
+
+// ---------------------------------------------------------------------------
 // Reductions: ||v||^2 in a fixed order (deterministic), then epsilon.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ double warp_sum(double x) {
@@ -242,6 +283,8 @@ struct PointParams {
   long long nbase;
   const double* eta_y;
   const double* eta_yy;
+  const double* eta_y_f;   // same values (read into FP32 by the remainder path)
+  const double* eta_yy_f;
   const unsigned char* bcflags;
   const double* eps;
   double2* out;
@@ -355,14 +398,21 @@ __global__ void k_coeffs(const PointParams P, double* coef) {
   for (int a = 0; a < D + 2; ++a) coef[((long long)j * (D + 2) + a) * NW + k] = res[a];
 }
 
+
+
+// Inputs: raw line-pass outputs (eta-derivatives in y); the coefficients have
+// the y metric folded in (k_coeffs_fold).  FP64 product for the tangent part;
+// the O(eps) remainder in FP32 from integer-split inputs and FP32 base tables,
+// so the two halves use different pipes.
 template <int D>
-__global__ void __launch_bounds__(128) k_point_fast(const PointParams P, const double* __restrict__ coef) {
+__global__ void __launch_bounds__(128) k_point_fast(const PointParams P, const double* __restrict__ coef,
+                                                   const float* __restrict__ btab_f) {
   constexpr int NW = pw::nw_inputs(D);
+  constexpr int o2 = (D + 3) + D * (D + 3), om = o2 + D * (D + 1);
   const double e = *P.eps;
   const bool visc = P.phys.visc;
   for (long long pt = (long long)blockIdx.x * blockDim.x + threadIdx.x; pt < P.npts; pt += (long long)gridDim.x * blockDim.x) {
     const int j = (int)((pt / P.nx) % P.ny);
-    const double ey = P.eta_y[j], eyy = P.eta_yy[j];
     const bool bc_row = (j == 0 || j == P.ny - 1);
     const unsigned fl = bc_row ? P.bcflags[(j == P.ny - 1 ? (long long)P.nx * P.nz : 0)] : 0u;
     const double* C = coef + (long long)j * (D + 2) * NW;
@@ -375,28 +425,17 @@ __global__ void __launch_bounds__(128) k_point_fast(const PointParams P, const d
       for (int f = 0; f < D + 2; ++f) w[f] = pick(P.v[(long long)f * P.npts + pt]);
       w[D + 2] = visc ? pick(S(P.s_Tw)) : 0.0;
 #pragma unroll
-      for (int ax = 0; ax < D; ++ax) {
-        const double sc = ax == 1 ? ey : 1.0;
+      for (int ax = 0; ax < D; ++ax)
 #pragma unroll
-        for (int f = 0; f < D + 3; ++f) w[D + 3 + ax * (D + 3) + f] = (f < D + 2 || visc) ? pick(S(P.s_d1[ax][f])) * sc : 0.0;
-      }
-      constexpr int o2 = (D + 3) + D * (D + 3), om = o2 + D * (D + 1);
+        for (int f = 0; f < D + 3; ++f) w[D + 3 + ax * (D + 3) + f] = (f < D + 2 || visc) ? pick(S(P.s_d1[ax][f])) : 0.0;
 #pragma unroll
       for (int ax = 0; ax < D; ++ax)
 #pragma unroll
-        for (int g = 0; g < D + 1; ++g) {
-          double v = 0.0;
-          if (visc) {
-            v = pick(S(P.s_d2[ax][g]));
-            if (ax == 1) v = fma(v, ey * ey, pick(S(P.s_d1[1][g < D ? 1 + g : D + 2])) * eyy);
-          }
-          w[o2 + ax * (D + 1) + g] = v;
-        }
+        for (int g = 0; g < D + 1; ++g) w[o2 + ax * (D + 1) + g] = visc ? pick(S(P.s_d2[ax][g])) : 0.0;
 #pragma unroll
       for (int a = 0; a < D; ++a)
 #pragma unroll
-        for (int c = 0; c < D; ++c)
-          w[om + a * D + c] = (visc && a != c) ? pick(S(P.s_mix[a][c])) * ((a == 1 || c == 1) ? ey : 1.0) : 0.0;
+        for (int c = 0; c < D; ++c) w[om + a * D + c] = (visc && a != c) ? pick(S(P.s_mix[a][c])) : 0.0;
       double res[D + 2];
 #pragma unroll
       for (int a = 0; a < D + 2; ++a) {
@@ -405,15 +444,26 @@ __global__ void __launch_bounds__(128) k_point_fast(const PointParams P, const d
         for (int q = 0; q < NW; ++q) acc = fma(__ldg(C + a * NW + q), w[q], acc);
         res[a] = acc;
       }
-      if (e != 0.0) {  // O(eps) remainder of the quotient, FP32
+      if (e != 0.0) {  // O(eps) remainder of the quotient, FP32, physical (metric-applied) inputs
+        const float ey = ff_split(P.eta_y[j]).hi, eyy = ff_split(P.eta_yy[j]).hi;
         pw::WIn<D, float> Wf;
 #pragma unroll
-        for (int q = 0; q < NW; ++q) set_input<D, float>(Wf, q, (float)w[q]);
-        auto B = [&](int slot) { return P.btab[(long long)slot * P.nbase + j]; };
-        pw::DN3 o[D + 2];
-        pw::rhs_num<D, pw::DN3>(P.phys, B, Wf, e, bc_row, fl, o);
+        for (int q = 0; q < NW; ++q) set_input<D, float>(Wf, q, ff_split(w[q]).hi);
 #pragma unroll
-        for (int a = 0; a < D + 2; ++a) res[a] += (double)o[a].w2;
+        for (int f = 0; f < D + 3; ++f) Wf.d1[1][f] *= ey;
+#pragma unroll
+        for (int g = 0; g < D + 1; ++g)
+          Wf.d2[1][g] = fmaf(Wf.d2[1][g], ey * ey, ff_split(w[D + 3 + (D + 3) + (g < D ? 1 + g : D + 2)]).hi * eyy);
+#pragma unroll
+        for (int a = 0; a < D; ++a)
+#pragma unroll
+          for (int c = 0; c < D; ++c)
+            if (a == 1 || c == 1) Wf.mix[a][c] *= ey;
+        auto Bf = [&](int slot) { return btab_f[(long long)slot * P.nbase + j]; };
+        pw::DN3 o[D + 2];
+        pw::rhs_num<D, pw::DN3>(P.phys, Bf, Wf, e, bc_row, fl, o);
+#pragma unroll
+        for (int a = 0; a < D + 2; ++a) res[a] += f2d_exact(o[a].w2);
       }
 #pragma unroll
       for (int a = 0; a < D + 2; ++a) {
@@ -425,6 +475,37 @@ __global__ void __launch_bounds__(128) k_point_fast(const PointParams P, const d
       }
     }
   }
+}
+
+// Fold the y metric into the per-row coefficients so that the pointwise kernel
+// can use the line passes' eta-derivatives directly:
+//   f_y = f_eta ey,  f_yy = f_etaeta ey^2 + f_eta eyy,  mixed with y: x ey.
+template <int D>
+__global__ void k_coeffs_fold(const double* coef, const double* eta_y, const double* eta_yy, int ny, double* out) {
+  constexpr int NW = pw::nw_inputs(D);
+  constexpr int o1 = D + 3, o2 = (D + 3) + D * (D + 3), om = o2 + D * (D + 1);
+  const int j = blockIdx.x, a = threadIdx.x;
+  if (j >= ny || a >= D + 2) return;
+  const double ey = eta_y[j], eyy = eta_yy[j];
+  const double* c = coef + ((long long)j * (D + 2) + a) * NW;
+  double f[NW];
+  for (int q = 0; q < NW; ++q) f[q] = c[q];
+  for (int fi = 0; fi < D + 3; ++fi) f[o1 + 1 * (D + 3) + fi] = c[o1 + 1 * (D + 3) + fi] * ey;
+  for (int g = 0; g < D + 1; ++g) {
+    f[o2 + 1 * (D + 1) + g] = c[o2 + 1 * (D + 1) + g] * ey * ey;
+    const int fi = g < D ? 1 + g : D + 2;
+    f[o1 + 1 * (D + 3) + fi] += c[o2 + 1 * (D + 1) + g] * eyy;
+  }
+  for (int i = 0; i < D; ++i)
+    for (int k = 0; k < D; ++k)
+      if (i != k && (i == 1 || k == 1)) f[om + i * D + k] = c[om + i * D + k] * ey;
+  double* o = out + ((long long)j * (D + 2) + a) * NW;
+  for (int q = 0; q < NW; ++q) o[q] = f[q];
+}
+
+__global__ void k_to_float_tab(const double* in, float* out, long long count) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (long long)gridDim.x * blockDim.x)
+    out[i] = (float)in[i];
 }
 
 // T's scaled difference split the same way: FP64 first order + FP32 rest
@@ -618,8 +699,10 @@ static cudaError_t run_pass(StabHandle* h, int axis, const PassParams& base_para
   P.h = A.h;
   P.tab[0] = A.tab[0];
   P.tab[1] = A.tab[1];
+
   P.K[0] = A.K[0];
   P.K[1] = A.K[1];
+
   P.stride = axis == 0 ? 1 : axis == 1 ? h->nx : (long long)h->nx * h->ny;
   P.nlines = h->npts / A.n;
   if (contiguous_lines >= 0) {  // lines stored back to back (line l at l * n), this axis's scheme
@@ -633,13 +716,14 @@ static cudaError_t run_pass(StabHandle* h, int axis, const PassParams& base_para
   P.c2[0] = (1.0 / 9.0) / (4.0 * A.h);
   P.c1[1] = (12.0 / 11.0) / (A.h * A.h);
   P.c2[1] = (3.0 / 11.0) / (4.0 * A.h * A.h);
+
   const int n = A.n;
   // chunks of 32 points (at most 64 per line: n <= 2048); lines per CTA so
   // that 8 planes of L x n doubles stay near 96 KB (two CTAs per SM)
   P.C = 32;
   P.nchunks = (n + P.C - 1) / P.C;
-  if (P.nchunks > 64 || n > 2048) return cudaErrorInvalidValue;
-  const long long LS = 33LL * P.nchunks + 1;
+  if (n > 2048) return cudaErrorInvalidValue;
+  const long long LS = (long long)(P.C + 1) * P.nchunks + 1;
   int L = (int)(98304 / (8 * 8 * LS));
   const int maxL = 1024 / (4 * P.nchunks);
   if (L > maxL) L = maxL;
@@ -734,6 +818,8 @@ static PointParams point_params(StabHandle* h, const double2* v) {
   P.nbase = h->nbase;
   P.eta_y = h->d_metric;
   P.eta_yy = h->d_metric + h->ny;
+  P.eta_y_f = P.eta_y;
+  P.eta_yy_f = P.eta_yy;
   P.bcflags = h->d_bcflags;
   P.eps = h->d_eps;
   P.phys = phys_of(h);
@@ -870,6 +956,13 @@ cudaError_t jv_setup(StabHandle* h, const double* q0_host) {
     if (D == 2) k_coeffs<2><<<h->ny, 32, 0, h->stream>>>(PP, h->d_coef);
     else k_coeffs<3><<<h->ny, 64, 0, h->stream>>>(PP, h->d_coef);
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    if ((err = cudaMalloc(&h->d_coef_f, (size_t)h->ny * (D + 2) * nw * sizeof(double))) != cudaSuccess) return err;
+    if (D == 2) k_coeffs_fold<2><<<h->ny, 32, 0, h->stream>>>(h->d_coef, h->d_metric, h->d_metric + h->ny, h->ny, h->d_coef_f);
+    else k_coeffs_fold<3><<<h->ny, 32, 0, h->stream>>>(h->d_coef, h->d_metric, h->d_metric + h->ny, h->ny, h->d_coef_f);
+    const long long nbt = (long long)bt_count(D) * h->nbase;
+    if ((err = cudaMalloc(&h->d_btab_f, nbt * sizeof(float))) != cudaSuccess) return err;
+    k_to_float_tab<<<64, 256, 0, h->stream>>>(h->d_btab, h->d_btab_f, nbt);
+    if ((err = cudaGetLastError()) != cudaSuccess) return err;
   }
   if ((err = cudaStreamSynchronize(h->stream)) != cudaSuccess) return err;
   cudaFree(bv);
@@ -915,8 +1008,8 @@ cudaError_t jv_apply(StabHandle* h, const double2* v, double2* out, double2 shif
   src[D + 2] = Tw;
   if ((err = run_derivatives(h, src)) != cudaSuccess) return err;
   if (fast) {
-    if (D == 2) k_point_fast<2><<<grid_for(h->npts, thr), thr, 0, h->stream>>>(P, h->d_coef);
-    else k_point_fast<3><<<grid_for(h->npts, thr), thr, 0, h->stream>>>(P, h->d_coef);
+    if (D == 2) k_point_fast<2><<<grid_for(h->npts, thr), thr, 0, h->stream>>>(P, h->d_coef_f, h->d_btab_f);
+    else k_point_fast<3><<<grid_for(h->npts, thr), thr, 0, h->stream>>>(P, h->d_coef_f, h->d_btab_f);
   } else {
     if (D == 2) k_point<2><<<grid_for(h->npts, thr), thr, 0, h->stream>>>(P);
     else k_point<3><<<grid_for(h->npts, thr), thr, 0, h->stream>>>(P);

@@ -213,7 +213,7 @@ __device__ __forceinline__ void rhs_num(const Phys& P, const BaseFn& B, const WI
 #pragma unroll
   for (int a = 0; a < D; ++a) u[a] = O::make(B(bt_val(D, 1 + a)), W.v[1 + a]);
   Num s = O::make(B(bt_val(D, D + 1)), W.v[D + 1]);
-  const double rho0 = B(bt_val(D, D + 3)), irho0 = B(bt_extra(D, X_IRHO)), ip0 = B(bt_extra(D, X_IP));
+  const auto rho0 = B(bt_val(D, D + 3)), irho0 = B(bt_extra(D, X_IRHO)), ip0 = B(bt_extra(D, X_IP));
   Num rho = make_rho(P.C, rho0, ip0, p, s, e);
   Num irho = rcp_t(rho, irho0, e);
   Num dp[D], ds[D], du[D][D];
@@ -233,14 +233,14 @@ __device__ __forceinline__ void rhs_num(const Phys& P, const BaseFn& B, const WI
 #pragma unroll
   for (int a = 0; a < D; ++a) vis[a] = O::zero();
   if (P.visc) {
-    const double T0 = B(bt_val(D, D + 2)), iT0 = B(bt_extra(D, X_IT));
+    const auto T0 = B(bt_val(D, D + 2)), iT0 = B(bt_extra(D, X_IT));
     Num T = O::make(T0, W.v[D + 2]);
     Num dT[D];
 #pragma unroll
     for (int a = 0; a < D; ++a) dT[a] = O::make(B(bt_d1(D, a, D + 2)), W.d1[a][D + 2]);
     // Sutherland: mu = (1+S)/Re T^{3/2}/(T+S);  dmu/dT = mu (3/(2T) - 1/(T+S))
     Num sqT = sqrt_t(T, B(bt_extra(D, X_SQT)), iT0, e);
-    const double iTS0 = B(bt_extra(D, X_ITS));
+    const auto iTS0 = B(bt_extra(D, X_ITS));
     Num rTS = rcp_t(add(T, P.S), iTS0, e);
     Num mu = ((1.0 + P.S) / P.Re) * mul(mul(T, sqT, e), rTS, e);
     Num dmu = mul(mu, 1.5 * rcp_t(T, iT0, e) - rTS, e);

@@ -107,7 +107,6 @@ int gmres(StabHandle* h, cd sigma, const double2* b, double2* x, int eps_mode, b
     std::fill(g.begin(), g.end(), cd(0.0));
     g[0] = beta;
     int jend = 0;
-    bool done = false;
     for (int j = 0; j < m; ++j) {
       double2* Vj = W.V + (size_t)j * n;
       double2* Vn = W.V + (size_t)(j + 1) * n;
@@ -140,7 +139,7 @@ int gmres(StabHandle* h, cd sigma, const double2* b, double2* x, int eps_mode, b
       ++total;
       jend = j + 1;
       const double res = std::abs(g[j + 1]);
-      if (res <= tol * bnorm || wn == 0.0) { done = true; break; }
+      if (res <= tol * bnorm || wn == 0.0) break;
       ck(h, kry_scale(h, Vn, n, W.dnorm, nullptr), "scale");
     }
     // y = R^{-1} g (upper triangular jend x jend)
@@ -157,7 +156,6 @@ int gmres(StabHandle* h, cd sigma, const double2* b, double2* x, int eps_mode, b
     ck(h, kry_axpby(h, make_double2(1.0, 0.0), b, make_double2(-1.0, 0.0), W.r, n), "axpby");
     ck(h, launch_norm2(h, W.r, n, W.dnorm, 1), "norm");
     beta = read_scalar(h, W.dnorm);
-    (void)done;
     if (!(beta < INFINITY)) fail(h, STAB_ERR_NUMERIC, "GMRES: non-finite residual");
     if (beta <= tol * bnorm) { *converged = true; break; }
   }
