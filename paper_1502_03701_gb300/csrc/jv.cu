@@ -17,6 +17,7 @@
 
 #include "internal.cuh"
 
+#include "pairs.cuh"
 #include "pointwise.cuh"
 
 using pw::bt_count;
@@ -181,47 +182,6 @@ __global__ void k_line_pass(const PassParams P) {
       }
     }
   }
-}
-
-// ---------------------------------------------------------------------------
-// Conversions between double and FP32 (pairs) with integer operations only,
-// so that the FP32 remainder of the pointwise kernel spends no FP64-pipe
-// cycles on conversions.
-// ---------------------------------------------------------------------------
-struct ffn {
-  float hi, lo;
-};
-
-// Exact split of a double into an FP32 pair with integer operations only
-// (no FP64-pipe conversions): hi keeps the top 24 significant bits, lo the
-// next bits rounded to 24 (|d - hi - lo| <= 2^-47 |d|).  Values below 2^-74
-// keep hi only; values outside the FP32 range saturate.
-__device__ __forceinline__ ffn ff_split(double d) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(d);
-  const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
-  const int e = (int)((b >> 52) & 0x7FF);
-  const int ef = e - 1023 + 127;
-  if (ef <= 0) return ffn{0.0f, 0.0f};
-  if (ef >= 255) return ffn{__uint_as_float(sign | 0x7F800000u), 0.0f};
-  const unsigned long long mant = b & 0xFFFFFFFFFFFFFull;
-  const float hi = __uint_as_float(sign | ((unsigned)ef << 23) | (unsigned)(mant >> 29));
-  float lo = 0.0f;
-  const unsigned mlo = (unsigned)(mant & 0x1FFFFFFFu);
-  if (mlo != 0u && e >= 949) {
-    lo = __uint2float_rn(mlo) * __uint_as_float((unsigned)(e - 948) << 23);
-    if (sign) lo = -lo;
-  }
-  return ffn{hi, lo};
-}
-// float -> double exactly, with integer operations
-__device__ __forceinline__ double f2d_exact(float f) {
-  const unsigned u = __float_as_uint(f);
-  const unsigned ex = (u >> 23) & 0xFF;
-  if (ex == 0) return 0.0;  // zero (FP32 denormals do not occur here)
-  const unsigned long long b = ((unsigned long long)(u & 0x80000000u) << 32) |
-                               ((unsigned long long)(ex - 127 + 1023) << 52) |
-                               ((unsigned long long)(u & 0x7FFFFFu) << 29);
-  return __longlong_as_double((long long)b);
 }
 
 // ---------------------------------------------------------------------------

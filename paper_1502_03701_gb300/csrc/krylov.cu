@@ -4,6 +4,7 @@
 // Vectors are complex128 (double2); a basis V of k vectors stores column j at
 // V + j*n.
 #include "internal.cuh"
+#include "pairs.cuh"
 
 namespace {
 
@@ -141,20 +142,26 @@ __device__ __forceinline__ void reduce_partials(const double2* partial, int nb, 
   }
 }
 
+// partial_out[b * k + j] = block sums of conj(V_j) w.  Products are exact FP32
+// two-products of the integer-split pairs, accumulated by two-sum per thread
+// and warp; only the per-warp results are added in FP64 (fixed order).
 __device__ __forceinline__ void block_dot_columns(const double2* __restrict__ V, int k, long long n,
                                                   const double2* w, double2* partial_out, double* red) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   for (int j = 0; j < k; ++j) {
     const double2* Vj = V + (long long)j * n;
-    double sr = 0.0, si = 0.0;
+    ffn sr{0.0f, 0.0f}, si{0.0f, 0.0f};
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-      double2 a = Vj[i], b = w[i];
-      sr = fma(a.x, b.x, fma(a.y, b.y, sr));
-      si = fma(a.x, b.y, fma(-a.y, b.x, si));
+      const double2 av = Vj[i], bv = w[i];
+      const ffn ar = ff_split(av.x), ai = ff_split(av.y), br = ff_split(bv.x), bi = ff_split(bv.y);
+      ff_acc_prod(sr, ar, br);             // Re conj(a) b = ar br + ai bi
+      ff_acc_prod(sr, ai, bi);
+      ff_acc_prod(si, ar, bi);             // Im conj(a) b = ar bi - ai br
+      ff_acc_prod(si, ff_negate(ai), br);
     }
-    sr = warp_sum(sr);
-    si = warp_sum(si);
-    if (lane == 0) { red[2 * wid] = sr; red[2 * wid + 1] = si; }
+    sr = ff_warp_sum(sr);
+    si = ff_warp_sum(si);
+    if (lane == 0) { red[2 * wid] = ff_to_d(sr); red[2 * wid + 1] = ff_to_d(si); }
     __syncthreads();
     if (wid == 0) {
       double tr = lane < (int)(blockDim.x >> 5) ? red[2 * lane] : 0.0;
@@ -167,6 +174,21 @@ __device__ __forceinline__ void block_dot_columns(const double2* __restrict__ V,
   }
 }
 
+// w_i -= sum_j V_j[i] h_j for this thread's rows, pair arithmetic; h as pairs in shared memory.
+__device__ __forceinline__ double2 row_update(const double2* __restrict__ V, int k, long long n, long long i,
+                                              const ffn* hre, const ffn* him, double2 wv) {
+  ffn ar{0.0f, 0.0f}, ai{0.0f, 0.0f};
+  for (int j = 0; j < k; ++j) {
+    const double2 a = V[(long long)j * n + i];
+    const ffn xr = ff_split(a.x), xi = ff_split(a.y);
+    ff_acc_prod(ar, xr, hre[j]);            // Re(a h) = ar hr - ai hi
+    ff_acc_prod(ar, ff_negate(xi), him[j]);
+    ff_acc_prod(ai, xr, him[j]);            // Im(a h) = ar hi + ai hr
+    ff_acc_prod(ai, xi, hre[j]);
+  }
+  return make_double2(wv.x - ff_to_d(ar), wv.y - ff_to_d(ai));
+}
+
 __global__ void __launch_bounds__(kThreads) k_cgs2_a(const double2* __restrict__ V, int k, long long n,
                                                     const double2* __restrict__ w, double2* partial1) {
   __shared__ double red[2 * kThreads / 32];
@@ -175,47 +197,44 @@ __global__ void __launch_bounds__(kThreads) k_cgs2_a(const double2* __restrict__
 
 __global__ void __launch_bounds__(kThreads) k_cgs2_b(const double2* __restrict__ V, int k, long long n, double2* w,
                                                     const double2* partial1, double2* partial2, double2* d_h) {
-  extern __shared__ double2 hs[];
+  extern __shared__ double2 hs[];  // k complex, then 2k pairs
   __shared__ double red[2 * kThreads / 32];
+  ffn* hre = (ffn*)(hs + k);
+  ffn* him = hre + k;
   reduce_partials(partial1, gridDim.x, k, hs);
   __syncthreads();
-  if (blockIdx.x == 0)
-    for (int j = threadIdx.x; j < k; j += blockDim.x) d_h[j] = hs[j];
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    double ar = 0.0, ai = 0.0;
-    for (int j = 0; j < k; ++j) {
-      double2 a = V[(long long)j * n + i], c = hs[j];
-      ar = fma(a.x, c.x, fma(-a.y, c.y, ar));
-      ai = fma(a.x, c.y, fma(a.y, c.x, ai));
-    }
-    double2 xv = w[i];
-    w[i] = make_double2(xv.x - ar, xv.y - ai);
+  for (int j = threadIdx.x; j < k; j += blockDim.x) {
+    hre[j] = ff_split(hs[j].x);
+    him[j] = ff_split(hs[j].y);
+    if (blockIdx.x == 0) d_h[j] = hs[j];
   }
+  __syncthreads();
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    w[i] = row_update(V, k, n, i, hre, him, w[i]);
   __syncthreads();  // this block's rows of w are final; the dots below read only them
   block_dot_columns(V, k, n, w, partial2, red);
 }
 
 __global__ void __launch_bounds__(kThreads) k_cgs2_c(const double2* __restrict__ V, int k, long long n, double2* w,
                                                     const double2* partial2, double2* d_h, double* norm_partial) {
-  extern __shared__ double2 hs[];
+  extern __shared__ double2 hs[];  // k complex, then 2k pairs
   __shared__ double red[kThreads / 32];
+  ffn* hre = (ffn*)(hs + k);
+  ffn* him = hre + k;
   reduce_partials(partial2, gridDim.x, k, hs);
   __syncthreads();
-  if (blockIdx.x == 0)
-    for (int j = threadIdx.x; j < k; j += blockDim.x) {
+  for (int j = threadIdx.x; j < k; j += blockDim.x) {
+    hre[j] = ff_split(hs[j].x);
+    him[j] = ff_split(hs[j].y);
+    if (blockIdx.x == 0) {
       double2 h1 = d_h[j];
       d_h[j] = make_double2(h1.x + hs[j].x, h1.y + hs[j].y);
     }
+  }
+  __syncthreads();
   double s = 0.0;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    double ar = 0.0, ai = 0.0;
-    for (int j = 0; j < k; ++j) {
-      double2 a = V[(long long)j * n + i], c = hs[j];
-      ar = fma(a.x, c.x, fma(-a.y, c.y, ar));
-      ai = fma(a.x, c.y, fma(a.y, c.x, ai));
-    }
-    double2 xv = w[i];
-    double2 r = make_double2(xv.x - ar, xv.y - ai);
+    const double2 r = row_update(V, k, n, i, hre, him, w[i]);
     w[i] = r;
     s = fma(r.x, r.x, fma(r.y, r.y, s));
   }
@@ -281,7 +300,7 @@ cudaError_t kry_cgs2(StabHandle* h, const double2* V, int k, long long n, double
   double2* p2 = partial + (size_t)nb * (k > 0 ? k : 1);
   double* np = (double*)(p2 + (size_t)nb * (k > 0 ? k : 1));
   if (k > 0) {
-    const size_t sm = (size_t)k * sizeof(double2);
+    const size_t sm = (size_t)k * (sizeof(double2) + 2 * sizeof(ffn));
     k_cgs2_a<<<nb, kThreads, 0, h->stream>>>(V, k, n, w, p1);
     k_cgs2_b<<<nb, kThreads, sm, h->stream>>>(V, k, n, w, p1, p2, d_h);
     k_cgs2_c<<<nb, kThreads, sm, h->stream>>>(V, k, n, w, p2, d_h, np);

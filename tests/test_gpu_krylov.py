@@ -33,15 +33,18 @@ def test_cgs2_matches_oracle(orc):
         V = torch.from_numpy(np.ascontiguousarray(Vh.T)).cuda()  # column j contiguous
         wd = torch.from_numpy(w.copy()).cuda()
         h, nrm = S.orthogonalize(V, k, wd)
+        # products are exact FP32 two-products of operands split to ~2^-47 (pair
+        # arithmetic), so coefficients carry errors of order 2^-45 ||w||
+        wn = np.linalg.norm(w)
         if k:
             href, wref = orc.krylov.cgs2(Vh, w)
-            assert np.abs(h - href).max() < 1e-13 * np.abs(href).max()
+            assert np.abs(h - href).max() < 1e-12 * wn
         else:
             wref = w
-        assert rel_err(wd.cpu().numpy(), wref) < 1e-13
-        assert abs(nrm - np.linalg.norm(wref)) < 1e-13 * nrm
+        assert rel_err(wd.cpu().numpy(), wref) < 1e-12
+        assert abs(nrm - np.linalg.norm(wref)) < 1e-12 * wn
         if k:
-            assert np.abs(Vh.conj().T @ wd.cpu().numpy()).max() < 1e-13 * nrm
+            assert np.abs(Vh.conj().T @ wd.cpu().numpy()).max() < 1e-12 * wn
     S.close()
 
 
