@@ -79,6 +79,17 @@ class ClockSampler:
             self.proc = None
         return self
 
+    def wait_first_sample(self, limit_s: float = 5.0):
+        """Block until nvidia-smi has written its first row (its start-up takes a moment)."""
+        t0 = time.time()
+        while self.proc is not None and time.time() - t0 < limit_s:
+            try:
+                if os.path.getsize(self.path) > 0:
+                    return
+            except OSError:
+                pass
+            time.sleep(0.02)
+
     def __exit__(self, *a):
         if self.proc is not None:
             self.proc.terminate()
@@ -246,6 +257,62 @@ def gmres_throughput(args, Stab, torch, q0, g, f):
             "precond_build_s": t_build, "sigma": sigma, "tile": [8, 8], "block": 256, "precond": "FP32 inverses"}
 
 
+# Algorithmic FP64 flops of the compact line pass per real output value (FMA = 2):
+#   first derivative  : stencil a(f+1 - f-1) + b(f+2 - f-2)        5  + tridiagonal solve 5 = 10
+#   second derivative : stencil a(f+1 - 2f + f-1) + b(f+2 - 2f + f-2) 9 + tridiagonal solve 5 = 14
+# (solve: forward elimination one FMA, back substitution one FMA and one multiply).
+LINE_FLOP_D1, LINE_FLOP_D2 = 10, 14
+FP64_PEAK_GFLOPS = 1250.0  # GB300 FP64 (non-tensor) nominal; 1.2 TFLOP/s measured by an FMA microbenchmark
+# DRAM bytes per launch of the line pass from ncu (dram__bytes_read.sum + dram__bytes_write.sum) on the
+# 512 x 1024 layer: y pass 42.5 + 12.6 MB, x pass 58.8 + 29.2 MB; scaled by grid points to the run's grid.
+LINE_TRAFFIC_512x1024 = {"line_y": (42.548480 + 12.626944) * 1e6, "line_x": (58.759680 + 29.232896) * 1e6}
+
+
+def line_pass_flops(g, visc: bool) -> dict:
+    """Per-launch algorithmic FP64 flops of the y, z and x line passes."""
+    d = g.dim
+    nf1 = d + 3 if visc else d + 2          # p, u_i, s (and T) first derivatives
+    nf2 = d + 1 if visc else 0              # u_i and T second derivatives
+    base = 2 * (nf1 * LINE_FLOP_D1 + nf2 * LINE_FLOP_D2) * g.npts  # x2: real and imaginary parts
+    mix_x = (2 if d == 2 else 4) if visc else 0
+    mix_z = 2 if (d == 3 and visc) else 0
+    out = {"line_y": base, "line_x": base + 2 * mix_x * LINE_FLOP_D1 * g.npts}
+    if d == 3:
+        out["line_z"] = base + 2 * mix_z * LINE_FLOP_D1 * g.npts
+    return out
+
+
+def jv_roofline(g, f, phases: dict, step_s: float, hbm, tangent_s: float) -> dict:
+    """Roofline of the dominant kernel of the timed J v steps (per-phase CUDA events)."""
+    ms = {k: v[0] for k, v in phases.items() if k != "dropped"}
+    cnt = {k: v[1] for k, v in phases.items() if k != "dropped"}
+    total = sum(ms.values())
+    line_keys = [k for k in ("line_y", "line_z", "line_x") if cnt.get(k)]
+    line_ms = sum(ms[k] for k in line_keys)
+    launches = sum(cnt[k] for k in line_keys)
+    flops = line_pass_flops(g, f.Re > 0)
+    line_flops = sum(flops[k] * cnt[k] for k in line_keys)
+    avg_s = line_ms / 1e3 / launches
+    achieved = line_flops / launches / avg_s / 1e9
+    scale = g.npts / (512 * 1024)
+    traffic = None
+    if g.dim == 2 and f.Re > 0 and LINE_TRAFFIC_512x1024:
+        traffic = sum(LINE_TRAFFIC_512x1024[k] * cnt[k] for k in ("line_y", "line_x")) / launches * scale
+    share = {k: (ms[k] / total if total else None) for k in ms if cnt[k]}
+    op_achieved = g.n * JV_BYTES_PER_DOF / step_s / 1e9
+    return {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
+            "frac": achieved / FP64_PEAK_GFLOPS, "traffic": traffic,
+            "kernel": "k_line_pass (compact-derivative line sweeps; y and x launches per J v)",
+            "flop_per_launch": line_flops / launches, "launch_ms": avg_s * 1e3, "launches": launches,
+            "peak_source": "FP64 nominal 1.25 TFLOP/s (recipe table); FMA microbenchmark measures 1.2",
+            "traffic_source": "ncu dram bytes of the 512x1024 launches scaled by grid points" if traffic else None,
+            "phase_share": share,
+            "operator": {"bound": "hbm", "achieved": op_achieved, "peak": hbm, "unit": "GB/s",
+                         "frac": (op_achieved / hbm) if hbm else None, "bytes_per_step": g.n * JV_BYTES_PER_DOF,
+                         "step_ms": step_s * 1e3, "tangent_step_ms": tangent_s * 1e3,
+                         "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}}
+
+
 def _time_jv(S, v, out, steps, flush, stream, torch):
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     for s in range(steps):
@@ -286,40 +353,35 @@ def run_ours(args):
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
         return float(t.item())
 
-    # J v roofline on the Ma 0.3 layer (both forms), measured live
+    # J v on the Ma 0.3 layer (both forms)
     g, f, q0 = _layer(args.nx, args.ny, 0.3)
     n = g.n
     Sj = Stab(q0, g, f.Ma, f.Re, f.Pr)
     St = Stab(q0, g, f.Ma, f.Re, f.Pr, eps_mode=2)
     v = torch.from_numpy(si.random_complex(11 + rank, n)).cuda()
     out = torch.empty_like(v)
-    for _ in range(3):
+    for _ in range(max(args.warmup, 3)):
         Sj.apply_J(v, out)
         St.apply_J(v, out)
-    jv_eps = _time_jv(Sj, v, out, 20, flush, stream, torch)
     jv_tan = _time_jv(St, v, out, 20, flush, stream, torch)
     bytes_jv = n * JV_BYTES_PER_DOF
-    jv_eps_t = statistics.mean(jv_eps)
-    achieved = bytes_jv / jv_eps_t / 1e9
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                "frac": (achieved / hbm) if hbm else None, "traffic": None,
-                "kernel": "J v operator, cancellation-free epsilon-quotient (one stab_apply_J call)",
-                "bytes_per_launch": bytes_jv, "launch_ms": jv_eps_t * 1e3,
-                "tangent_launch_ms": statistics.mean(jv_tan) * 1e3,
-                "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)",
-                "note": "FP64-pipe bound on GB300 (FP64 1.2 TFLOP/s measured); see profiles/"}
 
     if args.workload == "jv":
         sampler = ClockSampler(local, 50)
         barrier()
         with sampler:
+            sampler.wait_first_sample()
+            Sj.timing(True)
             steps_t = _time_jv(Sj, v, out, args.steps, flush, stream, torch)
+            phases = Sj.timing_read()
+            Sj.timing(False)
             barrier()
         clock_sum = sampler.summary()
         t_max = max_over_ranks(sum(steps_t))
         value = world * args.steps * bytes_jv / t_max / 1e9
         unit = "GB/s"
         ms_step = t_max / args.steps * 1e3
+        roofline = jv_roofline(g, f, phases, sum(steps_t) / args.steps, hbm, statistics.mean(jv_tan))
         config = {"workload": f"jv_mixing_layer_{g.nx}x{g.ny}", "nx": g.nx, "ny": g.ny, "Ma": f.Ma, "Re": f.Re,
                   "eps_mode": "cancellation-free epsilon-quotient", "l2": "flushed between timed steps",
                   "parallelism": f"replicas{world}"}
@@ -344,6 +406,11 @@ def run_ours(args):
         if args.gmres_restarts > 0:
             extra["gmres_256x512"] = gmres_throughput(args, Stab, torch, q0, g, f)
     else:
+        # roofline of the J v kernels from a short phase-timed sample (the solves below are host-driven)
+        Sj.timing(True)
+        sample_t = _time_jv(Sj, v, out, 50, flush, stream, torch)
+        roofline = jv_roofline(g, f, Sj.timing_read(), statistics.mean(sample_t), hbm, statistics.mean(jv_tan))
+        Sj.timing(False)
         sweep = (0.3, 0.6, 0.9)
         handles = []
         for Ma in sweep:
@@ -446,7 +513,7 @@ def run_ours(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="jv", choices=["eigs", "jv"])

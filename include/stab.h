@@ -180,6 +180,34 @@ stab_status stab_get_stats(stab_handle h, stab_stats* stats);
 stab_status stab_orthogonalize_noalloc(const void* V, int k, long long n, void* w, double* hcoef, double* norm,
                                        void* stream);
 
+/* Per-kernel device timing (measurement aid; the paper has no counterpart).
+ * While enabled, every entry point records a CUDA event pair on the handle's
+ * stream around each of the phases below, so a phase's time is its kernels'
+ * device time plus the launch gaps inside it.  Work replayed from a captured
+ * CUDA graph (the GMRES cycles of stab_solve and stab_eigs) is not split into
+ * phases.  Phases: */
+typedef enum {
+  STAB_PHASE_EPS = 0,        /* ||v|| reduction that fixes epsilon (Eq. frechet) */
+  STAB_PHASE_TEMPERATURE = 1,/* temperature perturbation field for the heat flux */
+  STAB_PHASE_LINE_Y = 2,     /* compact-derivative line pass along y (first, second derivatives) */
+  STAB_PHASE_LINE_Z = 3,     /* line pass along z (3-D only), with the yz mixed derivatives */
+  STAB_PHASE_LINE_X = 4,     /* line pass along x, with the xy (xz) mixed derivatives */
+  STAB_PHASE_POINTWISE = 5,  /* pointwise assembly of J v - shift v */
+  STAB_PHASE_CGS2 = 6,       /* one CGS2 orthogonalisation (all its kernels) */
+  STAB_PHASE_PRECOND_APPLY = 7, /* one block-Jacobi apply */
+  STAB_PHASE_COUNT = 8
+} stab_phase;
+
+/* enable = 1 starts recording (discarding anything recorded), 0 stops.  At
+ * most 65536 phase intervals are kept; later ones are counted as dropped. */
+stab_status stab_timing(stab_handle h, int enable);
+
+/* Synchronise the stream and return, per phase, the summed milliseconds
+ * (ms[STAB_PHASE_COUNT]) and the number of intervals (count[STAB_PHASE_COUNT]);
+ * either may be NULL.  dropped (may be NULL) receives the intervals not kept.
+ * The record is cleared; recording continues if enabled. */
+stab_status stab_timing_read(stab_handle h, double* ms, long long* count, long long* dropped);
+
 #ifdef __cplusplus
 }
 #endif

@@ -22,7 +22,11 @@ STATUS = {0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "CUDA", 4: "NOT_CONVERGED", 5:
 
 SYMBOLS = ["stab_default_opts", "stab_create", "stab_destroy", "stab_last_error", "stab_size", "stab_apply_J",
            "stab_last_eps", "stab_solve", "stab_precond_build", "stab_precond_apply", "stab_precond_block",
-           "stab_orthogonalize", "stab_eigs", "stab_get_stats", "stab_orthogonalize_noalloc"]
+           "stab_orthogonalize", "stab_eigs", "stab_get_stats", "stab_orthogonalize_noalloc", "stab_timing",
+           "stab_timing_read"]
+
+# stab_phase, in enum order
+PHASES = ["eps", "temperature", "line_y", "line_z", "line_x", "pointwise", "cgs2", "precond_apply"]
 
 
 class StabError(RuntimeError):
@@ -87,6 +91,8 @@ def load():
                             ctypes.POINTER(Stats)]
     L.stab_get_stats.argtypes = [vp, ctypes.POINTER(Stats)]
     L.stab_orthogonalize_noalloc.argtypes = [vp, i, ctypes.c_longlong, vp, dp, dp, vp]
+    L.stab_timing.argtypes = [vp, i]
+    L.stab_timing_read.argtypes = [vp, dp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]
     for name in SYMBOLS:
         if name not in ("stab_default_opts", "stab_destroy", "stab_last_error", "stab_size"):
             getattr(L, name).restype = ctypes.c_int
@@ -237,6 +243,20 @@ class Stab:
                                            _ptr(vecs), res.ctypes.data_as(dp), ctypes.byref(nconv),
                                            ctypes.byref(stats)), allow=(4,))
         return EigResult(lam.view(np.complex128), res, nconv.value, st, stats.as_dict())
+
+    def timing(self, enable: bool = True):
+        """Start (discarding earlier records) or stop per-phase event timing."""
+        self._check(self._L.stab_timing(self._h, int(bool(enable))))
+
+    def timing_read(self) -> dict:
+        """{phase: (summed ms, intervals)} since the last read, plus 'dropped'."""
+        ms = (ctypes.c_double * len(PHASES))()
+        cnt = (ctypes.c_longlong * len(PHASES))()
+        dropped = ctypes.c_longlong()
+        self._check(self._L.stab_timing_read(self._h, ms, cnt, ctypes.byref(dropped)))
+        out = {p: (ms[i], cnt[i]) for i, p in enumerate(PHASES)}
+        out["dropped"] = dropped.value
+        return out
 
     def stats(self) -> dict:
         s = Stats()

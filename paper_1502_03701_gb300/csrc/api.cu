@@ -60,6 +60,7 @@ static void free_handle(stab_handle h) {
     cudaFree(h->ax[a].tab[0]);
     cudaFree(h->d_dmat[a]);
   }
+  for (cudaEvent_t e : h->timer.ev) cudaEventDestroy(e);
   delete h;
 }
 
@@ -167,6 +168,59 @@ extern "C" stab_status stab_last_eps(stab_handle h, double* eps) {
   if (!h || !eps) return STAB_ERR_INVALID_ARG;
   STAB_CUDA(h, cudaMemcpyAsync(eps, h->d_eps, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
   STAB_CUDA(h, cudaStreamSynchronize(h->stream));
+  return STAB_OK;
+}
+
+// ---------------------------------------------------------------------------
+// phase timing
+int phase_begin(StabHandle* h, int phase) {
+  PhaseTimer& T = h->timer;
+  if (!T.on) return -1;
+  if (T.used >= PhaseTimer::kMax) { ++T.dropped; return -1; }
+  const int slot = T.used;
+  while ((int)T.ev.size() < 2 * (slot + 1)) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) { ++T.dropped; return -1; }
+    T.ev.push_back(e);
+  }
+  if ((int)T.phase.size() <= slot) T.phase.resize(slot + 1);
+  T.phase[slot] = phase;
+  if (cudaEventRecord(T.ev[2 * slot], h->stream) != cudaSuccess) { ++T.dropped; return -1; }
+  T.used = slot + 1;
+  return slot;
+}
+
+void phase_end(StabHandle* h, int slot) {
+  if (slot < 0) return;
+  cudaEventRecord(h->timer.ev[2 * slot + 1], h->stream);
+}
+
+extern "C" stab_status stab_timing(stab_handle h, int enable) {
+  if (!h) return STAB_ERR_INVALID_ARG;
+  STAB_CUDA(h, cudaStreamSynchronize(h->stream));
+  h->timer.on = enable != 0;
+  h->timer.used = 0;
+  h->timer.dropped = 0;
+  return STAB_OK;
+}
+
+extern "C" stab_status stab_timing_read(stab_handle h, double* ms, long long* count, long long* dropped) {
+  if (!h) return STAB_ERR_INVALID_ARG;
+  STAB_CUDA(h, cudaStreamSynchronize(h->stream));
+  double acc[STAB_PHASE_COUNT] = {0};
+  long long cnt[STAB_PHASE_COUNT] = {0};
+  PhaseTimer& T = h->timer;
+  for (int i = 0; i < T.used; ++i) {
+    float t = 0.f;
+    STAB_CUDA(h, cudaEventElapsedTime(&t, T.ev[2 * i], T.ev[2 * i + 1]));
+    const int p = T.phase[i];
+    if (p >= 0 && p < STAB_PHASE_COUNT) { acc[p] += t; cnt[p]++; }
+  }
+  if (ms) for (int p = 0; p < STAB_PHASE_COUNT; ++p) ms[p] = acc[p];
+  if (count) for (int p = 0; p < STAB_PHASE_COUNT; ++p) count[p] = cnt[p];
+  if (dropped) *dropped = T.dropped;
+  T.used = 0;
+  T.dropped = 0;
   return STAB_OK;
 }
 

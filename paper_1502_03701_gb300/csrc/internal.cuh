@@ -44,6 +44,17 @@ struct Slots {
   int count;
 };
 
+// Event pairs around library phases (stab_timing); recording is a no-op
+// unless enabled.
+struct PhaseTimer {
+  static constexpr int kMax = 65536;
+  bool on = false;
+  std::vector<cudaEvent_t> ev;       // pool, reused after every read
+  std::vector<int> phase;            // per interval
+  int used = 0;                      // intervals recorded since the last read
+  long long dropped = 0;
+};
+
 struct StabHandle {
   // problem
   int dim, nx, ny, nz, nv;
@@ -88,8 +99,14 @@ struct StabHandle {
   bool force_dn_path;    // use the full FP64 difference-number pointwise kernel
   // statistics
   stab_stats stats;
+  PhaseTimer timer;
   std::string err;
 };
+
+// api.cu: phase timing.  phase_begin returns the interval's slot (or -1 when
+// not recording); phase_end records its closing event.
+int phase_begin(StabHandle* h, int phase);
+void phase_end(StabHandle* h, int slot);
 
 // jv.cu
 cudaError_t jv_setup(StabHandle* h, const double* q0_host);

@@ -732,7 +732,9 @@ static cudaError_t run_derivatives(StabHandle* h, const double2* const* src) {
   {  // y
     std::vector<LineJob> jobs;
     field_jobs(1, jobs);
+    const int ts = phase_begin(h, STAB_PHASE_LINE_Y);
     if ((err = run_pass(h, 1, P, jobs)) != cudaSuccess) return err;
+    phase_end(h, ts);
   }
   if (D == 3) {  // z, plus d/dz of d/dy v and d/dy w
     std::vector<LineJob> jobs;
@@ -741,7 +743,9 @@ static cudaError_t run_derivatives(StabHandle* h, const double2* const* src) {
       jobs.push_back(LineJob{slot(S.d1[1][2]), slot(S.mix[2][1]), nullptr});
       jobs.push_back(LineJob{slot(S.d1[1][3]), slot(S.mix[1][2]), nullptr});
     }
+    const int ts = phase_begin(h, STAB_PHASE_LINE_Z);
     if ((err = run_pass(h, 2, P, jobs)) != cudaSuccess) return err;
+    phase_end(h, ts);
   }
   {  // x, plus d/dx of d/dy u, d/dy v (and d/dz u, d/dz w)
     std::vector<LineJob> jobs;
@@ -754,7 +758,9 @@ static cudaError_t run_derivatives(StabHandle* h, const double2* const* src) {
         jobs.push_back(LineJob{slot(S.d1[2][1]), slot(S.mix[2][0]), nullptr});
       }
     }
+    const int ts = phase_begin(h, STAB_PHASE_LINE_X);
     if ((err = run_pass(h, 0, P, jobs)) != cudaSuccess) return err;
+    phase_end(h, ts);
   }
   return cudaSuccess;
 }
@@ -949,7 +955,9 @@ cudaError_t jv_apply(StabHandle* h, const double2* v, double2* out, double2 shif
   if (eps_mode == 2) {
     if (h->last_eps_mode != 2) k_set_scalar<<<1, 1, 0, h->stream>>>(h->d_eps, 0.0);
   } else {
+    const int ts = phase_begin(h, STAB_PHASE_EPS);
     if ((err = launch_norm2(h, v, h->n, h->d_eps, 2)) != cudaSuccess) return err;
+    phase_end(h, ts);
   }
   h->last_eps_mode = eps_mode;
   PointParams P = point_params(h, v);
@@ -959,14 +967,17 @@ cudaError_t jv_apply(StabHandle* h, const double2* v, double2* out, double2 shif
   const int thr = 128;
   const bool fast = h->homog && h->d_coef && !h->force_dn_path;
   if (h->visc) {
+    const int ts = phase_begin(h, STAB_PHASE_TEMPERATURE);
     if (fast) k_temperature_fast<<<grid_for(h->npts, thr), thr, 0, h->stream>>>(P, Tw);
     else k_temperature<<<grid_for(h->npts, thr), thr, 0, h->stream>>>(P, Tw);
+    phase_end(h, ts);
   }
   const int D = h->dim;
   const double2* src[6];
   for (int f = 0; f < D + 2; ++f) src[f] = v + (long long)f * h->npts;
   src[D + 2] = Tw;
   if ((err = run_derivatives(h, src)) != cudaSuccess) return err;
+  const int tp = phase_begin(h, STAB_PHASE_POINTWISE);
   if (fast) {
     if (D == 2) k_point_fast<2><<<grid_for(h->npts, thr), thr, 0, h->stream>>>(P, h->d_coef_f, h->d_btab_f);
     else k_point_fast<3><<<grid_for(h->npts, thr), thr, 0, h->stream>>>(P, h->d_coef_f, h->d_btab_f);
@@ -974,6 +985,7 @@ cudaError_t jv_apply(StabHandle* h, const double2* v, double2* out, double2 shif
     if (D == 2) k_point<2><<<grid_for(h->npts, thr), thr, 0, h->stream>>>(P);
     else k_point<3><<<grid_for(h->npts, thr), thr, 0, h->stream>>>(P);
   }
+  phase_end(h, tp);
   h->stats.jv_calls++;
   return cudaGetLastError();
 }

@@ -299,15 +299,20 @@ cudaError_t kry_cgs2(StabHandle* h, const double2* V, int k, long long n, double
   double2* p1 = partial;
   double2* p2 = partial + (size_t)nb * (k > 0 ? k : 1);
   double* np = (double*)(p2 + (size_t)nb * (k > 0 ? k : 1));
+  const int ts = phase_begin(h, STAB_PHASE_CGS2);
+  cudaError_t e;
   if (k > 0) {
     const size_t sm = (size_t)k * (sizeof(double2) + 2 * sizeof(ffn));
     k_cgs2_a<<<nb, kThreads, 0, h->stream>>>(V, k, n, w, p1);
     k_cgs2_b<<<nb, kThreads, sm, h->stream>>>(V, k, n, w, p1, p2, d_h);
     k_cgs2_c<<<nb, kThreads, sm, h->stream>>>(V, k, n, w, p2, d_h, np);
     k_norm_final<<<1, 32, 0, h->stream>>>(np, nb, d_norm);
-    return cudaGetLastError();
+    e = cudaGetLastError();
+  } else {
+    e = launch_norm2(h, w, n, d_norm, 1);
   }
-  return launch_norm2(h, w, n, d_norm, 1);
+  phase_end(h, ts);
+  return e;
 }
 
 cudaError_t kry_scale(StabHandle* h, double2* x, long long n, const double* d_norm, double2* out) {

@@ -409,8 +409,10 @@ cudaError_t pc_apply(StabHandle* h, const double2* q, double2* z) {
   P.q = q; P.z = z; P.inv = h->d_pinv;
   P.nx = h->nx; P.ny = h->ny; P.tx = g.tx; P.ty = g.ty; P.tz = g.tz; P.ntx = g.ntx; P.nty = g.nty;
   P.ntpts = g.ntpts; P.bsz = g.bsz; P.npts = h->npts;
+  const int ts = phase_begin(h, STAB_PHASE_PRECOND_APPLY);
   if (h->pprec == 64) k_apply<double><<<(unsigned)g.ntiles, 256, g.bsz * sizeof(double2), h->stream>>>(P);
   else k_apply<float><<<(unsigned)g.ntiles, 256, g.bsz * sizeof(float2), h->stream>>>(P);
+  phase_end(h, ts);
   return cudaGetLastError();
 }
 

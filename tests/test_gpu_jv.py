@@ -131,3 +131,28 @@ def test_jv_full_size_3d_128x256x64(orc):
     ref = orc.core.jv(orc.Problem.from_inputs(g, f), q0, v, "tangent")
     assert max_rel_err(got, ref) < TOL
     assert rel_err(got, ref) < TOL
+
+
+def test_phase_timing_records_every_launch_group():
+    """stab_timing: one interval per phase per J v, none when disabled."""
+    import torch
+    from paper_1502_03701_gb300 import Stab
+    for g, f, expect_z in ((si.Grid(2, 32, 64, 1, si.LX_04, -15, 15), si.Flow(0.3, 1000.0), 0),
+                           (si.Grid(3, 12, 16, 8, si.LX_04, -15, 15, si.LX_04), si.Flow(0.5, 800.0), 1)):
+        q0 = si.tanh_base_flow(g, f)
+        S = Stab(q0, g, f.Ma, f.Re, f.Pr)
+        v = torch.from_numpy(si.random_complex(7, g.n)).cuda()
+        out = torch.empty_like(v)
+        S.timing(True)
+        for _ in range(5):
+            S.apply_J(v, out)
+        ph = S.timing_read()
+        for k in ("eps", "temperature", "line_y", "line_x", "pointwise"):
+            assert ph[k][1] == 5 and ph[k][0] > 0, k
+        assert ph["line_z"][1] == 5 * expect_z
+        assert ph["cgs2"][1] == 0 and ph["dropped"] == 0
+        S.timing(False)
+        S.apply_J(v, out)
+        ph = S.timing_read()
+        assert all(ph[k][1] == 0 for k in ph if k != "dropped")
+        S.close()
