@@ -23,7 +23,8 @@ STATUS = {0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "CUDA", 4: "NOT_CONVERGED", 5:
 SYMBOLS = ["stab_default_opts", "stab_create", "stab_destroy", "stab_last_error", "stab_size", "stab_apply_J",
            "stab_last_eps", "stab_solve", "stab_precond_build", "stab_precond_apply", "stab_precond_block",
            "stab_orthogonalize", "stab_eigs", "stab_get_stats", "stab_orthogonalize_noalloc", "stab_timing",
-           "stab_timing_read"]
+           "stab_timing_read", "stab_autotune", "stab_autotune_save", "stab_autotune_load",
+           "stab_set_line_config"]
 
 # stab_phase, in enum order
 PHASES = ["eps", "temperature", "line_y", "line_z", "line_x", "pointwise", "cgs2", "precond_apply"]
@@ -92,6 +93,10 @@ def load():
     L.stab_get_stats.argtypes = [vp, ctypes.POINTER(Stats)]
     L.stab_orthogonalize_noalloc.argtypes = [vp, i, ctypes.c_longlong, vp, dp, dp, vp]
     L.stab_timing.argtypes = [vp, i]
+    L.stab_autotune.argtypes = [vp, i, ctypes.POINTER(ctypes.c_int), dp]
+    L.stab_autotune_save.argtypes = [ctypes.c_char_p]
+    L.stab_set_line_config.argtypes = [vp, i, i, i]
+    L.stab_autotune_load.argtypes = [ctypes.c_char_p]
     L.stab_timing_read.argtypes = [vp, dp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]
     for name in SYMBOLS:
         if name not in ("stab_default_opts", "stab_destroy", "stab_last_error", "stab_size"):
@@ -244,6 +249,17 @@ class Stab:
                                            ctypes.byref(stats)), allow=(4,))
         return EigResult(lam.view(np.complex128), res, nconv.value, st, stats.as_dict())
 
+    def autotune(self, force: bool = False) -> dict:
+        """Tune the line-pass launch shape per axis; {axis: (C, L, ms)} (ms -1: from the cache)."""
+        cfg = (ctypes.c_int * 6)()
+        ms = (ctypes.c_double * 3)()
+        self._check(self._L.stab_autotune(self._h, int(bool(force)), cfg, ms))
+        return {ax: (cfg[2 * a], cfg[2 * a + 1], ms[a]) for a, ax in enumerate("xyz") if cfg[2 * a] > 0}
+
+    def set_line_config(self, axis: int, C: int, L: int):
+        """Pin the line-pass shape of an axis (0 x, 1 y, 2 z); (0, 0) restores the default."""
+        self._check(self._L.stab_set_line_config(self._h, axis, C, L))
+
     def timing(self, enable: bool = True):
         """Start (discarding earlier records) or stop per-phase event timing."""
         self._check(self._L.stab_timing(self._h, int(bool(enable))))
@@ -262,3 +278,13 @@ class Stab:
         s = Stats()
         self._check(self._L.stab_get_stats(self._h, ctypes.byref(s)))
         return s.as_dict()
+
+
+def autotune_save(path: str) -> int:
+    """Write the process-wide line-pass tuning cache; returns the entry count."""
+    return load().stab_autotune_save(path.encode())
+
+
+def autotune_load(path: str) -> int:
+    """Read a tuning cache written by autotune_save; returns the entry count (-1: unreadable)."""
+    return load().stab_autotune_load(path.encode())

@@ -61,6 +61,8 @@ static void free_handle(stab_handle h) {
     cudaFree(h->d_dmat[a]);
   }
   for (cudaEvent_t e : h->timer.ev) cudaEventDestroy(e);
+  if (h->gm_exec) cudaGraphExecDestroy(h->gm_exec);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   delete h;
 }
 
@@ -136,6 +138,7 @@ extern "C" stab_status stab_create(stab_handle* out, const double* base_flow, in
     free_handle(h);
     return st;
   }
+  jv_tune_apply_cached(h);
   *out = h;
   return STAB_OK;
 }
@@ -175,7 +178,7 @@ extern "C" stab_status stab_last_eps(stab_handle h, double* eps) {
 // phase timing
 int phase_begin(StabHandle* h, int phase) {
   PhaseTimer& T = h->timer;
-  if (!T.on) return -1;
+  if (!T.on || h->capturing) return -1;
   if (T.used >= PhaseTimer::kMax) { ++T.dropped; return -1; }
   const int slot = T.used;
   while ((int)T.ev.size() < 2 * (slot + 1)) {
@@ -223,6 +226,38 @@ extern "C" stab_status stab_timing_read(stab_handle h, double* ms, long long* co
   T.dropped = 0;
   return STAB_OK;
 }
+
+extern "C" stab_status stab_autotune(stab_handle h, int force, int* cfg, double* ms) {
+  if (!h) return STAB_ERR_INVALID_ARG;
+  double t[3] = {0.0, 0.0, 0.0};
+  STAB_CUDA(h, jv_autotune(h, force, t));
+  if (cfg)
+    for (int a = 0; a < 3; ++a) {
+      cfg[2 * a] = a < h->dim ? h->line_cfg[a].C : 0;
+      cfg[2 * a + 1] = a < h->dim ? h->line_cfg[a].L : 0;
+    }
+  if (ms)
+    for (int a = 0; a < 3; ++a) ms[a] = a < h->dim ? t[a] : 0.0;
+  return STAB_OK;
+}
+
+extern "C" stab_status stab_set_line_config(stab_handle h, int axis, int C, int L) {
+  if (!h) return STAB_ERR_INVALID_ARG;
+  if (axis < 0 || axis >= h->dim) { h->err = "stab_set_line_config: bad axis"; return STAB_ERR_INVALID_ARG; }
+  if (C == 0 && L == 0) { h->line_cfg[axis] = LineCfg{}; return STAB_OK; }
+  const int n = h->ax[axis].n;
+  const long long LS = n + (n >> 5) + 1;
+  const int nch = (C > 0) ? (n + C - 1) / C : 0;
+  if ((C != 16 && C != 32 && C != 64) || L < 1 || L > 32 || 4 * nch * L > 1024 || 64 * LS * L > 200 * 1024) {
+    h->err = "stab_set_line_config: C must be 16, 32 or 64 and L in 1..32 within 1024 threads and 200 KB";
+    return STAB_ERR_INVALID_ARG;
+  }
+  h->line_cfg[axis] = LineCfg{C, L};
+  return STAB_OK;
+}
+
+extern "C" int stab_autotune_save(const char* path) { return path ? jv_tune_save(path) : -1; }
+extern "C" int stab_autotune_load(const char* path) { return path ? jv_tune_load(path) : -1; }
 
 extern "C" stab_status stab_get_stats(stab_handle h, stab_stats* s) {
   if (!h || !s) return STAB_ERR_INVALID_ARG;

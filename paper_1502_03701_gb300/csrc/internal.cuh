@@ -44,6 +44,26 @@ struct Slots {
   int count;
 };
 
+// What a captured GMRES cycle graph depends on (replayed while unchanged).
+struct GmGraphKey {
+  bool valid = false;
+  double sigma_re = 0, sigma_im = 0;
+  int eps_mode = -1, m = 0, pc = 0, pprec = 0;
+  const void* ws = nullptr;
+  const void* pinv = nullptr;
+  long long n = 0;
+  bool operator==(const GmGraphKey& o) const {
+    return valid && o.valid && sigma_re == o.sigma_re && sigma_im == o.sigma_im && eps_mode == o.eps_mode &&
+           m == o.m && pc == o.pc && pprec == o.pprec && ws == o.ws && pinv == o.pinv && n == o.n;
+  }
+};
+
+// Launch shape of the compact-derivative line pass along one axis: C points
+// per sweep chunk, L lines per CTA (0: built-in default).
+struct LineCfg {
+  int C = 0, L = 0;
+};
+
 // Event pairs around library phases (stab_timing); recording is a no-op
 // unless enabled.
 struct PhaseTimer {
@@ -100,6 +120,15 @@ struct StabHandle {
   // statistics
   stab_stats stats;
   PhaseTimer timer;
+  LineCfg line_cfg[3];  // per axis, from stab_autotune
+  // graph capture of the GMRES cycle (solver.cu): while gate is set, the
+  // gated kernels launched by jv_apply, pc_apply, kry_cgs2 and kry_scale
+  // return at once when *gate != 0 (the cycle has converged)
+  const int* gate = nullptr;
+  bool capturing = false;
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t gm_exec = nullptr;
+  GmGraphKey gm_key;
   std::string err;
 };
 
@@ -112,13 +141,18 @@ void phase_end(StabHandle* h, int slot);
 cudaError_t jv_setup(StabHandle* h, const double* q0_host);
 cudaError_t jv_apply(StabHandle* h, const double2* v, double2* out, double2 shift, int eps_mode);
 cudaError_t launch_norm2(StabHandle* h, const double2* v, long long n, double* d_out, int mode);
+cudaError_t jv_autotune(StabHandle* h, int force, double* ms_out);
+int jv_tune_save(const char* path);
+int jv_tune_load(const char* path);
+void jv_tune_apply_cached(StabHandle* h);
 cudaError_t jv_derivative_matrices(StabHandle* h, int axis, double2* work, double2* out1, double2* out2);
 
 // krylov.cu
 cudaError_t kry_dot(StabHandle* h, const double2* V, int k, long long n, const double2* w, double2* d_h,
                     double2* partial, int accumulate);
 cudaError_t kry_gemv_sub(StabHandle* h, const double2* V, int k, long long n, const double2* d_h, double2* w);
-cudaError_t kry_gemv_add(StabHandle* h, const double2* V, int k, long long n, const double2* d_y, double2* x);
+cudaError_t kry_gemv_add(StabHandle* h, const double2* V, int k, long long n, const double2* d_y, double2* x,
+                         const int* kdev = nullptr);
 cudaError_t kry_cgs2(StabHandle* h, const double2* V, int k, long long n, double2* w, double2* d_h2k, double* d_norm,
                      double2* partial);
 cudaError_t kry_scale(StabHandle* h, double2* x, long long n, const double* d_norm, double2* out_or_null);

@@ -12,8 +12,12 @@
 //   4. pointwise assembly of [N(q0 + eps v) - N(q0)]/eps in
 //      difference-number arithmetic, minus shift * v.
 // With eps = 0 the same arithmetic yields the exact tangent J(q0) v.
+#include <algorithm>
 #include <cfloat>
 #include <cmath>
+#include <cstdio>
+#include <map>
+#include <mutex>
 
 #include "internal.cuh"
 
@@ -43,11 +47,13 @@ struct PassParams {
   long long nlines;
   long long stride;
   int L, C, nchunks;
+  int LS;  // padded shared-memory line stride in doubles, n + n/32 + 1
   int periodic;
   double c1[2], c2[2];  // interior stencil weights per kind
   double h;
   const double* tab[2];
   int K[2];
+  const int* gate;  // when set and nonzero the launch does nothing (graph-captured GMRES after convergence)
 };
 
 __device__ __forceinline__ long long line_base(const PassParams& P, long long l) {
@@ -90,14 +96,17 @@ __device__ __forceinline__ double stencil_rhs(const PassParams& P, const double*
   return fma(P.c1[1], f(tp1) - 2.0 * f0 + f(tm1), P.c2[1] * (f(tp2) - 2.0 * f0 + f(tm2)));
 }
 
+constexpr long long kLineSmemMax = 200 * 1024;  // dynamic shared memory opt-in of k_line_pass
+
 // Shared memory (doubles): R[kind][comp][lt][LS], then F[comp][lt][LS]
 // aliased by G[kind][comp][lt][LS] once R is complete; LS = padded line
 // stride (33 doubles per 32-point chunk, plus one).
 __global__ void k_line_pass(const PassParams P) {
+  if (P.gate && *P.gate) return;
   extern __shared__ double sm[];
   const LineJob J = P.job[blockIdx.y];
   const int n = P.n, L = P.L;
-  const int LS = 33 * P.nchunks + 1;
+  const int LS = P.LS;
   const size_t plane = (size_t)L * LS;  // one (kind, comp) or (comp) plane
   double* R = sm;                      // 4 planes
   double* F = sm + 4 * plane;          // 2 planes
@@ -192,7 +201,8 @@ __device__ __forceinline__ double warp_sum(double x) {
   return x;
 }
 
-__global__ void k_norm2_partial(const double2* __restrict__ v, long long n, double* partial) {
+__global__ void k_norm2_partial(const double2* __restrict__ v, long long n, double* partial, const int* gate) {
+  if (gate && *gate) return;
   double s = 0.0;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     double2 z = v[i];
@@ -210,7 +220,9 @@ __global__ void k_norm2_partial(const double2* __restrict__ v, long long n, doub
 }
 
 // mode 0: out = sum;  mode 1: out = sqrt(sum);  mode 2: epsilon from ||v||
-__global__ void k_norm2_final(const double* partial, int nb, double* out, int mode, double q0norm, double fixed_eps) {
+__global__ void k_norm2_final(const double* partial, int nb, double* out, int mode, double q0norm, double fixed_eps,
+                              const int* gate) {
+  if (gate && *gate) return;
   double s = 0.0;
   for (int i = threadIdx.x; i < nb; i += 32) s += partial[i];
   s = warp_sum(s);
@@ -250,9 +262,11 @@ struct PointParams {
   double2* out;
   double2 shift;
   pw::Phys phys;
+  const int* gate;  // as PassParams::gate
 };
 
 __global__ void k_temperature(const PointParams P, double2* Tw) {
+  if (P.gate && *P.gate) return;
   const int D = P.nz > 1 ? 3 : 2;
   const double e = *P.eps;
   for (long long pt = (long long)blockIdx.x * blockDim.x + threadIdx.x; pt < P.npts; pt += (long long)gridDim.x * blockDim.x) {
@@ -269,6 +283,7 @@ __global__ void k_temperature(const PointParams P, double2* Tw) {
 
 template <int D>
 __global__ void __launch_bounds__(128) k_point(const PointParams P) {
+  if (P.gate && *P.gate) return;
   const double e = *P.eps;
   const bool visc = P.phys.visc;
   for (long long pt = (long long)blockIdx.x * blockDim.x + threadIdx.x; pt < P.npts; pt += (long long)gridDim.x * blockDim.x) {
@@ -367,6 +382,7 @@ __global__ void k_coeffs(const PointParams P, double* coef) {
 template <int D>
 __global__ void __launch_bounds__(128) k_point_fast(const PointParams P, const double* __restrict__ coef,
                                                    const float* __restrict__ btab_f) {
+  if (P.gate && *P.gate) return;
   constexpr int NW = pw::nw_inputs(D);
   constexpr int o2 = (D + 3) + D * (D + 3), om = o2 + D * (D + 1);
   const double e = *P.eps;
@@ -470,6 +486,7 @@ __global__ void k_to_float_tab(const double* in, float* out, long long count) {
 
 // T's scaled difference split the same way: FP64 first order + FP32 rest
 __global__ void k_temperature_fast(const PointParams P, double2* Tw) {
+  if (P.gate && *P.gate) return;
   const int D = P.nz > 1 ? 3 : 2;
   const double e = *P.eps;
   const float ef = (float)e;
@@ -678,26 +695,33 @@ static cudaError_t run_pass(StabHandle* h, int axis, const PassParams& base_para
   P.c2[1] = (3.0 / 11.0) / (4.0 * A.h * A.h);
 
   const int n = A.n;
-  // chunks of 32 points (at most 64 per line: n <= 2048); lines per CTA so
-  // that 8 planes of L x n doubles stay near 96 KB (two CTAs per SM)
-  P.C = 32;
-  P.nchunks = (n + P.C - 1) / P.C;
   if (n > 2048) return cudaErrorInvalidValue;
-  const long long LS = (long long)(P.C + 1) * P.nchunks + 1;
-  int L = (int)(98304 / (8 * 8 * LS));
-  const int maxL = 1024 / (4 * P.nchunks);
-  if (L > maxL) L = maxL;
-  if (L > 32) L = 32;
+  // launch shape: C points per sweep chunk, L lines per CTA.  Either tuned
+  // (stab_autotune) or by default chunks of 32 and L such that 8 planes of
+  // L x n doubles stay near 96 KB (two CTAs per SM), lowered on small grids
+  // so that the CTAs cover the SMs (but at least a warp of sweep threads).
+  const LineCfg cfg = contiguous_lines >= 0 ? LineCfg{} : h->line_cfg[axis];
+  P.C = cfg.C > 0 ? cfg.C : 32;
+  P.nchunks = (n + P.C - 1) / P.C;
+  if (4 * P.nchunks > 1024) return cudaErrorInvalidValue;
+  P.LS = n + (n >> 5) + 1;
+  const long long LS = P.LS;
+  const int maxL = std::min<long long>(std::min(1024 / (4 * P.nchunks), 32), kLineSmemMax / (8 * 8 * LS));
+  if (maxL < 1) return cudaErrorInvalidValue;
+  int L;
+  if (cfg.L > 0) {
+    L = std::min(cfg.L, maxL);
+  } else {
+    L = std::min<long long>(maxL, 98304 / (8 * 8 * LS));
+    const long long fill = (P.nlines * (long long)jobs.size() + 2 * 152 - 1) / (2 * 152);
+    const int Lwarp = (32 + 4 * P.nchunks - 1) / (4 * P.nchunks);
+    if (L > fill) L = (int)std::min<long long>(maxL, std::max<long long>(fill, Lwarp));
+  }
   if (L < 1) L = 1;
   P.L = L;
   int threads = 4 * L * P.nchunks;
   threads = ((threads + 31) / 32) * 32;
   size_t smem = (size_t)8 * LS * L * sizeof(double);
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaFuncSetAttribute(k_line_pass, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    attr_set = true;
-  }
   for (size_t j0 = 0; j0 < jobs.size(); j0 += STAB_MAX_JOBS) {
     P.njobs = (int)std::min<size_t>(STAB_MAX_JOBS, jobs.size() - j0);
     for (int q = 0; q < P.njobs; ++q) P.job[q] = jobs[j0 + q];
@@ -707,66 +731,212 @@ static cudaError_t run_pass(StabHandle* h, int axis, const PassParams& base_para
   return cudaGetLastError();
 }
 
-// all derivative passes for field sources src[f] (f = 0..D+2)
-static cudaError_t run_derivatives(StabHandle* h, const double2* const* src) {
+// jobs of the line pass along axis ax for field sources src[f] (f = 0..D+2):
+// first (and second) derivatives of every field, plus the mixed derivatives
+// formed from y derivatives (z pass: d/dz of d/dy v, w; x pass: d/dx of d/dy
+// u, v and, in 3-D, of d/dz u, w)
+static void axis_jobs(StabHandle* h, int ax, const double2* const* src, std::vector<LineJob>& jobs) {
   const int D = h->dim;
   const Slots& S = h->slots;
   double2* sc = h->d_scratch;
   auto slot = [&](int s) -> double2* { return s >= 0 ? sc + (long long)s * h->npts : nullptr; };
-  PassParams P{};
   const int nf = h->visc ? D + 3 : D + 2;
-  auto field_jobs = [&](int ax, std::vector<LineJob>& jobs) {
-    for (int f = 0; f < nf; ++f) {
-      LineJob J;
-      J.in = src[f];
-      J.out1 = slot(S.d1[ax][f]);
-      J.out2 = nullptr;
-      if (h->visc) {
-        if (f >= 1 && f <= D) J.out2 = slot(S.d2[ax][f - 1]);
-        if (f == D + 2) J.out2 = slot(S.d2[ax][D]);
-      }
-      jobs.push_back(J);
-    }
-  };
-  cudaError_t err;
-  {  // y
-    std::vector<LineJob> jobs;
-    field_jobs(1, jobs);
-    const int ts = phase_begin(h, STAB_PHASE_LINE_Y);
-    if ((err = run_pass(h, 1, P, jobs)) != cudaSuccess) return err;
-    phase_end(h, ts);
-  }
-  if (D == 3) {  // z, plus d/dz of d/dy v and d/dy w
-    std::vector<LineJob> jobs;
-    field_jobs(2, jobs);
+  for (int f = 0; f < nf; ++f) {
+    LineJob J;
+    J.in = src[f];
+    J.out1 = slot(S.d1[ax][f]);
+    J.out2 = nullptr;
     if (h->visc) {
-      jobs.push_back(LineJob{slot(S.d1[1][2]), slot(S.mix[2][1]), nullptr});
-      jobs.push_back(LineJob{slot(S.d1[1][3]), slot(S.mix[1][2]), nullptr});
+      if (f >= 1 && f <= D) J.out2 = slot(S.d2[ax][f - 1]);
+      if (f == D + 2) J.out2 = slot(S.d2[ax][D]);
     }
-    const int ts = phase_begin(h, STAB_PHASE_LINE_Z);
-    if ((err = run_pass(h, 2, P, jobs)) != cudaSuccess) return err;
-    phase_end(h, ts);
+    jobs.push_back(J);
   }
-  {  // x, plus d/dx of d/dy u, d/dy v (and d/dz u, d/dz w)
-    std::vector<LineJob> jobs;
-    field_jobs(0, jobs);
-    if (h->visc) {
-      jobs.push_back(LineJob{slot(S.d1[1][2]), slot(S.mix[0][1]), nullptr});
-      jobs.push_back(LineJob{slot(S.d1[1][1]), slot(S.mix[1][0]), nullptr});
-      if (D == 3) {
-        jobs.push_back(LineJob{slot(S.d1[2][3]), slot(S.mix[0][2]), nullptr});
-        jobs.push_back(LineJob{slot(S.d1[2][1]), slot(S.mix[2][0]), nullptr});
-      }
+  if (!h->visc) return;
+  if (ax == 2) {
+    jobs.push_back(LineJob{slot(S.d1[1][2]), slot(S.mix[2][1]), nullptr});
+    jobs.push_back(LineJob{slot(S.d1[1][3]), slot(S.mix[1][2]), nullptr});
+  } else if (ax == 0) {
+    jobs.push_back(LineJob{slot(S.d1[1][2]), slot(S.mix[0][1]), nullptr});
+    jobs.push_back(LineJob{slot(S.d1[1][1]), slot(S.mix[1][0]), nullptr});
+    if (D == 3) {
+      jobs.push_back(LineJob{slot(S.d1[2][3]), slot(S.mix[0][2]), nullptr});
+      jobs.push_back(LineJob{slot(S.d1[2][1]), slot(S.mix[2][0]), nullptr});
     }
-    const int ts = phase_begin(h, STAB_PHASE_LINE_X);
-    if ((err = run_pass(h, 0, P, jobs)) != cudaSuccess) return err;
+  }
+}
+
+// all derivative passes for field sources src[f] (f = 0..D+2): y, then z,
+// then x (the mixed derivatives need the y and z passes)
+static cudaError_t run_derivatives(StabHandle* h, const double2* const* src) {
+  PassParams P{};
+  P.gate = h->gate;
+  static const int order[3] = {1, 2, 0};
+  static const int phase[3] = {STAB_PHASE_LINE_Y, STAB_PHASE_LINE_Z, STAB_PHASE_LINE_X};
+  for (int q = 0; q < 3; ++q) {
+    const int ax = order[q];
+    if (ax >= h->dim) continue;
+    std::vector<LineJob> jobs;
+    axis_jobs(h, ax, src, jobs);
+    const int ts = phase_begin(h, phase[q]);
+    cudaError_t err = run_pass(h, ax, P, jobs);
+    if (err != cudaSuccess) return err;
     phase_end(h, ts);
   }
   return cudaSuccess;
 }
 
+// ---------------------------------------------------------------------------
+// Autotuner of the line-pass launch shape (C, L) per axis: every admissible
+// candidate is timed with CUDA events on this handle's jobs, the fastest is
+// kept in the handle and in a process-wide cache keyed by device, line length,
+// line count, job count and boundary type.  C changes where the sweeps'
+// warm-up starts, so results may differ at the rounding level between shapes;
+// L does not change any result.
+// ---------------------------------------------------------------------------
+namespace {
+struct TuneKey {
+  int dev, n, njobs, periodic;
+  long long nlines;
+  bool operator<(const TuneKey& o) const {
+    if (dev != o.dev) return dev < o.dev;
+    if (n != o.n) return n < o.n;
+    if (nlines != o.nlines) return nlines < o.nlines;
+    if (njobs != o.njobs) return njobs < o.njobs;
+    return periodic < o.periodic;
+  }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, LineCfg> g_tune;
+}  // namespace
+
+static TuneKey tune_key(StabHandle* h, int ax, int njobs) {
+  TuneKey k;
+  cudaGetDevice(&k.dev);
+  k.n = h->ax[ax].n;
+  k.nlines = h->npts / h->ax[ax].n;
+  k.njobs = njobs;
+  k.periodic = h->ax[ax].periodic;
+  return k;
+}
+
+cudaError_t jv_autotune(StabHandle* h, int force, double* ms_out) {
+  const int D = h->dim;
+  double2* tmp = nullptr;
+  cudaError_t err = cudaSuccess;
+  for (int ax = 0; ax < D && err == cudaSuccess; ++ax) {
+    std::vector<LineJob> jobs;
+    const double2* src[6];
+    if (!tmp) {
+      if ((err = cudaMalloc(&tmp, (size_t)h->n * sizeof(double2))) != cudaSuccess) break;
+      if ((err = cudaMemsetAsync(tmp, 0, (size_t)h->n * sizeof(double2), h->stream)) != cudaSuccess) break;
+    }
+    for (int f = 0; f < D + 2; ++f) src[f] = tmp + (long long)f * h->npts;
+    src[D + 2] = h->d_scratch + (long long)h->slots.Tw * h->npts;
+    axis_jobs(h, ax, src, jobs);
+    const TuneKey key = tune_key(h, ax, (int)jobs.size());
+    if (!force) {
+      std::lock_guard<std::mutex> lk(g_tune_mu);
+      auto it = g_tune.find(key);
+      if (it != g_tune.end()) {
+        h->line_cfg[ax] = it->second;
+        if (ms_out) ms_out[ax] = -1.0;
+        continue;
+      }
+    }
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    PassParams P{};
+    LineCfg best{};
+    double best_ms = 1e300;
+    const int n = h->ax[ax].n;
+    for (int C : {16, 32, 64}) {
+      if (C > 16 && C >= 2 * n) continue;
+      for (int L : {1, 2, 4, 8, 16, 32}) {
+        const int nch = (n + C - 1) / C;
+        const long long LS = n + (n >> 5) + 1;
+        if (4 * nch * L > 1024 || 8 * 8 * LS * L > kLineSmemMax) continue;
+        h->line_cfg[ax] = LineCfg{C, L};
+        if ((err = run_pass(h, ax, P, jobs)) != cudaSuccess) break;  // warm-up
+        float t[5];
+        for (int r = 0; r < 5 && err == cudaSuccess; ++r) {
+          cudaEventRecord(e0, h->stream);
+          err = run_pass(h, ax, P, jobs);
+          cudaEventRecord(e1, h->stream);
+          cudaEventSynchronize(e1);
+          cudaEventElapsedTime(&t[r], e0, e1);
+        }
+        if (err != cudaSuccess) break;
+        std::sort(t, t + 5);
+        if (t[2] < best_ms) { best_ms = t[2]; best = LineCfg{C, L}; }
+      }
+      if (err != cudaSuccess) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (err != cudaSuccess) break;
+    h->line_cfg[ax] = best;
+    if (ms_out) ms_out[ax] = best_ms;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune[key] = best;
+  }
+  if (tmp) {
+    cudaStreamSynchronize(h->stream);
+    cudaFree(tmp);
+  }
+  if (err != cudaSuccess) for (int ax = 0; ax < 3; ++ax) h->line_cfg[ax] = LineCfg{};
+  return err;
+}
+
+// cache file: one line per entry, "n nlines njobs periodic C L" (device 0 entries are
+// applied to the current device when loaded)
+int jv_tune_save(const char* path) {
+  FILE* f = std::fopen(path, "w");
+  if (!f) return -1;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  for (const auto& kv : g_tune)
+    std::fprintf(f, "%d %lld %d %d %d %d\n", kv.first.n, kv.first.nlines, kv.first.njobs, kv.first.periodic,
+                 kv.second.C, kv.second.L);
+  std::fclose(f);
+  return (int)g_tune.size();
+}
+
+int jv_tune_load(const char* path) {
+  FILE* f = std::fopen(path, "r");
+  if (!f) return -1;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  int count = 0;
+  TuneKey k;
+  LineCfg c;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  while (std::fscanf(f, "%d %lld %d %d %d %d", &k.n, &k.nlines, &k.njobs, &k.periodic, &c.C, &c.L) == 6) {
+    if (c.C < 1 || c.L < 1 || k.n < 1) continue;
+    k.dev = dev;
+    g_tune[k] = c;
+    ++count;
+  }
+  std::fclose(f);
+  return count;
+}
+
+// apply cached shapes (if any) to a new handle
+void jv_tune_apply_cached(StabHandle* h) {
+  const double2* src[6] = {};
+  for (int ax = 0; ax < h->dim; ++ax) {
+    std::vector<LineJob> jobs;
+    axis_jobs(h, ax, src, jobs);
+    const TuneKey key = tune_key(h, ax, (int)jobs.size());
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) h->line_cfg[ax] = it->second;
+  }
+}
+
 static PointParams point_params(StabHandle* h, const double2* v) {
   PointParams P{};
+  P.gate = h->gate;
   P.v = v;
   P.scratch = h->d_scratch;
   P.npts = h->npts;
@@ -804,14 +974,18 @@ cudaError_t launch_norm2(StabHandle* h, const double2* v, long long n, double* d
   long long nb = (n + 1023) / 1024;
   if (nb > h->red_blocks) nb = h->red_blocks;
   if (nb < 1) nb = 1;
-  k_norm2_partial<<<(int)nb, 256, 0, h->stream>>>(v, n, h->d_red);
-  k_norm2_final<<<1, 32, 0, h->stream>>>(h->d_red, (int)nb, d_out, mode, h->q0norm, h->opts.eps);
+  k_norm2_partial<<<(int)nb, 256, 0, h->stream>>>(v, n, h->d_red, h->gate);
+  k_norm2_final<<<1, 32, 0, h->stream>>>(h->d_red, (int)nb, d_out, mode, h->q0norm, h->opts.eps, h->gate);
   return cudaGetLastError();
 }
 
 cudaError_t jv_setup(StabHandle* h, const double* q0_host) {
   const int D = h->dim;
   cudaError_t err;
+  // set once per handle (current device), never during a stream capture
+  if ((err = cudaFuncSetAttribute(k_line_pass, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLineSmemMax)) !=
+      cudaSuccess)
+    return err;
   make_slots(h);
   // axis tables: x (0) periodic, y (1) bounded in eta, z (2) periodic
   const int lens[3] = {h->nx, h->ny, h->nz};
@@ -993,7 +1167,7 @@ cudaError_t jv_apply(StabHandle* h, const double2* v, double2* out, double2 shif
 // ||v||_2 on an explicit stream with caller-provided partials (nb blocks,
 // fixed by the caller so the summation order is reproducible).
 cudaError_t launch_norm2_stream(cudaStream_t st, const double2* v, long long n, double* partial, int nb, double* d_out) {
-  k_norm2_partial<<<nb, 256, 0, st>>>(v, n, partial);
-  k_norm2_final<<<1, 32, 0, st>>>(partial, nb, d_out, 1, 0.0, 0.0);
+  k_norm2_partial<<<nb, 256, 0, st>>>(v, n, partial, nullptr);
+  k_norm2_final<<<1, 32, 0, st>>>(partial, nb, d_out, 1, 0.0, 0.0, nullptr);
   return cudaGetLastError();
 }

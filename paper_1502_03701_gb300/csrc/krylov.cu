@@ -61,8 +61,11 @@ __global__ void k_dot_final(const double2* partial, int nb, int k, double2* out,
 }
 
 // w[i] -= sum_j V_j[i] h[j]   (sign = -1)   or   x[i] += sum_j V_j[i] y[j]   (sign = +1)
+// (kdev, when set, lowers k to *kdev: the column count is known only on the device)
 __global__ void __launch_bounds__(kThreads) k_gemv(const double2* __restrict__ V, int k, long long n,
-                                                  const double2* __restrict__ h, double2* x, double sign) {
+                                                  const double2* __restrict__ h, double2* x, double sign,
+                                                  const int* kdev) {
+  if (kdev) k = min(k, *kdev);
   extern __shared__ double2 hs[];
   for (int j = threadIdx.x; j < k; j += blockDim.x) hs[j] = h[j];
   __syncthreads();
@@ -78,8 +81,9 @@ __global__ void __launch_bounds__(kThreads) k_gemv(const double2* __restrict__ V
   }
 }
 
-// x = x / *d_norm  (into out if given)
-__global__ void k_scale_inv(double2* x, long long n, const double* d_norm, double2* out) {
+// x = x / *d_norm  (into out if given); gate as in the J v kernels
+__global__ void k_scale_inv(double2* x, long long n, const double* d_norm, double2* out, const int* gate) {
+  if (gate && *gate) return;
   const double s = 1.0 / *d_norm;
   double2* o = out ? out : x;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
@@ -120,11 +124,14 @@ __global__ void __launch_bounds__(kVqRows) k_vq(const double2* __restrict__ V, i
 }
 
 // ---------------------------------------------------------------------------
-// Fused CGS2.  Pass A: partial1 = block sums of V^H w.  Pass B: every block
-// reduces partial1 to h1 (same fixed order in every block), updates its rows
-// w -= V h1 and forms the block sums of V^H w' (partial2).  Pass C: every
-// block reduces partial2 to h2, updates w -= V h2, forms the block sums of
-// |w|^2; block 0 stores h = h1 + h2.  A final warp sums the norm partials.
+// Fused CGS2.  Block b owns the contiguous rows [r0, r1) of every vector.
+// Pass A: partial1 = per-block sums of V^H w.  Pass B: every block reduces
+// partial1 to h1 (same fixed order in every block), updates its rows
+// w -= V h1 and forms its sums of V^H w' (partial2).  Pass C: every block
+// reduces partial2 to h2, updates w -= V h2 and forms its sum of |w|^2;
+// block 0 stores h = h1 + h2.  A final warp sums the norm partials.
+// Dot products: one warp per column (a warp group per column when k is
+// smaller than the warp count), so no block barrier is taken per column.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void reduce_partials(const double2* partial, int nb, int k, double2* hs) {
   // hs[j] = sum_b partial[b * k + j]; one warp per column, fixed order
@@ -142,39 +149,61 @@ __device__ __forceinline__ void reduce_partials(const double2* partial, int nb, 
   }
 }
 
-// partial_out[b * k + j] = block sums of conj(V_j) w.  Products are exact FP32
-// two-products of the integer-split pairs, accumulated by two-sum per thread
-// and warp; only the per-warp results are added in FP64 (fixed order).
-__device__ __forceinline__ void block_dot_columns(const double2* __restrict__ V, int k, long long n,
-                                                  const double2* w, double2* partial_out, double* red) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  for (int j = 0; j < k; ++j) {
-    const double2* Vj = V + (long long)j * n;
-    ffn sr{0.0f, 0.0f}, si{0.0f, 0.0f};
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-      const double2 av = Vj[i], bv = w[i];
-      const ffn ar = ff_split(av.x), ai = ff_split(av.y), br = ff_split(bv.x), bi = ff_split(bv.y);
-      ff_acc_prod(sr, ar, br);             // Re conj(a) b = ar br + ai bi
-      ff_acc_prod(sr, ai, bi);
-      ff_acc_prod(si, ar, bi);             // Im conj(a) b = ar bi - ai br
-      ff_acc_prod(si, ff_negate(ai), br);
-    }
-    sr = ff_warp_sum(sr);
-    si = ff_warp_sum(si);
-    if (lane == 0) { red[2 * wid] = ff_to_d(sr); red[2 * wid + 1] = ff_to_d(si); }
-    __syncthreads();
-    if (wid == 0) {
-      double tr = lane < (int)(blockDim.x >> 5) ? red[2 * lane] : 0.0;
-      double ti = lane < (int)(blockDim.x >> 5) ? red[2 * lane + 1] : 0.0;
-      tr = warp_sum(tr);
-      ti = warp_sum(ti);
-      if (lane == 0) partial_out[(long long)blockIdx.x * k + j] = make_double2(tr, ti);
-    }
-    __syncthreads();
+// sum over rows [q0, q1) of conj(x_i) w_i by one warp: exact FP32
+// two-products of the integer-split pairs, accumulated by two-sum; every
+// lane returns the warp's total.
+__device__ __forceinline__ double2 warp_dot(const double2* __restrict__ x, const double2* __restrict__ w, long long q0,
+                                            long long q1) {
+  const int lane = threadIdx.x & 31;
+  ffn sr{0.0f, 0.0f}, si{0.0f, 0.0f};
+  for (long long i = q0 + lane; i < q1; i += 32) {
+    const double2 av = x[i], bv = w[i];
+    const ffn ar = ff_split(av.x), ai = ff_split(av.y), br = ff_split(bv.x), bi = ff_split(bv.y);
+    ff_acc_prod(sr, ar, br);             // Re conj(a) b = ar br + ai bi
+    ff_acc_prod(sr, ai, bi);
+    ff_acc_prod(si, ar, bi);             // Im conj(a) b = ar bi - ai br
+    ff_acc_prod(si, ff_negate(ai), br);
   }
+  sr = ff_warp_sum(sr);
+  si = ff_warp_sum(si);
+  return make_double2(ff_to_d(sr), ff_to_d(si));
 }
 
-// w_i -= sum_j V_j[i] h_j for this thread's rows, pair arithmetic; h as pairs in shared memory.
+// partial_out[b * k + j] = this block's sum of conj(V_j) w over [r0, r1).
+// red: shared, one double2 per warp.  Block-uniform control flow.
+__device__ __forceinline__ void block_dot_columns(const double2* __restrict__ V, int k, long long n, long long r0,
+                                                  long long r1, const double2* w, double2* partial_out,
+                                                  double2* red) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if (k >= nw) {
+    for (int j = wid; j < k; j += nw) {
+      const double2 d = warp_dot(V + (long long)j * n, w, r0, r1);
+      if (lane == 0) partial_out[(long long)blockIdx.x * k + j] = d;
+    }
+    return;
+  }
+  const int G = nw / k;  // warps per column, each over a fixed sub-range
+  double2 d = make_double2(0.0, 0.0);
+  if (wid < G * k) {
+    const int j = wid / G, sg = wid - j * G;
+    const long long len = r1 - r0;
+    d = warp_dot(V + (long long)j * n, w, r0 + len * sg / G, r0 + len * (sg + 1) / G);
+  }
+  if (lane == 0) red[wid] = d;
+  __syncthreads();
+  if ((int)threadIdx.x < k) {
+    const int j = threadIdx.x;
+    double sr = 0.0, si = 0.0;
+    for (int q = 0; q < G; ++q) {
+      sr += red[j * G + q].x;
+      si += red[j * G + q].y;
+    }
+    partial_out[(long long)blockIdx.x * k + j] = make_double2(sr, si);
+  }
+  __syncthreads();
+}
+
+// w_i -= sum_j V_j[i] h_j for one row, pair arithmetic; h as pairs in shared memory.
 __device__ __forceinline__ double2 row_update(const double2* __restrict__ V, int k, long long n, long long i,
                                               const ffn* hre, const ffn* him, double2 wv) {
   ffn ar{0.0f, 0.0f}, ai{0.0f, 0.0f};
@@ -189,16 +218,28 @@ __device__ __forceinline__ double2 row_update(const double2* __restrict__ V, int
   return make_double2(wv.x - ff_to_d(ar), wv.y - ff_to_d(ai));
 }
 
+__device__ __forceinline__ void block_rows(long long n, long long& r0, long long& r1) {
+  const long long rows = (n + gridDim.x - 1) / gridDim.x;
+  r0 = (long long)blockIdx.x * rows;
+  r1 = r0 + rows < n ? r0 + rows : n;
+}
+
 __global__ void __launch_bounds__(kThreads) k_cgs2_a(const double2* __restrict__ V, int k, long long n,
-                                                    const double2* __restrict__ w, double2* partial1) {
-  __shared__ double red[2 * kThreads / 32];
-  block_dot_columns(V, k, n, w, partial1, red);
+                                                    const double2* __restrict__ w, double2* partial1,
+                                                    const int* gate) {
+  if (gate && *gate) return;
+  __shared__ double2 red[kThreads / 32];
+  long long r0, r1;
+  block_rows(n, r0, r1);
+  block_dot_columns(V, k, n, r0, r1, w, partial1, red);
 }
 
 __global__ void __launch_bounds__(kThreads) k_cgs2_b(const double2* __restrict__ V, int k, long long n, double2* w,
-                                                    const double2* partial1, double2* partial2, double2* d_h) {
+                                                    const double2* partial1, double2* partial2, double2* d_h,
+                                                    const int* gate) {
+  if (gate && *gate) return;
   extern __shared__ double2 hs[];  // k complex, then 2k pairs
-  __shared__ double red[2 * kThreads / 32];
+  __shared__ double2 red[kThreads / 32];
   ffn* hre = (ffn*)(hs + k);
   ffn* him = hre + k;
   reduce_partials(partial1, gridDim.x, k, hs);
@@ -209,14 +250,17 @@ __global__ void __launch_bounds__(kThreads) k_cgs2_b(const double2* __restrict__
     if (blockIdx.x == 0) d_h[j] = hs[j];
   }
   __syncthreads();
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-    w[i] = row_update(V, k, n, i, hre, him, w[i]);
+  long long r0, r1;
+  block_rows(n, r0, r1);
+  for (long long i = r0 + threadIdx.x; i < r1; i += blockDim.x) w[i] = row_update(V, k, n, i, hre, him, w[i]);
   __syncthreads();  // this block's rows of w are final; the dots below read only them
-  block_dot_columns(V, k, n, w, partial2, red);
+  block_dot_columns(V, k, n, r0, r1, w, partial2, red);
 }
 
 __global__ void __launch_bounds__(kThreads) k_cgs2_c(const double2* __restrict__ V, int k, long long n, double2* w,
-                                                    const double2* partial2, double2* d_h, double* norm_partial) {
+                                                    const double2* partial2, double2* d_h, double* norm_partial,
+                                                    const int* gate) {
+  if (gate && *gate) return;
   extern __shared__ double2 hs[];  // k complex, then 2k pairs
   __shared__ double red[kThreads / 32];
   ffn* hre = (ffn*)(hs + k);
@@ -232,8 +276,10 @@ __global__ void __launch_bounds__(kThreads) k_cgs2_c(const double2* __restrict__
     }
   }
   __syncthreads();
+  long long r0, r1;
+  block_rows(n, r0, r1);
   double s = 0.0;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+  for (long long i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
     const double2 r = row_update(V, k, n, i, hre, him, w[i]);
     w[i] = r;
     s = fma(r.x, r.x, fma(r.y, r.y, s));
@@ -249,11 +295,20 @@ __global__ void __launch_bounds__(kThreads) k_cgs2_c(const double2* __restrict__
   }
 }
 
-__global__ void k_norm_final(const double* partial, int nb, double* out) {
+__global__ void k_norm_final(const double* partial, int nb, double* out, const int* gate) {
+  if (gate && *gate) return;
   double s = 0.0;
   for (int i = threadIdx.x; i < nb; i += 32) s += partial[i];
   s = warp_sum(s);
   if (threadIdx.x == 0) *out = sqrt(s);
+}
+
+// blocks of the fused CGS2: about 64 rows each (short latency on small
+// vectors), at most four per SM on large ones
+int cgs_blocks(long long n) {
+  long long b = (n + 63) / 64;
+  if (b > 152 * 4) b = 152 * 4;
+  return (int)(b < 1 ? 1 : b);
 }
 
 int red_blocks(long long n) {
@@ -280,13 +335,14 @@ cudaError_t kry_dot(StabHandle* h, const double2* V, int k, long long n, const d
 
 cudaError_t kry_gemv_sub(StabHandle* h, const double2* V, int k, long long n, const double2* d_h, double2* w) {
   if (k <= 0) return cudaSuccess;
-  k_gemv<<<grid_n(n), kThreads, k * sizeof(double2), h->stream>>>(V, k, n, d_h, w, -1.0);
+  k_gemv<<<grid_n(n), kThreads, k * sizeof(double2), h->stream>>>(V, k, n, d_h, w, -1.0, nullptr);
   return cudaGetLastError();
 }
 
-cudaError_t kry_gemv_add(StabHandle* h, const double2* V, int k, long long n, const double2* d_y, double2* x) {
+cudaError_t kry_gemv_add(StabHandle* h, const double2* V, int k, long long n, const double2* d_y, double2* x,
+                         const int* kdev) {
   if (k <= 0) return cudaSuccess;
-  k_gemv<<<grid_n(n), kThreads, k * sizeof(double2), h->stream>>>(V, k, n, d_y, x, 1.0);
+  k_gemv<<<grid_n(n), kThreads, k * sizeof(double2), h->stream>>>(V, k, n, d_y, x, 1.0, kdev);
   return cudaGetLastError();
 }
 
@@ -295,7 +351,7 @@ cudaError_t kry_gemv_add(StabHandle* h, const double2* V, int k, long long n, co
 // the norm partials); d_h holds 2k complex.
 cudaError_t kry_cgs2(StabHandle* h, const double2* V, int k, long long n, double2* w, double2* d_h, double* d_norm,
                      double2* partial) {
-  const int nb = red_blocks(n);
+  const int nb = cgs_blocks(n);
   double2* p1 = partial;
   double2* p2 = partial + (size_t)nb * (k > 0 ? k : 1);
   double* np = (double*)(p2 + (size_t)nb * (k > 0 ? k : 1));
@@ -303,10 +359,10 @@ cudaError_t kry_cgs2(StabHandle* h, const double2* V, int k, long long n, double
   cudaError_t e;
   if (k > 0) {
     const size_t sm = (size_t)k * (sizeof(double2) + 2 * sizeof(ffn));
-    k_cgs2_a<<<nb, kThreads, 0, h->stream>>>(V, k, n, w, p1);
-    k_cgs2_b<<<nb, kThreads, sm, h->stream>>>(V, k, n, w, p1, p2, d_h);
-    k_cgs2_c<<<nb, kThreads, sm, h->stream>>>(V, k, n, w, p2, d_h, np);
-    k_norm_final<<<1, 32, 0, h->stream>>>(np, nb, d_norm);
+    k_cgs2_a<<<nb, kThreads, 0, h->stream>>>(V, k, n, w, p1, h->gate);
+    k_cgs2_b<<<nb, kThreads, sm, h->stream>>>(V, k, n, w, p1, p2, d_h, h->gate);
+    k_cgs2_c<<<nb, kThreads, sm, h->stream>>>(V, k, n, w, p2, d_h, np, h->gate);
+    k_norm_final<<<1, 32, 0, h->stream>>>(np, nb, d_norm, h->gate);
     e = cudaGetLastError();
   } else {
     e = launch_norm2(h, w, n, d_norm, 1);
@@ -316,7 +372,7 @@ cudaError_t kry_cgs2(StabHandle* h, const double2* V, int k, long long n, double
 }
 
 cudaError_t kry_scale(StabHandle* h, double2* x, long long n, const double* d_norm, double2* out) {
-  k_scale_inv<<<grid_n(n), kThreads, 0, h->stream>>>(x, n, d_norm, out);
+  k_scale_inv<<<grid_n(n), kThreads, 0, h->stream>>>(x, n, d_norm, out, h->gate);
   return cudaGetLastError();
 }
 
@@ -343,7 +399,7 @@ cudaError_t kry_update_basis(StabHandle* h, double2* V, int m, int kk, long long
 }
 
 int kry_partial_elems(long long n, int k) {
-  const int nb = red_blocks(n);
+  const int nb = cgs_blocks(n);
   return 2 * nb * (k > 0 ? k : 1) + (nb + 1) / 2 + 1;
 }
 
@@ -359,7 +415,7 @@ cudaError_t kry_cgs2_stream(cudaStream_t st, const double2* V, int k, long long 
       double2* hp = d_h + (size_t)pass * k;
       k_dot_partial<<<nb, kThreads, 0, st>>>(V, k, n, w, partial);
       k_dot_final<<<k, 32, 0, st>>>(partial, nb, k, hp, 0);
-      k_gemv<<<grid_n(n), kThreads, k * sizeof(double2), st>>>(V, k, n, hp, w, -1.0);
+      k_gemv<<<grid_n(n), kThreads, k * sizeof(double2), st>>>(V, k, n, hp, w, -1.0, nullptr);
     }
     k_axpby<<<1, 64, 0, st>>>(make_double2(1.0, 0.0), d_h + k, make_double2(1.0, 0.0), d_h, k);
   }

@@ -9,6 +9,7 @@
 // elimination with partial pivoting (first row of maximum modulus) and
 // applied as a batched block matrix-vector product.
 // Local unknown order inside a tile: [var][lz][ly][lx], lx fastest.
+#include <algorithm>
 #include <cstring>
 #include <vector>
 
@@ -223,6 +224,7 @@ struct ApplyParams {
   const void* inv;
   int nx, ny, tx, ty, tz, ntx, nty, ntpts, bsz;
   long long npts;
+  const int* gate;  // when set and nonzero the launch does nothing (graph-captured GMRES after convergence)
 };
 
 __device__ __forceinline__ long long tile_dof(const ApplyParams& P, long long tile, int r) {
@@ -232,12 +234,17 @@ __device__ __forceinline__ long long tile_dof(const ApplyParams& P, long long ti
   return (long long)var * P.npts + ((long long)(tZ * P.tz + pz) * P.ny + (tY * P.ty + py)) * P.nx + tX * P.tx + px;
 }
 
-// z_tile = Minv_tile q_tile; one CTA per tile, one warp per row at a time
+// z_tile = Minv_tile q_tile.  Grid (tiles, row slices): a CTA stages its
+// tile of q in shared memory and computes the rows of its slice, one warp per
+// row at a time (slices > 1 only when there are too few tiles to cover the SMs).
 template <class R>
 __global__ void k_apply(const ApplyParams P) {
+  if (P.gate && *P.gate) return;
   extern __shared__ unsigned char smraw[];
   C2<R>* qs = (C2<R>*)smraw;
   const long long tile = blockIdx.x;
+  const int rb0 = (int)((long long)P.bsz * blockIdx.y / gridDim.y);
+  const int rb1 = (int)((long long)P.bsz * (blockIdx.y + 1) / gridDim.y);
   const C2<R>* M = (const C2<R>*)P.inv + (long long)tile * P.bsz * P.bsz;
   for (int r = threadIdx.x; r < P.bsz; r += blockDim.x) {
     double2 v = P.q[tile_dof(P, tile, r)];
@@ -245,7 +252,7 @@ __global__ void k_apply(const ApplyParams P) {
   }
   __syncthreads();
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int r = wid; r < P.bsz; r += nw) {
+  for (int r = rb0 + wid; r < rb1; r += nw) {
     const C2<R>* row = M + (long long)r * P.bsz;
     R ar = 0, ai = 0;
     for (int c = lane; c < P.bsz; c += 32) {
@@ -409,9 +416,14 @@ cudaError_t pc_apply(StabHandle* h, const double2* q, double2* z) {
   P.q = q; P.z = z; P.inv = h->d_pinv;
   P.nx = h->nx; P.ny = h->ny; P.tx = g.tx; P.ty = g.ty; P.tz = g.tz; P.ntx = g.ntx; P.nty = g.nty;
   P.ntpts = g.ntpts; P.bsz = g.bsz; P.npts = h->npts;
+  P.gate = h->gate;
   const int ts = phase_begin(h, STAB_PHASE_PRECOND_APPLY);
-  if (h->pprec == 64) k_apply<double><<<(unsigned)g.ntiles, 256, g.bsz * sizeof(double2), h->stream>>>(P);
-  else k_apply<float><<<(unsigned)g.ntiles, 256, g.bsz * sizeof(float2), h->stream>>>(P);
+  // row slices so that small grids still spread over the SMs
+  int slices = (int)((2 * 152 + g.ntiles - 1) / g.ntiles);
+  slices = std::max(1, std::min(slices, g.bsz / 32));
+  const dim3 grid((unsigned)g.ntiles, (unsigned)slices);
+  if (h->pprec == 64) k_apply<double><<<grid, 256, g.bsz * sizeof(double2), h->stream>>>(P);
+  else k_apply<float><<<grid, 256, g.bsz * sizeof(float2), h->stream>>>(P);
   phase_end(h, ts);
   return cudaGetLastError();
 }

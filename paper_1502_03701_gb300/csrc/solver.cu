@@ -6,7 +6,8 @@
 //    (Algorithm iram, Eqs. cayley_transform / cayley_arnoldi / ritz_estimate)
 //    with CGS2 orthogonalisation and exact shifts.
 // The small (m x m) Hessenberg algebra of the restart stays on the device
-// (k_restart); GMRES's Givens least-squares update runs on the host.
+// (k_restart), and so does GMRES's Givens least-squares update (k_gm_step):
+// a GMRES cycle is one replayed CUDA graph and one host read.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -15,7 +16,6 @@
 #include <vector>
 
 #include "hess_dev.cuh"
-#include "hessenberg.h"
 #include "internal.cuh"
 
 typedef std::complex<double> cd;
@@ -53,25 +53,63 @@ double2* ensure(StabHandle* h, double2** p, size_t* have, size_t need) {
 
 // GMRES workspace layout (complex elements)
 struct GmresWs {
-  double2 *V, *Z, *r, *partial, *dh, *y;
+  double2 *V, *Z, *r, *b, *x, *partial, *dh, *y;
   double* dnorm;
 };
 
-GmresWs gmres_ws(StabHandle* h) {
+constexpr int kMaxGmresM = 200;  // stab_create rejects larger gmres_m
+
+// Device-resident least-squares state of one GMRES cycle: the rotated
+// Hessenberg columns R (m x m, row-major), the rotated right-hand side g,
+// the Givens rotations (cs, sn), flags [done, jend, status] and the scalars
+// [tol ||b||, |g_{j+1}|].
+struct GmDev {
+  hd::zc *R, *g, *sn;
+  double* cs;
+  int* flags;
+  double* sc;
+  const double2* dh;
+  const double* dnorm;
+  double2* y;
+  int m;
+};
+
+struct GmReport {  // read by the host once per cycle
+  double beta;     // ||b - A x|| after the cycle
+  int jend;        // iterations performed in the cycle
+  int status;      // 0, or 1 when a Krylov quantity was not finite
+};
+
+GmresWs gmres_ws(StabHandle* h, GmDev* D, GmReport** rep) {
   const long long n = h->n;
   const int m = h->opts.gmres_m;
   const bool pc = h->opts.precond == 1;
   const size_t part = (size_t)kry_partial_elems(n, m + 1);
-  size_t need = (size_t)(m + 1) * n + (pc ? (size_t)m * n : 0) + n + part + 2 * (m + 1) + (m + 1) + 4;
+  const size_t small = (size_t)m * m + (m + 1) + m + (m + 1) / 2 + 1 + 4 + 4;
+  size_t need = (size_t)(m + 1) * n + (pc ? (size_t)m * n : 0) + 3 * (size_t)n + part + 2 * (m + 1) + (m + 1) + 4 + small;
   double2* base = ensure(h, &h->d_gm, &h->gm_elems, need);
   GmresWs w;
   w.V = base;
   w.Z = pc ? base + (size_t)(m + 1) * n : nullptr;
   w.r = base + (size_t)(m + 1) * n + (pc ? (size_t)m * n : 0);
-  w.partial = w.r + n;
+  w.b = w.r + n;
+  w.x = w.b + n;
+  w.partial = w.x + n;
   w.dh = w.partial + part;
   w.y = w.dh + 2 * (m + 1);
   w.dnorm = (double*)(w.y + (m + 1));
+  double2* p = w.y + (m + 1) + 4;
+  D->R = (hd::zc*)p; p += (size_t)m * m;
+  D->g = (hd::zc*)p; p += m + 1;
+  D->sn = (hd::zc*)p; p += m;
+  D->cs = (double*)p; p += (m + 1) / 2 + 1;
+  D->flags = (int*)p; p += 1;        // 4 ints
+  D->sc = (double*)p; p += 1;        // 2 doubles
+  *rep = (GmReport*)p; p += 1;       // 16 bytes
+  D->dh = w.dh;
+  D->dnorm = w.dnorm;
+  D->y = w.y;
+  D->m = m;
   return w;
 }
 
@@ -82,83 +120,207 @@ double read_scalar(StabHandle* h, const double* d) {
   return v;
 }
 
-// (J - sigma I) x = b.  Returns the iteration count; sets *converged.
-int gmres(StabHandle* h, cd sigma, const double2* b, double2* x, int eps_mode, bool* converged) {
+__global__ void k_gm_tol(GmDev d, double tol) { d.sc[0] = tol * (*d.dnorm); }
+
+// start of a cycle: g = (beta, 0, ...), beta = ||r|| (in dnorm)
+__global__ void k_gm_cycle_init(GmDev d) {
+  if (threadIdx.x == 0) {
+    d.flags[0] = 0;
+    d.flags[1] = 0;
+    d.flags[2] = 0;
+  }
+  for (int i = threadIdx.x; i <= d.m; i += blockDim.x) d.g[i] = hd::mk(i == 0 ? *d.dnorm : 0.0);
+}
+
+__device__ __forceinline__ bool finite_zc(hd::zc z) { return fabs(z.re) < INFINITY && fabs(z.im) < INFINITY; }
+
+// Arnoldi column j (h_0..h_j from CGS2, h_{j+1} = ||w||): previous rotations,
+// the new rotation that annihilates h_{j+1}, the rotated right-hand side and
+// the convergence test |g_{j+1}| <= tol ||b|| (or w = 0).  One warp: the
+// column and the rotations are staged in shared memory by all lanes, the
+// rotation chain runs on lane 0.
+__global__ void k_gm_step(GmDev d, int j) {
+  __shared__ hd::zc col[kMaxGmresM + 1], sn[kMaxGmresM];
+  __shared__ double cs[kMaxGmresM];
+  if (d.flags[0]) return;
+  const int m = d.m, lane = threadIdx.x;
+  const double wn = *d.dnorm;
+  int bad = !(fabs(wn) < INFINITY);
+  for (int i = lane; i <= j; i += 32) {
+    const hd::zc v = hd::mk(d.dh[i].x, d.dh[i].y);
+    bad |= !finite_zc(v);
+    col[i] = v;
+  }
+  for (int i = lane; i < j; i += 32) {
+    cs[i] = d.cs[i];
+    sn[i] = d.sn[i];
+  }
+  bad = __any_sync(0xffffffffu, bad);
+  __syncwarp();
+  if (bad) {
+    if (lane == 0) { d.flags[2] = 1; d.flags[0] = 1; }
+    return;
+  }
+  if (lane == 0) {
+    for (int i = 0; i < j; ++i) {
+      const hd::zc a = col[i], b = col[i + 1];
+      col[i] = cs[i] * a + sn[i] * b;
+      col[i + 1] = cs[i] * b - hd::conj(sn[i]) * a;
+    }
+    double c;
+    hd::zc s;
+    const hd::zc sub = hd::mk(wn);
+    hd::givens(col[j], sub, c, s);
+    d.cs[j] = c;
+    d.sn[j] = s;
+    col[j] = c * col[j] + s * sub;
+    const hd::zc gj = d.g[j];
+    d.g[j + 1] = -(hd::conj(s) * gj);
+    d.g[j] = c * gj;
+    d.flags[1] = j + 1;
+    const double res = hd::zabs(d.g[j + 1]);
+    d.sc[1] = res;
+    if (res <= d.sc[0] || wn == 0.0) d.flags[0] = 1;
+  }
+  __syncwarp();
+  for (int i = lane; i <= j; i += 32) d.R[i * m + j] = col[i];
+}
+
+// y = R^{-1} g over the jend columns of the cycle, by columns: y_i from the
+// diagonal, then every thread removes y_i's contribution from its rows.
+__global__ void k_gm_solve(GmDev d) {
+  __shared__ hd::zc s[kMaxGmresM];
+  __shared__ hd::zc yi;
+  const int m = d.m, je = d.flags[1];
+  for (int l = threadIdx.x; l < je; l += blockDim.x) s[l] = d.g[l];
+  __syncthreads();
+  for (int i = je - 1; i >= 0; --i) {
+    if (threadIdx.x == 0) {
+      yi = s[i] / d.R[i * m + i];
+      d.y[i] = make_double2(yi.re, yi.im);
+    }
+    __syncthreads();
+    for (int l = threadIdx.x; l < i; l += blockDim.x) s[l] = s[l] - d.R[l * m + i] * yi;
+    __syncthreads();
+  }
+}
+
+__global__ void k_gm_report(GmDev d, GmReport* rep) {
+  rep->beta = *d.dnorm;
+  rep->jend = d.flags[1];
+  rep->status = d.flags[2];
+}
+
+// One GMRES cycle as a CUDA graph: V_0 = r / beta; m Arnoldi steps, each
+// (right preconditioner, J v - sigma v, CGS2, Givens update, scaling) gated
+// on the device flag that the Givens update raises at convergence; the
+// least-squares solve, x += Z y (V y), and the true residual r = b - A x with
+// its norm.  Captured once per handle, shift and workspace, replayed for
+// every cycle of every solve: the host only reads the report once per cycle.
+cudaGraphExec_t gm_graph(StabHandle* h, cd sigma, int eps_mode, const GmresWs& W, const GmDev& D, GmReport* rep) {
   const long long n = h->n;
   const int m = h->opts.gmres_m;
   const bool pc = h->opts.precond == 1;
-  const double tol = h->opts.gmres_tol;
-  GmresWs W = gmres_ws(h);
-  ck(h, launch_norm2(h, b, n, W.dnorm, 1), "norm");
-  const double bnorm = read_scalar(h, W.dnorm);
-  ck(h, cudaMemsetAsync(x, 0, n * sizeof(double2), h->stream), "memset");
-  *converged = false;
-  if (!(bnorm < INFINITY)) fail(h, STAB_ERR_NUMERIC, "GMRES: right-hand side is not finite");
-  if (bnorm == 0.0) { *converged = true; return 0; }
-  ck(h, kry_copy(h, b, W.r, n), "copy");
-  double beta = bnorm;
-  int total = 0;
-  std::vector<cd> H((size_t)(m + 1) * m), g(m + 1), sn(m), hcol(2 * (m + 1));
-  std::vector<double> cs(m);
-  std::vector<double> hbuf(2 * (m + 1) + 2);
-  for (int cycle = 0; cycle < h->opts.gmres_max_restarts; ++cycle) {
-    // V_0 = r / beta (W.dnorm holds beta on the device)
-    ck(h, kry_scale(h, W.r, n, W.dnorm, W.V), "scale");
-    std::fill(g.begin(), g.end(), cd(0.0));
-    g[0] = beta;
-    int jend = 0;
-    for (int j = 0; j < m; ++j) {
+  GmGraphKey key;
+  key.valid = true;
+  key.sigma_re = sigma.real();
+  key.sigma_im = sigma.imag();
+  key.eps_mode = eps_mode;
+  key.m = m;
+  key.pc = pc;
+  key.pprec = h->pprec;
+  key.ws = h->d_gm;
+  key.pinv = pc ? h->d_pinv : nullptr;
+  key.n = n;
+  if (h->gm_exec && key == h->gm_key) return h->gm_exec;
+  if (h->gm_exec) {
+    cudaGraphExecDestroy(h->gm_exec);
+    h->gm_exec = nullptr;
+    h->gm_key.valid = false;
+  }
+  if (!h->cap_stream) ck(h, cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking), "capture stream");
+  const stab_stats saved_stats = h->stats;
+  cudaStream_t saved_stream = h->stream;
+  h->stream = h->cap_stream;
+  h->capturing = true;
+  h->last_eps_mode = -1;  // the first captured J v sets epsilon's mode explicitly
+  cudaGraph_t graph = nullptr;
+  cudaError_t err = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal);
+  auto step = [&](cudaError_t e) { if (err == cudaSuccess && e != cudaSuccess) err = e; };
+  if (err == cudaSuccess) {
+    k_gm_cycle_init<<<1, 64, 0, h->stream>>>(D);
+    step(kry_scale(h, W.r, n, W.dnorm, W.V));
+    for (int j = 0; j < m && err == cudaSuccess; ++j) {
       double2* Vj = W.V + (size_t)j * n;
       double2* Vn = W.V + (size_t)(j + 1) * n;
-      double2* zj = Vj;
-      if (pc) {
-        zj = W.Z + (size_t)j * n;
-        ck(h, pc_apply(h, Vj, zj), "preconditioner apply");
-      }
-      ck(h, jv_apply(h, zj, Vn, d2(sigma), eps_mode), "J v");
-      ck(h, kry_cgs2(h, W.V, j + 1, n, Vn, W.dh, W.dnorm, W.partial), "CGS2");
-      // fetch h(0..j) and ||w|| in one copy (dnorm follows dh + 2(m+1) + (m+1))
-      ck(h, cudaMemcpyAsync(hbuf.data(), W.dh, sizeof(double2) * (j + 1), cudaMemcpyDeviceToHost, h->stream), "copy h");
-      double wn;
-      ck(h, cudaMemcpyAsync(&wn, W.dnorm, sizeof(double), cudaMemcpyDeviceToHost, h->stream), "copy norm");
-      ck(h, cudaStreamSynchronize(h->stream), "sync");
-      for (int i = 0; i <= j; ++i) hcol[i] = cd(hbuf[2 * i], hbuf[2 * i + 1]);
-      hcol[j + 1] = wn;
-      if (!(wn < INFINITY)) fail(h, STAB_ERR_NUMERIC, "GMRES: non-finite Krylov vector");
-      for (int i = 0; i < j; ++i) {  // previous rotations
-        cd a = hcol[i], bb = hcol[i + 1];
-        hcol[i] = cs[i] * a + sn[i] * bb;
-        hcol[i + 1] = -std::conj(sn[i]) * a + cs[i] * bb;
-      }
-      hess::givens_ls(hcol[j], hcol[j + 1], cs[j], sn[j]);
-      hcol[j] = cs[j] * hcol[j] + sn[j] * hcol[j + 1];
-      hcol[j + 1] = 0.0;
-      g[j + 1] = -std::conj(sn[j]) * g[j];
-      g[j] = cs[j] * g[j];
-      for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = hcol[i];
-      ++total;
-      jend = j + 1;
-      const double res = std::abs(g[j + 1]);
-      if (res <= tol * bnorm || wn == 0.0) break;
-      ck(h, kry_scale(h, Vn, n, W.dnorm, nullptr), "scale");
+      double2* zj = pc ? W.Z + (size_t)j * n : Vj;
+      h->gate = D.flags;
+      if (pc) step(pc_apply(h, Vj, zj));
+      step(jv_apply(h, zj, Vn, d2(sigma), eps_mode));
+      step(kry_cgs2(h, W.V, j + 1, n, Vn, W.dh, W.dnorm, W.partial));
+      h->gate = nullptr;
+      k_gm_step<<<1, 32, 0, h->stream>>>(D, j);
+      h->gate = D.flags;
+      step(kry_scale(h, Vn, n, W.dnorm, nullptr));
+      h->gate = nullptr;
     }
-    // y = R^{-1} g (upper triangular jend x jend)
-    std::vector<cd> y(jend);
-    for (int i = jend - 1; i >= 0; --i) {
-      cd s = g[i];
-      for (int l = i + 1; l < jend; ++l) s -= H[(size_t)i * m + l] * y[l];
-      y[i] = s / H[(size_t)i * m + i];
-    }
-    ck(h, cudaMemcpyAsync(W.y, y.data(), sizeof(double2) * jend, cudaMemcpyHostToDevice, h->stream), "copy y");
-    ck(h, kry_gemv_add(h, pc ? W.Z : W.V, jend, n, W.y, x), "x update");
-    // true residual r = b - (J - sigma I) x
-    ck(h, jv_apply(h, x, W.r, d2(sigma), eps_mode), "J v");
-    ck(h, kry_axpby(h, make_double2(1.0, 0.0), b, make_double2(-1.0, 0.0), W.r, n), "axpby");
-    ck(h, launch_norm2(h, W.r, n, W.dnorm, 1), "norm");
-    beta = read_scalar(h, W.dnorm);
-    if (!(beta < INFINITY)) fail(h, STAB_ERR_NUMERIC, "GMRES: non-finite residual");
-    if (beta <= tol * bnorm) { *converged = true; break; }
+    k_gm_solve<<<1, 64, 0, h->stream>>>(D);
+    step(kry_gemv_add(h, pc ? W.Z : W.V, m, n, W.y, W.x, D.flags + 1));
+    step(jv_apply(h, W.x, W.r, d2(sigma), eps_mode));
+    step(kry_axpby(h, make_double2(1.0, 0.0), W.b, make_double2(-1.0, 0.0), W.r, n));
+    step(launch_norm2(h, W.r, n, W.dnorm, 1));
+    k_gm_report<<<1, 1, 0, h->stream>>>(D, rep);
+    step(cudaGetLastError());
+    const cudaError_t e2 = cudaStreamEndCapture(h->cap_stream, &graph);
+    if (err == cudaSuccess) err = e2;
   }
+  h->gate = nullptr;
+  h->capturing = false;
+  h->stream = saved_stream;
+  h->stats = saved_stats;
+  cudaGraphExec_t exec = nullptr;
+  if (err == cudaSuccess) err = cudaGraphInstantiate(&exec, graph, 0);
+  if (graph) cudaGraphDestroy(graph);
+  ck(h, err, "GMRES cycle graph");
+  h->gm_exec = exec;
+  h->gm_key = key;
+  return exec;
+}
+
+// (J - sigma I) x = b.  Returns the iteration count; sets *converged.
+int gmres(StabHandle* h, cd sigma, const double2* b, double2* x, int eps_mode, bool* converged) {
+  const long long n = h->n;
+  const double tol = h->opts.gmres_tol;
+  GmDev D;
+  GmReport* d_rep;
+  GmresWs W = gmres_ws(h, &D, &d_rep);
+  cudaGraphExec_t exec = gm_graph(h, sigma, eps_mode, W, D, d_rep);
+  ck(h, kry_copy(h, b, W.b, n), "copy b");
+  ck(h, launch_norm2(h, W.b, n, W.dnorm, 1), "norm");
+  const double bnorm = read_scalar(h, W.dnorm);
+  *converged = false;
+  if (!(bnorm < INFINITY)) fail(h, STAB_ERR_NUMERIC, "GMRES: right-hand side is not finite");
+  if (bnorm == 0.0) {
+    ck(h, cudaMemsetAsync(x, 0, n * sizeof(double2), h->stream), "memset");
+    *converged = true;
+    return 0;
+  }
+  ck(h, cudaMemsetAsync(W.x, 0, n * sizeof(double2), h->stream), "memset");
+  ck(h, kry_copy(h, W.b, W.r, n), "copy");
+  k_gm_tol<<<1, 1, 0, h->stream>>>(D, tol);
+  int total = 0;
+  GmReport rep{};
+  for (int cycle = 0; cycle < h->opts.gmres_max_restarts; ++cycle) {
+    ck(h, cudaGraphLaunch(exec, h->stream), "GMRES cycle");
+    ck(h, cudaMemcpyAsync(&rep, d_rep, sizeof(GmReport), cudaMemcpyDeviceToHost, h->stream), "report");
+    ck(h, cudaStreamSynchronize(h->stream), "sync");
+    total += rep.jend;
+    h->stats.jv_calls += rep.jend + 1;
+    if (rep.status) fail(h, STAB_ERR_NUMERIC, "GMRES: non-finite Krylov vector");
+    if (!(rep.beta < INFINITY)) fail(h, STAB_ERR_NUMERIC, "GMRES: non-finite residual");
+    if (rep.beta <= tol * bnorm) { *converged = true; break; }
+  }
+  ck(h, kry_copy(h, W.x, x, n), "copy x");
   h->stats.gmres_iterations += total;
   h->stats.gmres_solves += 1;
   return total;

@@ -34,3 +34,16 @@ def test_default_opts_and_create_rejects_bad_grid():
     st = L.stab_create(ctypes.byref(h), ctypes.c_void_p(1), 0, ctypes.byref(g), 0.3, 1000.0, 0.71, None, None)
     assert st == 1 and not h.value
     assert b"nx" in L.stab_last_error(None)
+
+
+def test_autotune_cache_file_roundtrip(tmp_path):
+    """The tuning cache file format reads back (no GPU needed)."""
+    from paper_1502_03701_gb300 import binding
+    src = tmp_path / "tune.txt"
+    src.write_text("256 512 7 1 32 4\n512 256 5 0 16 2\nbad line\n")
+    assert binding.autotune_load(str(src)) == 2
+    dst = tmp_path / "out.txt"
+    assert binding.autotune_save(str(dst)) >= 2
+    lines = set(dst.read_text().split("\n"))
+    assert "256 512 7 1 32 4" in lines and "512 256 5 0 16 2" in lines
+    assert binding.autotune_load(str(tmp_path / "missing.txt")) == -1
