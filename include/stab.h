@@ -228,11 +228,102 @@ stab_status stab_autotune(stab_handle h, int force, int* cfg, double* ms);
  * than 1024 threads or the shared-memory limit). */
 stab_status stab_set_line_config(stab_handle h, int axis, int C, int L);
 
+/* Handles take device memory from a library-owned, stream-ordered pool (one
+ * per device; allocation and release are ordered on the handle's stream, so
+ * handles on different streams never wait for each other's frees).  Memory a
+ * destroyed handle released stays cached for later handles; this returns it
+ * to the device.  Returns the number of pools trimmed. */
+int stab_trim_memory(void);
+
 /* Write / read the process-wide tuning cache as text ("n nlines njobs
  * periodic C L" per line; loaded entries apply to the current device).
  * Return the number of entries, or -1 if the file cannot be opened. */
 int stab_autotune_save(const char* path);
 int stab_autotune_load(const char* path);
+
+/* ---------------------------------------------------------------------------
+ * Many problems on one GPU (the paper solves one problem at a time; these
+ * entry points have no counterpart there).
+ * ------------------------------------------------------------------------- */
+
+/* Device memory a handle for this grid and options needs, in bytes, through
+ * a full stab_eigs(nev, ncv) including the preconditioner (an upper estimate
+ * for the viscous case; yonly = 1 when the base flow varies in y only).
+ * -1 for a bad grid. */
+long long stab_estimate_bytes(const stab_grid* grid, const stab_opts* opts, int yonly, int nev, int ncv);
+
+/* One solve of a batch: the arguments of stab_eigs, then its outputs. */
+typedef struct {
+  double sigma_re, sigma_im, tau_re, tau_im;
+  int nev, ncv;
+  double tol;
+  const void* v0;     /* device start vector or NULL */
+  double* lambda;     /* host complex128 nev */
+  void* vecs;         /* device n x nev or NULL */
+  double* resid;      /* host nev or NULL */
+  int nconv;          /* out */
+  stab_status status; /* out: the solve's own status */
+  stab_stats stats;   /* out */
+} stab_eig_job;
+
+/* Run stab_eigs(handles[i], jobs[i]) for i < count side by side: up to
+ * `concurrency` host threads (<= 0: count), each handle on a private stream
+ * for the duration (ordered after the handle's stream; the handle's stream is
+ * restored and idle on return).  The handles must be distinct.  Each job gets
+ * exactly the result a lone stab_eigs call would give.  Returns STAB_OK or the
+ * first failing job's status. */
+stab_status stab_eigs_batch(stab_handle* handles, stab_eig_job* jobs, int count, int concurrency);
+
+/* Continuous-batching server: requests of any grid and flow parameters are
+ * queued first come, first served; a request starts when one of `slots`
+ * worker threads is free and its estimated memory (stab_estimate_bytes) fits
+ * in what the running requests leave of mem_budget_bytes.  Each running
+ * request has its own handle and stream on the device current at creation,
+ * so requests overlap on the GPU; a slot takes the next request as soon as
+ * its solve ends.  autotune = 1 tunes (or takes from the cache) the line-pass
+ * shapes of each new grid before solving. */
+typedef struct stab_server_s* stab_server;
+
+typedef struct {
+  const double* base_flow;  /* host FP64 [var][z][y][x]; copied at submit */
+  stab_grid grid;
+  double Ma, Re, Pr;
+  const stab_opts* opts;    /* NULL: defaults; copied at submit */
+  double sigma_re, sigma_im, tau_re, tau_im;
+  int nev, ncv;
+  double tol;
+} stab_request;
+
+typedef struct {
+  stab_status status;       /* the solve's stab_eigs status */
+  int nconv;
+  double queued_s;          /* submit -> start */
+  double run_s;             /* start -> end */
+  double latency_s;         /* submit -> end */
+  long long est_bytes;      /* admission estimate */
+  stab_stats stats;
+} stab_request_info;
+
+stab_status stab_server_create(stab_server* server, int slots, long long mem_budget_bytes, int autotune);
+
+/* Queue a request; *id identifies it.  OOM if its estimate exceeds the whole budget. */
+stab_status stab_server_submit(stab_server server, const stab_request* request, long long* id);
+
+/* Wait until request id has finished (timeout_s < 0: no limit).  TIMEOUT if it
+ * has not finished in time; INVALID_ARG for an unknown id. */
+stab_status stab_server_wait(stab_server server, long long id, double timeout_s);
+
+/* Results of a finished request: lambda (host complex128 nev, eigenvalues as
+ * stab_eigs orders them), resid (host nev), info; any may be NULL.  The
+ * request is forgotten afterwards.  BUSY if it has not finished. */
+stab_status stab_server_result(stab_server server, long long id, double* lambda, double* resid,
+                               stab_request_info* info);
+
+/* Peak admitted memory estimate and peak concurrent requests since creation; current queue and running counts. */
+stab_status stab_server_stats(stab_server server, long long* peak_bytes, int* peak_running, int* queued, int* running);
+
+/* Stop: requests not yet started finish with status BUSY; running ones complete; threads are joined. */
+void stab_server_destroy(stab_server server);
 
 #ifdef __cplusplus
 }

@@ -24,7 +24,9 @@ SYMBOLS = ["stab_default_opts", "stab_create", "stab_destroy", "stab_last_error"
            "stab_last_eps", "stab_solve", "stab_precond_build", "stab_precond_apply", "stab_precond_block",
            "stab_orthogonalize", "stab_eigs", "stab_get_stats", "stab_orthogonalize_noalloc", "stab_timing",
            "stab_timing_read", "stab_autotune", "stab_autotune_save", "stab_autotune_load",
-           "stab_set_line_config"]
+           "stab_set_line_config", "stab_trim_memory", "stab_estimate_bytes", "stab_eigs_batch",
+           "stab_server_create", "stab_server_submit", "stab_server_wait", "stab_server_result",
+           "stab_server_stats", "stab_server_destroy"]
 
 # stab_phase, in enum order
 PHASES = ["eps", "temperature", "line_y", "line_z", "line_x", "pointwise", "cgs2", "precond_apply"]
@@ -58,6 +60,27 @@ class Stats(ctypes.Structure):
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class EigJob(ctypes.Structure):
+    _fields_ = [("sigma_re", ctypes.c_double), ("sigma_im", ctypes.c_double), ("tau_re", ctypes.c_double),
+                ("tau_im", ctypes.c_double), ("nev", ctypes.c_int), ("ncv", ctypes.c_int), ("tol", ctypes.c_double),
+                ("v0", ctypes.c_void_p), ("lambda_", ctypes.POINTER(ctypes.c_double)), ("vecs", ctypes.c_void_p),
+                ("resid", ctypes.POINTER(ctypes.c_double)), ("nconv", ctypes.c_int), ("status", ctypes.c_int),
+                ("stats", Stats)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("base_flow", ctypes.POINTER(ctypes.c_double)), ("grid", Grid), ("Ma", ctypes.c_double),
+                ("Re", ctypes.c_double), ("Pr", ctypes.c_double), ("opts", ctypes.POINTER(Opts)),
+                ("sigma_re", ctypes.c_double), ("sigma_im", ctypes.c_double), ("tau_re", ctypes.c_double),
+                ("tau_im", ctypes.c_double), ("nev", ctypes.c_int), ("ncv", ctypes.c_int), ("tol", ctypes.c_double)]
+
+
+class RequestInfo(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("nconv", ctypes.c_int), ("queued_s", ctypes.c_double),
+                ("run_s", ctypes.c_double), ("latency_s", ctypes.c_double), ("est_bytes", ctypes.c_longlong),
+                ("stats", Stats)]
 
 
 _lib = None
@@ -96,10 +119,22 @@ def load():
     L.stab_autotune.argtypes = [vp, i, ctypes.POINTER(ctypes.c_int), dp]
     L.stab_autotune_save.argtypes = [ctypes.c_char_p]
     L.stab_set_line_config.argtypes = [vp, i, i, i]
+    L.stab_trim_memory.argtypes = []
+    L.stab_estimate_bytes.argtypes = [ctypes.POINTER(Grid), ctypes.POINTER(Opts), i, i, i]
+    L.stab_estimate_bytes.restype = ctypes.c_longlong
+    L.stab_eigs_batch.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(EigJob), i, i]
+    L.stab_server_create.argtypes = [ctypes.POINTER(vp), i, ctypes.c_longlong, i]
+    L.stab_server_submit.argtypes = [vp, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_longlong)]
+    L.stab_server_wait.argtypes = [vp, ctypes.c_longlong, d]
+    L.stab_server_result.argtypes = [vp, ctypes.c_longlong, dp, dp, ctypes.POINTER(RequestInfo)]
+    L.stab_server_stats.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_int),
+                                    ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
+    L.stab_server_destroy.argtypes = [vp]
     L.stab_autotune_load.argtypes = [ctypes.c_char_p]
     L.stab_timing_read.argtypes = [vp, dp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]
     for name in SYMBOLS:
-        if name not in ("stab_default_opts", "stab_destroy", "stab_last_error", "stab_size"):
+        if name not in ("stab_default_opts", "stab_destroy", "stab_last_error", "stab_size", "stab_estimate_bytes",
+                        "stab_server_destroy"):
             getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -288,3 +323,109 @@ def autotune_save(path: str) -> int:
 def autotune_load(path: str) -> int:
     """Read a tuning cache written by autotune_save; returns the entry count (-1: unreadable)."""
     return load().stab_autotune_load(path.encode())
+
+
+def _grid(grid) -> Grid:
+    return Grid(grid.dim, grid.nx, grid.ny, grid.nz, grid.lx, grid.ly0, grid.ly1, grid.lz, grid.stretch)
+
+
+def estimate_bytes(grid, nev: int, ncv: int, yonly: bool = True, **opts) -> int:
+    """Device memory estimate of one full solve (stab_estimate_bytes)."""
+    g = _grid(grid)
+    o = default_opts(**opts)
+    return int(load().stab_estimate_bytes(ctypes.byref(g), ctypes.byref(o), int(yonly), nev, ncv))
+
+
+def eigs_batch(handles, args, concurrency: int = 0):
+    """stab_eigs_batch: args[i] = (sigma, tau, nev, ncv, tol) for handles[i]; returns [EigResult]."""
+    L = load()
+    count = len(handles)
+    hs = (ctypes.c_void_p * count)(*[h._h.value for h in handles])
+    jobs = (EigJob * count)()
+    keep = []
+    for i, (sigma, tau, nev, ncv, tol) in enumerate(args):
+        lam = np.zeros(2 * nev)
+        res = np.zeros(nev)
+        keep.append((lam, res))
+        J = jobs[i]
+        J.sigma_re, J.sigma_im = complex(sigma).real, complex(sigma).imag
+        J.tau_re, J.tau_im = complex(tau).real, complex(tau).imag
+        J.nev, J.ncv, J.tol = nev, ncv, tol
+        J.lambda_ = lam.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        J.resid = res.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    st = L.stab_eigs_batch(hs, jobs, count, concurrency)
+    out = [EigResult(lam.view(np.complex128), res, jobs[i].nconv, jobs[i].status, jobs[i].stats.as_dict())
+           for i, (lam, res) in enumerate(keep)]
+    if st not in (0, 4):
+        raise StabError(st, "stab_eigs_batch: " + "; ".join(
+            L.stab_last_error(h._h).decode() for h, r in zip(handles, out) if r.status not in (0, 4)))
+    return out
+
+
+class Server:
+    """Continuous-batching stability server (stab_server_*) on the current CUDA device."""
+
+    def __init__(self, slots: int, mem_budget_bytes: int, autotune: bool = False):
+        self._L = load()
+        self._s = ctypes.c_void_p()
+        st = self._L.stab_server_create(ctypes.byref(self._s), slots, int(mem_budget_bytes), int(autotune))
+        if st != 0:
+            raise StabError(st, "stab_server_create failed")
+        self._nev = {}
+
+    def submit(self, base_flow, grid, Ma: float, Re: float, Pr: float, sigma: complex, tau: complex, nev: int,
+               ncv: int, tol: float, **opts) -> int:
+        bf = np.ascontiguousarray(np.asarray(base_flow, dtype=np.float64).reshape(-1))
+        o = default_opts(**opts)
+        q = Request()
+        q.base_flow = bf.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        q.grid = _grid(grid)
+        q.Ma, q.Re, q.Pr = Ma, Re, Pr
+        q.opts = ctypes.pointer(o)
+        q.sigma_re, q.sigma_im = complex(sigma).real, complex(sigma).imag
+        q.tau_re, q.tau_im = complex(tau).real, complex(tau).imag
+        q.nev, q.ncv, q.tol = nev, ncv, tol
+        rid = ctypes.c_longlong()
+        st = self._L.stab_server_submit(self._s, ctypes.byref(q), ctypes.byref(rid))
+        if st != 0:
+            raise StabError(st, "stab_server_submit failed")
+        self._nev[rid.value] = nev
+        return rid.value
+
+    def wait(self, rid: int, timeout_s: float = -1.0) -> bool:
+        st = self._L.stab_server_wait(self._s, rid, timeout_s)
+        if st not in (0, 7):
+            raise StabError(st, "stab_server_wait: unknown request")
+        return st == 0
+
+    def result(self, rid: int):
+        """(eigenvalues, residuals, info dict) of a finished request (forgotten afterwards)."""
+        nev = self._nev.pop(rid)
+        lam = np.zeros(2 * nev)
+        res = np.zeros(nev)
+        info = RequestInfo()
+        dp = ctypes.POINTER(ctypes.c_double)
+        st = self._L.stab_server_result(self._s, rid, lam.ctypes.data_as(dp), res.ctypes.data_as(dp),
+                                        ctypes.byref(info))
+        if st != 0:
+            self._nev[rid] = nev
+            raise StabError(st, "stab_server_result: not finished or unknown")
+        d = {k: getattr(info, k) for k, _ in info._fields_ if k != "stats"}
+        d["stats"] = info.stats.as_dict()
+        return lam.view(np.complex128), res, d
+
+    def stats(self) -> dict:
+        pb, pr, q, r = ctypes.c_longlong(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        self._L.stab_server_stats(self._s, ctypes.byref(pb), ctypes.byref(pr), ctypes.byref(q), ctypes.byref(r))
+        return {"peak_bytes": pb.value, "peak_running": pr.value, "queued": q.value, "running": r.value}
+
+    def close(self):
+        if getattr(self, "_s", None):
+            self._L.stab_server_destroy(self._s)
+            self._s = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -4,6 +4,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
 
 #include "internal.cuh"
@@ -43,22 +44,22 @@ extern "C" void stab_default_opts(stab_opts* o) {
 
 static void free_handle(stab_handle h) {
   if (!h) return;
-  cudaFree(h->d_q0);
-  cudaFree(h->d_btab);
-  cudaFree(h->d_metric);
-  cudaFree(h->d_bcflags);
-  cudaFree(h->d_scratch);
-  cudaFree(h->d_red);
-  cudaFree(h->d_gm);
-  cudaFree(h->d_ir);
-  cudaFree(h->d_pinv);
-  cudaFree(h->d_pblk);
-  cudaFree(h->d_coef);
-  cudaFree(h->d_coef_f);
-  cudaFree(h->d_btab_f);
+  dfree(h, h->d_q0);
+  dfree(h, h->d_btab);
+  dfree(h, h->d_metric);
+  dfree(h, h->d_bcflags);
+  dfree(h, h->d_scratch);
+  dfree(h, h->d_red);
+  dfree(h, h->d_gm);
+  dfree(h, h->d_ir);
+  dfree(h, h->d_pinv);
+  dfree(h, h->d_pblk);
+  dfree(h, h->d_coef);
+  dfree(h, h->d_coef_f);
+  dfree(h, h->d_btab_f);
   for (int a = 0; a < 3; ++a) {
-    cudaFree(h->ax[a].tab[0]);
-    cudaFree(h->d_dmat[a]);
+    dfree(h, h->ax[a].tab[0]);
+    dfree(h, h->d_dmat[a]);
   }
   for (cudaEvent_t e : h->timer.ev) cudaEventDestroy(e);
   if (h->gm_exec) cudaGraphExecDestroy(h->gm_exec);
@@ -106,11 +107,15 @@ extern "C" stab_status stab_create(stab_handle* out, const double* base_flow, in
   h->visc = Re > 0.0;
   h->opts = o;
   h->stream = (cudaStream_t)cuda_stream;
+  cudaGetDevice(&h->device);
   h->last_eps_mode = -1;
   // host copy of the base state: homogeneity test, norm, boundary flags
   std::vector<double> q0((size_t)h->n);
   cudaError_t e;
-  if (base_on_device) e = cudaMemcpy(q0.data(), base_flow, h->n * sizeof(double), cudaMemcpyDeviceToHost);
+  if (base_on_device) {
+    e = cudaMemcpyAsync(q0.data(), base_flow, h->n * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  }
   else { std::memcpy(q0.data(), base_flow, h->n * sizeof(double)); e = cudaSuccess; }
   if (e != cudaSuccess) { g_create_err = std::string("stab_create: copy of base_flow: ") + cudaGetErrorString(e); free_handle(h); return STAB_ERR_CUDA; }
   double nrm = 0.0;
@@ -129,9 +134,10 @@ extern "C" stab_status stab_create(stab_handle* out, const double* base_flow, in
   h->q0norm = std::sqrt(nrm);
   h->homog = homog;
   h->nbase = homog ? h->ny : h->npts;
-  e = cudaMalloc(&h->d_q0, h->n * sizeof(double));
-  if (e == cudaSuccess) e = cudaMemcpy(h->d_q0, q0.data(), h->n * sizeof(double), cudaMemcpyHostToDevice);
+  e = dalloc(h, &h->d_q0, h->n * sizeof(double));
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h->d_q0, q0.data(), h->n * sizeof(double), cudaMemcpyHostToDevice, h->stream);
   if (e == cudaSuccess) e = jv_setup(h, q0.data());
+  if (e == cudaSuccess) e = kry_init_attributes();
   if (e != cudaSuccess) {
     g_create_err = std::string("stab_create: ") + cudaGetErrorString(e);
     stab_status st = e == cudaErrorMemoryAllocation ? STAB_ERR_OOM : STAB_ERR_CUDA;
@@ -172,6 +178,51 @@ extern "C" stab_status stab_last_eps(stab_handle h, double* eps) {
   STAB_CUDA(h, cudaMemcpyAsync(eps, h->d_eps, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
   STAB_CUDA(h, cudaStreamSynchronize(h->stream));
   return STAB_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Device memory: one library-owned, stream-ordered pool per device.  Handles
+// allocate and free on their own stream (no device-wide synchronisation, so
+// handles on different streams run side by side); freed memory stays cached
+// in the pool for later handles until stab_trim_memory.
+namespace {
+std::mutex g_pool_mu;
+cudaMemPool_t g_pool[64] = {};
+}  // namespace
+
+cudaError_t dev_alloc(StabHandle* h, void** p, size_t bytes) {
+  *p = nullptr;
+  if (bytes == 0) return cudaSuccess;
+  const int dev = h->device;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  cudaMemPool_t pool;
+  {
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    if (!g_pool[dev]) {
+      cudaMemPoolProps props = {};
+      props.allocType = cudaMemAllocationTypePinned;
+      props.location.type = cudaMemLocationTypeDevice;
+      props.location.id = dev;
+      cudaError_t e = cudaMemPoolCreate(&g_pool[dev], &props);
+      if (e != cudaSuccess) { g_pool[dev] = nullptr; return e; }
+      unsigned long long keep = ~0ULL;
+      cudaMemPoolSetAttribute(g_pool[dev], cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    pool = g_pool[dev];
+  }
+  return cudaMallocFromPoolAsync(p, bytes, pool, h->stream);
+}
+
+void dev_free(StabHandle* h, void* p) {
+  if (p) cudaFreeAsync(p, h->stream);
+}
+
+extern "C" int stab_trim_memory(void) {
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  int count = 0;
+  for (int d = 0; d < 64; ++d)
+    if (g_pool[d] && cudaMemPoolTrimTo(g_pool[d], 0) == cudaSuccess) ++count;
+  return count;
 }
 
 // ---------------------------------------------------------------------------

@@ -88,6 +88,7 @@ struct StabHandle {
   double q0norm;
   stab_opts opts;
   cudaStream_t stream;
+  int device = 0;  // current device at stab_create; the handle's memory lives there
   Slots slots;
   AxisTables ax[3];
   // device memory
@@ -132,6 +133,16 @@ struct StabHandle {
   std::string err;
 };
 
+// api.cu: stream-ordered device memory from the library's pool on the
+// handle's stream (dalloc: typed wrapper).
+cudaError_t dev_alloc(StabHandle* h, void** p, size_t bytes);
+void dev_free(StabHandle* h, void* p);
+template <class T>
+inline cudaError_t dalloc(StabHandle* h, T** p, size_t bytes) {
+  return dev_alloc(h, (void**)p, bytes);
+}
+inline void dfree(StabHandle* h, const void* p) { dev_free(h, const_cast<void*>(p)); }
+
 // api.cu: phase timing.  phase_begin returns the interval's slot (or -1 when
 // not recording); phase_end records its closing event.
 int phase_begin(StabHandle* h, int phase);
@@ -160,6 +171,7 @@ cudaError_t kry_axpby(StabHandle* h, double2 a, const double2* x, double2 b, dou
 cudaError_t kry_copy(StabHandle* h, const double2* x, double2* y, long long n);
 cudaError_t kry_update_basis(StabHandle* h, double2* V, int m, int kk, long long n, const double2* d_Q, double2* tmp);
 int kry_partial_elems(long long n, int k);
+cudaError_t kry_init_attributes();
 cudaError_t kry_cgs2_stream(cudaStream_t st, const double2* V, int k, long long n, double2* w, double2* d_h,
                             double* d_norm, double2* partial, double* norm_partial, int norm_blocks);
 cudaError_t launch_norm2_stream(cudaStream_t st, const double2* v, long long n, double* partial, int nb,

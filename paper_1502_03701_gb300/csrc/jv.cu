@@ -828,7 +828,7 @@ cudaError_t jv_autotune(StabHandle* h, int force, double* ms_out) {
     std::vector<LineJob> jobs;
     const double2* src[6];
     if (!tmp) {
-      if ((err = cudaMalloc(&tmp, (size_t)h->n * sizeof(double2))) != cudaSuccess) break;
+      if ((err = dalloc(h, &tmp, (size_t)h->n * sizeof(double2))) != cudaSuccess) break;
       if ((err = cudaMemsetAsync(tmp, 0, (size_t)h->n * sizeof(double2), h->stream)) != cudaSuccess) break;
     }
     for (int f = 0; f < D + 2; ++f) src[f] = tmp + (long long)f * h->npts;
@@ -883,7 +883,7 @@ cudaError_t jv_autotune(StabHandle* h, int force, double* ms_out) {
   }
   if (tmp) {
     cudaStreamSynchronize(h->stream);
-    cudaFree(tmp);
+    dfree(h, tmp);
   }
   if (err != cudaSuccess) for (int ax = 0; ax < 3; ++ax) h->line_cfg[ax] = LineCfg{};
   return err;
@@ -999,8 +999,8 @@ cudaError_t jv_setup(StabHandle* h, const double* q0_host) {
     std::vector<double> host;
     fill_axis_tables(A, host);
     double* d;
-    if ((err = cudaMalloc(&d, host.size() * sizeof(double))) != cudaSuccess) return err;
-    cudaMemcpy(d, host.data(), host.size() * sizeof(double), cudaMemcpyHostToDevice);
+    if ((err = dalloc(h, &d, host.size() * sizeof(double))) != cudaSuccess) return err;
+    if ((err = cudaMemcpyAsync(d, host.data(), host.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream)) != cudaSuccess) return err;
     A.tab[0] = d;
     A.tab[1] = d + 3 * A.n;
   }
@@ -1018,8 +1018,8 @@ cudaError_t jv_setup(StabHandle* h, const double* q0_host) {
       met[j] = 1.0 / yp;
       met[h->ny + j] = -ypp / (yp * yp * yp);
     }
-    if ((err = cudaMalloc(&h->d_metric, met.size() * sizeof(double))) != cudaSuccess) return err;
-    cudaMemcpy(h->d_metric, met.data(), met.size() * sizeof(double), cudaMemcpyHostToDevice);
+    if ((err = dalloc(h, &h->d_metric, met.size() * sizeof(double))) != cudaSuccess) return err;
+    if ((err = cudaMemcpyAsync(h->d_metric, met.data(), met.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream)) != cudaSuccess) return err;
   }
   // non-reflective boundary flags from the base state (frozen switch)
   {
@@ -1040,20 +1040,20 @@ cudaError_t jv_setup(StabHandle* h, const double* q0_host) {
           bool dropc = top ? (v0 < 0.0) : (v0 > 0.0);
           fl[top * nxz + (long long)k * h->nx + i] = (in_plus ? 1 : 0) | (in_minus ? 2 : 0) | (dropc ? 4 : 0);
         }
-    if ((err = cudaMalloc(&h->d_bcflags, fl.size())) != cudaSuccess) return err;
-    cudaMemcpy(h->d_bcflags, fl.data(), fl.size(), cudaMemcpyHostToDevice);
+    if ((err = dalloc(h, &h->d_bcflags, fl.size())) != cudaSuccess) return err;
+    if ((err = cudaMemcpyAsync(h->d_bcflags, fl.data(), fl.size(), cudaMemcpyHostToDevice, h->stream)) != cudaSuccess) return err;
   }
   // scratch, reductions, eps
-  if ((err = cudaMalloc(&h->d_scratch, (size_t)h->slots.count * h->npts * sizeof(double2))) != cudaSuccess) return err;
+  if ((err = dalloc(h, &h->d_scratch, (size_t)h->slots.count * h->npts * sizeof(double2))) != cudaSuccess) return err;
   h->red_blocks = 1024;
-  if ((err = cudaMalloc(&h->d_red, (h->red_blocks + 64) * sizeof(double))) != cudaSuccess) return err;
+  if ((err = dalloc(h, &h->d_red, (h->red_blocks + 64) * sizeof(double))) != cudaSuccess) return err;
   h->d_eps = h->d_red + h->red_blocks;
   k_set_scalar<<<1, 1, 0, h->stream>>>(h->d_eps, 0.0);
   // base tables: derivatives of the base fields through the same passes
   const int nbt = bt_count(D);
-  if ((err = cudaMalloc(&h->d_btab, (size_t)nbt * h->nbase * sizeof(double))) != cudaSuccess) return err;
+  if ((err = dalloc(h, &h->d_btab, (size_t)nbt * h->nbase * sizeof(double))) != cudaSuccess) return err;
   double2* bv;
-  if ((err = cudaMalloc(&bv, (size_t)(h->nv + 1) * h->npts * sizeof(double2))) != cudaSuccess) return err;
+  if ((err = dalloc(h, &bv, (size_t)(h->nv + 1) * h->npts * sizeof(double2))) != cudaSuccess) return err;
   double2* bT = bv + (long long)h->nv * h->npts;
   int thr = 256;
   k_base_fields<<<grid_for(h->npts, thr), thr, 0, h->stream>>>(h->d_q0, h->npts, h->nv, h->R, 1.0 / h->gamma,
@@ -1091,21 +1091,21 @@ cudaError_t jv_setup(StabHandle* h, const double* q0_host) {
   if ((err = cudaGetLastError()) != cudaSuccess) return err;
   if (h->homog) {
     const int nw = pw::nw_inputs(D);
-    if ((err = cudaMalloc(&h->d_coef, (size_t)h->ny * (D + 2) * nw * sizeof(double))) != cudaSuccess) return err;
+    if ((err = dalloc(h, &h->d_coef, (size_t)h->ny * (D + 2) * nw * sizeof(double))) != cudaSuccess) return err;
     PointParams PP = point_params(h, nullptr);
     if (D == 2) k_coeffs<2><<<h->ny, 32, 0, h->stream>>>(PP, h->d_coef);
     else k_coeffs<3><<<h->ny, 64, 0, h->stream>>>(PP, h->d_coef);
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
-    if ((err = cudaMalloc(&h->d_coef_f, (size_t)h->ny * (D + 2) * nw * sizeof(double))) != cudaSuccess) return err;
+    if ((err = dalloc(h, &h->d_coef_f, (size_t)h->ny * (D + 2) * nw * sizeof(double))) != cudaSuccess) return err;
     if (D == 2) k_coeffs_fold<2><<<h->ny, 32, 0, h->stream>>>(h->d_coef, h->d_metric, h->d_metric + h->ny, h->ny, h->d_coef_f);
     else k_coeffs_fold<3><<<h->ny, 32, 0, h->stream>>>(h->d_coef, h->d_metric, h->d_metric + h->ny, h->ny, h->d_coef_f);
     const long long nbt = (long long)bt_count(D) * h->nbase;
-    if ((err = cudaMalloc(&h->d_btab_f, nbt * sizeof(float))) != cudaSuccess) return err;
+    if ((err = dalloc(h, &h->d_btab_f, nbt * sizeof(float))) != cudaSuccess) return err;
     k_to_float_tab<<<64, 256, 0, h->stream>>>(h->d_btab, h->d_btab_f, nbt);
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
   }
   if ((err = cudaStreamSynchronize(h->stream)) != cudaSuccess) return err;
-  cudaFree(bv);
+  dfree(h, bv);
   return cudaSuccess;
 }
 

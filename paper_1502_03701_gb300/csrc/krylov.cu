@@ -389,13 +389,13 @@ cudaError_t kry_copy(StabHandle* h, const double2* x, double2* y, long long n) {
 cudaError_t kry_update_basis(StabHandle* h, double2* V, int m, int kk, long long n, const double2* d_Q, double2* tmp) {
   const size_t smem = (size_t)m * kVqRows * sizeof(double2);
   if (smem > 200 * 1024) return cudaErrorInvalidValue;
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_vq, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    attr = true;
-  }
   k_vq<<<(unsigned)((n + kVqRows - 1) / kVqRows), kVqRows, smem, h->stream>>>(V, m, n, d_Q, kk, tmp);
   return cudaGetLastError();
+}
+
+// kernel attributes of this file, set for the current device at handle creation
+cudaError_t kry_init_attributes() {
+  return cudaFuncSetAttribute(k_vq, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
 }
 
 int kry_partial_elems(long long n, int k) {

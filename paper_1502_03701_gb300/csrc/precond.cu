@@ -293,10 +293,10 @@ cudaError_t ensure_dmats(StabHandle* h) {
     if (h->d_dmat[a]) continue;
     const int n = h->ax[a].n;
     double2* buf;
-    if ((e = cudaMalloc(&buf, (size_t)3 * n * n * sizeof(double2))) != cudaSuccess) return e;
+    if ((e = dalloc(h, &buf, (size_t)3 * n * n * sizeof(double2))) != cudaSuccess) return e;
     // [D1 | D2 | work]
     if ((e = jv_derivative_matrices(h, a, buf + (size_t)2 * n * n, buf, buf + (size_t)n * n)) != cudaSuccess) {
-      cudaFree(buf);
+      dfree(h, buf);
       return e;
     }
     h->d_dmat[a] = (double*)buf;
@@ -358,9 +358,9 @@ cudaError_t pc_build(StabHandle* h, double2 sigma) {
   const size_t esz = prec == 64 ? sizeof(double2) : sizeof(float2);
   const size_t bb = (size_t)g.bsz * g.bsz;
   if (!h->d_pinv || h->ntiles != g.ntiles || h->bsize != g.bsz || h->pprec != prec) {
-    cudaFree(h->d_pinv);
+    dfree(h, h->d_pinv);
     h->d_pinv = nullptr;
-    if ((e = cudaMalloc(&h->d_pinv, bb * g.ntiles * esz)) != cudaSuccess) return e;
+    if ((e = dalloc(h, &h->d_pinv, bb * g.ntiles * esz)) != cudaSuccess) return e;
     h->ntiles = g.ntiles;
     h->bsize = g.bsz;
     h->pprec = prec;
@@ -371,10 +371,10 @@ cudaError_t pc_build(StabHandle* h, double2 sigma) {
   if (batch < 1) batch = 1;
   if (batch > g.ntiles) batch = g.ntiles;
   if (prec == 32 && !h->d_pblk) {
-    if ((e = cudaMalloc(&h->d_pblk, bb * batch * sizeof(double2))) != cudaSuccess) return e;
+    if ((e = dalloc(h, &h->d_pblk, bb * batch * sizeof(double2))) != cudaSuccess) return e;
   }
   int* d_info;
-  if ((e = cudaMalloc(&d_info, sizeof(int))) != cudaSuccess) return e;
+  if ((e = dalloc(h, &d_info, sizeof(int))) != cudaSuccess) return e;
   cudaMemsetAsync(d_info, 0, sizeof(int), h->stream);
   AsmParams P = asm_params(h, g, sigma);
   const size_t smem = (size_t)2 * g.bsz * esz + g.bsz * sizeof(int);
@@ -398,7 +398,7 @@ cudaError_t pc_build(StabHandle* h, double2 sigma) {
   int info = 0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&info, d_info, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-  cudaFree(d_info);
+  dfree(h, d_info);
   if (e != cudaSuccess) return e;
   if (info) return cudaErrorInvalidValue;  // a singular block
   h->pvalid = true;
@@ -455,11 +455,11 @@ extern "C" stab_status stab_precond_block(stab_handle hh, double sr, double si, 
   Geo g;
   if (!out || !tile_geo(h, g) || t < 0 || t >= g.ntiles) { h->err = "stab_precond_block: bad tile or output"; return STAB_ERR_INVALID_ARG; }
   double2* d;
-  cudaError_t e = cudaMalloc(&d, (size_t)g.bsz * g.bsz * sizeof(double2));
+  cudaError_t e = dalloc(h, &d, (size_t)g.bsz * g.bsz * sizeof(double2));
   if (e == cudaSuccess) e = pc_block(h, make_double2(sr, si), t, d);
   if (e == cudaSuccess) e = cudaMemcpyAsync(out, d, (size_t)g.bsz * g.bsz * sizeof(double2), cudaMemcpyDeviceToHost, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-  cudaFree(d);
+  dfree(h, d);
   if (e != cudaSuccess) { h->err = std::string("stab_precond_block: ") + cudaGetErrorString(e); return STAB_ERR_CUDA; }
   return STAB_OK;
 }

@@ -43,10 +43,10 @@ inline double2 d2(cd z) { return make_double2(z.real(), z.imag()); }
 // grow-only device workspace
 double2* ensure(StabHandle* h, double2** p, size_t* have, size_t need) {
   if (*have >= need) return *p;
-  cudaFree(*p);
+  dfree(h, *p);
   *p = nullptr;
   *have = 0;
-  ck(h, cudaMalloc(p, need * sizeof(double2)), "workspace allocation");
+  ck(h, dalloc(h, p, need * sizeof(double2)), "workspace allocation");
   *have = need;
   return *p;
 }

@@ -47,3 +47,19 @@ def test_autotune_cache_file_roundtrip(tmp_path):
     lines = set(dst.read_text().split("\n"))
     assert "256 512 7 1 32 4" in lines and "512 256 5 0 16 2" in lines
     assert binding.autotune_load(str(tmp_path / "missing.txt")) == -1
+
+
+def test_memory_estimate_grows_with_the_problem():
+    """stab_estimate_bytes (host arithmetic only)."""
+    import stab_inputs as si
+    from paper_1502_03701_gb300 import estimate_bytes
+    g, _ = si.mixing_layer_2d(32, 64, Ma=0.3)
+    g2, _ = si.mixing_layer_2d(64, 128, Ma=0.3)
+    base = estimate_bytes(g, 4, 30, precond=0)
+    n = 4 * 32 * 64
+    assert base > (30 + 31 + 3) * n * 16        # Arnoldi and GMRES bases at least
+    assert estimate_bytes(g, 4, 40, precond=0) - base == 10 * n * 16 + (10 * n * 16) // 10
+    assert estimate_bytes(g, 4, 30, precond=1, tile=(8, 8)) > base + 32 * 256 * 256 * 8
+    fixed = 8 << 20                              # tables and alignment allowance
+    assert estimate_bytes(g2, 4, 30, precond=0) - fixed > 3.5 * (base - fixed)
+    assert estimate_bytes(g, 4, 30, yonly=False, precond=0) > base
