@@ -11,7 +11,12 @@ traffic (32 B per complex unknown).  Also reported, measured in the same run:
     exact-tangent J v): converged eigenpairs per second (true residual
     < 1e-8), the p50 / p99 solve latency and the J v count per solve;
   * "gmres_256x512": preconditioned FGMRES(50) iterations per second on the
-    256 x 512 layer (block-Jacobi over 8 x 8-point tiles, FP32 inverses).
+    256 x 512 layer (block-Jacobi over 8 x 8-point tiles, FP32 inverses);
+  * "many_small": uneven small layers solved one at a time on the plain FP64
+    path, as one mixed-precision batch (stab_eigs_batch), and as a Poisson
+    stream through the continuous-batching server (p50 / p99 latency).
+The line-pass launch shapes of the timed grid are autotuned first
+(--tune-cache FILE reuses and stores the tuned shapes).
 
 --workload eigs makes the 256 x 512 Cayley-IRAM solve the timed step (slow:
 its inner solves need thousands of preconditioned iterations each).
@@ -264,8 +269,8 @@ def gmres_throughput(args, Stab, torch, q0, g, f):
 LINE_FLOP_D1, LINE_FLOP_D2 = 10, 14
 FP64_PEAK_GFLOPS = 1250.0  # GB300 FP64 (non-tensor) nominal; 1.2 TFLOP/s measured by an FMA microbenchmark
 # DRAM bytes per launch of the line pass from ncu (dram__bytes_read.sum + dram__bytes_write.sum) on the
-# 512 x 1024 layer: y pass 42.5 + 12.6 MB, x pass 58.8 + 29.2 MB; scaled by grid points to the run's grid.
-LINE_TRAFFIC_512x1024 = {"line_y": (42.548480 + 12.626944) * 1e6, "line_x": (58.759680 + 29.232896) * 1e6}
+# 512 x 1024 layer (tuned shapes): y pass 42.5 + 12.5 MB, x pass 58.8 + 27.0 MB; scaled by grid points.
+LINE_TRAFFIC_512x1024 = {"line_y": (42.483712 + 12.522240) * 1e6, "line_x": (58.795520 + 26.962944) * 1e6}
 
 
 def line_pass_flops(g, visc: bool) -> dict:
@@ -313,6 +318,85 @@ def jv_roofline(g, f, phases: dict, step_s: float, hbm, tangent_s: float) -> dic
                          "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}}
 
 
+# Many small problems (uneven 2-D instances drawn like the 64-instance batch
+# configuration, with Nx in {16, 32}, Ny in {32, 64} so that the section ends
+# in seconds): Cayley-IRAM sigma 1, tau -1, 2 of 12, tol 1e-10, FGMRES(30) to
+# 1e-10 with block-Jacobi over 8 x 8 tiles, exact-tangent J v.
+FLEET_SIZES = dict(nxs=(16, 32), nys=(32, 64))
+FLEET_EIG = (1.0, -1.0, 2, 12, 1e-10)
+FLEET_OPTS = dict(eps_mode=2, precond=1, tile=(8, 8), gmres_m=30, gmres_tol=1e-10, max_restarts=60)
+
+
+def _fleet_problem(p):
+    g, _ = si.mixing_layer_2d(p["nx"], p["ny"])
+    f = si.Flow(float(p["Ma"]), float(p["Re"]))
+    return g, f, si.tanh_base_flow(g, f)
+
+
+def fleet(args, torch) -> dict:
+    """Plain one-at-a-time FP64 path vs batched mixed-precision path vs served Poisson stream."""
+    from paper_1502_03701_gb300 import Server, Stab, eigs_batch
+    insts = si.batched_instances(args.fleet, 1234, **FLEET_SIZES)
+    probs = [_fleet_problem(p) for p in insts]
+    nev = FLEET_EIG[2]
+
+    def good(lam_res):
+        return int(np.sum(lam_res[1] < RESID_OK))
+
+    # plain: one instance at a time, FP64 block inverses
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    plain, n_plain = [], 0
+    for g, f, q0 in probs:
+        S = Stab(q0, g, f.Ma, f.Re, f.Pr, precond_prec=64, **FLEET_OPTS)
+        r = S.eigs(*FLEET_EIG)
+        S.close()
+        plain.append((r.lam, r.resid))
+        n_plain += good((r.lam, r.resid)) if r.nconv == nev else 0
+    t_plain = time.perf_counter() - t0
+    # batched: FP32 block inverses (FP64 outer FGMRES, J v, Arnoldi, residuals), all side by side
+    t0 = time.perf_counter()
+    hs = [Stab(q0, g, f.Ma, f.Re, f.Pr, precond_prec=32, **FLEET_OPTS) for g, f, q0 in probs]
+    res = eigs_batch(hs, [FLEET_EIG] * len(hs), concurrency=len(hs))
+    for h in hs:
+        h.close()
+    t_batch = time.perf_counter() - t0
+    n_batch = sum(good((r.lam, r.resid)) for r in res if r.nconv == nev)
+    err = [float(np.max(np.abs(r.lam - p[0]) / np.abs(p[0]))) for r, p in zip(res, plain)]
+    # served: Poisson arrivals, continuous batching
+    arrivals = si.poisson_arrivals(len(probs), args.rate, 4321)
+    srv = Server(slots=args.slots, mem_budget_bytes=args.budget_gb << 30)
+    t0 = time.perf_counter()
+    ids = []
+    for (g, f, q0), ta in zip(probs, arrivals):
+        dt = t0 + ta - time.perf_counter()
+        if dt > 0:
+            time.sleep(dt)
+        ids.append(srv.submit(q0, g, f.Ma, f.Re, f.Pr, *FLEET_EIG, precond_prec=32, **FLEET_OPTS))
+    lat, n_srv = [], 0
+    for rid in ids:
+        srv.wait(rid)
+        lam, resid, info = srv.result(rid)
+        lat.append(info["latency_s"])
+        n_srv += good((lam, resid)) if info["nconv"] == nev else 0
+    t_srv = time.perf_counter() - t0
+    st = srv.stats()
+    srv.close()
+    lat.sort()
+    return {"workload": f"{len(probs)} uneven 2-D layers, Nx in {FLEET_SIZES['nxs']}, Ny in {FLEET_SIZES['nys']}, "
+                        "Ma U[0.1,0.9], Re log-U[500,5000], seed 1234",
+            "eig": {"sigma": 1.0, "tau": -1.0, "nev": nev, "ncv": FLEET_EIG[3], "tol": FLEET_EIG[4],
+                    "gmres": "FGMRES(30) to 1e-10, block-Jacobi 8x8"},
+            "plain_fp64_one_at_a_time": {"value": n_plain / t_plain, "unit": "eigenpairs/s", "seconds": t_plain},
+            "batched_mixed": {"value": n_batch / t_batch, "unit": "eigenpairs/s", "seconds": t_batch,
+                              "speedup_vs_plain": (n_batch / t_batch) / (n_plain / t_plain) if n_plain else None,
+                              "max_rel_diff_vs_plain_fp64": max(err)},
+            "served": {"value": n_srv / t_srv, "unit": "eigenpairs/s", "seconds": t_srv,
+                       "arrivals_per_s": args.rate, "slots": args.slots,
+                       "latency_ms": {"p50": lat[len(lat) // 2] * 1e3, "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))] * 1e3},
+                       "peak_running": st["peak_running"], "peak_bytes": st["peak_bytes"]}}
+
+
 def _time_jv(S, v, out, steps, flush, stream, torch):
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     for s in range(steps):
@@ -328,7 +412,7 @@ def run_ours(args):
     import torch
     import torch.distributed as dist
 
-    from paper_1502_03701_gb300 import Stab, build
+    from paper_1502_03701_gb300 import Stab, binding, build
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -357,6 +441,11 @@ def run_ours(args):
     g, f, q0 = _layer(args.nx, args.ny, 0.3)
     n = g.n
     Sj = Stab(q0, g, f.Ma, f.Re, f.Pr)
+    if args.tune_cache and os.path.exists(args.tune_cache):
+        binding.autotune_load(args.tune_cache)
+    tuned = Sj.autotune()                    # line-pass launch shapes for this grid (cached for St)
+    if args.tune_cache:
+        binding.autotune_save(args.tune_cache)
     St = Stab(q0, g, f.Ma, f.Re, f.Pr, eps_mode=2)
     v = torch.from_numpy(si.random_complex(11 + rank, n)).cuda()
     out = torch.empty_like(v)
@@ -383,6 +472,7 @@ def run_ours(args):
         ms_step = t_max / args.steps * 1e3
         roofline = jv_roofline(g, f, phases, sum(steps_t) / args.steps, hbm, statistics.mean(jv_tan))
         config = {"workload": f"jv_mixing_layer_{g.nx}x{g.ny}", "nx": g.nx, "ny": g.ny, "Ma": f.Ma, "Re": f.Re,
+                  "line_pass_shapes": {ax: [c, l] for ax, (c, l, _) in tuned.items()},
                   "eps_mode": "cancellation-free epsilon-quotient", "l2": "flushed between timed steps",
                   "parallelism": f"replicas{world}"}
         vh = torch.from_numpy(si.random_complex(11 + rank, n)).pin_memory()
@@ -405,6 +495,8 @@ def run_ours(args):
             extra["eigs"] = small_layer_eigs(args, Stab, torch, rank)
         if args.gmres_restarts > 0:
             extra["gmres_256x512"] = gmres_throughput(args, Stab, torch, q0, g, f)
+        if args.fleet > 0 and world == 1:
+            extra["many_small"] = fleet(args, torch)
     else:
         # roofline of the J v kernels from a short phase-timed sample (the solves below are host-driven)
         Sj.timing(True)
@@ -517,12 +609,17 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="jv", choices=["eigs", "jv"])
-    ap.add_argument("--eig-steps", type=int, default=3)
+    ap.add_argument("--eig-steps", type=int, default=2)
     ap.add_argument("--gmres-restarts", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--nx", type=int, default=256)
     ap.add_argument("--ny", type=int, default=512)
     ap.add_argument("--ref-jv-per-solve", type=int, default=20000)
+    ap.add_argument("--fleet", type=int, default=8, help="instances of the many-small-problems section (0: skip)")
+    ap.add_argument("--rate", type=float, default=50.0, help="Poisson arrival rate of the served stream (1/s)")
+    ap.add_argument("--slots", type=int, default=8)
+    ap.add_argument("--budget-gb", type=int, default=64)
+    ap.add_argument("--tune-cache", default="", help="line-pass tuning cache file to load before and save after tuning")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

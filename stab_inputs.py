@@ -159,15 +159,22 @@ LARGE_2D = dict(nx=256, ny=512, Ma=0.3, Re=1000.0, nev=10, ncv=60, gmres_m=50,
 LARGE_3D = dict(nx=128, ny=256, nz=64, Ma=0.3, Re=1000.0, nev=8, ncv=40, tile=(4, 4, 4))
 
 
-def batched_instances(count: int = 64, seed: int = 1234) -> list[dict]:
-    """Uneven 2-D instances: Nx in {32..256}, Ny in {64..512}, Ma ~ U[0.1, 0.9],
-    Re log-uniform on [500, 5000]."""
+def batched_instances(count: int = 64, seed: int = 1234, nxs=(32, 64, 128, 256),
+                      nys=(64, 128, 256, 512)) -> list[dict]:
+    """Uneven 2-D instances: Nx and Ny drawn uniformly from the sets (by default
+    {32..256} and {64..512}), Ma ~ U[0.1, 0.9], Re log-uniform on [500, 5000]."""
     u = splitmix64_uniform(seed, 4 * count) + 0.5
-    nxs = (32, 64, 128, 256)
-    nys = (64, 128, 256, 512)
     out = []
     for i in range(count):
-        out.append(dict(nx=nxs[min(3, int(u[4 * i] * 4))], ny=nys[min(3, int(u[4 * i + 1] * 4))],
+        out.append(dict(nx=nxs[min(len(nxs) - 1, int(u[4 * i] * len(nxs)))],
+                        ny=nys[min(len(nys) - 1, int(u[4 * i + 1] * len(nys)))],
                         Ma=0.1 + 0.8 * u[4 * i + 2],
                         Re=math.exp(math.log(500.0) + (math.log(5000.0) - math.log(500.0)) * u[4 * i + 3])))
     return out
+
+
+def poisson_arrivals(count: int, rate: float, seed: int = 4321) -> np.ndarray:
+    """Arrival times (s) of a Poisson stream: exponential gaps of mean 1/rate."""
+    u = splitmix64_uniform(seed, count) + 0.5          # [0, 1)
+    gaps = -np.log1p(-u) / rate
+    return np.cumsum(gaps)
