@@ -24,7 +24,9 @@ struct AxisTables {
   int periodic;
   double h;
   int K[2];             // warm-up length of a chunked sweep (influence decays below 2^-56)
-  double* tab[2];       // device: [l(n), dinv(n), m(n)] per kind
+  double pdinv[2];      // periodic: 1/c of the factorised circulant, per kind (folded into the stencil)
+  double* tab[2];       // device, per kind: [l'(n), dinv(n), m(n)]: Thomas factors of the sweep on the
+                        // right-hand side scaled by dinv (l'_t = l_t d_{t-1} / d_t)
 };
 
 struct LineJob {

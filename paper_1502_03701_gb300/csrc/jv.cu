@@ -130,7 +130,9 @@ __global__ void k_line_pass(const PassParams P) {
     const int t = idx % n;
     const int rest = idx / n;
     const int lt = rest % L, comp = (rest / L) & 1, kind = rest / (2 * L);
-    R[((size_t)(kind * 2 + comp) * L + lt) * LS + sidx(t)] = stencil_rhs(P, F + (size_t)comp * plane + (size_t)lt * LS, t, kind);
+    double r = stencil_rhs(P, F + (size_t)comp * plane + (size_t)lt * LS, t, kind);
+    if (!P.periodic) r *= __ldg(P.tab[kind] + n + t);  // bounded: row scale 1/d_t (periodic: in c1, c2)
+    R[((size_t)(kind * 2 + comp) * L + lt) * LS + sidx(t)] = r;
   }
   __syncthreads();
   // thread -> (chunk, line, comp, kind); x lines: chunk fastest, strided
@@ -145,7 +147,6 @@ __global__ void k_line_pass(const PassParams P) {
   const int t0 = ch * P.C, t1 = min(n, t0 + P.C);
   const int kk = kind < 2 ? kind : 0;
   const double* tl = P.tab[kk];
-  const double* tdinv = tl + n;
   const double* tm = tl + 2 * n;
   const int K = P.K[kk];
   const double* Rk = R + ((size_t)(kk * 2 + comp) * L + lt) * LS;
@@ -175,18 +176,18 @@ __global__ void k_line_pass(const PassParams P) {
     const long long base = line_base(P, l0 + lt);
     double* o = (double*)out + comp;
     if (P.periodic) {
-      const double di = __ldg(tdinv), mm = __ldg(tm);
+      const double mm = __ldg(tm);
       int te = t1 - 1 + K;
       int tt = wrap_small(te, n);
       for (int s = te; s >= t0; --s) {
-        x = fma(Gk[sidx(tt)], di, -mm * x);
+        x = fma(-mm, x, Gk[sidx(tt)]);
         if (s < t1) o[2 * (base + (long long)tt * P.stride)] = x;
         if (--tt < 0) tt = n - 1;
       }
     } else {
       const int te = (t1 - 1 + K > n - 9) ? n - 1 : t1 - 1 + K;
       for (int t = te; t >= t0; --t) {
-        x = fma(Gk[sidx(t)], __ldg(tdinv + t), -__ldg(tm + t) * x);
+        x = fma(-__ldg(tm + t), x, Gk[sidx(t)]);
         if (t < t1) o[2 * (base + (long long)t * P.stride)] = x;
       }
     }
@@ -620,6 +621,7 @@ static void fill_axis_tables(AxisTables& A, std::vector<double>& host) {
     if (A.periodic) {
       const double c = -al / r;  // circulant = c (1 - r S^-1)(1 - r S)
       for (int t = 0; t < n; ++t) { l[t] = -r; dinv[t] = 1.0 / c; m[t] = -r; }
+      A.pdinv[kind] = 1.0 / c;
     } else {
       std::vector<double> a(n, al), b(n, 1.0), cc(n, al);
       if (kind == 0) { cc[0] = 2.0; a[n - 1] = 2.0; a[1] = cc[1] = a[n - 2] = cc[n - 2] = 0.25; }
@@ -631,10 +633,11 @@ static void fill_axis_tables(AxisTables& A, std::vector<double>& host) {
       dinv[0] = 1.0 / d;
       m[0] = cc[0] / d;
       for (int t = 1; t < n; ++t) {
-        l[t] = a[t] / d;
-        d = b[t] - l[t] * cc[t - 1];
+        const double lt = a[t] / d, dprev = d;
+        d = b[t] - lt * cc[t - 1];
         dinv[t] = 1.0 / d;
         m[t] = cc[t] / d;
+        l[t] = lt * dprev * dinv[t];  // recurrence of the scaled forward sweep g'_t = g_t / d_t
       }
     }
   }
@@ -693,6 +696,11 @@ static cudaError_t run_pass(StabHandle* h, int axis, const PassParams& base_para
   P.c2[0] = (1.0 / 9.0) / (4.0 * A.h);
   P.c1[1] = (12.0 / 11.0) / (A.h * A.h);
   P.c2[1] = (3.0 / 11.0) / (4.0 * A.h * A.h);
+  if (A.periodic)  // the constant row scale 1/c of the factorised circulant
+    for (int k = 0; k < 2; ++k) {
+      P.c1[k] *= A.pdinv[k];
+      P.c2[k] *= A.pdinv[k];
+    }
 
   const int n = A.n;
   if (n > 2048) return cudaErrorInvalidValue;

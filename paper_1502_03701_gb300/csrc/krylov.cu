@@ -149,12 +149,27 @@ __device__ __forceinline__ void reduce_partials(const double2* partial, int nb, 
   }
 }
 
+// Columns with j % kFp64Every == kFp64Every - 1 are formed with native FP64
+// FMAs, the others in pair arithmetic: the pair path keeps the integer and
+// FP32 pipes busy, the FP64 pipe (1/58 of FP32 on GB300) takes the rest.
+constexpr int kFp64Every = 4;
+__device__ __forceinline__ bool fp64_column(int j) { return j % kFp64Every == kFp64Every - 1; }
+
 // sum over rows [q0, q1) of conj(x_i) w_i by one warp: exact FP32
-// two-products of the integer-split pairs, accumulated by two-sum; every
-// lane returns the warp's total.
+// two-products of the integer-split pairs, accumulated by two-sum (or FP64
+// FMAs for the FP64 columns); every lane returns the warp's total.
 __device__ __forceinline__ double2 warp_dot(const double2* __restrict__ x, const double2* __restrict__ w, long long q0,
-                                            long long q1) {
+                                            long long q1, bool fp64) {
   const int lane = threadIdx.x & 31;
+  if (fp64) {
+    double sr = 0.0, si = 0.0;
+    for (long long i = q0 + lane; i < q1; i += 32) {
+      const double2 a = x[i], b = w[i];
+      sr = fma(a.x, b.x, fma(a.y, b.y, sr));
+      si = fma(a.x, b.y, fma(-a.y, b.x, si));
+    }
+    return make_double2(warp_sum(sr), warp_sum(si));
+  }
   ffn sr{0.0f, 0.0f}, si{0.0f, 0.0f};
   for (long long i = q0 + lane; i < q1; i += 32) {
     const double2 av = x[i], bv = w[i];
@@ -177,7 +192,7 @@ __device__ __forceinline__ void block_dot_columns(const double2* __restrict__ V,
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   if (k >= nw) {
     for (int j = wid; j < k; j += nw) {
-      const double2 d = warp_dot(V + (long long)j * n, w, r0, r1);
+      const double2 d = warp_dot(V + (long long)j * n, w, r0, r1, fp64_column(j));
       if (lane == 0) partial_out[(long long)blockIdx.x * k + j] = d;
     }
     return;
@@ -187,7 +202,7 @@ __device__ __forceinline__ void block_dot_columns(const double2* __restrict__ V,
   if (wid < G * k) {
     const int j = wid / G, sg = wid - j * G;
     const long long len = r1 - r0;
-    d = warp_dot(V + (long long)j * n, w, r0 + len * sg / G, r0 + len * (sg + 1) / G);
+    d = warp_dot(V + (long long)j * n, w, r0 + len * sg / G, r0 + len * (sg + 1) / G, fp64_column(j));
   }
   if (lane == 0) red[wid] = d;
   __syncthreads();
@@ -203,19 +218,27 @@ __device__ __forceinline__ void block_dot_columns(const double2* __restrict__ V,
   __syncthreads();
 }
 
-// w_i -= sum_j V_j[i] h_j for one row, pair arithmetic; h as pairs in shared memory.
+// w_i -= sum_j V_j[i] h_j for one row: pair arithmetic with h as pairs in
+// shared memory, FP64 FMAs for the FP64 columns (h in FP64 in shared memory).
 __device__ __forceinline__ double2 row_update(const double2* __restrict__ V, int k, long long n, long long i,
-                                              const ffn* hre, const ffn* him, double2 wv) {
+                                              const double2* h64, const ffn* hre, const ffn* him, double2 wv) {
   ffn ar{0.0f, 0.0f}, ai{0.0f, 0.0f};
+  double dr = 0.0, di = 0.0;
   for (int j = 0; j < k; ++j) {
     const double2 a = V[(long long)j * n + i];
+    if (fp64_column(j)) {
+      const double2 c = h64[j];
+      dr = fma(a.x, c.x, fma(-a.y, c.y, dr));
+      di = fma(a.x, c.y, fma(a.y, c.x, di));
+      continue;
+    }
     const ffn xr = ff_split(a.x), xi = ff_split(a.y);
     ff_acc_prod(ar, xr, hre[j]);            // Re(a h) = ar hr - ai hi
     ff_acc_prod(ar, ff_negate(xi), him[j]);
     ff_acc_prod(ai, xr, him[j]);            // Im(a h) = ar hi + ai hr
     ff_acc_prod(ai, xi, hre[j]);
   }
-  return make_double2(wv.x - ff_to_d(ar), wv.y - ff_to_d(ai));
+  return make_double2(wv.x - (ff_to_d(ar) + dr), wv.y - (ff_to_d(ai) + di));
 }
 
 __device__ __forceinline__ void block_rows(long long n, long long& r0, long long& r1) {
@@ -252,7 +275,7 @@ __global__ void __launch_bounds__(kThreads) k_cgs2_b(const double2* __restrict__
   __syncthreads();
   long long r0, r1;
   block_rows(n, r0, r1);
-  for (long long i = r0 + threadIdx.x; i < r1; i += blockDim.x) w[i] = row_update(V, k, n, i, hre, him, w[i]);
+  for (long long i = r0 + threadIdx.x; i < r1; i += blockDim.x) w[i] = row_update(V, k, n, i, hs, hre, him, w[i]);
   __syncthreads();  // this block's rows of w are final; the dots below read only them
   block_dot_columns(V, k, n, r0, r1, w, partial2, red);
 }
@@ -280,7 +303,7 @@ __global__ void __launch_bounds__(kThreads) k_cgs2_c(const double2* __restrict__
   block_rows(n, r0, r1);
   double s = 0.0;
   for (long long i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
-    const double2 r = row_update(V, k, n, i, hre, him, w[i]);
+    const double2 r = row_update(V, k, n, i, hs, hre, him, w[i]);
     w[i] = r;
     s = fma(r.x, r.x, fma(r.y, r.y, s));
   }
