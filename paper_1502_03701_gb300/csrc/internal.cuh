@@ -118,6 +118,7 @@ struct StabHandle {
   double* d_dmat[3];     // dense 1-D derivative matrices [kind][n*n] per axis (assembly)
   double* d_coef;        // per-row tangent coefficients of the pointwise map (y-only base)
   double* d_coef_f;      // the same with the y metric folded in (inputs: eta-derivatives)
+  struct ffn* d_coef_p;  // d_coef_f as FP32 pairs (hi, lo), read by the pointwise kernel
   float* d_btab_f;       // FP32 copy of the base tables (for the O(eps) remainder)
   bool force_dn_path;    // use the full FP64 difference-number pointwise kernel
   // statistics

@@ -377,11 +377,12 @@ __global__ void k_coeffs(const PointParams P, double* coef) {
 
 
 // Inputs: raw line-pass outputs (eta-derivatives in y); the coefficients have
-// the y metric folded in (k_coeffs_fold).  FP64 product for the tangent part;
-// the O(eps) remainder in FP32 from integer-split inputs and FP32 base tables,
-// so the two halves use different pipes.
+// the y metric folded in (k_coeffs_fold) and are stored as FP32 pairs.  The
+// tangent part C_j w is formed with exact FP32 two-products of the pairs and
+// two-sum accumulation (~2^-47 relative per term), the O(eps) remainder in
+// FP32 from the inputs' high parts and FP32 base tables: no FP64 products.
 template <int D>
-__global__ void __launch_bounds__(128) k_point_fast(const PointParams P, const double* __restrict__ coef,
+__global__ void __launch_bounds__(128) k_point_fast(const PointParams P, const ffn* __restrict__ coefp,
                                                    const float* __restrict__ btab_f) {
   if (P.gate && *P.gate) return;
   constexpr int NW = pw::nw_inputs(D);
@@ -392,7 +393,7 @@ __global__ void __launch_bounds__(128) k_point_fast(const PointParams P, const d
     const int j = (int)((pt / P.nx) % P.ny);
     const bool bc_row = (j == 0 || j == P.ny - 1);
     const unsigned fl = bc_row ? P.bcflags[(j == P.ny - 1 ? (long long)P.nx * P.nz : 0)] : 0u;
-    const double* C = coef + (long long)j * (D + 2) * NW;
+    const float2* Cp = (const float2*)(coefp + (long long)j * (D + 2) * NW);
     auto S = [&](int slot) { return P.scratch[(long long)slot * P.npts + pt]; };
 #pragma unroll 1
     for (int part = 0; part < 2; ++part) {
@@ -413,19 +414,25 @@ __global__ void __launch_bounds__(128) k_point_fast(const PointParams P, const d
       for (int a = 0; a < D; ++a)
 #pragma unroll
         for (int c = 0; c < D; ++c) w[om + a * D + c] = (visc && a != c) ? pick(S(P.s_mix[a][c])) : 0.0;
+      ffn wp[NW];
+#pragma unroll
+      for (int q = 0; q < NW; ++q) wp[q] = ff_split(w[q]);
       double res[D + 2];
 #pragma unroll
       for (int a = 0; a < D + 2; ++a) {
-        double acc = 0.0;
+        ffn acc{0.0f, 0.0f};
 #pragma unroll
-        for (int q = 0; q < NW; ++q) acc = fma(__ldg(C + a * NW + q), w[q], acc);
-        res[a] = acc;
+        for (int q = 0; q < NW; ++q) {
+          const float2 c = __ldg(Cp + a * NW + q);
+          ff_acc_prod(acc, ffn{c.x, c.y}, wp[q]);
+        }
+        res[a] = ff_to_d(acc);
       }
       if (e != 0.0) {  // O(eps) remainder of the quotient, FP32, physical (metric-applied) inputs
         const float ey = ff_split(P.eta_y[j]).hi, eyy = ff_split(P.eta_yy[j]).hi;
         pw::WIn<D, float> Wf;
 #pragma unroll
-        for (int q = 0; q < NW; ++q) set_input<D, float>(Wf, q, ff_split(w[q]).hi);
+        for (int q = 0; q < NW; ++q) set_input<D, float>(Wf, q, wp[q].hi);
 #pragma unroll
         for (int f = 0; f < D + 3; ++f) Wf.d1[1][f] *= ey;
 #pragma unroll
@@ -478,6 +485,11 @@ __global__ void k_coeffs_fold(const double* coef, const double* eta_y, const dou
       if (i != k && (i == 1 || k == 1)) f[om + i * D + k] = c[om + i * D + k] * ey;
   double* o = out + ((long long)j * (D + 2) + a) * NW;
   for (int q = 0; q < NW; ++q) o[q] = f[q];
+}
+
+__global__ void k_split_pairs(const double* in, ffn* out, long long count) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (long long)gridDim.x * blockDim.x)
+    out[i] = ff_split(in[i]);
 }
 
 __global__ void k_to_float_tab(const double* in, float* out, long long count) {
@@ -1107,6 +1119,9 @@ cudaError_t jv_setup(StabHandle* h, const double* q0_host) {
     if ((err = dalloc(h, &h->d_coef_f, (size_t)h->ny * (D + 2) * nw * sizeof(double))) != cudaSuccess) return err;
     if (D == 2) k_coeffs_fold<2><<<h->ny, 32, 0, h->stream>>>(h->d_coef, h->d_metric, h->d_metric + h->ny, h->ny, h->d_coef_f);
     else k_coeffs_fold<3><<<h->ny, 32, 0, h->stream>>>(h->d_coef, h->d_metric, h->d_metric + h->ny, h->ny, h->d_coef_f);
+    const long long ncf = (long long)h->ny * (D + 2) * nw;
+    if ((err = dalloc(h, &h->d_coef_p, ncf * sizeof(ffn))) != cudaSuccess) return err;
+    k_split_pairs<<<64, 256, 0, h->stream>>>(h->d_coef_f, h->d_coef_p, ncf);
     const long long nbt = (long long)bt_count(D) * h->nbase;
     if ((err = dalloc(h, &h->d_btab_f, nbt * sizeof(float))) != cudaSuccess) return err;
     k_to_float_tab<<<64, 256, 0, h->stream>>>(h->d_btab, h->d_btab_f, nbt);
@@ -1161,8 +1176,8 @@ cudaError_t jv_apply(StabHandle* h, const double2* v, double2* out, double2 shif
   if ((err = run_derivatives(h, src)) != cudaSuccess) return err;
   const int tp = phase_begin(h, STAB_PHASE_POINTWISE);
   if (fast) {
-    if (D == 2) k_point_fast<2><<<grid_for(h->npts, thr), thr, 0, h->stream>>>(P, h->d_coef_f, h->d_btab_f);
-    else k_point_fast<3><<<grid_for(h->npts, thr), thr, 0, h->stream>>>(P, h->d_coef_f, h->d_btab_f);
+    if (D == 2) k_point_fast<2><<<grid_for(h->npts, thr), thr, 0, h->stream>>>(P, h->d_coef_p, h->d_btab_f);
+    else k_point_fast<3><<<grid_for(h->npts, thr), thr, 0, h->stream>>>(P, h->d_coef_p, h->d_btab_f);
   } else {
     if (D == 2) k_point<2><<<grid_for(h->npts, thr), thr, 0, h->stream>>>(P);
     else k_point<3><<<grid_for(h->npts, thr), thr, 0, h->stream>>>(P);
