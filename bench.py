@@ -472,7 +472,7 @@ def run_ours(args):
         ms_step = t_max / args.steps * 1e3
         roofline = jv_roofline(g, f, phases, sum(steps_t) / args.steps, hbm, statistics.mean(jv_tan))
         config = {"workload": f"jv_mixing_layer_{g.nx}x{g.ny}", "nx": g.nx, "ny": g.ny, "Ma": f.Ma, "Re": f.Re,
-                  "line_pass_shapes": {ax: [c, l] for ax, (c, l, _) in tuned.items()},
+                  "line_pass_shapes": {ax: {"C": c, "L": l, "kinds": k} for ax, (c, l, k, _) in tuned.items()},
                   "eps_mode": "cancellation-free epsilon-quotient", "l2": "flushed between timed steps",
                   "parallelism": f"replicas{world}"}
         vh = torch.from_numpy(si.random_complex(11 + rank, n)).pin_memory()

@@ -210,23 +210,26 @@ stab_status stab_timing_read(stab_handle h, double* ms, long long* count, long l
 
 /* Autotuner of the compact-derivative line pass (performance only; the paper
  * has no counterpart).  For every axis of h, times each admissible launch
- * shape (C = 16, 32 or 64 points per sweep chunk; L = 1..32 lines per CTA)
+ * shape (C = 16, 32 or 64 points per sweep chunk; L = 1..32 lines per CTA;
+ * the first and second derivatives side by side or one after the other)
  * with CUDA events on the handle's stream and keeps the fastest, in h and in a
  * process-wide cache keyed by device, line length, line count, job count and
  * boundary type; stab_create applies cached shapes to new handles.  force = 0
- * reuses a cached shape without timing.  cfg (host int[6], may be NULL)
- * receives (C, L) per axis (x, y, z; zeros for an absent z), ms (host
+ * reuses a cached shape without timing.  cfg (host int[9], may be NULL)
+ * receives (C, L, kinds) per axis (x, y, z; zeros for an absent z), ms (host
  * double[3], may be NULL) the tuned pass time per axis (-1 when cached).
  * The chunk length moves where the sweeps' warm-up starts, so results may
- * change at the rounding level (about 1e-16 relative); L changes nothing.
+ * change at the rounding level (about 1e-16 relative); L and kinds change nothing.
  * Allocates one temporary vector; synchronises the stream. */
 stab_status stab_autotune(stab_handle h, int force, int* cfg, double* ms);
 
 /* Pin the line-pass launch shape of one axis (0 x, 1 y, 2 z): C points per
- * sweep chunk (16, 32 or 64), L lines per CTA (1..32); C = L = 0 restores the
- * built-in default.  INVALID_ARG when the shape does not fit the line (more
- * than 1024 threads or the shared-memory limit). */
-stab_status stab_set_line_config(stab_handle h, int axis, int C, int L);
+ * sweep chunk (16, 32 or 64), L lines per CTA (1..32), kinds = 2 to sweep the
+ * first and second derivatives side by side or 1 to do them one after the
+ * other with half the shared memory; all zero restores the built-in default.
+ * INVALID_ARG when the shape does not fit the line (more than 1024 threads or
+ * the shared-memory limit). */
+stab_status stab_set_line_config(stab_handle h, int axis, int C, int L, int kinds);
 
 /* Handles take device memory from a library-owned, stream-ordered pool (one
  * per device; allocation and release are ordered on the handle's stream, so
@@ -236,7 +239,7 @@ stab_status stab_set_line_config(stab_handle h, int axis, int C, int L);
 int stab_trim_memory(void);
 
 /* Write / read the process-wide tuning cache as text ("n nlines njobs
- * periodic C L" per line; loaded entries apply to the current device).
+ * periodic C L kinds" per line; loaded entries apply to the current device).
  * Return the number of entries, or -1 if the file cannot be opened. */
 int stab_autotune_save(const char* path);
 int stab_autotune_load(const char* path);

@@ -118,7 +118,7 @@ def load():
     L.stab_timing.argtypes = [vp, i]
     L.stab_autotune.argtypes = [vp, i, ctypes.POINTER(ctypes.c_int), dp]
     L.stab_autotune_save.argtypes = [ctypes.c_char_p]
-    L.stab_set_line_config.argtypes = [vp, i, i, i]
+    L.stab_set_line_config.argtypes = [vp, i, i, i, i]
     L.stab_trim_memory.argtypes = []
     L.stab_estimate_bytes.argtypes = [ctypes.POINTER(Grid), ctypes.POINTER(Opts), i, i, i]
     L.stab_estimate_bytes.restype = ctypes.c_longlong
@@ -285,15 +285,15 @@ class Stab:
         return EigResult(lam.view(np.complex128), res, nconv.value, st, stats.as_dict())
 
     def autotune(self, force: bool = False) -> dict:
-        """Tune the line-pass launch shape per axis; {axis: (C, L, ms)} (ms -1: from the cache)."""
-        cfg = (ctypes.c_int * 6)()
+        """Tune the line-pass launch shape per axis; {axis: (C, L, kinds, ms)} (ms -1: from the cache)."""
+        cfg = (ctypes.c_int * 9)()
         ms = (ctypes.c_double * 3)()
         self._check(self._L.stab_autotune(self._h, int(bool(force)), cfg, ms))
-        return {ax: (cfg[2 * a], cfg[2 * a + 1], ms[a]) for a, ax in enumerate("xyz") if cfg[2 * a] > 0}
+        return {ax: (cfg[3 * a], cfg[3 * a + 1], cfg[3 * a + 2], ms[a]) for a, ax in enumerate("xyz") if cfg[3 * a] > 0}
 
-    def set_line_config(self, axis: int, C: int, L: int):
-        """Pin the line-pass shape of an axis (0 x, 1 y, 2 z); (0, 0) restores the default."""
-        self._check(self._L.stab_set_line_config(self._h, axis, C, L))
+    def set_line_config(self, axis: int, C: int, L: int, kinds: int):
+        """Pin the line-pass shape of an axis (0 x, 1 y, 2 z); (0, 0, 0) restores the default."""
+        self._check(self._L.stab_set_line_config(self._h, axis, C, L, kinds))
 
     def timing(self, enable: bool = True):
         """Start (discarding earlier records) or stop per-phase event timing."""

@@ -60,6 +60,7 @@ static void free_handle(stab_handle h) {
   dfree(h, h->d_btab_f);
   for (int a = 0; a < 3; ++a) {
     dfree(h, h->ax[a].tab[0]);
+    dfree(h, h->ax[a].tabf[0]);
     dfree(h, h->d_dmat[a]);
   }
   for (cudaEvent_t e : h->timer.ev) cudaEventDestroy(e);
@@ -285,26 +286,28 @@ extern "C" stab_status stab_autotune(stab_handle h, int force, int* cfg, double*
   STAB_CUDA(h, jv_autotune(h, force, t));
   if (cfg)
     for (int a = 0; a < 3; ++a) {
-      cfg[2 * a] = a < h->dim ? h->line_cfg[a].C : 0;
-      cfg[2 * a + 1] = a < h->dim ? h->line_cfg[a].L : 0;
+      cfg[3 * a] = a < h->dim ? h->line_cfg[a].C : 0;
+      cfg[3 * a + 1] = a < h->dim ? h->line_cfg[a].L : 0;
+      cfg[3 * a + 2] = a < h->dim ? h->line_cfg[a].kp : 0;
     }
   if (ms)
     for (int a = 0; a < 3; ++a) ms[a] = a < h->dim ? t[a] : 0.0;
   return STAB_OK;
 }
 
-extern "C" stab_status stab_set_line_config(stab_handle h, int axis, int C, int L) {
+extern "C" stab_status stab_set_line_config(stab_handle h, int axis, int C, int L, int kinds) {
   if (!h) return STAB_ERR_INVALID_ARG;
   if (axis < 0 || axis >= h->dim) { h->err = "stab_set_line_config: bad axis"; return STAB_ERR_INVALID_ARG; }
-  if (C == 0 && L == 0) { h->line_cfg[axis] = LineCfg{}; return STAB_OK; }
+  if (C == 0 && L == 0 && kinds == 0) { h->line_cfg[axis] = LineCfg{}; return STAB_OK; }
   const int n = h->ax[axis].n;
   const long long LS = n + (n >> 5) + 1;
   const int nch = (C > 0) ? (n + C - 1) / C : 0;
-  if ((C != 16 && C != 32 && C != 64) || L < 1 || L > 32 || 4 * nch * L > 1024 || 64 * LS * L > 200 * 1024) {
-    h->err = "stab_set_line_config: C must be 16, 32 or 64 and L in 1..32 within 1024 threads and 200 KB";
+  if ((C != 16 && C != 32 && C != 64) || L < 1 || L > 32 || kinds < 1 || kinds > 2 || 2 * kinds * nch * L > 1024 ||
+      (2 + 2 * kinds) * 8 * LS * L > 200 * 1024) {
+    h->err = "stab_set_line_config: C must be 16, 32 or 64, L in 1..32 and kinds 1 or 2, within 1024 threads and 200 KB";
     return STAB_ERR_INVALID_ARG;
   }
-  h->line_cfg[axis] = LineCfg{C, L};
+  h->line_cfg[axis] = LineCfg{C, L, kinds};
   return STAB_OK;
 }
 

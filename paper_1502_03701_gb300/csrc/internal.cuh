@@ -24,7 +24,9 @@ struct AxisTables {
   int periodic;
   double h;
   int K[2];             // warm-up length of a chunked sweep (influence decays below 2^-56)
+  int Wn[2];            // near part of the warm-up kept in FP64 (the rest runs in FP32)
   double pdinv[2];      // periodic: 1/c of the factorised circulant, per kind (folded into the stencil)
+  float* tabf[2];       // device FP32 copies [l'(n), m(n)] per kind (far warm-up)
   double* tab[2];       // device, per kind: [l'(n), dinv(n), m(n)]: Thomas factors of the sweep on the
                         // right-hand side scaled by dinv (l'_t = l_t d_{t-1} / d_t)
 };
@@ -61,9 +63,10 @@ struct GmGraphKey {
 };
 
 // Launch shape of the compact-derivative line pass along one axis: C points
-// per sweep chunk, L lines per CTA (0: built-in default).
+// per sweep chunk, L lines per CTA, kp derivative kinds at once (0: built-in
+// default).
 struct LineCfg {
-  int C = 0, L = 0;
+  int C = 0, L = 0, kp = 0;
 };
 
 // Event pairs around library phases (stab_timing); recording is a no-op

@@ -47,12 +47,15 @@ struct PassParams {
   long long nlines;
   long long stride;
   int L, C, nchunks;
+  int KP;  // derivative kinds processed at once (1 or 2)
   int LS;  // padded shared-memory line stride in doubles, n + n/32 + 1
   int periodic;
   double c1[2], c2[2];  // interior stencil weights per kind
   double h;
   const double* tab[2];
+  const float* tabf[2];  // FP32 copies [l'(n), m(n)] for the far part of the warm-up
   int K[2];
+  int Wn[2];             // near part of the warm-up kept in FP64
   const int* gate;  // when set and nonzero the launch does nothing (graph-captured GMRES after convergence)
 };
 
@@ -98,21 +101,35 @@ __device__ __forceinline__ double stencil_rhs(const PassParams& P, const double*
 
 constexpr long long kLineSmemMax = 200 * 1024;  // dynamic shared memory opt-in of k_line_pass
 
-// Shared memory (doubles): R[kind][comp][lt][LS], then F[comp][lt][LS]
-// aliased by G[kind][comp][lt][LS] once R is complete; LS = padded line
-// stride (33 doubles per 32-point chunk, plus one).
+// FP32 value of a double with integer operations (the FP64 pipe is the
+// bottleneck here): the high part of ff_split.
+__device__ __forceinline__ float d2f_hi(double d) { return ff_split(d).hi; }
+
+// Shared memory (doubles): F[comp][lt][LS] (the input lines) and
+// W[kind][comp][lt][LS] (right-hand side, then forward-sweep values, in
+// place); LS = padded line stride.  P.KP derivative kinds are done at once
+// (2: first and second side by side, more threads; 1: one after the other
+// with half the shared memory).  Per kind:
+//   1. W = right-hand side of the compact scheme, scaled by the pivots'
+//      reciprocals (stencil weights on periodic axes, 1/d_t on bounded);
+//   2. carry-in of each chunk's forward sweep: the recurrence over the K
+//      points before the chunk (read-only; far part in FP32, whose error is
+//      damped below 2^-56 by the near part of length Wn);
+//   3. forward sweep of the own chunk, in place (W becomes g');
+//   4. carry-in of the back substitution over the K points after the chunk;
+//   5. back substitution of the own chunk, written to global memory.
+// Threads: (kind, comp, line, chunk); x lines: chunk fastest, strided lines:
+// line fastest (neighbouring lines are neighbouring addresses).
 __global__ void k_line_pass(const PassParams P) {
   if (P.gate && *P.gate) return;
   extern __shared__ double sm[];
   const LineJob J = P.job[blockIdx.y];
-  const int n = P.n, L = P.L;
+  const int n = P.n, L = P.L, KP = P.KP;
   const int LS = P.LS;
-  const size_t plane = (size_t)L * LS;  // one (kind, comp) or (comp) plane
-  double* R = sm;                      // 4 planes
-  double* F = sm + 4 * plane;          // 2 planes
-  double* G = sm + 4 * plane;          // 4 planes (after R is built)
+  const size_t plane = (size_t)L * LS;
+  double* F = sm;              // 2 planes
+  double* W = sm + 2 * plane;  // 2 KP planes
   const long long l0 = (long long)blockIdx.x * L;
-  const bool need2 = J.out2 != nullptr;
 
   for (int idx = threadIdx.x; idx < n * L; idx += blockDim.x) {
     int lt, t;
@@ -123,72 +140,117 @@ __global__ void k_line_pass(const PassParams P) {
     F[(size_t)lt * LS + sidx(t)] = val.x;
     F[plane + (size_t)lt * LS + sidx(t)] = val.y;
   }
-  __syncthreads();
-  // compact right-hand sides, all points in parallel
-  const int nk = need2 ? 2 : 1;
-  for (int idx = threadIdx.x; idx < nk * 2 * L * n; idx += blockDim.x) {
-    const int t = idx % n;
-    const int rest = idx / n;
-    const int lt = rest % L, comp = (rest / L) & 1, kind = rest / (2 * L);
-    double r = stencil_rhs(P, F + (size_t)comp * plane + (size_t)lt * LS, t, kind);
-    if (!P.periodic) r *= __ldg(P.tab[kind] + n + t);  // bounded: row scale 1/d_t (periodic: in c1, c2)
-    R[((size_t)(kind * 2 + comp) * L + lt) * LS + sidx(t)] = r;
-  }
-  __syncthreads();
-  // thread -> (chunk, line, comp, kind); x lines: chunk fastest, strided
-  // lines: line fastest (neighbouring lines are neighbouring addresses)
   const int per = L * P.nchunks;
   const int ch = P.axis == 0 ? threadIdx.x % P.nchunks : (threadIdx.x / L) % P.nchunks;
   const int lt = P.axis == 0 ? (threadIdx.x / P.nchunks) % L : threadIdx.x % L;
   const int comp = (threadIdx.x / per) & 1;
-  const int kind = threadIdx.x / (2 * per);
-  double2* out = kind == 0 ? J.out1 : J.out2;
-  const bool active = kind < nk && out != nullptr && (l0 + lt) < P.nlines;
+  const int kt = threadIdx.x / (2 * per);  // this thread's kind within a group of KP
+  const bool active = kt < KP && (l0 + lt) < P.nlines;
   const int t0 = ch * P.C, t1 = min(n, t0 + P.C);
-  const int kk = kind < 2 ? kind : 0;
-  const double* tl = P.tab[kk];
-  const double* tm = tl + 2 * n;
-  const int K = P.K[kk];
-  const double* Rk = R + ((size_t)(kk * 2 + comp) * L + lt) * LS;
-  double* Gk = G + ((size_t)(kk * 2 + comp) * L + lt) * LS;
-  // forward sweep (reads R only; F is dead, so G may overwrite it)
-  if (active) {
+  const long long base = active ? line_base(P, l0 + lt) : 0;
+  const int nk = J.out2 ? 2 : 1;
+  for (int kb = 0; kb < nk; kb += KP) {
+    const int kg = min(KP, nk - kb);  // kinds in this group
+    __syncthreads();  // F complete / the previous group's W no longer read
+    for (int idx = threadIdx.x; idx < kg * 2 * L * n; idx += blockDim.x) {
+      const int t = idx % n;
+      const int rest = idx / n;
+      const int l = rest % L, c = (rest / L) & 1, k = rest / (2 * L);
+      double r = stencil_rhs(P, F + (size_t)c * plane + (size_t)l * LS, t, kb + k);
+      if (!P.periodic) r *= __ldg(P.tab[kb + k] + n + t);  // bounded: row scale 1/d_t (periodic: in c1, c2)
+      W[(size_t)(k * 2 + c) * plane + (size_t)l * LS + sidx(t)] = r;
+    }
+    __syncthreads();
+    const int kind = kb + kt;
+    const bool act = active && kt < kg;
+    double2* out = kind == 0 ? J.out1 : J.out2;
+    const double* tl = P.tab[kind & 1];
+    const double* tm = tl + 2 * n;
+    const float* tlf = P.tabf[kind & 1];
+    const float* tmf = tlf + n;
+    const int K = P.K[kind & 1], Wn = P.Wn[kind & 1];
+    double* Wk = W + (size_t)((kt & 1) * 2 + comp) * plane + (size_t)lt * LS;
+    // 2. forward carry-in g'_{t0-1}
     double g = 0.0;
-    if (P.periodic) {
-      const double lv = __ldg(tl);
-      int tt = wrap_small(t0 - K, n);
-      for (int s = t0 - K; s < t1; ++s) {
-        g = fma(-lv, g, Rk[sidx(tt)]);
-        if (s >= t0) Gk[sidx(tt)] = g;
-        if (++tt == n) tt = 0;
-      }
-    } else {
-      const int ts = (t0 - K < 8) ? 0 : t0 - K;
-      for (int t = ts; t < t1; ++t) {
-        g = fma(-__ldg(tl + t), g, Rk[sidx(t)]);
-        if (t >= t0) Gk[sidx(t)] = g;
+    if (act) {
+      if (P.periodic) {
+        const double lv = __ldg(tl);
+        const float lvf = __ldg(tlf);
+        float gf = 0.0f;
+        int tt = wrap_small(t0 - K, n);
+        int s = t0 - K;
+        for (; s < t0 - Wn; ++s) {
+          gf = fmaf(-lvf, gf, d2f_hi(Wk[sidx(tt)]));
+          if (++tt == n) tt = 0;
+        }
+        g = f2d_exact(gf);
+        for (; s < t0; ++s) {
+          g = fma(-lv, g, Wk[sidx(tt)]);
+          if (++tt == n) tt = 0;
+        }
+      } else if (t0 > 0) {
+        const int ts = (t0 - K < 8) ? 0 : t0 - K;
+        const int tw = max(ts, t0 - Wn);
+        float gf = 0.0f;
+        for (int t = ts; t < tw; ++t) gf = fmaf(-__ldg(tlf + t), gf, d2f_hi(Wk[sidx(t)]));
+        g = f2d_exact(gf);
+        for (int t = tw; t < t0; ++t) g = fma(-__ldg(tl + t), g, Wk[sidx(t)]);
       }
     }
-  }
-  __syncthreads();
-  if (active) {
-    double x = 0.0;
-    const long long base = line_base(P, l0 + lt);
-    double* o = (double*)out + comp;
-    if (P.periodic) {
-      const double mm = __ldg(tm);
-      int te = t1 - 1 + K;
-      int tt = wrap_small(te, n);
-      for (int s = te; s >= t0; --s) {
-        x = fma(-mm, x, Gk[sidx(tt)]);
-        if (s < t1) o[2 * (base + (long long)tt * P.stride)] = x;
-        if (--tt < 0) tt = n - 1;
+    __syncthreads();
+    // 3. forward sweep of the own chunk, in place
+    if (act) {
+      if (P.periodic) {
+        const double lv = __ldg(tl);
+        for (int t = t0; t < t1; ++t) {
+          g = fma(-lv, g, Wk[sidx(t)]);
+          Wk[sidx(t)] = g;
+        }
+      } else {
+        for (int t = t0; t < t1; ++t) {
+          g = fma(-__ldg(tl + t), g, Wk[sidx(t)]);
+          Wk[sidx(t)] = g;
+        }
       }
-    } else {
-      const int te = (t1 - 1 + K > n - 9) ? n - 1 : t1 - 1 + K;
-      for (int t = te; t >= t0; --t) {
-        x = fma(-__ldg(tm + t), x, Gk[sidx(t)]);
-        if (t < t1) o[2 * (base + (long long)t * P.stride)] = x;
+    }
+    __syncthreads();
+    // 4. back-substitution carry-in x_{t1}, 5. own chunk
+    if (act) {
+      double x = 0.0;
+      double* o = (double*)out + comp;
+      if (P.periodic) {
+        const double mm = __ldg(tm);
+        const float mmf = __ldg(tmf);
+        const int te = t1 - 1 + K;
+        int tt = wrap_small(te, n);
+        int s = te;
+        float xf = 0.0f;
+        for (; s > t1 - 1 + Wn; --s) {
+          xf = fmaf(-mmf, xf, d2f_hi(Wk[sidx(tt)]));
+          if (--tt < 0) tt = n - 1;
+        }
+        x = f2d_exact(xf);
+        for (; s >= t1; --s) {
+          x = fma(-mm, x, Wk[sidx(tt)]);
+          if (--tt < 0) tt = n - 1;
+        }
+        for (int t = t1 - 1; t >= t0; --t) {
+          x = fma(-mm, x, Wk[sidx(t)]);
+          o[2 * (base + (long long)t * P.stride)] = x;
+        }
+      } else {
+        if (t1 < n) {
+          const int te = (t1 - 1 + K > n - 9) ? n - 1 : t1 - 1 + K;
+          const int tw = min(te, t1 - 1 + Wn);
+          float xf = 0.0f;
+          for (int t = te; t > tw; --t) xf = fmaf(-__ldg(tmf + t), xf, d2f_hi(Wk[sidx(t)]));
+          x = f2d_exact(xf);
+          for (int t = tw; t >= t1; --t) x = fma(-__ldg(tm + t), x, Wk[sidx(t)]);
+        }
+        for (int t = t1 - 1; t >= t0; --t) {
+          x = fma(-__ldg(tm + t), x, Wk[sidx(t)]);
+          o[2 * (base + (long long)t * P.stride)] = x;
+        }
       }
     }
   }
@@ -630,6 +692,8 @@ static void fill_axis_tables(AxisTables& A, std::vector<double>& host) {
     const double al = kind == 0 ? 1.0 / 3.0 : 2.0 / 11.0;
     const double r = (-1.0 + std::sqrt(1.0 - 4.0 * al * al)) / (2.0 * al);
     A.K[kind] = (int)std::ceil(56.0 * std::log(2.0) / -std::log(std::fabs(r))) + 1;
+    // FP32 part of the warm-up: its relative error 2^-24 is damped by |r|^Wn <= 2^-32
+    A.Wn[kind] = (int)std::ceil(32.0 * std::log(2.0) / -std::log(std::fabs(r))) + 1;
     if (A.periodic) {
       const double c = -al / r;  // circulant = c (1 - r S^-1)(1 - r S)
       for (int t = 0; t < n; ++t) { l[t] = -r; dinv[t] = 1.0 / c; m[t] = -r; }
@@ -691,6 +755,10 @@ static cudaError_t run_pass(StabHandle* h, int axis, const PassParams& base_para
   P.h = A.h;
   P.tab[0] = A.tab[0];
   P.tab[1] = A.tab[1];
+  P.tabf[0] = A.tabf[0];
+  P.tabf[1] = A.tabf[1];
+  P.Wn[0] = A.Wn[0];
+  P.Wn[1] = A.Wn[1];
 
   P.K[0] = A.K[0];
   P.K[1] = A.K[1];
@@ -723,25 +791,30 @@ static cudaError_t run_pass(StabHandle* h, int axis, const PassParams& base_para
   const LineCfg cfg = contiguous_lines >= 0 ? LineCfg{} : h->line_cfg[axis];
   P.C = cfg.C > 0 ? cfg.C : 32;
   P.nchunks = (n + P.C - 1) / P.C;
-  if (4 * P.nchunks > 1024) return cudaErrorInvalidValue;
   P.LS = n + (n >> 5) + 1;
   const long long LS = P.LS;
-  const int maxL = std::min<long long>(std::min(1024 / (4 * P.nchunks), 32), kLineSmemMax / (8 * 8 * LS));
+  // default kinds at once: both when two CTAs of 32 lines' worth of work fit
+  // (short lines, small grids: latency matters), else one after the other
+  const long long fill = (P.nlines * (long long)jobs.size() + 2 * 152 - 1) / (2 * 152);
+  P.KP = cfg.kp > 0 ? cfg.kp : (fill <= 4 ? 2 : 1);
+  const int tpl = 2 * P.KP * P.nchunks;  // threads per line
+  if (tpl > 1024) return cudaErrorInvalidValue;
+  const long long smem_line = (2 + 2 * P.KP) * 8 * LS;
+  const int maxL = std::min<long long>(std::min(1024 / tpl, 32), kLineSmemMax / smem_line);
   if (maxL < 1) return cudaErrorInvalidValue;
   int L;
   if (cfg.L > 0) {
     L = std::min(cfg.L, maxL);
   } else {
-    L = std::min<long long>(maxL, 98304 / (8 * 8 * LS));
-    const long long fill = (P.nlines * (long long)jobs.size() + 2 * 152 - 1) / (2 * 152);
-    const int Lwarp = (32 + 4 * P.nchunks - 1) / (4 * P.nchunks);
+    L = std::min<long long>(maxL, 98304 / smem_line);
+    const int Lwarp = (32 + tpl - 1) / tpl;
     if (L > fill) L = (int)std::min<long long>(maxL, std::max<long long>(fill, Lwarp));
   }
   if (L < 1) L = 1;
   P.L = L;
-  int threads = 4 * L * P.nchunks;
+  int threads = tpl * L;
   threads = ((threads + 31) / 32) * 32;
-  size_t smem = (size_t)8 * LS * L * sizeof(double);
+  size_t smem = (size_t)smem_line * L;
   for (size_t j0 = 0; j0 < jobs.size(); j0 += STAB_MAX_JOBS) {
     P.njobs = (int)std::min<size_t>(STAB_MAX_JOBS, jobs.size() - j0);
     for (int q = 0; q < P.njobs; ++q) P.job[q] = jobs[j0 + q];
@@ -871,25 +944,28 @@ cudaError_t jv_autotune(StabHandle* h, int force, double* ms_out) {
     LineCfg best{};
     double best_ms = 1e300;
     const int n = h->ax[ax].n;
-    for (int C : {16, 32, 64}) {
-      if (C > 16 && C >= 2 * n) continue;
-      for (int L : {1, 2, 4, 8, 16, 32}) {
-        const int nch = (n + C - 1) / C;
-        const long long LS = n + (n >> 5) + 1;
-        if (4 * nch * L > 1024 || 8 * 8 * LS * L > kLineSmemMax) continue;
-        h->line_cfg[ax] = LineCfg{C, L};
-        if ((err = run_pass(h, ax, P, jobs)) != cudaSuccess) break;  // warm-up
-        float t[5];
-        for (int r = 0; r < 5 && err == cudaSuccess; ++r) {
-          cudaEventRecord(e0, h->stream);
-          err = run_pass(h, ax, P, jobs);
-          cudaEventRecord(e1, h->stream);
-          cudaEventSynchronize(e1);
-          cudaEventElapsedTime(&t[r], e0, e1);
+    for (int kp : {1, 2}) {
+      for (int C : {16, 32, 64}) {
+        if (C > 16 && C >= 2 * n) continue;
+        for (int L : {1, 2, 4, 8, 16, 32}) {
+          const int nch = (n + C - 1) / C;
+          const long long LS = n + (n >> 5) + 1;
+          if (2 * kp * nch * L > 1024 || (2 + 2 * kp) * 8 * LS * L > kLineSmemMax) continue;
+          h->line_cfg[ax] = LineCfg{C, L, kp};
+          if ((err = run_pass(h, ax, P, jobs)) != cudaSuccess) break;  // warm-up
+          float t[5];
+          for (int r = 0; r < 5 && err == cudaSuccess; ++r) {
+            cudaEventRecord(e0, h->stream);
+            err = run_pass(h, ax, P, jobs);
+            cudaEventRecord(e1, h->stream);
+            cudaEventSynchronize(e1);
+            cudaEventElapsedTime(&t[r], e0, e1);
+          }
+          if (err != cudaSuccess) break;
+          std::sort(t, t + 5);
+          if (t[2] < best_ms) { best_ms = t[2]; best = LineCfg{C, L, kp}; }
         }
         if (err != cudaSuccess) break;
-        std::sort(t, t + 5);
-        if (t[2] < best_ms) { best_ms = t[2]; best = LineCfg{C, L}; }
       }
       if (err != cudaSuccess) break;
     }
@@ -909,15 +985,15 @@ cudaError_t jv_autotune(StabHandle* h, int force, double* ms_out) {
   return err;
 }
 
-// cache file: one line per entry, "n nlines njobs periodic C L" (device 0 entries are
+// cache file: one line per entry, "n nlines njobs periodic C L kinds" (entries are
 // applied to the current device when loaded)
 int jv_tune_save(const char* path) {
   FILE* f = std::fopen(path, "w");
   if (!f) return -1;
   std::lock_guard<std::mutex> lk(g_tune_mu);
   for (const auto& kv : g_tune)
-    std::fprintf(f, "%d %lld %d %d %d %d\n", kv.first.n, kv.first.nlines, kv.first.njobs, kv.first.periodic,
-                 kv.second.C, kv.second.L);
+    std::fprintf(f, "%d %lld %d %d %d %d %d\n", kv.first.n, kv.first.nlines, kv.first.njobs, kv.first.periodic,
+                 kv.second.C, kv.second.L, kv.second.kp);
   std::fclose(f);
   return (int)g_tune.size();
 }
@@ -931,8 +1007,8 @@ int jv_tune_load(const char* path) {
   TuneKey k;
   LineCfg c;
   std::lock_guard<std::mutex> lk(g_tune_mu);
-  while (std::fscanf(f, "%d %lld %d %d %d %d", &k.n, &k.nlines, &k.njobs, &k.periodic, &c.C, &c.L) == 6) {
-    if (c.C < 1 || c.L < 1 || k.n < 1) continue;
+  while (std::fscanf(f, "%d %lld %d %d %d %d %d", &k.n, &k.nlines, &k.njobs, &k.periodic, &c.C, &c.L, &c.kp) == 7) {
+    if (c.C < 1 || c.L < 1 || c.kp < 1 || c.kp > 2 || k.n < 1) continue;
     k.dev = dev;
     g_tune[k] = c;
     ++count;
@@ -1015,6 +1091,7 @@ cudaError_t jv_setup(StabHandle* h, const double* q0_host) {
     A.periodic = ax != 1;
     A.h = ax == 0 ? h->lx / h->nx : ax == 1 ? 1.0 / (h->ny - 1) : (D == 3 ? h->lz / h->nz : 1.0);
     A.tab[0] = A.tab[1] = nullptr;
+    A.tabf[0] = A.tabf[1] = nullptr;
     if (ax >= D) continue;
     std::vector<double> host;
     fill_axis_tables(A, host);
@@ -1023,6 +1100,19 @@ cudaError_t jv_setup(StabHandle* h, const double* q0_host) {
     if ((err = cudaMemcpyAsync(d, host.data(), host.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream)) != cudaSuccess) return err;
     A.tab[0] = d;
     A.tab[1] = d + 3 * A.n;
+    std::vector<float> hf((size_t)4 * A.n);
+    for (int k = 0; k < 2; ++k)
+      for (int t = 0; t < A.n; ++t) {
+        hf[(size_t)k * 2 * A.n + t] = (float)host[(size_t)k * 3 * A.n + t];               // l'
+        hf[(size_t)k * 2 * A.n + A.n + t] = (float)host[(size_t)k * 3 * A.n + 2 * A.n + t];  // m
+      }
+    float* df;
+    if ((err = dalloc(h, &df, hf.size() * sizeof(float))) != cudaSuccess) return err;
+    if ((err = cudaMemcpyAsync(df, hf.data(), hf.size() * sizeof(float), cudaMemcpyHostToDevice, h->stream)) != cudaSuccess)
+      return err;
+    if ((err = cudaStreamSynchronize(h->stream)) != cudaSuccess) return err;  // host vectors go out of scope
+    A.tabf[0] = df;
+    A.tabf[1] = df + 2 * A.n;
   }
   // metric eta_y = 1/y', eta_yy = -y''/y'^3
   {

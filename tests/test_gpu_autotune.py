@@ -28,24 +28,27 @@ def test_every_line_shape_matches_oracle(orc, name, g, f):
     dv = torch.from_numpy(v).cuda()
     out = torch.empty_like(dv)
     tried = 0
-    for C in (16, 32, 64):
-        for L in (1, 3, 8, 32):
-            ok = True
-            for ax in range(g.dim):
-                try:
-                    S.set_line_config(ax, C, L)
-                except StabError:
-                    ok = False
-            if not ok:
-                continue
-            S.apply_J(dv, out)
-            got = out.cpu().numpy()
-            assert max_rel_err(got, ref) < TOL, (C, L)
-            assert rel_err(got, ref) < TOL, (C, L)
-            tried += 1
-    assert tried >= 6
+    for kinds in (1, 2):
+        for C in (16, 32, 64):
+            for L in (1, 3, 8, 32):
+                ok = True
+                for ax in range(g.dim):
+                    try:
+                        S.set_line_config(ax, C, L, kinds)
+                    except StabError:
+                        ok = False
+                if not ok:
+                    continue
+                S.apply_J(dv, out)
+                got = out.cpu().numpy()
+                assert max_rel_err(got, ref) < TOL, (C, L, kinds)
+                assert rel_err(got, ref) < TOL, (C, L, kinds)
+                tried += 1
+    assert tried >= 12
     with pytest.raises(StabError):
-        S.set_line_config(0, 24, 1)
+        S.set_line_config(0, 24, 1, 1)
+    with pytest.raises(StabError):
+        S.set_line_config(0, 32, 1, 3)
     S.close()
 
 
@@ -57,8 +60,8 @@ def test_autotune_picks_a_shape_and_shares_it(orc):
     S = Stab(q0, g, f.Ma, f.Re, f.Pr, eps_mode=2)
     res = S.autotune(force=True)
     assert set(res) == {"x", "y"}
-    for C, L, ms in res.values():
-        assert C in (16, 32, 64) and 1 <= L <= 32 and ms > 0
+    for C, L, kinds, ms in res.values():
+        assert C in (16, 32, 64) and 1 <= L <= 32 and kinds in (1, 2) and ms > 0
     v = si.random_complex(302, g.n)
     dv = torch.from_numpy(v).cuda()
     out = torch.empty_like(dv)
@@ -68,7 +71,7 @@ def test_autotune_picks_a_shape_and_shares_it(orc):
     S2 = Stab(q0, g, f.Ma, f.Re, f.Pr, eps_mode=2)
     res2 = S2.autotune(force=False)
     for ax in res:
-        assert res2[ax][:2] == res[ax][:2] and res2[ax][2] == -1.0
+        assert res2[ax][:3] == res[ax][:3] and res2[ax][3] == -1.0
     # the cached shape is applied at creation: identical results bit for bit
     out2 = torch.empty_like(dv)
     S3 = Stab(q0, g, f.Ma, f.Re, f.Pr, eps_mode=2)
