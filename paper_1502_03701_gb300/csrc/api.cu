@@ -80,6 +80,10 @@ extern "C" stab_status stab_create(stab_handle* out, const double* base_flow, in
     g_create_err = "stab_create: need dim 2 (nz = 1) or 3, and nx, ny (nz in 3-D) >= 6";
     return STAB_ERR_INVALID_ARG;
   }
+  if ((long long)g.nx * g.ny * g.nz >= (1ll << 31)) {
+    g_create_err = "stab_create: at most 2^31 - 1 grid points";
+    return STAB_ERR_INVALID_ARG;
+  }
   if (!(g.lx > 0) || !(g.ly1 > g.ly0) || (g.dim == 3 && !(g.lz > 0)) || g.stretch < 0 || !(Ma > 0) || !(Pr > 0)) {
     g_create_err = "stab_create: invalid lengths, stretch, Mach or Prandtl number";
     return STAB_ERR_INVALID_ARG;

@@ -40,6 +40,29 @@ namespace {
 // warm-up of K points, after which the influence of the unknown start value
 // has decayed below 2^-56), then backward.
 // ---------------------------------------------------------------------------
+// Division by an invariant divisor with a multiply and a shift (Granlund and
+// Montgomery, "Division by invariant integers using multiplication", 1994):
+// p = 31 + ceil(log2 d), m = ceil(2^p / d), x / d = umulhi(x, m) >> (p - 32)
+// for 0 <= x < 2^31.
+struct FastDiv {
+  unsigned d, m;
+  int s;
+};
+inline FastDiv make_fastdiv(unsigned d) {
+  FastDiv f{d, 0u, 0};
+  if (d > 1) {
+    int l = 0;
+    while ((1ull << l) < d) ++l;
+    const int p = 31 + l;
+    f.m = (unsigned)(((1ull << p) + d - 1) / d);
+    f.s = p - 32;
+  }
+  return f;
+}
+__device__ __forceinline__ unsigned fdiv(unsigned x, const FastDiv& f) {
+  return f.d == 1 ? x : (__umulhi(x, f.m) >> f.s);
+}
+
 struct PassParams {
   LineJob job[STAB_MAX_JOBS];
   int njobs;
@@ -48,7 +71,8 @@ struct PassParams {
   long long stride;
   int L, C, nchunks;
   int KP;  // derivative kinds processed at once (1 or 2)
-  int LS;  // padded shared-memory line stride in doubles, n + n/32 + 1
+  int LS;
+  FastDiv divn, divL, divnx;  // division by n, L and nx  // padded shared-memory line stride in doubles, n + n/32 + 1
   int periodic;
   double c1[2], c2[2];  // interior stencil weights per kind
   double h;
@@ -61,7 +85,10 @@ struct PassParams {
 
 __device__ __forceinline__ long long line_base(const PassParams& P, long long l) {
   if (P.axis == 0) return l * P.nx;
-  if (P.axis == 1) return (l / P.nx) * (long long)P.nx * P.ny + (l % P.nx);
+  if (P.axis == 1) {  // l < 2^31 (grids have fewer than 2^31 points)
+    const long long q = fdiv((unsigned)l, P.divnx);
+    return q * (long long)P.nx * P.ny + (l - q * P.nx);
+  }
   return l;
 }
 
@@ -133,7 +160,7 @@ __global__ void k_line_pass(const PassParams P) {
 
   for (int idx = threadIdx.x; idx < n * L; idx += blockDim.x) {
     int lt, t;
-    if (P.axis == 0) { lt = idx / n; t = idx - lt * n; } else { t = idx / L; lt = idx - t * L; }
+    if (P.axis == 0) { lt = (int)fdiv(idx, P.divn); t = idx - lt * n; } else { t = (int)fdiv(idx, P.divL); lt = idx - t * L; }
     const long long l = l0 + lt;
     double2 val = make_double2(0.0, 0.0);
     if (l < P.nlines) val = J.in[line_base(P, l) + (long long)t * P.stride];
@@ -153,9 +180,10 @@ __global__ void k_line_pass(const PassParams P) {
     const int kg = min(KP, nk - kb);  // kinds in this group
     __syncthreads();  // F complete / the previous group's W no longer read
     for (int idx = threadIdx.x; idx < kg * 2 * L * n; idx += blockDim.x) {
-      const int t = idx % n;
-      const int rest = idx / n;
-      const int l = rest % L, c = (rest / L) & 1, k = rest / (2 * L);
+      const int rest = (int)fdiv(idx, P.divn);
+      const int t = idx - rest * n;
+      const int r2 = (int)fdiv(rest, P.divL);
+      const int l = rest - r2 * L, c = r2 & 1, k = r2 >> 1;
       double r = stencil_rhs(P, F + (size_t)c * plane + (size_t)l * LS, t, kb + k);
       if (!P.periodic) r *= __ldg(P.tab[kb + k] + n + t);  // bounded: row scale 1/d_t (periodic: in c1, c2)
       W[(size_t)(k * 2 + c) * plane + (size_t)l * LS + sidx(t)] = r;
@@ -326,14 +354,21 @@ struct PointParams {
   double2 shift;
   pw::Phys phys;
   const int* gate;  // as PassParams::gate
+  FastDiv divnx, divny;  // division by nx and ny (points < 2^31)
 };
+
+// y index of grid point pt ([z][y][x] order)
+__device__ __forceinline__ int row_of(const PointParams& P, long long pt) {
+  const unsigned r = fdiv((unsigned)pt, P.divnx);
+  return (int)(r - fdiv(r, P.divny) * P.ny);
+}
 
 __global__ void k_temperature(const PointParams P, double2* Tw) {
   if (P.gate && *P.gate) return;
   const int D = P.nz > 1 ? 3 : 2;
   const double e = *P.eps;
   for (long long pt = (long long)blockIdx.x * blockDim.x + threadIdx.x; pt < P.npts; pt += (long long)gridDim.x * blockDim.x) {
-    int j = (int)((pt / P.nx) % P.ny);
+    int j = row_of(P, pt);
     long long b = P.homog ? j : pt;
     double ip0 = P.btab[bt_extra(D, pw::X_IP) * P.nbase + b];
     double T0 = P.btab[bt_val(D, D + 2) * P.nbase + b];
@@ -351,7 +386,7 @@ __global__ void __launch_bounds__(128) k_point(const PointParams P) {
   const bool visc = P.phys.visc;
   for (long long pt = (long long)blockIdx.x * blockDim.x + threadIdx.x; pt < P.npts; pt += (long long)gridDim.x * blockDim.x) {
     const int i = (int)(pt % P.nx);
-    const int j = (int)((pt / P.nx) % P.ny);
+    const int j = row_of(P, pt);
     const int k = (int)(pt / ((long long)P.nx * P.ny));
     const long long b = P.homog ? j : pt;
     const double ey = P.eta_y[j], eyy = P.eta_yy[j];
@@ -452,7 +487,7 @@ __global__ void __launch_bounds__(128) k_point_fast(const PointParams P, const f
   const double e = *P.eps;
   const bool visc = P.phys.visc;
   for (long long pt = (long long)blockIdx.x * blockDim.x + threadIdx.x; pt < P.npts; pt += (long long)gridDim.x * blockDim.x) {
-    const int j = (int)((pt / P.nx) % P.ny);
+    const int j = row_of(P, pt);
     const bool bc_row = (j == 0 || j == P.ny - 1);
     const unsigned fl = bc_row ? P.bcflags[(j == P.ny - 1 ? (long long)P.nx * P.nz : 0)] : 0u;
     const float2* Cp = (const float2*)(coefp + (long long)j * (D + 2) * NW);
@@ -567,7 +602,7 @@ __global__ void k_temperature_fast(const PointParams P, double2* Tw) {
   const float ef = (float)e;
   const pw::ClosureK C = P.phys.C;
   for (long long pt = (long long)blockIdx.x * blockDim.x + threadIdx.x; pt < P.npts; pt += (long long)gridDim.x * blockDim.x) {
-    const int j = (int)((pt / P.nx) % P.ny);
+    const int j = row_of(P, pt);
     const double ip0 = P.btab[pw::bt_extra(D, pw::X_IP) * P.nbase + j];
     const double T0 = P.btab[pw::bt_val(D, D + 2) * P.nbase + j];
     const double2 wp = P.v[pt], ws = P.v[(long long)(D + 1) * P.npts + pt];
@@ -812,6 +847,9 @@ static cudaError_t run_pass(StabHandle* h, int axis, const PassParams& base_para
   }
   if (L < 1) L = 1;
   P.L = L;
+  P.divn = make_fastdiv((unsigned)n);
+  P.divL = make_fastdiv((unsigned)L);
+  P.divnx = make_fastdiv((unsigned)P.nx);
   int threads = tpl * L;
   threads = ((threads + 31) / 32) * 32;
   size_t smem = (size_t)smem_line * L;
@@ -953,17 +991,19 @@ cudaError_t jv_autotune(StabHandle* h, int force, double* ms_out) {
           if (2 * kp * nch * L > 1024 || (2 + 2 * kp) * 8 * LS * L > kLineSmemMax) continue;
           h->line_cfg[ax] = LineCfg{C, L, kp};
           if ((err = run_pass(h, ax, P, jobs)) != cudaSuccess) break;  // warm-up
-          float t[5];
+          // three back-to-back launches per sample (less launch and clock noise), best of five samples
+          float best_t = 1e30f;
           for (int r = 0; r < 5 && err == cudaSuccess; ++r) {
             cudaEventRecord(e0, h->stream);
-            err = run_pass(h, ax, P, jobs);
+            for (int q = 0; q < 3 && err == cudaSuccess; ++q) err = run_pass(h, ax, P, jobs);
             cudaEventRecord(e1, h->stream);
             cudaEventSynchronize(e1);
-            cudaEventElapsedTime(&t[r], e0, e1);
+            float t = 0.f;
+            cudaEventElapsedTime(&t, e0, e1);
+            best_t = std::min(best_t, t / 3.0f);
           }
           if (err != cudaSuccess) break;
-          std::sort(t, t + 5);
-          if (t[2] < best_ms) { best_ms = t[2]; best = LineCfg{C, L, kp}; }
+          if (best_t < best_ms) { best_ms = best_t; best = LineCfg{C, L, kp}; }
         }
         if (err != cudaSuccess) break;
       }
@@ -1033,6 +1073,8 @@ void jv_tune_apply_cached(StabHandle* h) {
 static PointParams point_params(StabHandle* h, const double2* v) {
   PointParams P{};
   P.gate = h->gate;
+  P.divnx = make_fastdiv((unsigned)h->nx);
+  P.divny = make_fastdiv((unsigned)h->ny);
   P.v = v;
   P.scratch = h->d_scratch;
   P.npts = h->npts;
