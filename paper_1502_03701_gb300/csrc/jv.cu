@@ -292,6 +292,57 @@ __device__ __forceinline__ double warp_sum(double x) {
   return x;
 }
 
+__device__ __forceinline__ double block_sum(double s, double* red) {
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x < 32) {
+    t = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+    t = warp_sum(t);
+  }
+  return t;  // valid in thread 0
+}
+
+// mode 0: out = sum;  mode 1: out = sqrt(sum);  mode 2: epsilon from ||v||
+__device__ __forceinline__ double norm_result(double s, int mode, double q0norm, double fixed_eps) {
+  if (mode == 0) return s;
+  if (mode == 1) return sqrt(s);
+  if (fixed_eps > 0.0) return fixed_eps;
+  return s > 0.0 ? 1.4901161193847656e-08 * (1.0 + q0norm) / sqrt(s) : 0.0;  // sqrt(2^-52)
+}
+
+// ||v||^2 in one launch: per-block sums, then the last block to finish adds
+// them in block order (fixed order, reproducible) and resets the counter.
+__global__ void k_norm2(const double2* __restrict__ v, long long n, double* partial, unsigned* counter, double* out,
+                        int mode, double q0norm, double fixed_eps, const int* gate) {
+  if (gate && *gate) return;
+  __shared__ double red[32];
+  __shared__ bool last;
+  double s = 0.0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    double2 z = v[i];
+    s = fma(z.x, z.x, fma(z.y, z.y, s));
+  }
+  const double t = block_sum(s, red);
+  if (threadIdx.x == 0) {
+    partial[blockIdx.x] = t;
+    __threadfence();
+    last = atomicAdd(counter, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double a = 0.0;
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) a += ((volatile double*)partial)[b];
+  __syncthreads();
+  const double tot = block_sum(a, red);
+  if (threadIdx.x == 0) {
+    *out = norm_result(tot, mode, q0norm, fixed_eps);
+    *counter = 0u;
+  }
+}
+
 __global__ void k_norm2_partial(const double2* __restrict__ v, long long n, double* partial, const int* gate) {
   if (gate && *gate) return;
   double s = 0.0;
@@ -300,33 +351,17 @@ __global__ void k_norm2_partial(const double2* __restrict__ v, long long n, doub
     s = fma(z.x, z.x, fma(z.y, z.y, s));
   }
   __shared__ double red[32];
-  s = warp_sum(s);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    double t = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
-    t = warp_sum(t);
-    if (threadIdx.x == 0) partial[blockIdx.x] = t;
-  }
+  const double t = block_sum(s, red);
+  if (threadIdx.x == 0) partial[blockIdx.x] = t;
 }
 
-// mode 0: out = sum;  mode 1: out = sqrt(sum);  mode 2: epsilon from ||v||
 __global__ void k_norm2_final(const double* partial, int nb, double* out, int mode, double q0norm, double fixed_eps,
                               const int* gate) {
   if (gate && *gate) return;
   double s = 0.0;
   for (int i = threadIdx.x; i < nb; i += 32) s += partial[i];
   s = warp_sum(s);
-  if (threadIdx.x == 0) {
-    if (mode == 0) *out = s;
-    else if (mode == 1) *out = sqrt(s);
-    else {
-      double e = 0.0;
-      if (fixed_eps > 0.0) e = fixed_eps;
-      else if (s > 0.0) e = 1.4901161193847656e-08 * (1.0 + q0norm) / sqrt(s);  // sqrt(2^-52)
-      *out = e;
-    }
-  }
+  if (threadIdx.x == 0) *out = norm_result(s, mode, q0norm, fixed_eps);
 }
 
 __global__ void k_set_scalar(double* p, double v) { *p = v; }
@@ -479,7 +514,7 @@ __global__ void k_coeffs(const PointParams P, double* coef) {
 // two-sum accumulation (~2^-47 relative per term), the O(eps) remainder in
 // FP32 from the inputs' high parts and FP32 base tables: no FP64 products.
 template <int D>
-__global__ void __launch_bounds__(128) k_point_fast(const PointParams P, const ffn* __restrict__ coefp,
+__global__ void __launch_bounds__(128, 3) k_point_fast(const PointParams P, const ffn* __restrict__ coefp,
                                                    const float* __restrict__ btab_f) {
   if (P.gate && *P.gate) return;
   constexpr int NW = pw::nw_inputs(D);
@@ -534,7 +569,7 @@ __global__ void __launch_bounds__(128) k_point_fast(const PointParams P, const f
         for (int f = 0; f < D + 3; ++f) Wf.d1[1][f] *= ey;
 #pragma unroll
         for (int g = 0; g < D + 1; ++g)
-          Wf.d2[1][g] = fmaf(Wf.d2[1][g], ey * ey, ff_split(w[D + 3 + (D + 3) + (g < D ? 1 + g : D + 2)]).hi * eyy);
+          Wf.d2[1][g] = fmaf(Wf.d2[1][g], ey * ey, wp[D + 3 + (D + 3) + (g < D ? 1 + g : D + 2)].hi * eyy);
 #pragma unroll
         for (int a = 0; a < D; ++a)
 #pragma unroll
@@ -1112,8 +1147,8 @@ cudaError_t launch_norm2(StabHandle* h, const double2* v, long long n, double* d
   long long nb = (n + 1023) / 1024;
   if (nb > h->red_blocks) nb = h->red_blocks;
   if (nb < 1) nb = 1;
-  k_norm2_partial<<<(int)nb, 256, 0, h->stream>>>(v, n, h->d_red, h->gate);
-  k_norm2_final<<<1, 32, 0, h->stream>>>(h->d_red, (int)nb, d_out, mode, h->q0norm, h->opts.eps, h->gate);
+  k_norm2<<<(int)nb, 256, 0, h->stream>>>(v, n, h->d_red, (unsigned*)(h->d_red + h->red_blocks + 8), d_out, mode,
+                                         h->q0norm, h->opts.eps, h->gate);
   return cudaGetLastError();
 }
 
@@ -1200,6 +1235,8 @@ cudaError_t jv_setup(StabHandle* h, const double* q0_host) {
   h->red_blocks = 1024;
   if ((err = dalloc(h, &h->d_red, (h->red_blocks + 64) * sizeof(double))) != cudaSuccess) return err;
   h->d_eps = h->d_red + h->red_blocks;
+  // completion counter of the one-launch norm (k_norm2) at d_red + red_blocks + 8: starts at zero
+  if ((err = cudaMemsetAsync(h->d_red + h->red_blocks, 0, 64 * sizeof(double), h->stream)) != cudaSuccess) return err;
   k_set_scalar<<<1, 1, 0, h->stream>>>(h->d_eps, 0.0);
   // base tables: derivatives of the base fields through the same passes
   const int nbt = bt_count(D);
