@@ -397,6 +397,23 @@ def fleet(args, torch) -> dict:
                        "peak_running": st["peak_running"], "peak_bytes": st["peak_bytes"]}}
 
 
+def reduce_over_ranks(x: float, op: str, device: str) -> float:
+    """All-reduce one scalar over the process group ("max" or "sum"); identity without one."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def replica_throughput(local_units: float, local_seconds: float, device: str) -> tuple[float, float]:
+    """Replicas only: units processed by all ranks over the slowest rank's time; returns (value, t_max)."""
+    t_max = reduce_over_ranks(local_seconds, "max", device)
+    total = reduce_over_ranks(local_units, "sum", device)
+    return total / t_max, t_max
+
+
 def _time_jv(S, v, out, steps, flush, stream, torch):
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     for s in range(steps):
@@ -431,11 +448,6 @@ def run_ours(args):
             dist.barrier()
         torch.cuda.synchronize()
 
-    def max_over_ranks(x):
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        if world > 1:
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
 
     # J v on the Ma 0.3 layer (both forms)
     g, f, q0 = _layer(args.nx, args.ny, 0.3)
@@ -466,8 +478,7 @@ def run_ours(args):
             Sj.timing(False)
             barrier()
         clock_sum = sampler.summary()
-        t_max = max_over_ranks(sum(steps_t))
-        value = world * args.steps * bytes_jv / t_max / 1e9
+        value, t_max = replica_throughput(args.steps * bytes_jv / 1e9, sum(steps_t), "cuda")
         unit = "GB/s"
         ms_step = t_max / args.steps * 1e3
         roofline = jv_roofline(g, f, phases, sum(steps_t) / args.steps, hbm, statistics.mean(jv_tan))
@@ -545,14 +556,8 @@ def run_ours(args):
             barrier()
         sampler_summary = sampler.summary()
         good = [int(np.sum(r.resid[:r.nconv] < RESID_OK)) for r in results]
-        t_local = sum(step_t)
-        t_max = max_over_ranks(t_local)
-        total_good = max_over_ranks(0) * 0 + sum(good)
-        if world > 1:
-            tg = torch.tensor([float(total_good)], dtype=torch.float64, device="cuda")
-            dist.all_reduce(tg)
-            total_good = float(tg.item())
-        value = total_good / t_max
+        value, t_max = replica_throughput(float(sum(good)), sum(step_t), "cuda")
+        total_good = value * t_max
         unit = "eigenpairs/s"
         ms_step = t_max / args.steps * 1e3
         lat = sorted(step_t)
