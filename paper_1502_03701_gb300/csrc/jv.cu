@@ -854,12 +854,13 @@ static cudaError_t run_pass(StabHandle* h, int axis, const PassParams& base_para
 
   const int n = A.n;
   if (n > 2048) return cudaErrorInvalidValue;
-  // launch shape: C points per sweep chunk, L lines per CTA.  Either tuned
-  // (stab_autotune) or by default chunks of 32 and L such that 8 planes of
-  // L x n doubles stay near 96 KB (two CTAs per SM), lowered on small grids
-  // so that the CTAs cover the SMs (but at least a warp of sweep threads).
+  // launch shape: C points per sweep chunk, L lines per CTA, KP kinds at
+  // once.  Either tuned (stab_autotune) or by default chunks of 16 (32 on
+  // lines of 512 points or more), at most two lines per CTA, fewer on small
+  // grids so that the CTAs cover the SMs (but at least a warp of threads).
   const LineCfg cfg = contiguous_lines >= 0 ? LineCfg{} : h->line_cfg[axis];
-  P.C = cfg.C > 0 ? cfg.C : 32;
+  // default chunk: 16 points (more sweep threads) unless lines are long
+  P.C = cfg.C > 0 ? cfg.C : (n >= 512 ? 32 : 16);
   P.nchunks = (n + P.C - 1) / P.C;
   P.LS = n + (n >> 5) + 1;
   const long long LS = P.LS;
@@ -876,7 +877,7 @@ static cudaError_t run_pass(StabHandle* h, int axis, const PassParams& base_para
   if (cfg.L > 0) {
     L = std::min(cfg.L, maxL);
   } else {
-    L = std::min<long long>(maxL, 98304 / smem_line);
+    L = std::min<long long>(std::min<long long>(maxL, 98304 / smem_line), 2);
     const int Lwarp = (32 + tpl - 1) / tpl;
     if (L > fill) L = (int)std::min<long long>(maxL, std::max<long long>(fill, Lwarp));
   }
