@@ -177,6 +177,9 @@ cudaError_t kry_axpby(StabHandle* h, double2 a, const double2* x, double2 b, dou
 cudaError_t kry_copy(StabHandle* h, const double2* x, double2* y, long long n);
 cudaError_t kry_update_basis(StabHandle* h, double2* V, int m, int kk, long long n, const double2* d_Q, double2* tmp);
 int kry_partial_elems(long long n, int k);
+int kry_dgks_partial_elems(long long n, int k);
+cudaError_t kry_dgks(StabHandle* h, const double2* V, int k, long long n, double2* w, double2* d_h, double* d_norm,
+                     double2* partial);
 cudaError_t kry_init_attributes();
 cudaError_t kry_cgs2_stream(cudaStream_t st, const double2* V, int k, long long n, double2* w, double2* d_h,
                             double* d_norm, double2* partial, double* norm_partial, int norm_blocks);

@@ -326,6 +326,111 @@ __global__ void k_norm_final(const double* partial, int nb, double* out, const i
   if (threadIdx.x == 0) *out = sqrt(s);
 }
 
+// ---------------------------------------------------------------------------
+// Classical Gram-Schmidt with selective reorthogonalisation (Daniel, Gragg,
+// Kaufman and Stewart 1976) for the GMRES basis: one pass h1 = V^H w,
+// w' = w - V h1; a second pass only when ||w'|| < eta ||w|| (eta = 1/sqrt 2),
+// decided on the device; the second-pass kernels return at once otherwise.
+// Same dot and update arithmetic as the fused CGS2 kernels.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool gated(const int* a, const int* b) { return (a && *a) || (b && *b); }
+
+__device__ __forceinline__ double block_norm_partial(const double2* w, long long r0, long long r1, double* red) {
+  double s = 0.0;
+  for (long long i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+    const double2 z = w[i];
+    s = fma(z.x, z.x, fma(z.y, z.y, s));
+  }
+  s = warp_sum(s);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) red[wid] = s;
+  __syncthreads();
+  double t = 0.0;
+  if (wid == 0) {
+    t = lane < (int)(blockDim.x >> 5) ? red[lane] : 0.0;
+    t = warp_sum(t);
+  }
+  return t;
+}
+
+// pass-1 dots and the block's |w|^2
+__global__ void __launch_bounds__(kThreads) k_dgks_dots(const double2* __restrict__ V, int k, long long n,
+                                                       const double2* __restrict__ w, double2* partial,
+                                                       double* norm_partial, const int* gate, const int* skip) {
+  if (gated(gate, skip)) return;
+  __shared__ double2 red[kThreads / 32];
+  __shared__ double rn[kThreads / 32];
+  long long r0, r1;
+  block_rows(n, r0, r1);
+  block_dot_columns(V, k, n, r0, r1, w, partial, red);
+  if (norm_partial) {
+    const double t = block_norm_partial(w, r0, r1, rn);
+    if (threadIdx.x == 0) norm_partial[blockIdx.x] = t;
+  }
+}
+
+// h = reduced partial dots (block 0 stores or adds it to d_h), w -= V h over
+// the block's rows, the block's |w|^2
+__global__ void __launch_bounds__(kThreads) k_dgks_update(const double2* __restrict__ V, int k, long long n,
+                                                         double2* w, const double2* partial, double2* d_h,
+                                                         double* norm_partial, int accumulate, const int* gate,
+                                                         const int* skip) {
+  if (gated(gate, skip)) return;
+  extern __shared__ double2 hs[];  // k complex, then 2k pairs
+  __shared__ double red[kThreads / 32];
+  ffn* hre = (ffn*)(hs + k);
+  ffn* him = hre + k;
+  reduce_partials(partial, gridDim.x, k, hs);
+  __syncthreads();
+  for (int j = threadIdx.x; j < k; j += blockDim.x) {
+    hre[j] = ff_split(hs[j].x);
+    him[j] = ff_split(hs[j].y);
+    if (blockIdx.x == 0) {
+      if (accumulate) {
+        const double2 h1 = d_h[j];
+        d_h[j] = make_double2(h1.x + hs[j].x, h1.y + hs[j].y);
+      } else {
+        d_h[j] = hs[j];
+      }
+    }
+  }
+  __syncthreads();
+  long long r0, r1;
+  block_rows(n, r0, r1);
+  for (long long i = r0 + threadIdx.x; i < r1; i += blockDim.x) w[i] = row_update(V, k, n, i, hs, hre, him, w[i]);
+  __syncthreads();
+  const double t = block_norm_partial(w, r0, r1, red);
+  if (threadIdx.x == 0) norm_partial[blockIdx.x] = t;
+}
+
+// ||w||, ||w'|| from the partials; skip = (||w'|| >= eta ||w||); when skipping,
+// ||w'|| is the result
+__global__ void k_dgks_decide(const double* np0, const double* np1, int nb, double* d_norm, int* skip, double eta,
+                              const int* gate) {
+  if (gate && *gate) return;
+  double a = 0.0, b = 0.0;
+  for (int i = threadIdx.x; i < nb; i += 32) {
+    a += np0[i];
+    b += np1[i];
+  }
+  a = warp_sum(a);
+  b = warp_sum(b);
+  if (threadIdx.x == 0) {
+    const double n0 = sqrt(a), n1 = sqrt(b);
+    const int s = n1 >= eta * n0;  // NaN: reorthogonalise (and let the norm report it)
+    *skip = s;
+    if (s) *d_norm = n1;
+  }
+}
+
+__global__ void k_dgks_norm(const double* partial, int nb, double* out, const int* gate, const int* skip) {
+  if (gated(gate, skip)) return;
+  double s = 0.0;
+  for (int i = threadIdx.x; i < nb; i += 32) s += partial[i];
+  s = warp_sum(s);
+  if (threadIdx.x == 0) *out = sqrt(s);
+}
+
 // blocks of the fused CGS2: about 64 rows each (short latency on small
 // vectors), at most four per SM on large ones
 int cgs_blocks(long long n) {
@@ -413,6 +518,36 @@ cudaError_t kry_update_basis(StabHandle* h, double2* V, int m, int kk, long long
   const size_t smem = (size_t)m * kVqRows * sizeof(double2);
   if (smem > 200 * 1024) return cudaErrorInvalidValue;
   k_vq<<<(unsigned)((n + kVqRows - 1) / kVqRows), kVqRows, smem, h->stream>>>(V, m, n, d_Q, kk, tmp);
+  return cudaGetLastError();
+}
+
+int kry_dgks_partial_elems(long long n, int k) {
+  const int nb = cgs_blocks(n);
+  return 2 * nb * (k > 0 ? k : 1) + (3 * nb + 1) / 2 + 2;
+}
+
+// GMRES orthogonalisation with selective reorthogonalisation (see the kernels):
+// h (k complex in d_h) and ||w|| (d_norm); partial holds kry_dgks_partial_elems.
+cudaError_t kry_dgks(StabHandle* h, const double2* V, int k, long long n, double2* w, double2* d_h, double* d_norm,
+                     double2* partial) {
+  if (k <= 0) return kry_cgs2(h, V, k, n, w, d_h, d_norm, partial);
+  const int ts = phase_begin(h, STAB_PHASE_CGS2);
+  const int nb = cgs_blocks(n);
+  double2* p1 = partial;
+  double2* p2 = partial + (size_t)nb * k;
+  double* np0 = (double*)(p2 + (size_t)nb * k);
+  double* np1 = np0 + nb;
+  double* np2 = np1 + nb;
+  int* skip = (int*)(np2 + nb);
+  const size_t sm = (size_t)k * (sizeof(double2) + 2 * sizeof(ffn));
+  constexpr double eta = 0.70710678118654752;
+  k_dgks_dots<<<nb, kThreads, 0, h->stream>>>(V, k, n, w, p1, np0, h->gate, nullptr);
+  k_dgks_update<<<nb, kThreads, sm, h->stream>>>(V, k, n, w, p1, d_h, np1, 0, h->gate, nullptr);
+  k_dgks_decide<<<1, 32, 0, h->stream>>>(np0, np1, nb, d_norm, skip, eta, h->gate);
+  k_dgks_dots<<<nb, kThreads, 0, h->stream>>>(V, k, n, w, p2, nullptr, h->gate, skip);
+  k_dgks_update<<<nb, kThreads, sm, h->stream>>>(V, k, n, w, p2, d_h, np2, 1, h->gate, skip);
+  k_dgks_norm<<<1, 32, 0, h->stream>>>(np2, nb, d_norm, h->gate, skip);
+  phase_end(h, ts);
   return cudaGetLastError();
 }
 

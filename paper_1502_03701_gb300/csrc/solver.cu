@@ -84,7 +84,7 @@ GmresWs gmres_ws(StabHandle* h, GmDev* D, GmReport** rep) {
   const long long n = h->n;
   const int m = h->opts.gmres_m;
   const bool pc = h->opts.precond == 1;
-  const size_t part = (size_t)kry_partial_elems(n, m + 1);
+  const size_t part = (size_t)std::max(kry_partial_elems(n, m + 1), kry_dgks_partial_elems(n, m + 1));
   const size_t small = (size_t)m * m + (m + 1) + m + (m + 1) / 2 + 1 + 4 + 4;
   size_t need = (size_t)(m + 1) * n + (pc ? (size_t)m * n : 0) + 3 * (size_t)n + part + 2 * (m + 1) + (m + 1) + 4 + small;
   double2* base = ensure(h, &h->d_gm, &h->gm_elems, need);
@@ -212,7 +212,8 @@ __global__ void k_gm_report(GmDev d, GmReport* rep) {
 }
 
 // One GMRES cycle as a CUDA graph: V_0 = r / beta; m Arnoldi steps, each
-// (right preconditioner, J v - sigma v, CGS2, Givens update, scaling) gated
+// (right preconditioner, J v - sigma v, Gram-Schmidt with selective
+// reorthogonalisation, Givens update, scaling) gated
 // on the device flag that the Givens update raises at convergence; the
 // least-squares solve, x += Z y (V y), and the true residual r = b - A x with
 // its norm.  Captured once per handle, shift and workspace, replayed for
@@ -257,7 +258,7 @@ cudaGraphExec_t gm_graph(StabHandle* h, cd sigma, int eps_mode, const GmresWs& W
       h->gate = D.flags;
       if (pc) step(pc_apply(h, Vj, zj));
       step(jv_apply(h, zj, Vn, d2(sigma), eps_mode));
-      step(kry_cgs2(h, W.V, j + 1, n, Vn, W.dh, W.dnorm, W.partial));
+      step(kry_dgks(h, W.V, j + 1, n, Vn, W.dh, W.dnorm, W.partial));
       h->gate = nullptr;
       k_gm_step<<<1, 32, 0, h->stream>>>(D, j);
       h->gate = D.flags;
