@@ -252,13 +252,25 @@ __global__ void k_apply(const ApplyParams P) {
   }
   __syncthreads();
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  // FP32 rows of even length: two entries per 16-byte load (rows start 16-byte aligned)
+  const bool vec = sizeof(R) == 4 && (P.bsz & 1) == 0;
   for (int r = rb0 + wid; r < rb1; r += nw) {
     const C2<R>* row = M + (long long)r * P.bsz;
     R ar = 0, ai = 0;
-    for (int c = lane; c < P.bsz; c += 32) {
-      C2<R> m = row[c], x = qs[c];
-      ar += m.x * x.x - m.y * x.y;
-      ai += m.x * x.y + m.y * x.x;
+    if (vec) {
+      const float4* row4 = (const float4*)row;
+      for (int c2 = lane; c2 < P.bsz / 2; c2 += 32) {
+        const float4 m = __ldg(row4 + c2);
+        const C2<R> x0 = qs[2 * c2], x1 = qs[2 * c2 + 1];
+        ar += m.x * x0.x - m.y * x0.y + m.z * x1.x - m.w * x1.y;
+        ai += m.x * x0.y + m.y * x0.x + m.z * x1.y + m.w * x1.x;
+      }
+    } else {
+      for (int c = lane; c < P.bsz; c += 32) {
+        C2<R> m = row[c], x = qs[c];
+        ar += m.x * x.x - m.y * x.y;
+        ai += m.x * x.y + m.y * x.x;
+      }
     }
     for (int o = 16; o > 0; o >>= 1) {
       ar += __shfl_xor_sync(0xffffffffu, ar, o);

@@ -58,6 +58,7 @@ struct GmresWs {
 };
 
 constexpr int kMaxGmresM = 200;  // stab_create rejects larger gmres_m
+constexpr long long kSelectiveMinN = 16384;  // unknowns from which GMRES uses selective reorthogonalisation
 
 // Device-resident least-squares state of one GMRES cycle: the rotated
 // Hessenberg columns R (m x m, row-major), the rotated right-hand side g,
@@ -258,7 +259,10 @@ cudaGraphExec_t gm_graph(StabHandle* h, cd sigma, int eps_mode, const GmresWs& W
       h->gate = D.flags;
       if (pc) step(pc_apply(h, Vj, zj));
       step(jv_apply(h, zj, Vn, d2(sigma), eps_mode));
-      step(kry_dgks(h, W.V, j + 1, n, Vn, W.dh, W.dnorm, W.partial));
+      // tiny vectors: the fused four-kernel CGS2 (launch latency dominates); otherwise the
+      // selective form, which reads the basis half as often
+      if (n < kSelectiveMinN) step(kry_cgs2(h, W.V, j + 1, n, Vn, W.dh, W.dnorm, W.partial));
+      else step(kry_dgks(h, W.V, j + 1, n, Vn, W.dh, W.dnorm, W.partial));
       h->gate = nullptr;
       k_gm_step<<<1, 32, 0, h->stream>>>(D, j);
       h->gate = D.flags;
