@@ -187,18 +187,33 @@ __global__ void k_gauss_jordan(C2<R>* A, int b, int* info) {
     for (int j = threadIdx.x; j < b; j += nthr) {
       const C2<R> pj = prow[j];
       const C2<R> s = {pj.x * inv.x - pj.y * inv.y, pj.x * inv.y + pj.y * inv.x};  // prow[j] / pivot
-      for (int i = 0; i < b; ++i) {
-        C2<R>* a = &M[(long long)i * b + j];
-        const C2<R> ci = pcol[i];
-        if (i == k) {
-          *a = j == k ? inv : s;
-        } else if (j == k) {
-          *a = C2<R>{-(ci.x * inv.x - ci.y * inv.y), -(ci.x * inv.y + ci.y * inv.x)};
-        } else {
-          C2<R> v = *a;
-          v.x -= ci.x * s.x - ci.y * s.y;
-          v.y -= ci.x * s.y + ci.y * s.x;
-          *a = v;
+      C2<R>* col = M + j;
+      if (j == k) {  // the pivot column: -pcol / pivot, and 1 / pivot on the diagonal
+        for (int i = 0; i < b; ++i) {
+          const C2<R> ci = pcol[i];
+          col[(long long)i * b] = i == k ? inv : C2<R>{-(ci.x * inv.x - ci.y * inv.y), -(ci.x * inv.y + ci.y * inv.x)};
+        }
+        continue;
+      }
+      // rows in groups of 8: all loads first, so eight L2 round trips are in flight per thread
+      constexpr int G = 8;
+      for (int i0 = 0; i0 < b; i0 += G) {
+        C2<R> v[G];
+#pragma unroll
+        for (int q = 0; q < G; ++q)
+          if (i0 + q < b) v[q] = col[(long long)(i0 + q) * b];
+#pragma unroll
+        for (int q = 0; q < G; ++q) {
+          const int i = i0 + q;
+          if (i >= b) break;
+          const C2<R> ci = pcol[i];
+          if (i == k) {
+            v[q] = s;
+          } else {
+            v[q].x -= ci.x * s.x - ci.y * s.y;
+            v[q].y -= ci.x * s.y + ci.y * s.x;
+          }
+          col[(long long)i * b] = v[q];
         }
       }
     }
