@@ -69,7 +69,8 @@ typedef struct {
   double gmres_tol;       /* inner relative residual tolerance, default 1e-10 */
   int precond;            /* 0 none, 1 block-Jacobi */
   int tile[3];            /* block-Jacobi tile in grid points (x, y, z), default 8 x 8 x 1 */
-  int precond_prec;       /* block-Jacobi inverse storage: 64 (FP64) or 32 (FP32), default 32 */
+  int precond_prec;       /* block-Jacobi inverse storage: 64 (FP64), 32 (FP32, default) or 16 (BF16:
+                             inverted in FP32, stored in bfloat16, applied with FP32 accumulation) */
   int max_restarts;       /* IRAM restart limit, default 300 */
   unsigned long long seed;/* start vector seed when no v0 is given, default 0x5EED */
 } stab_opts;

@@ -9,6 +9,8 @@
 // elimination with partial pivoting (first row of maximum modulus) and
 // applied as a batched block matrix-vector product.
 // Local unknown order inside a tile: [var][lz][ly][lx], lx fastest.
+#include <cuda_bf16.h>
+
 #include <algorithm>
 #include <cstring>
 #include <vector>
@@ -123,6 +125,11 @@ template <class R>
 struct C2 {
   R x, y;
 };
+
+__global__ void k_to_bf16(const float2* in, __nv_bfloat162* out, long long count) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (long long)gridDim.x * blockDim.x)
+    out[i] = __float22bfloat162_rn(in[i]);
+}
 
 __global__ void k_to_float(const double2* in, float2* out, long long count) {
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (long long)gridDim.x * blockDim.x) {
@@ -295,6 +302,55 @@ __global__ void k_apply(const ApplyParams P) {
   }
 }
 
+// z_tile = Minv_tile q_tile with the inverse stored in BF16 (complex as
+// bfloat162), products accumulated in FP32; grid and rows as k_apply.
+__global__ void k_apply_bf16(const ApplyParams P) {
+  if (P.gate && *P.gate) return;
+  extern __shared__ unsigned char smraw[];
+  float2* qs = (float2*)smraw;
+  const long long tile = blockIdx.x;
+  const int rb0 = (int)((long long)P.bsz * blockIdx.y / gridDim.y);
+  const int rb1 = (int)((long long)P.bsz * (blockIdx.y + 1) / gridDim.y);
+  const __nv_bfloat162* M = (const __nv_bfloat162*)P.inv + (long long)tile * P.bsz * P.bsz;
+  for (int r = threadIdx.x; r < P.bsz; r += blockDim.x) {
+    const double2 v = P.q[tile_dof(P, tile, r)];
+    qs[r] = make_float2((float)v.x, (float)v.y);
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const bool vec = (P.bsz & 3) == 0;  // four entries per 16-byte load (rows start 16-byte aligned)
+  for (int r = rb0 + wid; r < rb1; r += nw) {
+    const __nv_bfloat162* row = M + (long long)r * P.bsz;
+    float ar = 0.f, ai = 0.f;
+    if (vec) {
+      const uint4* row4 = (const uint4*)row;
+      for (int c4 = lane; c4 < P.bsz / 4; c4 += 32) {
+        const uint4 u = __ldg(row4 + c4);
+        const unsigned w4[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          __nv_bfloat162 b;
+          memcpy(&b, &w4[q], sizeof(b));
+          const float2 m = __bfloat1622float2(b), x = qs[4 * c4 + q];
+          ar += m.x * x.x - m.y * x.y;
+          ai += m.x * x.y + m.y * x.x;
+        }
+      }
+    } else {
+      for (int c = lane; c < P.bsz; c += 32) {
+        const float2 m = __bfloat1622float2(row[c]), x = qs[c];
+        ar += m.x * x.x - m.y * x.y;
+        ai += m.x * x.y + m.y * x.x;
+      }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      ar += __shfl_xor_sync(0xffffffffu, ar, o);
+      ai += __shfl_xor_sync(0xffffffffu, ai, o);
+    }
+    if (lane == 0) P.z[tile_dof(P, tile, r)] = make_double2((double)ar, (double)ai);
+  }
+}
+
 struct Geo {
   int tx, ty, tz, ntx, nty, ntz, ntpts, bsz;
   long long ntiles;
@@ -382,7 +438,7 @@ cudaError_t pc_build(StabHandle* h, double2 sigma) {
   cudaError_t e;
   if ((e = ensure_dmats(h)) != cudaSuccess) return e;
   const int prec = h->opts.precond_prec;
-  const size_t esz = prec == 64 ? sizeof(double2) : sizeof(float2);
+  const size_t esz = prec == 64 ? sizeof(double2) : prec == 32 ? sizeof(float2) : sizeof(__nv_bfloat162);
   const size_t bb = (size_t)g.bsz * g.bsz;
   if (!h->d_pinv || h->ntiles != g.ntiles || h->bsize != g.bsz || h->pprec != prec) {
     dfree(h, h->d_pinv);
@@ -397,14 +453,16 @@ cudaError_t pc_build(StabHandle* h, double2 sigma) {
   long long batch = (long long)((1ull << 30) / (bb * sizeof(double2)));
   if (batch < 1) batch = 1;
   if (batch > g.ntiles) batch = g.ntiles;
-  if (prec == 32 && !h->d_pblk) {
+  if (prec != 64 && !h->d_pblk) {
     if ((e = dalloc(h, &h->d_pblk, bb * batch * sizeof(double2))) != cudaSuccess) return e;
   }
+  float2* f32 = nullptr;  // BF16 storage: FP32 inversion in a batch-sized buffer, then rounding
+  if (prec == 16 && (e = dalloc(h, &f32, bb * batch * sizeof(float2))) != cudaSuccess) return e;
   int* d_info;
   if ((e = dalloc(h, &d_info, sizeof(int))) != cudaSuccess) return e;
   cudaMemsetAsync(d_info, 0, sizeof(int), h->stream);
   AsmParams P = asm_params(h, g, sigma);
-  const size_t smem = (size_t)2 * g.bsz * esz + g.bsz * sizeof(int);
+  const size_t smem = (size_t)2 * g.bsz * (prec == 64 ? sizeof(double2) : sizeof(float2)) + g.bsz * sizeof(int);
   for (long long t0 = 0; t0 < g.ntiles; t0 += batch) {
     const long long nb = std::min(batch, g.ntiles - t0);
     P.tile0 = t0;
@@ -416,9 +474,11 @@ cudaError_t pc_build(StabHandle* h, double2 sigma) {
     } else {
       P.out = h->d_pblk;
       if ((e = launch_assemble(h, P, nb)) != cudaSuccess) break;
-      float2* dst = (float2*)h->d_pinv + bb * t0;
+      float2* dst = prec == 32 ? (float2*)h->d_pinv + bb * t0 : f32;
       k_to_float<<<1024, 256, 0, h->stream>>>(h->d_pblk, dst, (long long)(bb * nb));
       k_gauss_jordan<float><<<(unsigned)nb, gj_threads(g.bsz), smem, h->stream>>>((C2<float>*)dst, g.bsz, d_info);
+      if (prec == 16)
+        k_to_bf16<<<1024, 256, 0, h->stream>>>(f32, (__nv_bfloat162*)h->d_pinv + bb * t0, (long long)(bb * nb));
     }
     if ((e = cudaGetLastError()) != cudaSuccess) break;
   }
@@ -426,6 +486,7 @@ cudaError_t pc_build(StabHandle* h, double2 sigma) {
   if (e == cudaSuccess) e = cudaMemcpyAsync(&info, d_info, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   dfree(h, d_info);
+  dfree(h, f32);
   if (e != cudaSuccess) return e;
   if (info) return cudaErrorInvalidValue;  // a singular block
   h->pvalid = true;
@@ -450,7 +511,8 @@ cudaError_t pc_apply(StabHandle* h, const double2* q, double2* z) {
   slices = std::max(1, std::min(slices, g.bsz / 32));
   const dim3 grid((unsigned)g.ntiles, (unsigned)slices);
   if (h->pprec == 64) k_apply<double><<<grid, 256, g.bsz * sizeof(double2), h->stream>>>(P);
-  else k_apply<float><<<grid, 256, g.bsz * sizeof(float2), h->stream>>>(P);
+  else if (h->pprec == 32) k_apply<float><<<grid, 256, g.bsz * sizeof(float2), h->stream>>>(P);
+  else k_apply_bf16<<<grid, 256, g.bsz * sizeof(float2), h->stream>>>(P);
   phase_end(h, ts);
   return cudaGetLastError();
 }

@@ -61,7 +61,7 @@ extern "C" long long stab_estimate_bytes(const stab_grid* g, const stab_opts* op
     const long long bsz = nv * o.tile[0] * o.tile[1] * tz;
     const long long ntiles = npts / std::max<long long>(1, o.tile[0] * o.tile[1] * tz);
     const long long bb = bsz * bsz;
-    b += ntiles * bb * (o.precond_prec == 64 ? 16 : 8);    // inverses
+    b += ntiles * bb * (o.precond_prec == 64 ? 16 : o.precond_prec == 32 ? 8 : 4);  // inverses
     b += std::min<long long>(ntiles, std::max<long long>(1, (1ll << 30) / (bb * 16))) * bb * 16;  // assembly batch
     const long long la = std::max<long long>({(long long)g->nx, (long long)g->ny, D == 3 ? g->nz : 1});
     b += (long long)D * 3 * la * la * 16;                  // 1-D derivative matrices

@@ -42,7 +42,8 @@ def test_assembled_blocks_match_dense_jacobian(orc, name, g, f, general, tile, t
     S.close()
 
 
-@pytest.mark.parametrize("prec,tol", [(64, 1e-9), (32, 1e-3)])
+# FP64 inverse to rounding; FP32 / BF16 storage to their unit roundoff times the blocks' conditioning
+@pytest.mark.parametrize("prec,tol", [(64, 1e-9), (32, 1e-3), (16, 3e-2)])
 def test_apply_matches_oracle_lu(orc, prec, tol):
     import torch
     g, f = si.mixing_layer_2d(16, 32)
@@ -90,6 +91,28 @@ def test_preconditioned_gmres_and_eigs(orc):
     assert r.stats["precond_builds"] == 1
     S0.close()
     S1.close()
+
+
+def test_bf16_inverses_keep_fgmres_accuracy():
+    """BF16-stored block inverses inside FP64 flexible GMRES: the solve still
+    reaches the FP64 tolerance (the preconditioner only changes the iteration
+    count, which stays within 1.3x of FP32 storage)."""
+    import torch
+    from paper_1502_03701_gb300 import Stab
+    g, f = si.mixing_layer_2d(32, 64)
+    q0 = si.tanh_base_flow(g, f)
+    b = torch.from_numpy(si.random_complex(5, g.n)).cuda()
+    out = {}
+    for prec in (32, 16):
+        S = Stab(q0, g, f.Ma, f.Re, f.Pr, precond=1, tile=(8, 8), precond_prec=prec, eps_mode=2, gmres_m=50,
+                 gmres_tol=1e-10, gmres_max_restarts=400)
+        x = torch.zeros_like(b)
+        st, it = S.solve(1.0, b, x)
+        assert st == 0
+        out[prec] = (it, x.cpu().numpy())
+        S.close()
+    assert out[16][0] <= 1.3 * out[32][0]
+    assert rel_err(out[16][1], out[32][1]) < 1e-8
 
 
 def test_full_size_blocks_invert_consistently():
