@@ -126,11 +126,6 @@ struct C2 {
   R x, y;
 };
 
-__global__ void k_to_bf16(const float2* in, __nv_bfloat162* out, long long count) {
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (long long)gridDim.x * blockDim.x)
-    out[i] = __float22bfloat162_rn(in[i]);
-}
-
 __global__ void k_to_float(const double2* in, float2* out, long long count) {
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (long long)gridDim.x * blockDim.x) {
     double2 v = in[i];
@@ -256,11 +251,55 @@ __device__ __forceinline__ long long tile_dof(const ApplyParams& P, long long ti
   return (long long)var * P.npts + ((long long)(tZ * P.tz + pz) * P.ny + (tY * P.ty + py)) * P.nx + tX * P.tx + px;
 }
 
-// z_tile = Minv_tile q_tile.  Grid (tiles, row slices): a CTA stages its
-// tile of q in shared memory and computes the rows of its slice, one warp per
-// row at a time (slices > 1 only when there are too few tiles to cover the SMs).
+// z_tile = Minv_tile q_tile with the inverse stored column-major (BF16
+// storage: Mt[c * b + r] = Minv[r][c]).  Grid (tiles, row slices); a CTA stages its
+// tile of q in shared memory and each thread forms one row: every load is a
+// coalesced segment of a column, eight loads in flight per thread, no
+// reductions.  S: stored complex type, R: accumulation type.
+template <class S, class R>
+__device__ __forceinline__ void load_c(const S* p, R& x, R& y);
+template <>
+__device__ __forceinline__ void load_c<__nv_bfloat162, float>(const __nv_bfloat162* p, float& x, float& y) {
+  const float2 v = __bfloat1622float2(__ldg(p));
+  x = v.x;
+  y = v.y;
+}
+
+template <class S, class R>
+__global__ void k_apply_cols(const ApplyParams P) {
+  if (P.gate && *P.gate) return;
+  extern __shared__ unsigned char smraw[];
+  C2<R>* qs = (C2<R>*)smraw;
+  const long long tile = blockIdx.x;
+  const int b = P.bsz;
+  const int rb0 = (int)((long long)b * blockIdx.y / gridDim.y);
+  const int rb1 = (int)((long long)b * (blockIdx.y + 1) / gridDim.y);
+  const S* Mt = (const S*)P.inv + (long long)tile * b * b;
+  for (int r = threadIdx.x; r < b; r += blockDim.x) {
+    const double2 v = P.q[tile_dof(P, tile, r)];
+    qs[r] = C2<R>{(R)v.x, (R)v.y};
+  }
+  __syncthreads();
+  for (int r = rb0 + threadIdx.x; r < rb1; r += blockDim.x) {
+    const S* col = Mt + r;
+    R ar = 0, ai = 0;
+#pragma unroll 8
+    for (int c = 0; c < b; ++c) {
+      R mx, my;
+      load_c<S, R>(col + (long long)c * b, mx, my);
+      const C2<R> x = qs[c];
+      ar += mx * x.x - my * x.y;
+      ai += mx * x.y + my * x.x;
+    }
+    P.z[tile_dof(P, tile, r)] = make_double2((double)ar, (double)ai);
+  }
+}
+
+// z_tile = Minv_tile q_tile with the inverse stored row-major (FP64 or FP32):
+// one warp per row at a time, FP32 rows of even length read two entries per
+// 16-byte load; grid (tiles, row slices) as above.
 template <class R>
-__global__ void k_apply(const ApplyParams P) {
+__global__ void k_apply_rows(const ApplyParams P) {
   if (P.gate && *P.gate) return;
   extern __shared__ unsigned char smraw[];
   C2<R>* qs = (C2<R>*)smraw;
@@ -274,7 +313,6 @@ __global__ void k_apply(const ApplyParams P) {
   }
   __syncthreads();
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  // FP32 rows of even length: two entries per 16-byte load (rows start 16-byte aligned)
   const bool vec = sizeof(R) == 4 && (P.bsz & 1) == 0;
   for (int r = rb0 + wid; r < rb1; r += nw) {
     const C2<R>* row = M + (long long)r * P.bsz;
@@ -302,52 +340,13 @@ __global__ void k_apply(const ApplyParams P) {
   }
 }
 
-// z_tile = Minv_tile q_tile with the inverse stored in BF16 (complex as
-// bfloat162), products accumulated in FP32; grid and rows as k_apply.
-__global__ void k_apply_bf16(const ApplyParams P) {
-  if (P.gate && *P.gate) return;
-  extern __shared__ unsigned char smraw[];
-  float2* qs = (float2*)smraw;
-  const long long tile = blockIdx.x;
-  const int rb0 = (int)((long long)P.bsz * blockIdx.y / gridDim.y);
-  const int rb1 = (int)((long long)P.bsz * (blockIdx.y + 1) / gridDim.y);
-  const __nv_bfloat162* M = (const __nv_bfloat162*)P.inv + (long long)tile * P.bsz * P.bsz;
-  for (int r = threadIdx.x; r < P.bsz; r += blockDim.x) {
-    const double2 v = P.q[tile_dof(P, tile, r)];
-    qs[r] = make_float2((float)v.x, (float)v.y);
-  }
-  __syncthreads();
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const bool vec = (P.bsz & 3) == 0;  // four entries per 16-byte load (rows start 16-byte aligned)
-  for (int r = rb0 + wid; r < rb1; r += nw) {
-    const __nv_bfloat162* row = M + (long long)r * P.bsz;
-    float ar = 0.f, ai = 0.f;
-    if (vec) {
-      const uint4* row4 = (const uint4*)row;
-      for (int c4 = lane; c4 < P.bsz / 4; c4 += 32) {
-        const uint4 u = __ldg(row4 + c4);
-        const unsigned w4[4] = {u.x, u.y, u.z, u.w};
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          __nv_bfloat162 b;
-          memcpy(&b, &w4[q], sizeof(b));
-          const float2 m = __bfloat1622float2(b), x = qs[4 * c4 + q];
-          ar += m.x * x.x - m.y * x.y;
-          ai += m.x * x.y + m.y * x.x;
-        }
-      }
-    } else {
-      for (int c = lane; c < P.bsz; c += 32) {
-        const float2 m = __bfloat1622float2(row[c]), x = qs[c];
-        ar += m.x * x.x - m.y * x.y;
-        ai += m.x * x.y + m.y * x.x;
-      }
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-      ar += __shfl_xor_sync(0xffffffffu, ar, o);
-      ai += __shfl_xor_sync(0xffffffffu, ai, o);
-    }
-    if (lane == 0) P.z[tile_dof(P, tile, r)] = make_double2((double)ar, (double)ai);
+// FP32 row-major blocks -> BF16 column-major blocks
+__global__ void k_to_bf16_t(const float2* in, __nv_bfloat162* out, int b) {
+  const float2* M = in + (long long)blockIdx.x * b * b;
+  __nv_bfloat162* O = out + (long long)blockIdx.x * b * b;
+  for (long long idx = threadIdx.x; idx < (long long)b * b; idx += blockDim.x) {
+    const int c = (int)(idx / b), r = (int)(idx - (long long)c * b);  // write O[c][r] (coalesced)
+    O[idx] = __float22bfloat162_rn(M[(long long)r * b + c]);
   }
 }
 
@@ -478,7 +477,7 @@ cudaError_t pc_build(StabHandle* h, double2 sigma) {
       k_to_float<<<1024, 256, 0, h->stream>>>(h->d_pblk, dst, (long long)(bb * nb));
       k_gauss_jordan<float><<<(unsigned)nb, gj_threads(g.bsz), smem, h->stream>>>((C2<float>*)dst, g.bsz, d_info);
       if (prec == 16)
-        k_to_bf16<<<1024, 256, 0, h->stream>>>(f32, (__nv_bfloat162*)h->d_pinv + bb * t0, (long long)(bb * nb));
+        k_to_bf16_t<<<(unsigned)nb, 256, 0, h->stream>>>(f32, (__nv_bfloat162*)h->d_pinv + bb * t0, g.bsz);
     }
     if ((e = cudaGetLastError()) != cudaSuccess) break;
   }
@@ -506,13 +505,18 @@ cudaError_t pc_apply(StabHandle* h, const double2* q, double2* z) {
   P.ntpts = g.ntpts; P.bsz = g.bsz; P.npts = h->npts;
   P.gate = h->gate;
   const int ts = phase_begin(h, STAB_PHASE_PRECOND_APPLY);
-  // row slices so that small grids still spread over the SMs
+  // row slices so that small grids still spread over the SMs.  FP64 / FP32 storage is
+  // row-major (a warp per row), BF16 column-major (a thread per row): measured fastest each
   int slices = (int)((2 * 152 + g.ntiles - 1) / g.ntiles);
   slices = std::max(1, std::min(slices, g.bsz / 32));
   const dim3 grid((unsigned)g.ntiles, (unsigned)slices);
-  if (h->pprec == 64) k_apply<double><<<grid, 256, g.bsz * sizeof(double2), h->stream>>>(P);
-  else if (h->pprec == 32) k_apply<float><<<grid, 256, g.bsz * sizeof(float2), h->stream>>>(P);
-  else k_apply_bf16<<<grid, 256, g.bsz * sizeof(float2), h->stream>>>(P);
+  if (h->pprec == 64) k_apply_rows<double><<<grid, 256, g.bsz * sizeof(double2), h->stream>>>(P);
+  else if (h->pprec == 32) k_apply_rows<float><<<grid, 256, g.bsz * sizeof(float2), h->stream>>>(P);
+  else {
+    const int rows = (g.bsz + slices - 1) / slices;
+    const int thr = std::min(256, ((rows + 31) / 32) * 32);
+    k_apply_cols<__nv_bfloat162, float><<<grid, thr, g.bsz * sizeof(float2), h->stream>>>(P);
+  }
   phase_end(h, ts);
   return cudaGetLastError();
 }
