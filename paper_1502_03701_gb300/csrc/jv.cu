@@ -70,7 +70,7 @@ struct PassParams {
   long long nlines;
   long long stride;
   int L, C, nchunks;
-  int KP;  // derivative kinds processed at once (1 or 2)
+  int KP;  // 1: kinds in turn, 2: side by side, 3: in turn with the input reloaded (2 planes)
   int LS;
   FastDiv divn, divL, divnx;  // division by n, L and nx  // padded shared-memory line stride in doubles, n + n/32 + 1
   int periodic;
@@ -147,6 +147,101 @@ __device__ __forceinline__ float d2f_hi(double d) { return ff_split(d).hi; }
 //   5. back substitution of the own chunk, written to global memory.
 // Threads: (kind, comp, line, chunk); x lines: chunk fastest, strided lines:
 // line fastest (neighbouring lines are neighbouring addresses).
+// Steps 2-5 for one kind on the plane Wk of this thread's line and component
+// (block-uniform call: contains barriers).
+__device__ __forceinline__ void line_sweeps(const PassParams& P, double* Wk, int kind, bool act, int t0, int t1,
+                                            long long base, int comp, double2* out) {
+  const int n = P.n;
+  const double* tl = P.tab[kind & 1];
+  const double* tm = tl + 2 * n;
+  const float* tlf = P.tabf[kind & 1];
+  const float* tmf = tlf + n;
+  const int K = P.K[kind & 1], Wn = P.Wn[kind & 1];
+  // 2. forward carry-in g'_{t0-1}
+  double g = 0.0;
+  if (act) {
+    if (P.periodic) {
+      const double lv = __ldg(tl);
+      const float lvf = __ldg(tlf);
+      float gf = 0.0f;
+      int tt = wrap_small(t0 - K, n);
+      int s = t0 - K;
+      for (; s < t0 - Wn; ++s) {
+        gf = fmaf(-lvf, gf, d2f_hi(Wk[sidx(tt)]));
+        if (++tt == n) tt = 0;
+      }
+      g = f2d_exact(gf);
+      for (; s < t0; ++s) {
+        g = fma(-lv, g, Wk[sidx(tt)]);
+        if (++tt == n) tt = 0;
+      }
+    } else if (t0 > 0) {
+      const int ts = (t0 - K < 8) ? 0 : t0 - K;
+      const int tw = max(ts, t0 - Wn);
+      float gf = 0.0f;
+      for (int t = ts; t < tw; ++t) gf = fmaf(-__ldg(tlf + t), gf, d2f_hi(Wk[sidx(t)]));
+      g = f2d_exact(gf);
+      for (int t = tw; t < t0; ++t) g = fma(-__ldg(tl + t), g, Wk[sidx(t)]);
+    }
+  }
+  __syncthreads();
+  // 3. forward sweep of the own chunk, in place
+  if (act) {
+    if (P.periodic) {
+      const double lv = __ldg(tl);
+      for (int t = t0; t < t1; ++t) {
+        g = fma(-lv, g, Wk[sidx(t)]);
+        Wk[sidx(t)] = g;
+      }
+    } else {
+      for (int t = t0; t < t1; ++t) {
+        g = fma(-__ldg(tl + t), g, Wk[sidx(t)]);
+        Wk[sidx(t)] = g;
+      }
+    }
+  }
+  __syncthreads();
+  // 4. back-substitution carry-in x_{t1}, 5. own chunk
+  if (act) {
+    double x = 0.0;
+    double* o = (double*)out + comp;
+    if (P.periodic) {
+      const double mm = __ldg(tm);
+      const float mmf = __ldg(tmf);
+      const int te = t1 - 1 + K;
+      int tt = wrap_small(te, n);
+      int s = te;
+      float xf = 0.0f;
+      for (; s > t1 - 1 + Wn; --s) {
+        xf = fmaf(-mmf, xf, d2f_hi(Wk[sidx(tt)]));
+        if (--tt < 0) tt = n - 1;
+      }
+      x = f2d_exact(xf);
+      for (; s >= t1; --s) {
+        x = fma(-mm, x, Wk[sidx(tt)]);
+        if (--tt < 0) tt = n - 1;
+      }
+      for (int t = t1 - 1; t >= t0; --t) {
+        x = fma(-mm, x, Wk[sidx(t)]);
+        o[2 * (base + (long long)t * P.stride)] = x;
+      }
+    } else {
+      if (t1 < n) {
+        const int te = (t1 - 1 + K > n - 9) ? n - 1 : t1 - 1 + K;
+        const int tw = min(te, t1 - 1 + Wn);
+        float xf = 0.0f;
+        for (int t = te; t > tw; --t) xf = fmaf(-__ldg(tmf + t), xf, d2f_hi(Wk[sidx(t)]));
+        x = f2d_exact(xf);
+        for (int t = tw; t >= t1; --t) x = fma(-__ldg(tm + t), x, Wk[sidx(t)]);
+      }
+      for (int t = t1 - 1; t >= t0; --t) {
+        x = fma(-__ldg(tm + t), x, Wk[sidx(t)]);
+        o[2 * (base + (long long)t * P.stride)] = x;
+      }
+    }
+  }
+}
+
 __global__ void k_line_pass(const PassParams P) {
   if (P.gate && *P.gate) return;
   extern __shared__ double sm[];
@@ -155,27 +250,29 @@ __global__ void k_line_pass(const PassParams P) {
   const int LS = P.LS;
   const size_t plane = (size_t)L * LS;
   double* F = sm;              // 2 planes
-  double* W = sm + 2 * plane;  // 2 KP planes
+  double* W = sm + 2 * plane;  // 2 KP planes (none in the compact mode)
   const long long l0 = (long long)blockIdx.x * L;
-
-  for (int idx = threadIdx.x; idx < n * L; idx += blockDim.x) {
-    int lt, t;
-    if (P.axis == 0) { lt = (int)fdiv(idx, P.divn); t = idx - lt * n; } else { t = (int)fdiv(idx, P.divL); lt = idx - t * L; }
-    const long long l = l0 + lt;
-    double2 val = make_double2(0.0, 0.0);
-    if (l < P.nlines) val = J.in[line_base(P, l) + (long long)t * P.stride];
-    F[(size_t)lt * LS + sidx(t)] = val.x;
-    F[plane + (size_t)lt * LS + sidx(t)] = val.y;
-  }
+  auto load_lines = [&]() {
+    for (int idx = threadIdx.x; idx < n * L; idx += blockDim.x) {
+      int lt, t;
+      if (P.axis == 0) { lt = (int)fdiv(idx, P.divn); t = idx - lt * n; } else { t = (int)fdiv(idx, P.divL); lt = idx - t * L; }
+      const long long l = l0 + lt;
+      double2 val = make_double2(0.0, 0.0);
+      if (l < P.nlines) val = J.in[line_base(P, l) + (long long)t * P.stride];
+      F[(size_t)lt * LS + sidx(t)] = val.x;
+      F[plane + (size_t)lt * LS + sidx(t)] = val.y;
+    }
+  };
   const int per = L * P.nchunks;
   const int ch = P.axis == 0 ? threadIdx.x % P.nchunks : (threadIdx.x / L) % P.nchunks;
   const int lt = P.axis == 0 ? (threadIdx.x / P.nchunks) % L : threadIdx.x % L;
   const int comp = (threadIdx.x / per) & 1;
+  const int t0 = ch * P.C, t1 = min(n, t0 + P.C);
+  const int nk = J.out2 ? 2 : 1;
+  load_lines();
   const int kt = threadIdx.x / (2 * per);  // this thread's kind within a group of KP
   const bool active = kt < KP && (l0 + lt) < P.nlines;
-  const int t0 = ch * P.C, t1 = min(n, t0 + P.C);
   const long long base = active ? line_base(P, l0 + lt) : 0;
-  const int nk = J.out2 ? 2 : 1;
   for (int kb = 0; kb < nk; kb += KP) {
     const int kg = min(KP, nk - kb);  // kinds in this group
     __syncthreads();  // F complete / the previous group's W no longer read
@@ -190,97 +287,63 @@ __global__ void k_line_pass(const PassParams P) {
     }
     __syncthreads();
     const int kind = kb + kt;
-    const bool act = active && kt < kg;
-    double2* out = kind == 0 ? J.out1 : J.out2;
-    const double* tl = P.tab[kind & 1];
-    const double* tm = tl + 2 * n;
-    const float* tlf = P.tabf[kind & 1];
-    const float* tmf = tlf + n;
-    const int K = P.K[kind & 1], Wn = P.Wn[kind & 1];
     double* Wk = W + (size_t)((kt & 1) * 2 + comp) * plane + (size_t)lt * LS;
-    // 2. forward carry-in g'_{t0-1}
-    double g = 0.0;
-    if (act) {
-      if (P.periodic) {
-        const double lv = __ldg(tl);
-        const float lvf = __ldg(tlf);
-        float gf = 0.0f;
-        int tt = wrap_small(t0 - K, n);
-        int s = t0 - K;
-        for (; s < t0 - Wn; ++s) {
-          gf = fmaf(-lvf, gf, d2f_hi(Wk[sidx(tt)]));
-          if (++tt == n) tt = 0;
-        }
-        g = f2d_exact(gf);
-        for (; s < t0; ++s) {
-          g = fma(-lv, g, Wk[sidx(tt)]);
-          if (++tt == n) tt = 0;
-        }
-      } else if (t0 > 0) {
-        const int ts = (t0 - K < 8) ? 0 : t0 - K;
-        const int tw = max(ts, t0 - Wn);
-        float gf = 0.0f;
-        for (int t = ts; t < tw; ++t) gf = fmaf(-__ldg(tlf + t), gf, d2f_hi(Wk[sidx(t)]));
-        g = f2d_exact(gf);
-        for (int t = tw; t < t0; ++t) g = fma(-__ldg(tl + t), g, Wk[sidx(t)]);
-      }
+    line_sweeps(P, Wk, kind, active && kt < kg, t0, t1, base, comp, kind == 0 ? J.out1 : J.out2);
+  }
+}
+
+// Compact variant (KP = 3): kinds in turn, the input reloaded per kind into
+// the only plane of each component; each thread's chunk of right-hand sides
+// (C <= 16) passes through registers so that it can replace the input in
+// place.  Half the shared memory of the kinds-in-turn layout.
+constexpr int kCompactMaxThreads = 512;
+__global__ void __launch_bounds__(kCompactMaxThreads) k_line_pass_compact(const PassParams P) {
+  if (P.gate && *P.gate) return;
+  extern __shared__ double sm[];
+  const LineJob J = P.job[blockIdx.y];
+  const int n = P.n, L = P.L;
+  const int LS = P.LS;
+  const size_t plane = (size_t)L * LS;
+  const long long l0 = (long long)blockIdx.x * L;
+  const int per = L * P.nchunks;
+  const int ch = P.axis == 0 ? threadIdx.x % P.nchunks : (threadIdx.x / L) % P.nchunks;
+  const int lt = P.axis == 0 ? (threadIdx.x / P.nchunks) % L : threadIdx.x % L;
+  const int comp = (threadIdx.x / per) & 1;
+  const int t0 = ch * P.C, t1 = min(n, t0 + P.C);
+  const int nk = J.out2 ? 2 : 1;
+  const bool active = threadIdx.x < 2 * per && (l0 + lt) < P.nlines;
+  const long long base = active ? line_base(P, l0 + lt) : 0;
+  double* Wc = sm + (size_t)comp * plane + (size_t)lt * LS;
+  for (int kind = 0; kind < nk; ++kind) {
+    __syncthreads();  // the previous kind's sweeps no longer read the planes
+    for (int idx = threadIdx.x; idx < n * L; idx += blockDim.x) {
+      int l, t;
+      if (P.axis == 0) { l = (int)fdiv(idx, P.divn); t = idx - l * n; } else { t = (int)fdiv(idx, P.divL); l = idx - t * L; }
+      double2 val = make_double2(0.0, 0.0);
+      if (l0 + l < P.nlines) val = J.in[line_base(P, l0 + l) + (long long)t * P.stride];
+      sm[(size_t)l * LS + sidx(t)] = val.x;
+      sm[plane + (size_t)l * LS + sidx(t)] = val.y;
     }
     __syncthreads();
-    // 3. forward sweep of the own chunk, in place
-    if (act) {
-      if (P.periodic) {
-        const double lv = __ldg(tl);
-        for (int t = t0; t < t1; ++t) {
-          g = fma(-lv, g, Wk[sidx(t)]);
-          Wk[sidx(t)] = g;
+    double rr[16];
+    const int len = t1 - t0;
+    if (active) {
+#pragma unroll
+      for (int q = 0; q < 16; ++q)
+        if (q < len) {
+          double r = stencil_rhs(P, Wc, t0 + q, kind);
+          if (!P.periodic) r *= __ldg(P.tab[kind] + n + t0 + q);
+          rr[q] = r;
         }
-      } else {
-        for (int t = t0; t < t1; ++t) {
-          g = fma(-__ldg(tl + t), g, Wk[sidx(t)]);
-          Wk[sidx(t)] = g;
-        }
-      }
     }
     __syncthreads();
-    // 4. back-substitution carry-in x_{t1}, 5. own chunk
-    if (act) {
-      double x = 0.0;
-      double* o = (double*)out + comp;
-      if (P.periodic) {
-        const double mm = __ldg(tm);
-        const float mmf = __ldg(tmf);
-        const int te = t1 - 1 + K;
-        int tt = wrap_small(te, n);
-        int s = te;
-        float xf = 0.0f;
-        for (; s > t1 - 1 + Wn; --s) {
-          xf = fmaf(-mmf, xf, d2f_hi(Wk[sidx(tt)]));
-          if (--tt < 0) tt = n - 1;
-        }
-        x = f2d_exact(xf);
-        for (; s >= t1; --s) {
-          x = fma(-mm, x, Wk[sidx(tt)]);
-          if (--tt < 0) tt = n - 1;
-        }
-        for (int t = t1 - 1; t >= t0; --t) {
-          x = fma(-mm, x, Wk[sidx(t)]);
-          o[2 * (base + (long long)t * P.stride)] = x;
-        }
-      } else {
-        if (t1 < n) {
-          const int te = (t1 - 1 + K > n - 9) ? n - 1 : t1 - 1 + K;
-          const int tw = min(te, t1 - 1 + Wn);
-          float xf = 0.0f;
-          for (int t = te; t > tw; --t) xf = fmaf(-__ldg(tmf + t), xf, d2f_hi(Wk[sidx(t)]));
-          x = f2d_exact(xf);
-          for (int t = tw; t >= t1; --t) x = fma(-__ldg(tm + t), x, Wk[sidx(t)]);
-        }
-        for (int t = t1 - 1; t >= t0; --t) {
-          x = fma(-__ldg(tm + t), x, Wk[sidx(t)]);
-          o[2 * (base + (long long)t * P.stride)] = x;
-        }
-      }
+    if (active) {
+#pragma unroll
+      for (int q = 0; q < 16; ++q)
+        if (q < len) Wc[sidx(t0 + q)] = rr[q];
     }
+    __syncthreads();
+    line_sweeps(P, Wc, kind, active, t0, t1, base, comp, kind == 0 ? J.out1 : J.out2);
   }
 }
 
@@ -868,10 +931,12 @@ static cudaError_t run_pass(StabHandle* h, int axis, const PassParams& base_para
   // (short lines, small grids: latency matters), else one after the other
   const long long fill = (P.nlines * (long long)jobs.size() + 2 * 152 - 1) / (2 * 152);
   P.KP = cfg.kp > 0 ? cfg.kp : (fill <= 4 ? 2 : 1);
-  const int tpl = 2 * P.KP * P.nchunks;  // threads per line
-  if (tpl > 1024) return cudaErrorInvalidValue;
-  const long long smem_line = (2 + 2 * P.KP) * 8 * LS;
-  const int maxL = std::min<long long>(std::min(1024 / tpl, 32), kLineSmemMax / smem_line);
+  if (P.KP == 3 && P.C > 16) return cudaErrorInvalidValue;  // the compact kernel keeps a chunk in registers
+  const int tpl = (P.KP == 2 ? 4 : 2) * P.nchunks;  // threads per line
+  const int max_threads = P.KP == 3 ? kCompactMaxThreads : 1024;
+  if (tpl > max_threads) return cudaErrorInvalidValue;
+  const long long smem_line = (P.KP == 3 ? 2 : 2 + 2 * P.KP) * 8 * LS;
+  const int maxL = std::min<long long>(std::min(max_threads / tpl, 32), kLineSmemMax / smem_line);
   if (maxL < 1) return cudaErrorInvalidValue;
   int L;
   if (cfg.L > 0) {
@@ -893,7 +958,8 @@ static cudaError_t run_pass(StabHandle* h, int axis, const PassParams& base_para
     P.njobs = (int)std::min<size_t>(STAB_MAX_JOBS, jobs.size() - j0);
     for (int q = 0; q < P.njobs; ++q) P.job[q] = jobs[j0 + q];
     dim3 grid((unsigned)((P.nlines + L - 1) / L), (unsigned)P.njobs);
-    k_line_pass<<<grid, threads, smem, h->stream>>>(P);
+    if (P.KP == 3) k_line_pass_compact<<<grid, threads, smem, h->stream>>>(P);
+    else k_line_pass<<<grid, threads, smem, h->stream>>>(P);
   }
   return cudaGetLastError();
 }
@@ -1018,15 +1084,21 @@ cudaError_t jv_autotune(StabHandle* h, int force, double* ms_out) {
     LineCfg best{};
     double best_ms = 1e300;
     const int n = h->ax[ax].n;
-    for (int kp : {1, 2}) {
+    for (int kp : {1, 2, 3}) {
       for (int C : {16, 32, 64}) {
         if (C > 16 && C >= 2 * n) continue;
+        if (kp == 3 && C > 16) continue;
         for (int L : {1, 2, 4, 8, 16, 32}) {
           const int nch = (n + C - 1) / C;
           const long long LS = n + (n >> 5) + 1;
-          if (2 * kp * nch * L > 1024 || (2 + 2 * kp) * 8 * LS * L > kLineSmemMax) continue;
+          const int tpl = (kp == 2 ? 4 : 2) * nch;
+          const int planes = kp == 3 ? 2 : 2 + 2 * kp;
+          if (tpl * L > (kp == 3 ? kCompactMaxThreads : 1024) || planes * 8 * LS * L > kLineSmemMax) continue;
           h->line_cfg[ax] = LineCfg{C, L, kp};
-          if ((err = run_pass(h, ax, P, jobs)) != cudaSuccess) break;  // warm-up
+          if (run_pass(h, ax, P, jobs) != cudaSuccess) {  // a shape this device cannot launch: skip it
+            cudaGetLastError();
+            continue;
+          }
           // three back-to-back launches per sample (less launch and clock noise), best of five samples
           float best_t = 1e30f;
           for (int r = 0; r < 5 && err == cudaSuccess; ++r) {
@@ -1084,7 +1156,7 @@ int jv_tune_load(const char* path) {
   LineCfg c;
   std::lock_guard<std::mutex> lk(g_tune_mu);
   while (std::fscanf(f, "%d %lld %d %d %d %d %d", &k.n, &k.nlines, &k.njobs, &k.periodic, &c.C, &c.L, &c.kp) == 7) {
-    if (c.C < 1 || c.L < 1 || c.kp < 1 || c.kp > 2 || k.n < 1) continue;
+    if (c.C < 1 || c.L < 1 || c.kp < 1 || c.kp > 3 || (c.kp == 3 && c.C > 16) || k.n < 1) continue;
     k.dev = dev;
     g_tune[k] = c;
     ++count;
@@ -1158,7 +1230,9 @@ cudaError_t jv_setup(StabHandle* h, const double* q0_host) {
   cudaError_t err;
   // set once per handle (current device), never during a stream capture
   if ((err = cudaFuncSetAttribute(k_line_pass, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLineSmemMax)) !=
-      cudaSuccess)
+          cudaSuccess ||
+      (err = cudaFuncSetAttribute(k_line_pass_compact, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)kLineSmemMax)) != cudaSuccess)
     return err;
   make_slots(h);
   // axis tables: x (0) periodic, y (1) bounded in eta, z (2) periodic

@@ -28,7 +28,7 @@ def test_every_line_shape_matches_oracle(orc, name, g, f):
     dv = torch.from_numpy(v).cuda()
     out = torch.empty_like(dv)
     tried = 0
-    for kinds in (1, 2):
+    for kinds in (1, 2, 3):
         for C in (16, 32, 64):
             for L in (1, 3, 8, 32):
                 ok = True
@@ -44,9 +44,11 @@ def test_every_line_shape_matches_oracle(orc, name, g, f):
                 assert max_rel_err(got, ref) < TOL, (C, L, kinds)
                 assert rel_err(got, ref) < TOL, (C, L, kinds)
                 tried += 1
-    assert tried >= 12
+    assert tried >= 14
     with pytest.raises(StabError):
         S.set_line_config(0, 24, 1, 1)
+    with pytest.raises(StabError):
+        S.set_line_config(0, 32, 1, 4)
     with pytest.raises(StabError):
         S.set_line_config(0, 32, 1, 3)
     S.close()
@@ -61,7 +63,7 @@ def test_autotune_picks_a_shape_and_shares_it(orc):
     res = S.autotune(force=True)
     assert set(res) == {"x", "y"}
     for C, L, kinds, ms in res.values():
-        assert C in (16, 32, 64) and 1 <= L <= 32 and kinds in (1, 2) and ms > 0
+        assert C in (16, 32, 64) and 1 <= L <= 32 and kinds in (1, 2, 3) and ms > 0
     v = si.random_complex(302, g.n)
     dv = torch.from_numpy(v).cuda()
     out = torch.empty_like(dv)
