@@ -163,6 +163,7 @@ __device__ __forceinline__ double2 warp_dot(const double2* __restrict__ x, const
   const int lane = threadIdx.x & 31;
   if (fp64) {
     double sr = 0.0, si = 0.0;
+#pragma unroll 4
     for (long long i = q0 + lane; i < q1; i += 32) {
       const double2 a = x[i], b = w[i];
       sr = fma(a.x, b.x, fma(a.y, b.y, sr));
@@ -171,6 +172,7 @@ __device__ __forceinline__ double2 warp_dot(const double2* __restrict__ x, const
     return make_double2(warp_sum(sr), warp_sum(si));
   }
   ffn sr{0.0f, 0.0f}, si{0.0f, 0.0f};
+#pragma unroll 4
   for (long long i = q0 + lane; i < q1; i += 32) {
     const double2 av = x[i], bv = w[i];
     const ffn ar = ff_split(av.x), ai = ff_split(av.y), br = ff_split(bv.x), bi = ff_split(bv.y);
@@ -224,6 +226,7 @@ __device__ __forceinline__ double2 row_update(const double2* __restrict__ V, int
                                               const double2* h64, const ffn* hre, const ffn* him, double2 wv) {
   ffn ar{0.0f, 0.0f}, ai{0.0f, 0.0f};
   double dr = 0.0, di = 0.0;
+#pragma unroll 4
   for (int j = 0; j < k; ++j) {
     const double2 a = V[(long long)j * n + i];
     if (fp64_column(j)) {
