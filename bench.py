@@ -12,6 +12,7 @@ traffic (32 B per complex unknown).  Also reported, measured in the same run:
     < 1e-8), the p50 / p99 solve latency and the J v count per solve;
   * "gmres_256x512": preconditioned FGMRES(50) iterations per second on the
     256 x 512 layer (block-Jacobi over 8 x 8-point tiles, FP32 inverses);
+  * "jv_3d": the same J v on the 3-D 128 x 256 x 64 layer (10.5 M unknowns);
   * "many_small": uneven small layers solved one at a time on the plain FP64
     path, as one mixed-precision batch (stab_eigs_batch), and as a Poisson
     stream through the continuous-batching server (p50 / p99 latency).
@@ -243,6 +244,28 @@ def small_layer_eigs(args, Stab, torch, rank):
             "jv_per_solve": statistics.mean(r.stats["jv_calls"] for r in res),
             "gmres_iterations_per_solve": statistics.mean(r.stats["gmres_iterations"] for r in res),
             "restarts": [r.stats["restarts"] for r in res]}
+
+
+def jv_3d(args, Stab, torch, flush, stream) -> dict:
+    """J v on the 3-D 128 x 256 x 64 layer (10.5 M complex unknowns), autotuned, L2 flushed between steps."""
+    g, f = si.mixing_layer_3d(128, 256, 64, Ma=0.3)
+    q0 = si.tanh_base_flow(g, f)
+    S = Stab(q0, g, f.Ma, f.Re, f.Pr)
+    tuned = S.autotune()
+    v = torch.from_numpy(si.random_complex(21, g.n)).cuda()
+    out = torch.empty_like(v)
+    for _ in range(3):
+        S.apply_J(v, out)
+    S.timing(True)
+    steps = _time_jv(S, v, out, args.steps_3d, flush, stream, torch)
+    ph = S.timing_read()
+    S.close()
+    t = statistics.mean(steps)
+    total = sum(x[0] for k, x in ph.items() if k != "dropped")
+    return {"workload": "jv_mixing_layer_128x256x64", "value": g.n * JV_BYTES_PER_DOF / t / 1e9, "unit": "GB/s",
+            "ms_per_step": t * 1e3, "steps": args.steps_3d, "unknowns": g.n,
+            "line_pass_shapes": {ax: {"C": c, "L": l, "kinds": k} for ax, (c, l, k, _) in tuned.items()},
+            "phase_share": {k: x[0] / total for k, x in ph.items() if k != "dropped" and x[1]}}
 
 
 def gmres_throughput(args, Stab, torch, q0, g, f):
@@ -571,6 +594,8 @@ def run_ours(args):
             extra["gmres_256x512"] = gmres_throughput(args, Stab, torch, q0, g, f)
         if args.fleet > 0 and world == 1:
             extra["many_small"] = fleet(args, torch)
+        if args.steps_3d > 0:
+            extra["jv_3d"] = jv_3d(args, Stab, torch, flush, stream)
     else:
         # roofline of the J v kernels from a short phase-timed sample (the solves below are host-driven)
         Sj.timing(True)
@@ -690,6 +715,7 @@ def main():
     ap.add_argument("--rate", type=float, default=50.0, help="Poisson arrival rate of the served stream (1/s)")
     ap.add_argument("--slots", type=int, default=8)
     ap.add_argument("--budget-gb", type=int, default=64)
+    ap.add_argument("--steps-3d", type=int, default=50, help="timed J v steps on the 128 x 256 x 64 layer (0: skip)")
     ap.add_argument("--tune-cache", default="", help="line-pass tuning cache file to load before and save after tuning")
     args = ap.parse_args()
     if args.impl == "reference":
