@@ -299,6 +299,8 @@ typedef struct {
   double sigma_re, sigma_im, tau_re, tau_im;
   int nev, ncv;
   double tol;
+  void* vecs;               /* host complex128 n x nev (vector q at vecs + q n) receiving the unit
+                               eigenvectors, or NULL; must stay valid until the request has finished */
 } stab_request;
 
 typedef struct {

@@ -74,7 +74,8 @@ class Request(ctypes.Structure):
     _fields_ = [("base_flow", ctypes.POINTER(ctypes.c_double)), ("grid", Grid), ("Ma", ctypes.c_double),
                 ("Re", ctypes.c_double), ("Pr", ctypes.c_double), ("opts", ctypes.POINTER(Opts)),
                 ("sigma_re", ctypes.c_double), ("sigma_im", ctypes.c_double), ("tau_re", ctypes.c_double),
-                ("tau_im", ctypes.c_double), ("nev", ctypes.c_int), ("ncv", ctypes.c_int), ("tol", ctypes.c_double)]
+                ("tau_im", ctypes.c_double), ("nev", ctypes.c_int), ("ncv", ctypes.c_int), ("tol", ctypes.c_double),
+                ("vecs", ctypes.c_void_p)]
 
 
 class RequestInfo(ctypes.Structure):
@@ -374,7 +375,8 @@ class Server:
         self._nev = {}
 
     def submit(self, base_flow, grid, Ma: float, Re: float, Pr: float, sigma: complex, tau: complex, nev: int,
-               ncv: int, tol: float, **opts) -> int:
+               ncv: int, tol: float, vectors: bool = False, **opts) -> int:
+        """Queue a request; with vectors=True result() also returns the eigenvectors (nev x n)."""
         bf = np.ascontiguousarray(np.asarray(base_flow, dtype=np.float64).reshape(-1))
         o = default_opts(**opts)
         q = Request()
@@ -385,11 +387,16 @@ class Server:
         q.sigma_re, q.sigma_im = complex(sigma).real, complex(sigma).imag
         q.tau_re, q.tau_im = complex(tau).real, complex(tau).imag
         q.nev, q.ncv, q.tol = nev, ncv, tol
+        vecs = None
+        if vectors:
+            n = (grid.dim + 2) * grid.nx * grid.ny * grid.nz
+            vecs = np.zeros((nev, n), dtype=np.complex128)
+            q.vecs = vecs.ctypes.data
         rid = ctypes.c_longlong()
         st = self._L.stab_server_submit(self._s, ctypes.byref(q), ctypes.byref(rid))
         if st != 0:
             raise StabError(st, "stab_server_submit failed")
-        self._nev[rid.value] = nev
+        self._nev[rid.value] = (nev, vecs)
         return rid.value
 
     def wait(self, rid: int, timeout_s: float = -1.0) -> bool:
@@ -399,8 +406,9 @@ class Server:
         return st == 0
 
     def result(self, rid: int):
-        """(eigenvalues, residuals, info dict) of a finished request (forgotten afterwards)."""
-        nev = self._nev.pop(rid)
+        """(eigenvalues, residuals, info dict) of a finished request (forgotten afterwards); info["vecs"]
+        holds the eigenvectors when the request asked for them."""
+        nev, vecs = self._nev.pop(rid)
         lam = np.zeros(2 * nev)
         res = np.zeros(nev)
         info = RequestInfo()
@@ -408,10 +416,12 @@ class Server:
         st = self._L.stab_server_result(self._s, rid, lam.ctypes.data_as(dp), res.ctypes.data_as(dp),
                                         ctypes.byref(info))
         if st != 0:
-            self._nev[rid] = nev
+            self._nev[rid] = (nev, vecs)
             raise StabError(st, "stab_server_result: not finished or unknown")
         d = {k: getattr(info, k) for k, _ in info._fields_ if k != "stats"}
         d["stats"] = info.stats.as_dict()
+        if vecs is not None:
+            d["vecs"] = vecs
         return lam.view(np.complex128), res, d
 
     def stats(self) -> dict:

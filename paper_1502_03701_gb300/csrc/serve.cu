@@ -144,6 +144,7 @@ struct ServerReq {
   double sr = 0, si = 0, tr = 0, ti = 0, tol = 0;
   int nev = 0, ncv = 0;
   long long est = 0;
+  void* vecs_host = nullptr;
   // results
   bool done = false;
   stab_status status = STAB_OK;
@@ -197,9 +198,23 @@ void serve_one(stab_server_s* S, ServerReq* R, cudaStream_t st) {
     return;
   }
   if (S->autotune) stab_autotune(h, 0, nullptr, nullptr);
-  R->status = stab_eigs(h, R->sr, R->si, R->tr, R->ti, R->nev, R->ncv, R->tol, nullptr, R->lambda.data(), nullptr,
+  void* dvecs = nullptr;
+  const size_t vbytes = (size_t)R->nev * stab_size(h) * 2 * sizeof(double);
+  if (R->vecs_host && cudaMallocAsync(&dvecs, vbytes, st) != cudaSuccess) {
+    R->status = STAB_ERR_OOM;
+    R->err = "eigenvector buffer";
+    stab_destroy(h);
+    return;
+  }
+  R->status = stab_eigs(h, R->sr, R->si, R->tr, R->ti, R->nev, R->ncv, R->tol, nullptr, R->lambda.data(), dvecs,
                         R->resid.data(), &R->nconv, &R->stats);
   if (R->status != STAB_OK) R->err = stab_last_error(h);
+  if (dvecs) {
+    if (R->status == STAB_OK || R->status == STAB_ERR_NOT_CONVERGED)
+      cudaMemcpyAsync(R->vecs_host, dvecs, vbytes, cudaMemcpyDeviceToHost, st);
+    cudaFreeAsync(dvecs, st);
+    cudaStreamSynchronize(st);
+  }
   stab_destroy(h);
 }
 
@@ -278,7 +293,9 @@ extern "C" stab_status stab_server_submit(stab_server S, const stab_request* q, 
   R->nev = q->nev;
   R->ncv = q->ncv;
   R->tol = q->tol;
-  R->est = stab_estimate_bytes(&g, &R->opts, y_only(R->q0, g, g.dim + 2), q->nev, q->ncv);
+  R->vecs_host = q->vecs;
+  R->est = stab_estimate_bytes(&g, &R->opts, y_only(R->q0, g, g.dim + 2), q->nev, q->ncv) +
+           (q->vecs ? (long long)q->nev * n * 16 : 0);
   R->t_submit = Clock::now();
   {
     std::lock_guard<std::mutex> lk(S->mu);

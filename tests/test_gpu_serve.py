@@ -69,15 +69,27 @@ def test_server_same_alone_and_in_mix(alone):
     from paper_1502_03701_gb300 import Server
     srv = Server(slots=4, mem_budget_bytes=8 << 30)
     ids = []
-    for p in PROBLEMS:
+    for i, p in enumerate(PROBLEMS):
         g, f, q0 = _problem(*p)
-        ids.append(srv.submit(q0, g, f.Ma, f.Re, f.Pr, *EIG, **OPTS))
+        ids.append(srv.submit(q0, g, f.Ma, f.Re, f.Pr, *EIG, vectors=(i == 0), **OPTS))
     for rid, ref, p in zip(ids, alone, PROBLEMS):
         assert srv.wait(rid, 600.0)
         got, res, info = srv.result(rid)
         assert info["status"] == 0 and info["nconv"] == EIG[2], p
         assert _same(got, res, ref), (p, got, ref)
         assert info["latency_s"] >= info["run_s"] > 0 and info["est_bytes"] > 0
+        if "vecs" in info:  # unit eigenvectors with the reported residual ||J x - lambda x||
+            from paper_1502_03701_gb300 import Stab
+            import torch
+            g, f, q0 = _problem(*p)
+            S = Stab(q0, g, f.Ma, f.Re, f.Pr, eps_mode=2)
+            for q in range(EIG[2]):
+                x = torch.from_numpy(info["vecs"][q].copy()).cuda()
+                jx = torch.empty_like(x)
+                S.apply_J(x, jx, got[q])
+                assert abs(float(torch.linalg.vector_norm(x)) - 1.0) < 1e-12
+                assert float(torch.linalg.vector_norm(jx)) == pytest.approx(res[q], rel=1e-3, abs=1e-13)
+            S.close()
     st = srv.stats()
     assert st["peak_running"] >= 2          # requests overlapped on the device
     assert st["running"] == 0 and st["queued"] == 0
