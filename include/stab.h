@@ -73,6 +73,10 @@ typedef struct {
                              inverted in FP32, stored in bfloat16, applied with FP32 accumulation) */
   int max_restarts;       /* IRAM restart limit, default 300 */
   unsigned long long seed;/* start vector seed when no v0 is given, default 0x5EED */
+  int gmres_basis_prec;   /* GMRES Krylov basis and its orthogonalisation: 64 (FP64 flexible GMRES,
+                             default) or 32 (FP32 basis, non-flexible right preconditioning; J v, the
+                             solution update and the true residual of every restart stay FP64, so the
+                             restarts refine the solution to the FP64 tolerance) */
 } stab_opts;
 
 typedef struct {

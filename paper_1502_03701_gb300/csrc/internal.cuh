@@ -52,13 +52,14 @@ struct Slots {
 struct GmGraphKey {
   bool valid = false;
   double sigma_re = 0, sigma_im = 0;
-  int eps_mode = -1, m = 0, pc = 0, pprec = 0;
+  int eps_mode = -1, m = 0, pc = 0, pprec = 0, basis = 64;
   const void* ws = nullptr;
   const void* pinv = nullptr;
   long long n = 0;
   bool operator==(const GmGraphKey& o) const {
     return valid && o.valid && sigma_re == o.sigma_re && sigma_im == o.sigma_im && eps_mode == o.eps_mode &&
-           m == o.m && pc == o.pc && pprec == o.pprec && ws == o.ws && pinv == o.pinv && n == o.n;
+           m == o.m && pc == o.pc && pprec == o.pprec && ws == o.ws && pinv == o.pinv && n == o.n &&
+           basis == o.basis;
   }
 };
 
@@ -180,6 +181,13 @@ int kry_partial_elems(long long n, int k);
 int kry_dgks_partial_elems(long long n, int k);
 cudaError_t kry_dgks(StabHandle* h, const double2* V, int k, long long n, double2* w, double2* d_h, double* d_norm,
                      double2* partial);
+cudaError_t kry_dgks32(StabHandle* h, const float2* V, int k, long long n, float2* w, double2* d_h, double* d_norm,
+                       double2* partial);
+cudaError_t kry_to_f32(StabHandle* h, const double2* in, long long n, const double* d_norm, float2* out);
+cudaError_t kry_scale32(StabHandle* h, float2* x, long long n, const double* d_norm);
+cudaError_t kry_to_f64(StabHandle* h, const float2* in, long long n, double2* out);
+cudaError_t kry_gemv32(StabHandle* h, const float2* V, int k, const int* kdev, long long n, const double2* y,
+                       double2* out);
 cudaError_t kry_init_attributes();
 cudaError_t kry_cgs2_stream(cudaStream_t st, const double2* V, int k, long long n, double2* w, double2* d_h,
                             double* d_norm, double2* partial, double* norm_partial, int norm_blocks);
@@ -188,6 +196,6 @@ cudaError_t launch_norm2_stream(cudaStream_t st, const double2* v, long long n, 
 
 // precond.cu
 cudaError_t pc_build(StabHandle* h, double2 sigma);
-cudaError_t pc_apply(StabHandle* h, const double2* q, double2* z);
+cudaError_t pc_apply(StabHandle* h, const double2* q, double2* z, const float2* q32 = nullptr);
 cudaError_t pc_block(StabHandle* h, double2 sigma, long long t, double2* d_out);
 

@@ -188,13 +188,34 @@ __device__ __forceinline__ double2 warp_dot(const double2* __restrict__ x, const
 
 // partial_out[b * k + j] = this block's sum of conj(V_j) w over [r0, r1).
 // red: shared, one double2 per warp.  Block-uniform control flow.
-__device__ __forceinline__ void block_dot_columns(const double2* __restrict__ V, int k, long long n, long long r0,
-                                                  long long r1, const double2* w, double2* partial_out,
-                                                  double2* red) {
+// FP32 basis: FP32 FMAs per lane, FP64 across lanes (the basis itself carries FP32 precision)
+__device__ __forceinline__ double2 warp_dot32(const float2* __restrict__ x, const float2* __restrict__ w, long long q0,
+                                              long long q1) {
+  const int lane = threadIdx.x & 31;
+  float sr = 0.f, si = 0.f;
+#pragma unroll 4
+  for (long long i = q0 + lane; i < q1; i += 32) {
+    const float2 a = x[i], b = w[i];
+    sr = fmaf(a.x, b.x, fmaf(a.y, b.y, sr));
+    si = fmaf(a.x, b.y, fmaf(-a.y, b.x, si));
+  }
+  return make_double2(warp_sum((double)sr), warp_sum((double)si));
+}
+
+__device__ __forceinline__ double2 col_dot(const double2* x, const double2* w, long long q0, long long q1, int j) {
+  return warp_dot(x, w, q0, q1, fp64_column(j));
+}
+__device__ __forceinline__ double2 col_dot(const float2* x, const float2* w, long long q0, long long q1, int) {
+  return warp_dot32(x, w, q0, q1);
+}
+
+template <class T>
+__device__ __forceinline__ void block_dot_columns(const T* __restrict__ V, int k, long long n, long long r0,
+                                                  long long r1, const T* w, double2* partial_out, double2* red) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   if (k >= nw) {
     for (int j = wid; j < k; j += nw) {
-      const double2 d = warp_dot(V + (long long)j * n, w, r0, r1, fp64_column(j));
+      const double2 d = col_dot(V + (long long)j * n, w, r0, r1, j);
       if (lane == 0) partial_out[(long long)blockIdx.x * k + j] = d;
     }
     return;
@@ -204,7 +225,7 @@ __device__ __forceinline__ void block_dot_columns(const double2* __restrict__ V,
   if (wid < G * k) {
     const int j = wid / G, sg = wid - j * G;
     const long long len = r1 - r0;
-    d = warp_dot(V + (long long)j * n, w, r0 + len * sg / G, r0 + len * (sg + 1) / G, fp64_column(j));
+    d = col_dot(V + (long long)j * n, w, r0 + len * sg / G, r0 + len * (sg + 1) / G, j);
   }
   if (lane == 0) red[wid] = d;
   __syncthreads();
@@ -338,12 +359,13 @@ __global__ void k_norm_final(const double* partial, int nb, double* out, const i
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ bool gated(const int* a, const int* b) { return (a && *a) || (b && *b); }
 
-__device__ __forceinline__ double block_norm_partial(const double2* w, long long r0, long long r1, double* red) {
+__device__ __forceinline__ double norm2_of(double2 z) { return z.x * z.x + z.y * z.y; }
+__device__ __forceinline__ double norm2_of(float2 z) { return (double)fmaf(z.x, z.x, z.y * z.y); }
+
+template <class T>
+__device__ __forceinline__ double block_norm_partial(const T* w, long long r0, long long r1, double* red) {
   double s = 0.0;
-  for (long long i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
-    const double2 z = w[i];
-    s = fma(z.x, z.x, fma(z.y, z.y, s));
-  }
+  for (long long i = r0 + threadIdx.x; i < r1; i += blockDim.x) s += norm2_of(w[i]);
   s = warp_sum(s);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   if (lane == 0) red[wid] = s;
@@ -357,8 +379,9 @@ __device__ __forceinline__ double block_norm_partial(const double2* w, long long
 }
 
 // pass-1 dots and the block's |w|^2
-__global__ void __launch_bounds__(kThreads) k_dgks_dots(const double2* __restrict__ V, int k, long long n,
-                                                       const double2* __restrict__ w, double2* partial,
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_dgks_dots(const T* __restrict__ V, int k, long long n,
+                                                       const T* __restrict__ w, double2* partial,
                                                        double* norm_partial, const int* gate, const int* skip) {
   if (gated(gate, skip)) return;
   __shared__ double2 red[kThreads / 32];
@@ -432,6 +455,93 @@ __global__ void k_dgks_norm(const double* partial, int nb, double* out, const in
   for (int i = threadIdx.x; i < nb; i += 32) s += partial[i];
   s = warp_sum(s);
   if (threadIdx.x == 0) *out = sqrt(s);
+}
+
+// FP32 basis: h = reduced partials (block 0 stores or adds it to d_h in
+// FP64), w -= V h in FP32 over the block's rows, the block's |w|^2.
+__global__ void __launch_bounds__(kThreads) k_dgks32_update(const float2* __restrict__ V, int k, long long n, float2* w,
+                                                           const double2* partial, double2* d_h, double* norm_partial,
+                                                           int accumulate, const int* gate, const int* skip) {
+  if (gated(gate, skip)) return;
+  extern __shared__ double2 hs[];  // k complex (FP64), then k float2
+  __shared__ double red[kThreads / 32];
+  float2* hf = (float2*)(hs + k);
+  reduce_partials(partial, gridDim.x, k, hs);
+  __syncthreads();
+  for (int j = threadIdx.x; j < k; j += blockDim.x) {
+    hf[j] = make_float2((float)hs[j].x, (float)hs[j].y);
+    if (blockIdx.x == 0) {
+      if (accumulate) {
+        const double2 h1 = d_h[j];
+        d_h[j] = make_double2(h1.x + hs[j].x, h1.y + hs[j].y);
+      } else {
+        d_h[j] = hs[j];
+      }
+    }
+  }
+  __syncthreads();
+  long long r0, r1;
+  block_rows(n, r0, r1);
+  for (long long i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+    float ar = 0.f, ai = 0.f;
+#pragma unroll 4
+    for (int j = 0; j < k; ++j) {
+      const float2 a = V[(long long)j * n + i], c = hf[j];
+      ar = fmaf(a.x, c.x, fmaf(-a.y, c.y, ar));
+      ai = fmaf(a.x, c.y, fmaf(a.y, c.x, ai));
+    }
+    const float2 wv = w[i];
+    w[i] = make_float2(wv.x - ar, wv.y - ai);
+  }
+  __syncthreads();
+  const double t = block_norm_partial(w, r0, r1, red);
+  if (threadIdx.x == 0) norm_partial[blockIdx.x] = t;
+}
+
+// out (FP32) = in (FP64) / *d_norm (d_norm may be NULL: plain rounding); gated
+__global__ void k_to_f32(const double2* in, long long n, const double* d_norm, float2* out, const int* gate) {
+  if (gate && *gate) return;
+  const double s = d_norm ? 1.0 / *d_norm : 1.0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double2 v = in[i];
+    out[i] = make_float2((float)(v.x * s), (float)(v.y * s));
+  }
+}
+
+// out (FP64) = in (FP32); gated
+__global__ void k_to_f64(const float2* in, long long n, double2* out, const int* gate) {
+  if (gate && *gate) return;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    out[i] = make_double2(in[i].x, in[i].y);
+}
+
+// x (FP32) /= *d_norm in place; gated
+__global__ void k_scale32(float2* x, long long n, const double* d_norm, const int* gate) {
+  if (gate && *gate) return;
+  const float s = (float)(1.0 / *d_norm);
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const float2 v = x[i];
+    x[i] = make_float2(v.x * s, v.y * s);
+  }
+}
+
+// out (FP64) = sum_{j < min(k, *kdev)} V_j y_j over an FP32 basis (FP32 products)
+__global__ void __launch_bounds__(kThreads) k_gemv32(const float2* __restrict__ V, int k, const int* kdev, long long n,
+                                                    const double2* __restrict__ y, double2* out) {
+  if (kdev) k = min(k, *kdev);
+  extern __shared__ float2 ys[];
+  for (int j = threadIdx.x; j < k; j += blockDim.x) ys[j] = make_float2((float)y[j].x, (float)y[j].y);
+  __syncthreads();
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    float ar = 0.f, ai = 0.f;
+#pragma unroll 4
+    for (int j = 0; j < k; ++j) {
+      const float2 a = V[(long long)j * n + i], c = ys[j];
+      ar = fmaf(a.x, c.x, fmaf(-a.y, c.y, ar));
+      ai = fmaf(a.x, c.y, fmaf(a.y, c.x, ai));
+    }
+    out[i] = make_double2(ar, ai);
+  }
 }
 
 // blocks of the fused CGS2: about 64 rows each (short latency on small
@@ -544,13 +654,58 @@ cudaError_t kry_dgks(StabHandle* h, const double2* V, int k, long long n, double
   int* skip = (int*)(np2 + nb);
   const size_t sm = (size_t)k * (sizeof(double2) + 2 * sizeof(ffn));
   constexpr double eta = 0.70710678118654752;
-  k_dgks_dots<<<nb, kThreads, 0, h->stream>>>(V, k, n, w, p1, np0, h->gate, nullptr);
+  k_dgks_dots<double2><<<nb, kThreads, 0, h->stream>>>(V, k, n, w, p1, np0, h->gate, nullptr);
   k_dgks_update<<<nb, kThreads, sm, h->stream>>>(V, k, n, w, p1, d_h, np1, 0, h->gate, nullptr);
   k_dgks_decide<<<1, 32, 0, h->stream>>>(np0, np1, nb, d_norm, skip, eta, h->gate);
-  k_dgks_dots<<<nb, kThreads, 0, h->stream>>>(V, k, n, w, p2, nullptr, h->gate, skip);
+  k_dgks_dots<double2><<<nb, kThreads, 0, h->stream>>>(V, k, n, w, p2, nullptr, h->gate, skip);
   k_dgks_update<<<nb, kThreads, sm, h->stream>>>(V, k, n, w, p2, d_h, np2, 1, h->gate, skip);
   k_dgks_norm<<<1, 32, 0, h->stream>>>(np2, nb, d_norm, h->gate, skip);
   phase_end(h, ts);
+  return cudaGetLastError();
+}
+
+// FP32 basis: the selective Gram-Schmidt of kry_dgks in FP32 arithmetic
+// (h and ||w|| in FP64); partial holds kry_dgks_partial_elems complex.
+cudaError_t kry_dgks32(StabHandle* h, const float2* V, int k, long long n, float2* w, double2* d_h, double* d_norm,
+                       double2* partial) {
+  const int ts = phase_begin(h, STAB_PHASE_CGS2);
+  const int nb = cgs_blocks(n);
+  double2* p1 = partial;
+  double2* p2 = partial + (size_t)nb * k;
+  double* np0 = (double*)(p2 + (size_t)nb * k);
+  double* np1 = np0 + nb;
+  double* np2 = np1 + nb;
+  int* skip = (int*)(np2 + nb);
+  const size_t sm = (size_t)k * (sizeof(double2) + sizeof(float2));
+  constexpr double eta = 0.70710678118654752;
+  k_dgks_dots<float2><<<nb, kThreads, 0, h->stream>>>(V, k, n, w, p1, np0, h->gate, nullptr);
+  k_dgks32_update<<<nb, kThreads, sm, h->stream>>>(V, k, n, w, p1, d_h, np1, 0, h->gate, nullptr);
+  k_dgks_decide<<<1, 32, 0, h->stream>>>(np0, np1, nb, d_norm, skip, eta, h->gate);
+  k_dgks_dots<float2><<<nb, kThreads, 0, h->stream>>>(V, k, n, w, p2, nullptr, h->gate, skip);
+  k_dgks32_update<<<nb, kThreads, sm, h->stream>>>(V, k, n, w, p2, d_h, np2, 1, h->gate, skip);
+  k_dgks_norm<<<1, 32, 0, h->stream>>>(np2, nb, d_norm, h->gate, skip);
+  phase_end(h, ts);
+  return cudaGetLastError();
+}
+
+cudaError_t kry_to_f32(StabHandle* h, const double2* in, long long n, const double* d_norm, float2* out) {
+  k_to_f32<<<grid_n(n), kThreads, 0, h->stream>>>(in, n, d_norm, out, h->gate);
+  return cudaGetLastError();
+}
+
+cudaError_t kry_to_f64(StabHandle* h, const float2* in, long long n, double2* out) {
+  k_to_f64<<<grid_n(n), kThreads, 0, h->stream>>>(in, n, out, h->gate);
+  return cudaGetLastError();
+}
+
+cudaError_t kry_scale32(StabHandle* h, float2* x, long long n, const double* d_norm) {
+  k_scale32<<<grid_n(n), kThreads, 0, h->stream>>>(x, n, d_norm, h->gate);
+  return cudaGetLastError();
+}
+
+cudaError_t kry_gemv32(StabHandle* h, const float2* V, int k, const int* kdev, long long n, const double2* y,
+                       double2* out) {
+  k_gemv32<<<grid_n(n), kThreads, k * sizeof(float2), h->stream>>>(V, k, kdev, n, y, out);
   return cudaGetLastError();
 }
 

@@ -242,6 +242,7 @@ struct ApplyParams {
   int nx, ny, tx, ty, tz, ntx, nty, ntpts, bsz;
   long long npts;
   const int* gate;  // when set and nonzero the launch does nothing (graph-captured GMRES after convergence)
+  const float2* q32;  // FP32 input (GMRES with an FP32 basis) instead of q
 };
 
 __device__ __forceinline__ long long tile_dof(const ApplyParams& P, long long tile, int r) {
@@ -276,7 +277,8 @@ __global__ void k_apply_cols(const ApplyParams P) {
   const int rb1 = (int)((long long)b * (blockIdx.y + 1) / gridDim.y);
   const S* Mt = (const S*)P.inv + (long long)tile * b * b;
   for (int r = threadIdx.x; r < b; r += blockDim.x) {
-    const double2 v = P.q[tile_dof(P, tile, r)];
+    const long long d = tile_dof(P, tile, r);
+    const double2 v = P.q32 ? make_double2(P.q32[d].x, P.q32[d].y) : P.q[d];
     qs[r] = C2<R>{(R)v.x, (R)v.y};
   }
   __syncthreads();
@@ -308,7 +310,8 @@ __global__ void k_apply_rows(const ApplyParams P) {
   const int rb1 = (int)((long long)P.bsz * (blockIdx.y + 1) / gridDim.y);
   const C2<R>* M = (const C2<R>*)P.inv + (long long)tile * P.bsz * P.bsz;
   for (int r = threadIdx.x; r < P.bsz; r += blockDim.x) {
-    double2 v = P.q[tile_dof(P, tile, r)];
+    const long long d = tile_dof(P, tile, r);
+    const double2 v = P.q32 ? make_double2(P.q32[d].x, P.q32[d].y) : P.q[d];
     qs[r] = C2<R>{(R)v.x, (R)v.y};
   }
   __syncthreads();
@@ -495,12 +498,12 @@ cudaError_t pc_build(StabHandle* h, double2 sigma) {
   return cudaSuccess;
 }
 
-cudaError_t pc_apply(StabHandle* h, const double2* q, double2* z) {
+cudaError_t pc_apply(StabHandle* h, const double2* q, double2* z, const float2* q32) {
   if (!h->pvalid) return cudaErrorInvalidValue;
   Geo g;
   tile_geo(h, g);
   ApplyParams P{};
-  P.q = q; P.z = z; P.inv = h->d_pinv;
+  P.q = q; P.z = z; P.inv = h->d_pinv; P.q32 = q32;
   P.nx = h->nx; P.ny = h->ny; P.tx = g.tx; P.ty = g.ty; P.tz = g.tz; P.ntx = g.ntx; P.nty = g.nty;
   P.ntpts = g.ntpts; P.bsz = g.bsz; P.npts = h->npts;
   P.gate = h->gate;

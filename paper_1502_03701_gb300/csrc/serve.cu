@@ -53,7 +53,8 @@ extern "C" long long stab_estimate_bytes(const stab_grid* g, const stab_opts* op
   b += scratch_fields(D, visc) * npts * 16;                // derivative fields
   b += (nv + 1) * npts * 16;                               // set-up temporary
   const long long m = o.gmres_m, pc = o.precond == 1;
-  b += ((m + 1) + pc * m + 3) * n * 16;                    // GMRES basis, Z, r, b, x
+  if (o.gmres_basis_prec == 32) b += (m + 1) * n * 8 + 6 * n * 16;  // FP32 basis; r, b, x, w, z, t
+  else b += ((m + 1) + pc * m + 3) * n * 16;               // GMRES basis, Z, r, b, x
   b += 2 * 608 * (m + 2) * 16;                             // CGS2 partial sums
   b += ((long long)ncv + 2 + nev + 1) * n * 16;            // Arnoldi basis, f, x, restart temporary
   if (pc) {

@@ -51,10 +51,14 @@ double2* ensure(StabHandle* h, double2** p, size_t* have, size_t need) {
   return *p;
 }
 
-// GMRES workspace layout (complex elements)
+// GMRES workspace layout (complex elements).  FP64 basis: V, Z (flexible).
+// FP32 basis: V32, and FP64 work vectors w (J z), zt (preconditioned
+// direction or correction) and t (V32 y).
 struct GmresWs {
   double2 *V, *Z, *r, *b, *x, *partial, *dh, *y;
   double* dnorm;
+  float2* V32;
+  double2 *w, *zt, *t;
 };
 
 constexpr int kMaxGmresM = 200;  // stab_create rejects larger gmres_m
@@ -85,17 +89,31 @@ GmresWs gmres_ws(StabHandle* h, GmDev* D, GmReport** rep) {
   const long long n = h->n;
   const int m = h->opts.gmres_m;
   const bool pc = h->opts.precond == 1;
+  const bool b32 = h->opts.gmres_basis_prec == 32;
   const size_t part = (size_t)std::max(kry_partial_elems(n, m + 1), kry_dgks_partial_elems(n, m + 1));
   const size_t small = (size_t)m * m + (m + 1) + m + (m + 1) / 2 + 1 + 4 + 4;
-  size_t need = (size_t)(m + 1) * n + (pc ? (size_t)m * n : 0) + 3 * (size_t)n + part + 2 * (m + 1) + (m + 1) + 4 + small;
+  const size_t basis = b32 ? ((size_t)(m + 1) * n + 1) / 2 : (size_t)(m + 1) * n + (pc ? (size_t)m * n : 0);
+  const size_t work = b32 ? 6 * (size_t)n : 3 * (size_t)n;
+  size_t need = basis + work + part + 2 * (m + 1) + (m + 1) + 4 + small;
   double2* base = ensure(h, &h->d_gm, &h->gm_elems, need);
-  GmresWs w;
-  w.V = base;
-  w.Z = pc ? base + (size_t)(m + 1) * n : nullptr;
-  w.r = base + (size_t)(m + 1) * n + (pc ? (size_t)m * n : 0);
+  GmresWs w{};
+  if (b32) {
+    w.V32 = (float2*)base;
+  } else {
+    w.V = base;
+    w.Z = pc ? base + (size_t)(m + 1) * n : nullptr;
+  }
+  w.r = base + basis;
   w.b = w.r + n;
   w.x = w.b + n;
-  w.partial = w.x + n;
+  double2* q = w.x + n;
+  if (b32) {
+    w.w = q;
+    w.zt = q + n;
+    w.t = q + 2 * n;
+    q += 3 * n;
+  }
+  w.partial = q;
   w.dh = w.partial + part;
   w.y = w.dh + 2 * (m + 1);
   w.dnorm = (double*)(w.y + (m + 1));
@@ -234,6 +252,7 @@ cudaGraphExec_t gm_graph(StabHandle* h, cd sigma, int eps_mode, const GmresWs& W
   key.ws = h->d_gm;
   key.pinv = pc ? h->d_pinv : nullptr;
   key.n = n;
+  key.basis = h->opts.gmres_basis_prec;
   if (h->gm_exec && key == h->gm_key) return h->gm_exec;
   if (h->gm_exec) {
     cudaGraphExecDestroy(h->gm_exec);
@@ -248,8 +267,36 @@ cudaGraphExec_t gm_graph(StabHandle* h, cd sigma, int eps_mode, const GmresWs& W
   h->last_eps_mode = -1;  // the first captured J v sets epsilon's mode explicitly
   cudaGraph_t graph = nullptr;
   cudaError_t err = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal);
+  const bool began = err == cudaSuccess;  // a begun capture is always ended below
   auto step = [&](cudaError_t e) { if (err == cudaSuccess && e != cudaSuccess) err = e; };
-  if (err == cudaSuccess) {
+  if (err == cudaSuccess && key.basis == 32) {
+    // FP32 basis, right preconditioning M^{-1} applied on the fly: z = M^{-1} v_j (FP64),
+    // w = (J - sigma I) z (FP64), rounded into V32_{j+1}; x += M^{-1} (V32 y) at the end
+    k_gm_cycle_init<<<1, 64, 0, h->stream>>>(D);
+    step(kry_to_f32(h, W.r, n, W.dnorm, W.V32));
+    for (int j = 0; j < m && err == cudaSuccess; ++j) {
+      const float2* Vj = W.V32 + (size_t)j * n;
+      float2* Vn = W.V32 + (size_t)(j + 1) * n;
+      h->gate = D.flags;
+      if (pc) step(pc_apply(h, nullptr, W.zt, Vj));
+      else step(kry_to_f64(h, Vj, n, W.zt));
+      step(jv_apply(h, W.zt, W.w, d2(sigma), eps_mode));
+      step(kry_to_f32(h, W.w, n, nullptr, Vn));
+      step(kry_dgks32(h, W.V32, j + 1, n, Vn, W.dh, W.dnorm, W.partial));
+      h->gate = nullptr;
+      k_gm_step<<<1, 32, 0, h->stream>>>(D, j);
+      h->gate = D.flags;
+      step(kry_scale32(h, Vn, n, W.dnorm));
+      h->gate = nullptr;
+    }
+    k_gm_solve<<<1, 64, 0, h->stream>>>(D);
+    step(kry_gemv32(h, W.V32, m, D.flags + 1, n, W.y, W.t));
+    if (pc) step(pc_apply(h, W.t, W.zt));
+    step(kry_axpby(h, make_double2(1.0, 0.0), pc ? W.zt : W.t, make_double2(1.0, 0.0), W.x, n));
+    step(jv_apply(h, W.x, W.r, d2(sigma), eps_mode));
+    step(kry_axpby(h, make_double2(1.0, 0.0), W.b, make_double2(-1.0, 0.0), W.r, n));
+    step(launch_norm2(h, W.r, n, W.dnorm, 1));
+  } else if (err == cudaSuccess) {
     k_gm_cycle_init<<<1, 64, 0, h->stream>>>(D);
     step(kry_scale(h, W.r, n, W.dnorm, W.V));
     for (int j = 0; j < m && err == cudaSuccess; ++j) {
@@ -274,7 +321,9 @@ cudaGraphExec_t gm_graph(StabHandle* h, cd sigma, int eps_mode, const GmresWs& W
     step(jv_apply(h, W.x, W.r, d2(sigma), eps_mode));
     step(kry_axpby(h, make_double2(1.0, 0.0), W.b, make_double2(-1.0, 0.0), W.r, n));
     step(launch_norm2(h, W.r, n, W.dnorm, 1));
-    k_gm_report<<<1, 1, 0, h->stream>>>(D, rep);
+  }
+  if (began) {
+    if (err == cudaSuccess) k_gm_report<<<1, 1, 0, h->stream>>>(D, rep);
     step(cudaGetLastError());
     const cudaError_t e2 = cudaStreamEndCapture(h->cap_stream, &graph);
     if (err == cudaSuccess) err = e2;

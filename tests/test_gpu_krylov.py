@@ -143,3 +143,49 @@ def test_eigs_3d_mixed_precision_matches_dense_lapack(orc):
             assert np.abs(r.lam - l).min() < 1e-8 * abs(l), (prec, r.lam, ref)
         assert r.resid.max() < 1e-8
         S.close()
+
+
+@pytest.mark.parametrize("sigma", [0.25, 0.1 + 0.3j])
+def test_fp32_basis_gmres_refines_to_fp64_tolerance(orc, sigma):
+    """GMRES with an FP32 Krylov basis (J v, solution update and restart
+    residuals in FP64): the restarts refine the solution to the FP64
+    tolerance, checked against a dense solve."""
+    import torch
+    S, g, f, q0 = _stab(8, 16, eps_mode=2, gmres_m=40, gmres_tol=1e-12, gmres_max_restarts=400, gmres_basis_prec=32)
+    J = orc.core.dense_jacobian(orc.Problem.from_inputs(g, f), q0)
+    A = J - sigma * np.eye(g.n)
+    b = si.random_complex(77, g.n)
+    x = torch.zeros(g.n, dtype=torch.complex128, device="cuda")
+    st, iters = S.solve(sigma, torch.from_numpy(b).cuda(), x)
+    assert st == 0 and iters > 0
+    xh = x.cpu().numpy()
+    assert np.linalg.norm(b - A @ xh) <= 1.05e-12 * np.linalg.norm(b)
+    assert rel_err(xh, sla.solve(A, b)) < 1e-7
+    S.close()
+
+
+def test_fp32_basis_preconditioned_gmres_and_eigs(orc):
+    """FP32 basis with block-Jacobi (FP32 inverses) on 32 x 64: the same solution
+    as the FP64 flexible GMRES to 1e-8; eigenvalues of the tiny layer match LAPACK."""
+    import torch
+    common = dict(eps_mode=2, precond=1, tile=(8, 8), precond_prec=32, gmres_m=50, gmres_tol=1e-10,
+                  gmres_max_restarts=400)
+    S64, g, f, q0 = _stab(32, 64, **common)
+    S32, _, _, _ = _stab(32, 64, gmres_basis_prec=32, **common)
+    b = torch.from_numpy(si.random_complex(5, g.n)).cuda()
+    x64, x32 = torch.zeros_like(b), torch.zeros_like(b)
+    st64, it64 = S64.solve(1.0, b, x64)
+    st32, it32 = S32.solve(1.0, b, x32)
+    assert st64 == 0 and st32 == 0 and it32 <= 1.5 * it64
+    assert rel_err(x32.cpu().numpy(), x64.cpu().numpy()) < 1e-8
+    S64.close()
+    S32.close()
+    S, g, f, q0 = _stab(8, 16, eps_mode=2, gmres_m=30, gmres_tol=1e-12, gmres_max_restarts=400, gmres_basis_prec=32)
+    J = orc.core.dense_jacobian(orc.Problem.from_inputs(g, f), q0)
+    ref, _ = orc.stability.dense_reference(J, 0.25, -1.0, 2)
+    r = S.eigs(0.25, -1.0, nev=2, ncv=12, tol=1e-11)
+    assert r.status == 0 and r.nconv == 2
+    for l in ref:
+        assert np.abs(r.lam - l).min() < 1e-8 * abs(l)
+    assert r.resid.max() < 1e-8
+    S.close()
