@@ -577,7 +577,7 @@ __global__ void k_coeffs(const PointParams P, double* coef) {
 // two-sum accumulation (~2^-47 relative per term), the O(eps) remainder in
 // FP32 from the inputs' high parts and FP32 base tables: no FP64 products.
 template <int D>
-__global__ void __launch_bounds__(128, 3) k_point_fast(const PointParams P, const ffn* __restrict__ coefp,
+__global__ void __launch_bounds__(128, D == 2 ? 4 : 3) k_point_fast(const PointParams P, const ffn* __restrict__ coefp,
                                                    const float* __restrict__ btab_f) {
   if (P.gate && *P.gate) return;
   constexpr int NW = pw::nw_inputs(D);
