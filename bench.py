@@ -10,8 +10,11 @@ traffic (32 B per complex unknown).  Also reported, measured in the same run:
     (sigma 1, tau -1, nev 4, ncv 30, block-Jacobi over 16 x 16 tiles, FGMRES(50) to 1e-10,
     exact-tangent J v): converged eigenpairs per second (true residual
     < 1e-8), the p50 / p99 solve latency and the J v count per solve;
+  * "jv_pair_stencil": the same J v with the compact-scheme right-hand sides in
+    FP32 pair arithmetic (stencil_prec 48), and its difference to the main step's;
   * "gmres_256x512": preconditioned FGMRES(50) iterations per second on the
-    256 x 512 layer (block-Jacobi over 8 x 8-point tiles, FP32 inverses);
+    256 x 512 layer (block-Jacobi over 8 x 8-point tiles, FP32 inverses; also
+    BF16 inverses, and BF16 inverses with an FP32 Krylov basis);
   * "jv_3d": the same J v on the 3-D 128 x 256 x 64 layer (10.5 M unknowns);
   * "many_small": uneven small layers solved one at a time on the plain FP64
     path, as one mixed-precision batch (stab_eigs_batch), and as a Poisson
@@ -458,6 +461,26 @@ def replica_throughput(local_units: float, local_seconds: float, device: str) ->
     return total / t_max, t_max
 
 
+def pair_stencil_jv(args, Stab, torch, q0, g, f, v, out, flush, stream, bytes_jv):
+    """The same J v with the compact-scheme right-hand sides in FP32 pair arithmetic
+    (stencil_prec 48; sweeps, closures and the pointwise map unchanged), timed like
+    the main step, with its largest difference to the FP64-stencil result."""
+    S = Stab(q0, g, f.Ma, f.Re, f.Pr, stencil_prec=48)
+    tuned = S.autotune()
+    o2 = torch.empty_like(v)
+    for _ in range(3):
+        S.apply_J(v, o2)
+    steps = min(args.steps, 500)
+    t = _time_jv(S, v, o2, steps, flush, stream, torch)
+    diff = float((o2 - out).abs().max() / out.abs().max())
+    S.close()
+    return {"value": bytes_jv / (sum(t) / steps) / 1e9, "unit": "GB/s", "ms_per_step": sum(t) / steps * 1e3,
+            "steps": steps, "max_rel_diff_vs_fp64_stencil": diff,
+            "line_pass_shapes": {ax: {"C": c, "L": l, "kinds": k} for ax, (c, l, k, _) in tuned.items()},
+            "arith": "interior right-hand sides of the compact schemes in FP32 pairs (~2^-47 relative); "
+                     "Thomas sweeps, closure rows and the pointwise map as in the main step"}
+
+
 def _time_jv(S, v, out, steps, flush, stream, torch):
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     for s in range(steps):
@@ -592,6 +615,7 @@ def run_ours(args):
         # k_line_pass per axis, k_point_fast); the L2 flush between steps is torch's, not counted
         extra = {"gpu_launches": int(sum(v[1] for k, v in phases.items() if k != "dropped"))}
         sampler_summary = clock_sum
+        extra["jv_pair_stencil"] = pair_stencil_jv(args, Stab, torch, q0, g, f, v, out, flush, stream, bytes_jv)
         if args.eig_steps > 0:
             extra["eigs"] = small_layer_eigs(args, Stab, torch, rank)
         if args.gmres_restarts > 0:

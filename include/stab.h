@@ -77,6 +77,10 @@ typedef struct {
                              default) or 32 (FP32 basis, non-flexible right preconditioning; J v, the
                              solution update and the true residual of every restart stay FP64, so the
                              restarts refine the solution to the FP64 tolerance) */
+  int stencil_prec;       /* right-hand sides B f of the compact schemes inside J v: 64 (FP64, default) or
+                             48 (interior rows in FP32 pair arithmetic on exactly power-of-two-scaled
+                             inputs, ~2^-47 relative; the Thomas sweeps, the closure rows and the set-up
+                             stay FP64) */
 } stab_opts;
 
 typedef struct {

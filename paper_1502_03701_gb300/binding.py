@@ -49,7 +49,8 @@ class Opts(ctypes.Structure):
                 ("eps_mode", ctypes.c_int), ("eps", ctypes.c_double), ("gmres_m", ctypes.c_int),
                 ("gmres_max_restarts", ctypes.c_int), ("gmres_tol", ctypes.c_double), ("precond", ctypes.c_int),
                 ("tile", ctypes.c_int * 3), ("precond_prec", ctypes.c_int), ("max_restarts", ctypes.c_int),
-                ("seed", ctypes.c_ulonglong), ("gmres_basis_prec", ctypes.c_int)]
+                ("seed", ctypes.c_ulonglong), ("gmres_basis_prec", ctypes.c_int),
+                ("stencil_prec", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):

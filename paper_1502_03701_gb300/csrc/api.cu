@@ -41,6 +41,7 @@ extern "C" void stab_default_opts(stab_opts* o) {
   o->max_restarts = 300;
   o->seed = 0x5EEDULL;
   o->gmres_basis_prec = 64;
+  o->stencil_prec = 64;
 }
 
 static void free_handle(stab_handle h) {
@@ -99,7 +100,7 @@ extern "C" stab_status stab_create(stab_handle* out, const double* base_flow, in
   if (o.gmres_m < 1 || o.gmres_m > 200 || !(o.gmres_tol > 0) || o.gmres_max_restarts < 1 || o.eps < 0 ||
       !(o.gamma > 1) || o.sutherland_S < 0 || o.bulk_visc_ratio < 0 || o.max_restarts < 0 ||
       (o.precond_prec != 16 && o.precond_prec != 32 && o.precond_prec != 64) || (o.precond != 0 && o.precond != 1) ||
-      (o.gmres_basis_prec != 32 && o.gmres_basis_prec != 64)) {
+      (o.gmres_basis_prec != 32 && o.gmres_basis_prec != 64) || (o.stencil_prec != 48 && o.stencil_prec != 64)) {
     g_create_err = "stab_create: invalid option value";
     return STAB_ERR_INVALID_ARG;
   }
@@ -114,6 +115,7 @@ extern "C" stab_status stab_create(stab_handle* out, const double* base_flow, in
   h->cp = o.gamma * h->R / (o.gamma - 1.0);
   h->visc = Re > 0.0;
   h->opts = o;
+  h->stencil_ff = o.stencil_prec == 48 ? 1 : 0;
   h->stream = (cudaStream_t)cuda_stream;
   cudaGetDevice(&h->device);
   h->last_eps_mode = -1;

@@ -107,6 +107,7 @@ struct StabHandle {
   int red_blocks;
   double* d_eps;         // scalar: epsilon of the last J v
   int last_eps_mode;
+  int stencil_ff;        // 1: compact-scheme right-hand sides of J v in FP32 pairs (stencil_prec 48)
   // Krylov workspace (allocated on demand, grown as needed)
   double2* d_gm;   // GMRES
   size_t gm_elems;

@@ -75,6 +75,8 @@ struct PassParams {
   FastDiv divn, divL, divnx;  // division by n, L and nx  // padded shared-memory line stride in doubles, n + n/32 + 1
   int periodic;
   double c1[2], c2[2];  // interior stencil weights per kind
+  float c1h[2], c1l[2], c2h[2], c2l[2];  // the same weights as FP32 pairs (ff = 1)
+  int ff;  // 1: interior right-hand sides in FP32 pair arithmetic on exponent-shifted inputs
   double h;
   const double* tab[2];
   const float* tabf[2];  // FP32 copies [l'(n), m(n)] for the far part of the warm-up
@@ -103,30 +105,71 @@ __device__ __forceinline__ int wrap_small(int t, int n) {
 // chunk so that the chunk starts fall in different banks
 __device__ __forceinline__ int sidx(int t) { return t + (t >> 5); }
 
+// right-hand side of the one-sided and Pade closure rows of a bounded line
+// (t < 2 or t > n - 3) from the values f(q)
+template <class Get>
+__device__ __forceinline__ double closure_rhs(const PassParams& P, Get f, int t, int kind) {
+  const int n = P.n;
+  const double h = P.h;
+  if (kind == 0) {
+    if (t == 0) return (-2.5 * f(0) + 2.0 * f(1) + 0.5 * f(2)) / h;
+    if (t == n - 1) return (2.5 * f(n - 1) - 2.0 * f(n - 2) - 0.5 * f(n - 3)) / h;
+    return 0.75 * (f(t + 1) - f(t - 1)) / h;
+  }
+  const double ih2 = 1.0 / (h * h);
+  if (t == 0) return (13.0 * f(0) - 27.0 * f(1) + 15.0 * f(2) - f(3)) * ih2;
+  if (t == n - 1) return (13.0 * f(n - 1) - 27.0 * f(n - 2) + 15.0 * f(n - 3) - f(n - 4)) * ih2;
+  return 1.2 * (f(t + 1) - 2.0 * f(t) + f(t - 1)) * ih2;
+}
+
+// neighbour indices t-2 .. t+2 (wrapped on periodic lines)
+__device__ __forceinline__ void stencil_idx(const PassParams& P, int t, int& tm2, int& tm1, int& tp1, int& tp2) {
+  tm2 = t - 2; tm1 = t - 1; tp1 = t + 1; tp2 = t + 2;
+  if (P.periodic) {
+    const int n = P.n;
+    tm2 = wrap_small(tm2, n); tm1 = wrap_small(tm1, n); tp1 = wrap_small(tp1, n); tp2 = wrap_small(tp2, n);
+  }
+}
+
 // right-hand side (B f)_t of the compact scheme for one real component
 __device__ __forceinline__ double stencil_rhs(const PassParams& P, const double* fl, int t, int kind) {
-  const int n = P.n;
   auto f = [&](int q) { return fl[sidx(q)]; };
-  const double h = P.h;
-  if (!P.periodic && (t < 2 || t > n - 3)) {
-    if (kind == 0) {
-      if (t == 0) return (-2.5 * f(0) + 2.0 * f(1) + 0.5 * f(2)) / h;
-      if (t == n - 1) return (2.5 * f(n - 1) - 2.0 * f(n - 2) - 0.5 * f(n - 3)) / h;
-      return 0.75 * (f(t + 1) - f(t - 1)) / h;
-    }
-    const double ih2 = 1.0 / (h * h);
-    if (t == 0) return (13.0 * f(0) - 27.0 * f(1) + 15.0 * f(2) - f(3)) * ih2;
-    if (t == n - 1) return (13.0 * f(n - 1) - 27.0 * f(n - 2) + 15.0 * f(n - 3) - f(n - 4)) * ih2;
-    return 1.2 * (f(t + 1) - 2.0 * f(t) + f(t - 1)) * ih2;
-  }
-  int tm2 = t - 2, tm1 = t - 1, tp1 = t + 1, tp2 = t + 2;
-  if (P.periodic) { tm2 = wrap_small(tm2, n); tm1 = wrap_small(tm1, n); tp1 = wrap_small(tp1, n); tp2 = wrap_small(tp2, n); }
+  if (!P.periodic && (t < 2 || t > P.n - 3)) return closure_rhs(P, f, t, kind);
+  int tm2, tm1, tp1, tp2;
+  stencil_idx(P, t, tm2, tm1, tp1, tp2);
   if (kind == 0) return fma(P.c1[0], f(tp1) - f(tm1), P.c2[0] * (f(tp2) - f(tm2)));
   const double f0 = f(t);
   return fma(P.c1[1], f(tp1) - 2.0 * f0 + f(tm1), P.c2[1] * (f(tp2) - 2.0 * f0 + f(tm2)));
 }
 
+// The same right-hand side from a line of FP32 pairs holding f * 2^-sh: the
+// interior rows in pair arithmetic (~2^-47 relative; no FP64 work but the
+// final recombination), the closure rows in FP64 on the recombined values.
+__device__ __forceinline__ double stencil_rhs_ff(const PassParams& P, const float2* fl, int t, int kind, int sh) {
+  auto f = [&](int q) { const float2 v = fl[sidx(q)]; return ffn{v.x, v.y}; };
+  if (!P.periodic && (t < 2 || t > P.n - 3)) {
+    auto fd = [&](int q) { return ff_to_d_scaled(f(q), sh); };
+    return closure_rhs(P, fd, t, kind);
+  }
+  int tm2, tm1, tp1, tp2;
+  stencil_idx(P, t, tm2, tm1, tp1, tp2);
+  const ffn c1{P.c1h[kind], P.c1l[kind]}, c2{P.c2h[kind], P.c2l[kind]};
+  ffn r;
+  if (kind == 0) {
+    r = ff_add(ff_prod(c1, ff_sub(f(tp1), f(tm1))), ff_prod(c2, ff_sub(f(tp2), f(tm2))));
+  } else {
+    const ffn f0 = f(t);
+    const ffn m2{-2.0f * f0.hi, -2.0f * f0.lo};
+    r = ff_add(ff_prod(c1, ff_add(ff_add(f(tp1), f(tm1)), m2)), ff_prod(c2, ff_add(ff_add(f(tp2), f(tm2)), m2)));
+  }
+  return ff_to_d_scaled(r, sh);
+}
+
+// biased exponent of |d| (0 for zero and subnormals)
+__device__ __forceinline__ int dexp(double d) { return (int)((__double_as_longlong(d) >> 52) & 0x7FF); }
+
 constexpr long long kLineSmemMax = 200 * 1024;  // dynamic shared memory opt-in of k_line_pass
+constexpr long long kLineSmemExtra = 16;        // after the planes: the CTA's input exponent (pair stencil)
 
 // FP32 value of a double with integer operations (the FP64 pipe is the
 // bottleneck here): the high part of ff_split.
@@ -242,6 +285,7 @@ __device__ __forceinline__ void line_sweeps(const PassParams& P, double* Wk, int
   }
 }
 
+template <bool FF>
 __global__ void k_line_pass(const PassParams P) {
   if (P.gate && *P.gate) return;
   extern __shared__ double sm[];
@@ -250,8 +294,14 @@ __global__ void k_line_pass(const PassParams P) {
   const int LS = P.LS;
   const size_t plane = (size_t)L * LS;
   double* F = sm;              // 2 planes
-  double* W = sm + 2 * plane;  // 2 KP planes (none in the compact mode)
+  double* W = sm + 2 * plane;  // 2 KP planes
+  int* sE = (int*)(sm + (size_t)(2 + 2 * KP) * plane);  // FF: largest input exponent of the CTA
   const long long l0 = (long long)blockIdx.x * L;
+  if (FF) {
+    if (threadIdx.x == 0) *sE = 0;
+    __syncthreads();
+  }
+  int em = 0;
   auto load_lines = [&]() {
     for (int idx = threadIdx.x; idx < n * L; idx += blockDim.x) {
       int lt, t;
@@ -261,6 +311,7 @@ __global__ void k_line_pass(const PassParams P) {
       if (l < P.nlines) val = J.in[line_base(P, l) + (long long)t * P.stride];
       F[(size_t)lt * LS + sidx(t)] = val.x;
       F[plane + (size_t)lt * LS + sidx(t)] = val.y;
+      if (FF) em = max(em, max(dexp(val.x), dexp(val.y)));
     }
   };
   const int per = L * P.nchunks;
@@ -270,6 +321,22 @@ __global__ void k_line_pass(const PassParams P) {
   const int t0 = ch * P.C, t1 = min(n, t0 + P.C);
   const int nk = J.out2 ? 2 : 1;
   load_lines();
+  int sh = 0;
+  if (FF) {
+    // exact power-of-two scaling into the FP32 exponent range, then the
+    // split of every staged value into a pair, in place
+    em = __reduce_max_sync(0xffffffffu, em);
+    if ((threadIdx.x & 31) == 0) atomicMax(sE, em);
+    __syncthreads();
+    sh = *sE - 1023;
+    for (int idx = threadIdx.x; idx < 2 * n * L; idx += blockDim.x) {
+      const int r2 = (int)fdiv(idx, P.divn);
+      const int t = idx - r2 * n;
+      double* p = F + (size_t)r2 * LS + sidx(t);  // r2 = c * L + line: planes are L * LS apart
+      const ffn v = ff_split_scaled(*p, sh);
+      *(float2*)p = make_float2(v.hi, v.lo);
+    }
+  }
   const int kt = threadIdx.x / (2 * per);  // this thread's kind within a group of KP
   const bool active = kt < KP && (l0 + lt) < P.nlines;
   const long long base = active ? line_base(P, l0 + lt) : 0;
@@ -281,7 +348,8 @@ __global__ void k_line_pass(const PassParams P) {
       const int t = idx - rest * n;
       const int r2 = (int)fdiv(rest, P.divL);
       const int l = rest - r2 * L, c = r2 & 1, k = r2 >> 1;
-      double r = stencil_rhs(P, F + (size_t)c * plane + (size_t)l * LS, t, kb + k);
+      const size_t off = (size_t)c * plane + (size_t)l * LS;
+      double r = FF ? stencil_rhs_ff(P, (const float2*)(F + off), t, kb + k, sh) : stencil_rhs(P, F + off, t, kb + k);
       if (!P.periodic) r *= __ldg(P.tab[kb + k] + n + t);  // bounded: row scale 1/d_t (periodic: in c1, c2)
       W[(size_t)(k * 2 + c) * plane + (size_t)l * LS + sidx(t)] = r;
     }
@@ -297,6 +365,7 @@ __global__ void k_line_pass(const PassParams P) {
 // (C <= 16) passes through registers so that it can replace the input in
 // place.  Half the shared memory of the kinds-in-turn layout.
 constexpr int kCompactMaxThreads = 512;
+template <bool FF>
 __global__ void __launch_bounds__(kCompactMaxThreads) k_line_pass_compact(const PassParams P) {
   if (P.gate && *P.gate) return;
   extern __shared__ double sm[];
@@ -304,6 +373,7 @@ __global__ void __launch_bounds__(kCompactMaxThreads) k_line_pass_compact(const 
   const int n = P.n, L = P.L;
   const int LS = P.LS;
   const size_t plane = (size_t)L * LS;
+  int* sE = (int*)(sm + 2 * plane);  // FF: largest input exponent of the CTA
   const long long l0 = (long long)blockIdx.x * L;
   const int per = L * P.nchunks;
   const int ch = P.axis == 0 ? threadIdx.x % P.nchunks : (threadIdx.x / L) % P.nchunks;
@@ -314,8 +384,11 @@ __global__ void __launch_bounds__(kCompactMaxThreads) k_line_pass_compact(const 
   const bool active = threadIdx.x < 2 * per && (l0 + lt) < P.nlines;
   const long long base = active ? line_base(P, l0 + lt) : 0;
   double* Wc = sm + (size_t)comp * plane + (size_t)lt * LS;
+  if (FF && threadIdx.x == 0) *sE = 0;
+  int sh = 0;
   for (int kind = 0; kind < nk; ++kind) {
     __syncthreads();  // the previous kind's sweeps no longer read the planes
+    int em = 0;
     for (int idx = threadIdx.x; idx < n * L; idx += blockDim.x) {
       int l, t;
       if (P.axis == 0) { l = (int)fdiv(idx, P.divn); t = idx - l * n; } else { t = (int)fdiv(idx, P.divL); l = idx - t * L; }
@@ -323,6 +396,22 @@ __global__ void __launch_bounds__(kCompactMaxThreads) k_line_pass_compact(const 
       if (l0 + l < P.nlines) val = J.in[line_base(P, l0 + l) + (long long)t * P.stride];
       sm[(size_t)l * LS + sidx(t)] = val.x;
       sm[plane + (size_t)l * LS + sidx(t)] = val.y;
+      if (FF) em = max(em, max(dexp(val.x), dexp(val.y)));
+    }
+    if (FF) {
+      if (kind == 0) {
+        em = __reduce_max_sync(0xffffffffu, em);
+        if ((threadIdx.x & 31) == 0) atomicMax(sE, em);
+      }
+      __syncthreads();
+      sh = *sE - 1023;
+      for (int idx = threadIdx.x; idx < 2 * n * L; idx += blockDim.x) {
+        const int r2 = (int)fdiv(idx, P.divn);
+        const int t = idx - r2 * n;
+        double* p = sm + (size_t)r2 * LS + sidx(t);
+        const ffn v = ff_split_scaled(*p, sh);
+        *(float2*)p = make_float2(v.hi, v.lo);
+      }
     }
     __syncthreads();
     double rr[16];
@@ -331,7 +420,7 @@ __global__ void __launch_bounds__(kCompactMaxThreads) k_line_pass_compact(const 
 #pragma unroll
       for (int q = 0; q < 16; ++q)
         if (q < len) {
-          double r = stencil_rhs(P, Wc, t0 + q, kind);
+          double r = FF ? stencil_rhs_ff(P, (const float2*)Wc, t0 + q, kind, sh) : stencil_rhs(P, Wc, t0 + q, kind);
           if (!P.periodic) r *= __ldg(P.tab[kind] + n + t0 + q);
           rr[q] = r;
         }
@@ -914,6 +1003,12 @@ static cudaError_t run_pass(StabHandle* h, int axis, const PassParams& base_para
       P.c1[k] *= A.pdinv[k];
       P.c2[k] *= A.pdinv[k];
     }
+  for (int k = 0; k < 2; ++k) {  // pair split of the weights (host rounding to nearest)
+    P.c1h[k] = (float)P.c1[k];
+    P.c1l[k] = (float)(P.c1[k] - (double)P.c1h[k]);
+    P.c2h[k] = (float)P.c2[k];
+    P.c2l[k] = (float)(P.c2[k] - (double)P.c2h[k]);
+  }
 
   const int n = A.n;
   if (n > 2048) return cudaErrorInvalidValue;
@@ -936,7 +1031,7 @@ static cudaError_t run_pass(StabHandle* h, int axis, const PassParams& base_para
   const int max_threads = P.KP == 3 ? kCompactMaxThreads : 1024;
   if (tpl > max_threads) return cudaErrorInvalidValue;
   const long long smem_line = (P.KP == 3 ? 2 : 2 + 2 * P.KP) * 8 * LS;
-  const int maxL = std::min<long long>(std::min(max_threads / tpl, 32), kLineSmemMax / smem_line);
+  const int maxL = std::min<long long>(std::min(max_threads / tpl, 32), (kLineSmemMax - kLineSmemExtra) / smem_line);
   if (maxL < 1) return cudaErrorInvalidValue;
   int L;
   if (cfg.L > 0) {
@@ -953,13 +1048,18 @@ static cudaError_t run_pass(StabHandle* h, int axis, const PassParams& base_para
   P.divnx = make_fastdiv((unsigned)P.nx);
   int threads = tpl * L;
   threads = ((threads + 31) / 32) * 32;
-  size_t smem = (size_t)smem_line * L;
+  size_t smem = (size_t)smem_line * L + kLineSmemExtra;
   for (size_t j0 = 0; j0 < jobs.size(); j0 += STAB_MAX_JOBS) {
     P.njobs = (int)std::min<size_t>(STAB_MAX_JOBS, jobs.size() - j0);
     for (int q = 0; q < P.njobs; ++q) P.job[q] = jobs[j0 + q];
     dim3 grid((unsigned)((P.nlines + L - 1) / L), (unsigned)P.njobs);
-    if (P.KP == 3) k_line_pass_compact<<<grid, threads, smem, h->stream>>>(P);
-    else k_line_pass<<<grid, threads, smem, h->stream>>>(P);
+    if (P.KP == 3) {
+      if (P.ff) k_line_pass_compact<true><<<grid, threads, smem, h->stream>>>(P);
+      else k_line_pass_compact<false><<<grid, threads, smem, h->stream>>>(P);
+    } else {
+      if (P.ff) k_line_pass<true><<<grid, threads, smem, h->stream>>>(P);
+      else k_line_pass<false><<<grid, threads, smem, h->stream>>>(P);
+    }
   }
   return cudaGetLastError();
 }
@@ -1001,9 +1101,10 @@ static void axis_jobs(StabHandle* h, int ax, const double2* const* src, std::vec
 
 // all derivative passes for field sources src[f] (f = 0..D+2): y, then z,
 // then x (the mixed derivatives need the y and z passes)
-static cudaError_t run_derivatives(StabHandle* h, const double2* const* src) {
+static cudaError_t run_derivatives(StabHandle* h, const double2* const* src, int ff) {
   PassParams P{};
   P.gate = h->gate;
+  P.ff = ff;
   static const int order[3] = {1, 2, 0};
   static const int phase[3] = {STAB_PHASE_LINE_Y, STAB_PHASE_LINE_Z, STAB_PHASE_LINE_X};
   for (int q = 0; q < 3; ++q) {
@@ -1029,10 +1130,11 @@ static cudaError_t run_derivatives(StabHandle* h, const double2* const* src) {
 // ---------------------------------------------------------------------------
 namespace {
 struct TuneKey {
-  int dev, n, njobs, periodic;
+  int dev, n, njobs, periodic, ff;
   long long nlines;
   bool operator<(const TuneKey& o) const {
     if (dev != o.dev) return dev < o.dev;
+    if (ff != o.ff) return ff < o.ff;
     if (n != o.n) return n < o.n;
     if (nlines != o.nlines) return nlines < o.nlines;
     if (njobs != o.njobs) return njobs < o.njobs;
@@ -1050,6 +1152,7 @@ static TuneKey tune_key(StabHandle* h, int ax, int njobs) {
   k.nlines = h->npts / h->ax[ax].n;
   k.njobs = njobs;
   k.periodic = h->ax[ax].periodic;
+  k.ff = h->stencil_ff;
   return k;
 }
 
@@ -1081,6 +1184,7 @@ cudaError_t jv_autotune(StabHandle* h, int force, double* ms_out) {
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     PassParams P{};
+    P.ff = h->stencil_ff;
     LineCfg best{};
     double best_ms = 1e300;
     const int n = h->ax[ax].n;
@@ -1093,7 +1197,8 @@ cudaError_t jv_autotune(StabHandle* h, int force, double* ms_out) {
           const long long LS = n + (n >> 5) + 1;
           const int tpl = (kp == 2 ? 4 : 2) * nch;
           const int planes = kp == 3 ? 2 : 2 + 2 * kp;
-          if (tpl * L > (kp == 3 ? kCompactMaxThreads : 1024) || planes * 8 * LS * L > kLineSmemMax) continue;
+          if (tpl * L > (kp == 3 ? kCompactMaxThreads : 1024) || planes * 8 * LS * L + kLineSmemExtra > kLineSmemMax)
+            continue;
           h->line_cfg[ax] = LineCfg{C, L, kp};
           if (run_pass(h, ax, P, jobs) != cudaSuccess) {  // a shape this device cannot launch: skip it
             cudaGetLastError();
@@ -1133,15 +1238,16 @@ cudaError_t jv_autotune(StabHandle* h, int force, double* ms_out) {
   return err;
 }
 
-// cache file: one line per entry, "n nlines njobs periodic C L kinds" (entries are
-// applied to the current device when loaded)
+// cache file: one line per entry, "n nlines njobs periodic C L kinds ff" (ff: pair
+// stencil; a line without it is an FP64-stencil entry); entries are applied to the
+// current device when loaded
 int jv_tune_save(const char* path) {
   FILE* f = std::fopen(path, "w");
   if (!f) return -1;
   std::lock_guard<std::mutex> lk(g_tune_mu);
   for (const auto& kv : g_tune)
-    std::fprintf(f, "%d %lld %d %d %d %d %d\n", kv.first.n, kv.first.nlines, kv.first.njobs, kv.first.periodic,
-                 kv.second.C, kv.second.L, kv.second.kp);
+    std::fprintf(f, "%d %lld %d %d %d %d %d %d\n", kv.first.n, kv.first.nlines, kv.first.njobs, kv.first.periodic,
+                 kv.second.C, kv.second.L, kv.second.kp, kv.first.ff);
   std::fclose(f);
   return (int)g_tune.size();
 }
@@ -1155,8 +1261,14 @@ int jv_tune_load(const char* path) {
   TuneKey k;
   LineCfg c;
   std::lock_guard<std::mutex> lk(g_tune_mu);
-  while (std::fscanf(f, "%d %lld %d %d %d %d %d", &k.n, &k.nlines, &k.njobs, &k.periodic, &c.C, &c.L, &c.kp) == 7) {
-    if (c.C < 1 || c.L < 1 || c.kp < 1 || c.kp > 3 || (c.kp == 3 && c.C > 16) || k.n < 1) continue;
+  char line[256];
+  while (std::fgets(line, sizeof line, f)) {
+    k.ff = 0;
+    const int got = std::sscanf(line, "%d %lld %d %d %d %d %d %d", &k.n, &k.nlines, &k.njobs, &k.periodic, &c.C, &c.L,
+                                &c.kp, &k.ff);
+    if (got < 7) continue;
+    if (c.C < 1 || c.L < 1 || c.kp < 1 || c.kp > 3 || (c.kp == 3 && c.C > 16) || k.n < 1 || (k.ff != 0 && k.ff != 1))
+      continue;
     k.dev = dev;
     g_tune[k] = c;
     ++count;
@@ -1229,11 +1341,11 @@ cudaError_t jv_setup(StabHandle* h, const double* q0_host) {
   const int D = h->dim;
   cudaError_t err;
   // set once per handle (current device), never during a stream capture
-  if ((err = cudaFuncSetAttribute(k_line_pass, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLineSmemMax)) !=
-          cudaSuccess ||
-      (err = cudaFuncSetAttribute(k_line_pass_compact, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)kLineSmemMax)) != cudaSuccess)
-    return err;
+  const void* line_kernels[4] = {(const void*)k_line_pass<false>, (const void*)k_line_pass<true>,
+                                 (const void*)k_line_pass_compact<false>, (const void*)k_line_pass_compact<true>};
+  for (const void* k : line_kernels)
+    if ((err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLineSmemMax)) != cudaSuccess)
+      return err;
   make_slots(h);
   // axis tables: x (0) periodic, y (1) bounded in eta, z (2) periodic
   const int lens[3] = {h->nx, h->ny, h->nz};
@@ -1325,7 +1437,7 @@ cudaError_t jv_setup(StabHandle* h, const double* q0_host) {
   const double2* src[6];
   for (int f = 0; f < D + 2; ++f) src[f] = bv + (long long)f * h->npts;
   src[D + 2] = bT;
-  if ((err = run_derivatives(h, src)) != cudaSuccess) return err;
+  if ((err = run_derivatives(h, src, 0)) != cudaSuccess) return err;  // base tables: FP64 right-hand sides
   PackParams K{};
   K.q0 = h->d_q0;
   K.scratch = h->d_scratch;
@@ -1417,7 +1529,7 @@ cudaError_t jv_apply(StabHandle* h, const double2* v, double2* out, double2 shif
   const double2* src[6];
   for (int f = 0; f < D + 2; ++f) src[f] = v + (long long)f * h->npts;
   src[D + 2] = Tw;
-  if ((err = run_derivatives(h, src)) != cudaSuccess) return err;
+  if ((err = run_derivatives(h, src, h->stencil_ff)) != cudaSuccess) return err;
   const int tp = phase_begin(h, STAB_PHASE_POINTWISE);
   if (fast) {
     if (D == 2) k_point_fast<2><<<grid_for(h->npts, thr), thr, 0, h->stream>>>(P, h->d_coef_p, h->d_btab_f);

@@ -62,6 +62,41 @@ __device__ __forceinline__ void ff_acc_prod(ffn& acc, ffn a, ffn b) {
   acc.hi = s;
 }
 __device__ __forceinline__ ffn ff_negate(ffn a) { return ffn{-a.hi, -a.lo}; }
+__device__ __forceinline__ ffn ff_sub(ffn a, ffn b) { return ff_add(a, ff_negate(b)); }
+// c * d as an unnormalised pair: the exact product of the high parts (FMA)
+// plus the cross terms (the lo * lo term is below the pair's precision)
+__device__ __forceinline__ ffn ff_prod(ffn c, ffn d) {
+  const float p = c.hi * d.hi;
+  float e = fmaf(c.hi, d.hi, -p);
+  e = fmaf(c.hi, d.lo, fmaf(c.lo, d.hi, e));
+  return ffn{p, e};
+}
+// d * 2^-sh split into a pair (exponents shifted with integer operations, so
+// the scaling is exact); doubles whose scaled value falls below the double
+// range give zero
+__device__ __forceinline__ ffn ff_split_scaled(double d, int sh) {
+  const long long b = __double_as_longlong(d);
+  const int e = (int)((b >> 52) & 0x7FF);
+  if (e == 0) return ffn{0.0f, 0.0f};
+  const int es = e - sh;
+  if (es <= 0) return ffn{0.0f, 0.0f};
+  return ff_split(__longlong_as_double(b - ((long long)sh << 52)));
+}
+// float * 2^sh -> double exactly, with integer operations (zero below the
+// double range)
+__device__ __forceinline__ double f2d_exact_scaled(float f, int sh) {
+  const unsigned u = __float_as_uint(f);
+  const int ex = (int)((u >> 23) & 0xFF);
+  if (ex == 0) return 0.0;
+  const int E = ex - 127 + 1023 + sh;
+  if (E <= 0) return 0.0;
+  const unsigned long long b = ((unsigned long long)(u & 0x80000000u) << 32) | ((unsigned long long)E << 52) |
+                               ((unsigned long long)(u & 0x7FFFFFu) << 29);
+  return __longlong_as_double((long long)b);
+}
+__device__ __forceinline__ double ff_to_d_scaled(ffn a, int sh) {
+  return f2d_exact_scaled(a.hi, sh) + f2d_exact_scaled(a.lo, sh);
+}
 __device__ __forceinline__ double ff_to_d(ffn a) { return f2d_exact(a.hi) + f2d_exact(a.lo); }
 __device__ __forceinline__ ffn ff_warp_sum(ffn x) {
   for (int o = 16; o > 0; o >>= 1) {

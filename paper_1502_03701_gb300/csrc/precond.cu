@@ -266,7 +266,7 @@ __device__ __forceinline__ void load_c<__nv_bfloat162, float>(const __nv_bfloat1
   y = v.y;
 }
 
-template <class S, class R>
+template <class S, class R, bool Q32>
 __global__ void k_apply_cols(const ApplyParams P) {
   if (P.gate && *P.gate) return;
   extern __shared__ unsigned char smraw[];
@@ -278,8 +278,13 @@ __global__ void k_apply_cols(const ApplyParams P) {
   const S* Mt = (const S*)P.inv + (long long)tile * b * b;
   for (int r = threadIdx.x; r < b; r += blockDim.x) {
     const long long d = tile_dof(P, tile, r);
-    const double2 v = P.q32 ? make_double2(P.q32[d].x, P.q32[d].y) : P.q[d];
-    qs[r] = C2<R>{(R)v.x, (R)v.y};
+    if (Q32) {
+      const float2 v = P.q32[d];
+      qs[r] = C2<R>{(R)v.x, (R)v.y};
+    } else {
+      const double2 v = P.q[d];
+      qs[r] = C2<R>{(R)v.x, (R)v.y};
+    }
   }
   __syncthreads();
   for (int r = rb0 + threadIdx.x; r < rb1; r += blockDim.x) {
@@ -297,10 +302,55 @@ __global__ void k_apply_cols(const ApplyParams P) {
   }
 }
 
+// The same product for blocks of a multiple of four rows: each thread forms
+// four consecutive rows from one 16-byte load per column (four BF16 complex
+// entries), so a warp moves 512 bytes per load instruction.
+template <bool Q32>
+__global__ void k_apply_cols4(const ApplyParams P) {
+  if (P.gate && *P.gate) return;
+  extern __shared__ unsigned char smraw[];
+  float2* qs = (float2*)smraw;
+  const long long tile = blockIdx.x;
+  const int b = P.bsz, b4 = P.bsz >> 2;
+  const int q0 = (int)((long long)b4 * blockIdx.y / gridDim.y);
+  const int q1 = (int)((long long)b4 * (blockIdx.y + 1) / gridDim.y);
+  const uint4* Mt = (const uint4*)((const __nv_bfloat162*)P.inv + (long long)tile * b * b);
+  for (int r = threadIdx.x; r < b; r += blockDim.x) {
+    const long long d = tile_dof(P, tile, r);
+    if (Q32) {
+      qs[r] = P.q32[d];
+    } else {
+      const double2 v = P.q[d];
+      qs[r] = make_float2((float)v.x, (float)v.y);
+    }
+  }
+  __syncthreads();
+  for (int r4 = q0 + threadIdx.x; r4 < q1; r4 += blockDim.x) {
+    const uint4* col = Mt + r4;
+    float ar[4] = {0.f, 0.f, 0.f, 0.f}, ai[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 8
+    for (int c = 0; c < b; ++c) {
+      const uint4 u = __ldg(col + (long long)c * b4);
+      const float2 x = qs[c];
+      const unsigned w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        __nv_bfloat162 e;
+        memcpy(&e, &w[k], sizeof(e));
+        const float2 m = __bfloat1622float2(e);
+        ar[k] += m.x * x.x - m.y * x.y;
+        ai[k] += m.x * x.y + m.y * x.x;
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) P.z[tile_dof(P, tile, 4 * r4 + k)] = make_double2((double)ar[k], (double)ai[k]);
+  }
+}
+
 // z_tile = Minv_tile q_tile with the inverse stored row-major (FP64 or FP32):
 // one warp per row at a time, FP32 rows of even length read two entries per
 // 16-byte load; grid (tiles, row slices) as above.
-template <class R>
+template <class R, bool Q32>
 __global__ void k_apply_rows(const ApplyParams P) {
   if (P.gate && *P.gate) return;
   extern __shared__ unsigned char smraw[];
@@ -311,8 +361,13 @@ __global__ void k_apply_rows(const ApplyParams P) {
   const C2<R>* M = (const C2<R>*)P.inv + (long long)tile * P.bsz * P.bsz;
   for (int r = threadIdx.x; r < P.bsz; r += blockDim.x) {
     const long long d = tile_dof(P, tile, r);
-    const double2 v = P.q32 ? make_double2(P.q32[d].x, P.q32[d].y) : P.q[d];
-    qs[r] = C2<R>{(R)v.x, (R)v.y};
+    if (Q32) {
+      const float2 v = P.q32[d];
+      qs[r] = C2<R>{(R)v.x, (R)v.y};
+    } else {
+      const double2 v = P.q[d];
+      qs[r] = C2<R>{(R)v.x, (R)v.y};
+    }
   }
   __syncthreads();
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -513,12 +568,24 @@ cudaError_t pc_apply(StabHandle* h, const double2* q, double2* z, const float2* 
   int slices = (int)((2 * 152 + g.ntiles - 1) / g.ntiles);
   slices = std::max(1, std::min(slices, g.bsz / 32));
   const dim3 grid((unsigned)g.ntiles, (unsigned)slices);
-  if (h->pprec == 64) k_apply_rows<double><<<grid, 256, g.bsz * sizeof(double2), h->stream>>>(P);
-  else if (h->pprec == 32) k_apply_rows<float><<<grid, 256, g.bsz * sizeof(float2), h->stream>>>(P);
-  else {
+  // the input's precision is a template parameter (FP32 basis: float2 input)
+  const bool q32v = q32 != nullptr;
+  if (h->pprec == 64) {
+    if (q32v) k_apply_rows<double, true><<<grid, 256, g.bsz * sizeof(double2), h->stream>>>(P);
+    else k_apply_rows<double, false><<<grid, 256, g.bsz * sizeof(double2), h->stream>>>(P);
+  } else if (h->pprec == 32) {
+    if (q32v) k_apply_rows<float, true><<<grid, 256, g.bsz * sizeof(float2), h->stream>>>(P);
+    else k_apply_rows<float, false><<<grid, 256, g.bsz * sizeof(float2), h->stream>>>(P);
+  } else if (g.bsz % 4 == 0) {
+    const int quads = (g.bsz / 4 + slices - 1) / slices;
+    const int thr = std::min(256, ((quads + 31) / 32) * 32);
+    if (q32v) k_apply_cols4<true><<<grid, thr, g.bsz * sizeof(float2), h->stream>>>(P);
+    else k_apply_cols4<false><<<grid, thr, g.bsz * sizeof(float2), h->stream>>>(P);
+  } else {
     const int rows = (g.bsz + slices - 1) / slices;
     const int thr = std::min(256, ((rows + 31) / 32) * 32);
-    k_apply_cols<__nv_bfloat162, float><<<grid, thr, g.bsz * sizeof(float2), h->stream>>>(P);
+    if (q32v) k_apply_cols<__nv_bfloat162, float, true><<<grid, thr, g.bsz * sizeof(float2), h->stream>>>(P);
+    else k_apply_cols<__nv_bfloat162, float, false><<<grid, thr, g.bsz * sizeof(float2), h->stream>>>(P);
   }
   phase_end(h, ts);
   return cudaGetLastError();

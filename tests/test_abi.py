@@ -40,12 +40,13 @@ def test_autotune_cache_file_roundtrip(tmp_path):
     """The tuning cache file format reads back (no GPU needed)."""
     from paper_1502_03701_gb300 import binding
     src = tmp_path / "tune.txt"
-    src.write_text("256 512 7 1 32 4 1\n512 256 5 0 16 2 2\nbad line\n")
+    # seven columns: an FP64-stencil entry; the eighth marks the pair stencil
+    src.write_text("256 512 7 1 32 4 1\n512 256 5 0 16 2 2 1\nbad line\n512 256 5 0 16 2 2 7\n")
     assert binding.autotune_load(str(src)) == 2
     dst = tmp_path / "out.txt"
     assert binding.autotune_save(str(dst)) >= 2
     lines = set(dst.read_text().split("\n"))
-    assert "256 512 7 1 32 4 1" in lines and "512 256 5 0 16 2 2" in lines
+    assert "256 512 7 1 32 4 1 0" in lines and "512 256 5 0 16 2 2 1" in lines
     assert binding.autotune_load(str(tmp_path / "missing.txt")) == -1
 
 

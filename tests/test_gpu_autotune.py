@@ -16,13 +16,14 @@ CASES = [
 ]
 
 
+@pytest.mark.parametrize("stencil_prec", [64, 48])
 @pytest.mark.parametrize("name,g,f", CASES, ids=[c[0] for c in CASES])
-def test_every_line_shape_matches_oracle(orc, name, g, f):
+def test_every_line_shape_matches_oracle(orc, name, g, f, stencil_prec):
     import torch
     from paper_1502_03701_gb300 import Stab, StabError
     q0 = si.tanh_base_flow(g, f)
     v = si.random_complex(301, g.n)
-    S = Stab(q0, g, f.Ma, f.Re, f.Pr, eps_mode=2)
+    S = Stab(q0, g, f.Ma, f.Re, f.Pr, eps_mode=2, stencil_prec=stencil_prec)
     P = orc.Problem.from_inputs(g, f)
     ref = orc.core.jv(P, q0, v, "tangent")
     dv = torch.from_numpy(v).cuda()

@@ -39,11 +39,12 @@ CASES = [
 ]
 
 
+@pytest.mark.parametrize("stencil_prec", [64, 48])
 @pytest.mark.parametrize("name,g,f,general", CASES, ids=[c[0] for c in CASES])
-def test_jv_eps_quotient_matches_quad_oracle(orc, name, g, f, general):
+def test_jv_eps_quotient_matches_quad_oracle(orc, name, g, f, general, stencil_prec):
     q0 = si.perturbed_base_flow(g, f, seed=21) if general else si.tanh_base_flow(g, f)
     v = si.random_complex(101, g.n)
-    got, eps = _gpu(q0, g, f, v)
+    got, eps = _gpu(q0, g, f, v, stencil_prec=stencil_prec)
     assert eps > 0
     P = orc.Problem.from_inputs(g, f)
     ref = orc.core.jv(P, q0, v, "quad", eps)
@@ -52,11 +53,12 @@ def test_jv_eps_quotient_matches_quad_oracle(orc, name, g, f, general):
     assert rel_err(got, ref) < TOL, name
 
 
+@pytest.mark.parametrize("stencil_prec", [64, 48])
 @pytest.mark.parametrize("name,g,f,general", CASES, ids=[c[0] for c in CASES])
-def test_jv_tangent_matches_complex_step(orc, name, g, f, general):
+def test_jv_tangent_matches_complex_step(orc, name, g, f, general, stencil_prec):
     q0 = si.perturbed_base_flow(g, f, seed=22) if general else si.tanh_base_flow(g, f)
     v = si.random_complex(102, g.n)
-    got, eps = _gpu(q0, g, f, v, eps_mode=2)
+    got, eps = _gpu(q0, g, f, v, eps_mode=2, stencil_prec=stencil_prec)
     assert eps == 0.0
     ref = orc.core.jv(orc.Problem.from_inputs(g, f), q0, v, "tangent")
     assert max_rel_err(got, ref) < TOL, name
@@ -110,13 +112,14 @@ def test_invalid_arguments_fail_loudly():
         Stab(bad, g, f.Ma, f.Re, f.Pr)
 
 
+@pytest.mark.parametrize("stencil_prec", [64, 48])
 @pytest.mark.parametrize("mode", ["tangent", "quad"])
-def test_jv_full_size_256x512(orc, mode):
+def test_jv_full_size_256x512(orc, mode, stencil_prec):
     """The 256 x 512 layer (524,288 unknowns): every element against the oracle."""
     g, f = si.mixing_layer_2d(256, 512)
     q0 = si.tanh_base_flow(g, f)
     v = si.random_complex(2024, g.n)
-    got, eps = _gpu(q0, g, f, v, eps_mode=2 if mode == "tangent" else 0)
+    got, eps = _gpu(q0, g, f, v, eps_mode=2 if mode == "tangent" else 0, stencil_prec=stencil_prec)
     ref = orc.core.jv(orc.Problem.from_inputs(g, f), q0, v, mode, eps if mode == "quad" else None)
     assert max_rel_err(got, ref) < TOL
 
@@ -156,3 +159,28 @@ def test_phase_timing_records_every_launch_group():
         ph = S.timing_read()
         assert all(ph[k][1] == 0 for k in ph if k != "dropped")
         S.close()
+
+
+@pytest.mark.parametrize("scale_exp", [-40, 0, 40])
+def test_pair_stencil_scales_exactly(scale_exp):
+    """The pair right-hand sides work on exponent-shifted copies of each CTA's
+    input, so J(2^k v) = 2^k J v (exact tangent, linear in v) to rounding, and the
+    pair-stencil J v agrees with the FP64-stencil J v to ~1e-13."""
+    import torch
+    from paper_1502_03701_gb300 import Stab
+    g, f = si.mixing_layer_2d(32, 48)
+    q0 = si.tanh_base_flow(g, f)
+    v = torch.from_numpy(si.random_complex(77, g.n)).cuda()
+    S = Stab(q0, g, f.Ma, f.Re, f.Pr, eps_mode=2, stencil_prec=48)
+    S64 = Stab(q0, g, f.Ma, f.Re, f.Pr, eps_mode=2)
+    a, b, c = torch.empty_like(v), torch.empty_like(v), torch.empty_like(v)
+    S.apply_J(v, a)
+    S64.apply_J(v, c)
+    s = 2.0 ** scale_exp
+    S.apply_J(v * s, b)
+    torch.cuda.synchronize()
+    ref = c.cpu().numpy()
+    assert max_rel_err(a.cpu().numpy(), ref) < 1e-12
+    assert max_rel_err(b.cpu().numpy() / s, ref) < 1e-12
+    S.close()
+    S64.close()

@@ -60,6 +60,43 @@ def test_apply_matches_oracle_lu(orc, prec, tol):
     S.close()
 
 
+BF16_CASES = [
+    ("2d_8x8", si.Grid(2, 16, 32, 1, si.LX_04, -15, 15), si.Flow(0.3, 1000.0), (8, 8)),      # 256 rows, one slice
+    ("2d_4x4", si.Grid(2, 16, 32, 1, si.LX_04, -15, 15), si.Flow(0.3, 1000.0), (4, 4)),      # 64 rows, row slices
+    ("3d_3x3x1", si.Grid(3, 12, 18, 6, si.LX_04, -15, 15, si.LX_04), si.Flow(0.5, 800.0), (3, 3, 1)),  # 45 rows
+]
+
+
+@pytest.mark.parametrize("name,g,f,tile", BF16_CASES, ids=[c[0] for c in BF16_CASES])
+def test_bf16_apply_columns_are_the_rounded_fp32_inverse(name, g, f, tile):
+    """Applied to unit vectors, the BF16 apply returns columns of the inverse
+    exactly (products with 1 and 0 are exact): they must equal the FP32-storage
+    apply's columns rounded to bfloat16 (nearest, ties to even), bit for bit.
+    Pins the column-major layout, the four-rows-per-thread kernel (row counts
+    divisible by four) and the one-row-per-thread kernel (45 rows)."""
+    import torch
+    S16, _ = _make(g, f, tile=tile, precond_prec=16)
+    S32, _ = _make(g, f, tile=tile, precond_prec=32)
+    S16.precond_build(0.25)
+    S32.precond_build(0.25)
+    rng = np.random.default_rng(5)
+    for j in rng.choice(g.n, 6, replace=False):
+        q = torch.zeros(g.n, dtype=torch.complex128, device="cuda")
+        q[int(j)] = 1.0
+        z16, z32 = torch.empty_like(q), torch.empty_like(q)
+        S16.precond_apply(q, z16)
+        S32.precond_apply(q, z32)
+        a = z32.cpu().numpy()
+        parts = np.stack([a.real, a.imag]).astype(np.float32)
+        bits = parts.view(np.uint32).astype(np.uint64)
+        rounded = (((bits + 0x7FFF + ((bits >> 16) & 1)) >> 16) << 16).astype(np.uint32).view(np.float32)
+        b = z16.cpu().numpy()
+        assert np.array_equal(np.stack([b.real, b.imag]), rounded.astype(np.float64)), int(j)
+        assert np.count_nonzero(a) > 0
+    S16.close()
+    S32.close()
+
+
 def test_preconditioned_gmres_and_eigs(orc):
     import torch
     gold = json.load(open(GOLD))
