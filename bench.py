@@ -313,8 +313,9 @@ def gmres_throughput(args, Stab, torch, q0, g, f):
 LINE_FLOP_D1, LINE_FLOP_D2 = 10, 14
 FP64_PEAK_GFLOPS = 1250.0  # GB300 FP64 (non-tensor) nominal; 1.2 TFLOP/s measured by an FMA microbenchmark
 # DRAM bytes per launch of the line pass from ncu (dram__bytes_read.sum + dram__bytes_write.sum) on the
-# 512 x 1024 layer (tuned shapes): y pass 42.2 + 12.1 MB, x pass 58.9 + 27.0 MB; scaled by grid points.
-LINE_TRAFFIC_512x1024 = {"line_y": (42.164992 + 12.131584) * 1e6, "line_x": (58.860800 + 27.033600) * 1e6}
+# 512 x 1024 layer (tuned shapes, FP64 right-hand sides): y pass 42.2 + 12.0 MB, x pass 58.8 + 24.3 MB;
+# scaled by grid points.
+LINE_TRAFFIC_512x1024 = {"line_y": (42.208512 + 12.032000) * 1e6, "line_x": (58.796800 + 24.282112) * 1e6}
 
 
 def line_pass_flops(g, visc: bool) -> dict:

@@ -118,7 +118,13 @@ long long stab_size(stab_handle h);
 
 /* Jv = J(q0) v - shift v   (Eq. frechet; with shift = tau it is the Cayley
  * right-hand side of Eq. cayley_arnoldi).  v, Jv: device complex128, n
- * entries each, must not overlap.  The J v form follows opts.eps_mode. */
+ * entries each, must not overlap.  The J v form follows opts.eps_mode.
+ * Range: parts of the operator run in FP32 pair arithmetic and in FP32
+ * warm-ups, so entries of v (and of its derivative fields) keep full FP64-class
+ * accuracy between about 2^-74 and 2^100 in magnitude; smaller entries are
+ * resolved to FP32 precision relative to themselves, entries below 2^-126 are
+ * dropped, and v with entries above 2^100 is outside the supported range.  The
+ * solvers always pass normalised vectors. */
 stab_status stab_apply_J(stab_handle h, const void* v, void* Jv, double shift_re, double shift_im);
 
 /* epsilon used by the last stab_apply_J call (0 for the exact tangent).  Synchronises the stream. */
