@@ -16,6 +16,8 @@ traffic (32 B per complex unknown).  Also reported, measured in the same run:
     256 x 512 layer (block-Jacobi over 8 x 8-point tiles, FP32 inverses; also
     BF16 inverses, and BF16 inverses with an FP32 Krylov basis);
   * "jv_3d": the same J v on the 3-D 128 x 256 x 64 layer (10.5 M unknowns);
+  * "jv_batch_64": J v of the 64 uneven instances of the batch configuration as one
+    batched call (one launch per phase) against 64 single-problem calls;
   * "many_small": uneven small layers solved one at a time on the plain FP64
     path, as one mixed-precision batch (stab_eigs_batch), and as a Poisson
     stream through the continuous-batching server (p50 / p99 latency).
@@ -378,6 +380,57 @@ def _fleet_problem(p):
     return g, f, si.tanh_base_flow(g, f)
 
 
+def jv_batch_64(args, torch) -> dict:
+    """J v of the 64 uneven instances of the batch configuration (Nx in {32..256}, Ny in {64..512}, Ma
+    U[0.1, 0.9], Re log-U[500, 5000], seed 1234): one stab_jv_batch_apply per step (one launch per phase for
+    all instances) against the 64 stab_apply_J calls of the plain path, both on one stream.  Inputs and
+    outputs (236 MB) exceed L2, so no flush is needed between steps."""
+    from paper_1502_03701_gb300 import JvBatch, Stab
+    insts = si.batched_instances(64, 1234)
+    hs = []
+    for p in insts:
+        g, f, q0 = _fleet_problem(p)
+        S = Stab(q0, g, f.Ma, f.Re, f.Pr)
+        S.autotune()
+        hs.append(S)
+    vs = [torch.from_numpy(si.random_complex(900 + i, S.n)).cuda() for i, S in enumerate(hs)]
+    outs = [torch.empty_like(v) for v in vs]
+    refs = [torch.empty_like(v) for v in vs]
+    B = JvBatch(hs)
+    stream = torch.cuda.current_stream()
+    steps = max(3, min(args.steps // 20, 100))
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1e3 / steps
+
+    def plain():
+        for S, v, o in zip(hs, vs, refs):
+            S.apply_J(v, o)
+
+    t_plain = timed(plain)
+    t_batch = timed(lambda: B.apply(vs, outs))
+    same = all(torch.equal(o, r) for o, r in zip(outs, refs))
+    n_total = sum(S.n for S in hs)
+    B.close()
+    for S in hs:
+        S.close()
+    return {"workload": "jv_batch_64_uneven_2d", "instances": 64, "unknowns": n_total, "steps": steps,
+            "batched": {"value": 64 / t_batch, "unit": "instance J v/s", "ms_per_step": t_batch * 1e3,
+                        "GB_per_s": n_total * JV_BYTES_PER_DOF / t_batch / 1e9, "launches_per_step": "5 to 9"},
+            "plain_one_at_a_time": {"value": 64 / t_plain, "unit": "instance J v/s", "ms_per_step": t_plain * 1e3,
+                                    "GB_per_s": n_total * JV_BYTES_PER_DOF / t_plain / 1e9},
+            "speedup": t_plain / t_batch, "bitwise_equal_to_plain": same}
+
+
 def fleet(args, torch) -> dict:
     """Plain one-at-a-time FP64 path vs batched mixed-precision path vs served Poisson stream."""
     from paper_1502_03701_gb300 import Server, Stab, eigs_batch
@@ -622,6 +675,7 @@ def run_ours(args):
         if args.gmres_restarts > 0:
             extra["gmres_256x512"] = gmres_throughput(args, Stab, torch, q0, g, f)
         if args.fleet > 0 and world == 1:
+            extra["jv_batch_64"] = jv_batch_64(args, torch)
             extra["many_small"] = fleet(args, torch)
         if args.steps_3d > 0:
             extra["jv_3d"] = jv_3d(args, Stab, torch, flush, stream)

@@ -127,6 +127,30 @@ long long stab_size(stab_handle h);
  * solvers always pass normalised vectors. */
 stab_status stab_apply_J(stab_handle h, const void* v, void* Jv, double shift_re, double shift_im);
 
+/* Batched J v over several problems with uneven grids, on one stream.  Every
+ * phase of Eq. frechet's J v (epsilon norm, temperature differences, the y,
+ * z and x compact-derivative passes, the pointwise assembly) is one launch
+ * for all instances (one per kernel variant in use), each instance with its
+ * own options and tuned line-pass shapes, so each result equals what its
+ * handle's stab_apply_J returns, bit for bit.
+ *   create: handles distinct, created on the current device, each with a base
+ *           flow that depends on y only (else STAB_ERR_UNSUPPORTED); count in
+ *           [1, 4096]; cuda_stream runs every call of the batch.  The batch
+ *           keeps the handle pointers (not ownership).
+ *   apply:  v[i], Jv[i]: device complex128 vectors of handle i's size, not
+ *           overlapping each other; shifts: NULL or 2*count doubles
+ *           (re, im of each instance's shift).  Returns when the work is
+ *           queued.  While it is in flight, the handles must not be used
+ *           on other streams.
+ * A batch is used by one host thread at a time; its messages are in
+ * stab_jv_batch_last_error.  destroy waits for the batch's last parameter
+ * transfer (not for its kernels) and releases its buffers in stream order. */
+typedef struct stab_jv_batch_s* stab_jv_batch;
+stab_status stab_jv_batch_create(stab_jv_batch* b, const stab_handle* handles, int count, void* cuda_stream);
+stab_status stab_jv_batch_apply(stab_jv_batch b, const void* const* v, void* const* Jv, const double* shifts);
+const char* stab_jv_batch_last_error(stab_jv_batch b);
+void stab_jv_batch_destroy(stab_jv_batch b);
+
 /* epsilon used by the last stab_apply_J call (0 for the exact tangent).  Synchronises the stream. */
 stab_status stab_last_eps(stab_handle h, double* eps);
 

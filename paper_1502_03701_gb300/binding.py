@@ -26,7 +26,8 @@ SYMBOLS = ["stab_default_opts", "stab_create", "stab_destroy", "stab_last_error"
            "stab_timing_read", "stab_autotune", "stab_autotune_save", "stab_autotune_load",
            "stab_set_line_config", "stab_trim_memory", "stab_estimate_bytes", "stab_eigs_batch",
            "stab_server_create", "stab_server_submit", "stab_server_wait", "stab_server_result",
-           "stab_server_stats", "stab_server_destroy"]
+           "stab_server_stats", "stab_server_destroy", "stab_jv_batch_create", "stab_jv_batch_apply",
+           "stab_jv_batch_last_error", "stab_jv_batch_destroy"]
 
 # stab_phase, in enum order
 PHASES = ["eps", "temperature", "line_y", "line_z", "line_x", "pointwise", "cgs2", "precond_apply"]
@@ -134,9 +135,15 @@ def load():
     L.stab_server_destroy.argtypes = [vp]
     L.stab_autotune_load.argtypes = [ctypes.c_char_p]
     L.stab_timing_read.argtypes = [vp, dp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]
+    L.stab_jv_batch_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(vp), i, vp]
+    L.stab_jv_batch_apply.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), dp]
+    L.stab_jv_batch_last_error.argtypes = [vp]
+    L.stab_jv_batch_last_error.restype = ctypes.c_char_p
+    L.stab_jv_batch_destroy.argtypes = [vp]
+    L.stab_jv_batch_destroy.restype = None
     for name in SYMBOLS:
         if name not in ("stab_default_opts", "stab_destroy", "stab_last_error", "stab_size", "stab_estimate_bytes",
-                        "stab_server_destroy"):
+                        "stab_server_destroy", "stab_jv_batch_last_error", "stab_jv_batch_destroy"):
             getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -362,6 +369,52 @@ def eigs_batch(handles, args, concurrency: int = 0):
         raise StabError(st, "stab_eigs_batch: " + "; ".join(
             L.stab_last_error(h._h).decode() for h, r in zip(handles, out) if r.status not in (0, 4)))
     return out
+
+
+class JvBatch:
+    """stab_jv_batch_*: J v of several problems (uneven grids) with one launch per phase."""
+
+    def __init__(self, handles, stream=None):
+        import torch
+        self._L = load()
+        self.handles = list(handles)  # keeps the problems alive while the batch exists
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        count = len(self.handles)
+        hs = (ctypes.c_void_p * count)(*[h._h.value for h in self.handles])
+        b = ctypes.c_void_p()
+        st = self._L.stab_jv_batch_create(ctypes.byref(b), hs, count, self.stream.cuda_stream)
+        if st != 0:
+            raise StabError(st, "stab_jv_batch_create: handles must be distinct, on this device, with y-only base flows")
+        self._b = b
+
+    def apply(self, vs, outs, shifts=None):
+        """outs[i] = J_i vs[i] - shifts[i] vs[i] (complex128 device tensors)."""
+        count = len(self.handles)
+        if len(vs) != count or len(outs) != count:
+            raise ValueError("one input and one output vector per handle")
+        v = (ctypes.c_void_p * count)(*[_ptr(x) for x in vs])
+        o = (ctypes.c_void_p * count)(*[_ptr(x) for x in outs])
+        sh = None
+        if shifts is not None:
+            arr = np.zeros(2 * count)
+            for i, z in enumerate(shifts):
+                arr[2 * i], arr[2 * i + 1] = complex(z).real, complex(z).imag
+            sh = arr.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        st = self._L.stab_jv_batch_apply(self._b, v, o, sh)
+        if st != 0:
+            raise StabError(st, self._L.stab_jv_batch_last_error(self._b).decode())
+        return outs
+
+    def close(self):
+        if getattr(self, "_b", None) is not None and self._b.value:
+            self._L.stab_jv_batch_destroy(self._b)
+            self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Server:

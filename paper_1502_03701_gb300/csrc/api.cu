@@ -200,10 +200,11 @@ std::mutex g_pool_mu;
 cudaMemPool_t g_pool[64] = {};
 }  // namespace
 
-cudaError_t dev_alloc(StabHandle* h, void** p, size_t bytes) {
+cudaError_t dev_alloc(StabHandle* h, void** p, size_t bytes) { return dev_alloc_stream(h->device, h->stream, p, bytes); }
+
+cudaError_t dev_alloc_stream(int dev, cudaStream_t stream, void** p, size_t bytes) {
   *p = nullptr;
   if (bytes == 0) return cudaSuccess;
-  const int dev = h->device;
   if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
   cudaMemPool_t pool;
   {
@@ -220,7 +221,7 @@ cudaError_t dev_alloc(StabHandle* h, void** p, size_t bytes) {
     }
     pool = g_pool[dev];
   }
-  return cudaMallocFromPoolAsync(p, bytes, pool, h->stream);
+  return cudaMallocFromPoolAsync(p, bytes, pool, stream);
 }
 
 void dev_free(StabHandle* h, void* p) {

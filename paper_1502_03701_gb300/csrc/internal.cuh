@@ -144,6 +144,7 @@ struct StabHandle {
 // api.cu: stream-ordered device memory from the library's pool on the
 // handle's stream (dalloc: typed wrapper).
 cudaError_t dev_alloc(StabHandle* h, void** p, size_t bytes);
+cudaError_t dev_alloc_stream(int device, cudaStream_t stream, void** p, size_t bytes);
 void dev_free(StabHandle* h, void* p);
 template <class T>
 inline cudaError_t dalloc(StabHandle* h, T** p, size_t bytes) {

@@ -16,6 +16,7 @@
 #include <cfloat>
 #include <cmath>
 #include <cstdio>
+#include <cstring>
 #include <map>
 #include <mutex>
 
@@ -285,18 +286,19 @@ __device__ __forceinline__ void line_sweeps(const PassParams& P, double* Wk, int
   }
 }
 
+// One CTA's work of the line pass: line block bx of job by.
 template <bool FF>
-__global__ void k_line_pass(const PassParams P) {
+__device__ __forceinline__ void line_pass_body(const PassParams& P, const unsigned bx, const unsigned by) {
   if (P.gate && *P.gate) return;
   extern __shared__ double sm[];
-  const LineJob J = P.job[blockIdx.y];
+  const LineJob J = P.job[by];
   const int n = P.n, L = P.L, KP = P.KP;
   const int LS = P.LS;
   const size_t plane = (size_t)L * LS;
   double* F = sm;              // 2 planes
   double* W = sm + 2 * plane;  // 2 KP planes
   int* sE = (int*)(sm + (size_t)(2 + 2 * KP) * plane);  // FF: largest input exponent of the CTA
-  const long long l0 = (long long)blockIdx.x * L;
+  const long long l0 = (long long)bx * L;
   if (FF) {
     if (threadIdx.x == 0) *sE = 0;
     __syncthreads();
@@ -360,21 +362,26 @@ __global__ void k_line_pass(const PassParams P) {
   }
 }
 
+template <bool FF>
+__global__ void k_line_pass(const PassParams P) {
+  line_pass_body<FF>(P, blockIdx.x, blockIdx.y);
+}
+
 // Compact variant (KP = 3): kinds in turn, the input reloaded per kind into
 // the only plane of each component; each thread's chunk of right-hand sides
 // (C <= 16) passes through registers so that it can replace the input in
 // place.  Half the shared memory of the kinds-in-turn layout.
 constexpr int kCompactMaxThreads = 512;
 template <bool FF>
-__global__ void __launch_bounds__(kCompactMaxThreads) k_line_pass_compact(const PassParams P) {
+__device__ __forceinline__ void line_pass_compact_body(const PassParams& P, const unsigned bx, const unsigned by) {
   if (P.gate && *P.gate) return;
   extern __shared__ double sm[];
-  const LineJob J = P.job[blockIdx.y];
+  const LineJob J = P.job[by];
   const int n = P.n, L = P.L;
   const int LS = P.LS;
   const size_t plane = (size_t)L * LS;
   int* sE = (int*)(sm + 2 * plane);  // FF: largest input exponent of the CTA
-  const long long l0 = (long long)blockIdx.x * L;
+  const long long l0 = (long long)bx * L;
   const int per = L * P.nchunks;
   const int ch = P.axis == 0 ? threadIdx.x % P.nchunks : (threadIdx.x / L) % P.nchunks;
   const int lt = P.axis == 0 ? (threadIdx.x / P.nchunks) % L : threadIdx.x % L;
@@ -436,6 +443,11 @@ __global__ void __launch_bounds__(kCompactMaxThreads) k_line_pass_compact(const 
   }
 }
 
+template <bool FF>
+__global__ void __launch_bounds__(kCompactMaxThreads) k_line_pass_compact(const PassParams P) {
+  line_pass_compact_body<FF>(P, blockIdx.x, blockIdx.y);
+}
+
 // ---------------------------------------------------------------------------
 // Reductions: ||v||^2 in a fixed order (deterministic), then epsilon.
 // ---------------------------------------------------------------------------
@@ -466,33 +478,40 @@ __device__ __forceinline__ double norm_result(double s, int mode, double q0norm,
 
 // ||v||^2 in one launch: per-block sums, then the last block to finish adds
 // them in block order (fixed order, reproducible) and resets the counter.
-__global__ void k_norm2(const double2* __restrict__ v, long long n, double* partial, unsigned* counter, double* out,
-                        int mode, double q0norm, double fixed_eps, const int* gate) {
-  if (gate && *gate) return;
+// Block bidx of nb blocks.
+__device__ __forceinline__ void norm2_body(const double2* __restrict__ v, long long n, double* partial, unsigned* counter,
+                                           double* out, int mode, double q0norm, double fixed_eps, unsigned bidx,
+                                           unsigned nb) {
   __shared__ double red[32];
   __shared__ bool last;
   double s = 0.0;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+  for (long long i = (long long)bidx * blockDim.x + threadIdx.x; i < n; i += (long long)nb * blockDim.x) {
     double2 z = v[i];
     s = fma(z.x, z.x, fma(z.y, z.y, s));
   }
   const double t = block_sum(s, red);
   if (threadIdx.x == 0) {
-    partial[blockIdx.x] = t;
+    partial[bidx] = t;
     __threadfence();
-    last = atomicAdd(counter, 1u) == gridDim.x - 1;
+    last = atomicAdd(counter, 1u) == nb - 1;
   }
   __syncthreads();
   if (!last) return;
   __threadfence();
   double a = 0.0;
-  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) a += ((volatile double*)partial)[b];
+  for (int b = threadIdx.x; b < (int)nb; b += blockDim.x) a += ((volatile double*)partial)[b];
   __syncthreads();
   const double tot = block_sum(a, red);
   if (threadIdx.x == 0) {
     *out = norm_result(tot, mode, q0norm, fixed_eps);
     *counter = 0u;
   }
+}
+
+__global__ void k_norm2(const double2* __restrict__ v, long long n, double* partial, unsigned* counter, double* out,
+                        int mode, double q0norm, double fixed_eps, const int* gate) {
+  if (gate && *gate) return;
+  norm2_body(v, n, partial, counter, out, mode, q0norm, fixed_eps, blockIdx.x, gridDim.x);
 }
 
 __global__ void k_norm2_partial(const double2* __restrict__ v, long long n, double* partial, const int* gate) {
@@ -666,14 +685,13 @@ __global__ void k_coeffs(const PointParams P, double* coef) {
 // two-sum accumulation (~2^-47 relative per term), the O(eps) remainder in
 // FP32 from the inputs' high parts and FP32 base tables: no FP64 products.
 template <int D>
-__global__ void __launch_bounds__(128, D == 2 ? 4 : 3) k_point_fast(const PointParams P, const ffn* __restrict__ coefp,
-                                                   const float* __restrict__ btab_f) {
-  if (P.gate && *P.gate) return;
+__device__ __forceinline__ void point_fast_body(const PointParams& P, const ffn* __restrict__ coefp,
+                                                const float* __restrict__ btab_f, unsigned bidx, unsigned nb) {
   constexpr int NW = pw::nw_inputs(D);
   constexpr int o2 = (D + 3) + D * (D + 3), om = o2 + D * (D + 1);
   const double e = *P.eps;
   const bool visc = P.phys.visc;
-  for (long long pt = (long long)blockIdx.x * blockDim.x + threadIdx.x; pt < P.npts; pt += (long long)gridDim.x * blockDim.x) {
+  for (long long pt = (long long)bidx * blockDim.x + threadIdx.x; pt < P.npts; pt += (long long)nb * blockDim.x) {
     const int j = row_of(P, pt);
     const bool bc_row = (j == 0 || j == P.ny - 1);
     const unsigned fl = bc_row ? P.bcflags[(j == P.ny - 1 ? (long long)P.nx * P.nz : 0)] : 0u;
@@ -745,6 +763,13 @@ __global__ void __launch_bounds__(128, D == 2 ? 4 : 3) k_point_fast(const PointP
   }
 }
 
+template <int D>
+__global__ void __launch_bounds__(128, D == 2 ? 4 : 3) k_point_fast(const PointParams P, const ffn* __restrict__ coefp,
+                                                   const float* __restrict__ btab_f) {
+  if (P.gate && *P.gate) return;
+  point_fast_body<D>(P, coefp, btab_f, blockIdx.x, gridDim.x);
+}
+
 // Fold the y metric into the per-row coefficients so that the pointwise kernel
 // can use the line passes' eta-derivatives directly:
 //   f_y = f_eta ey,  f_yy = f_etaeta ey^2 + f_eta eyy,  mixed with y: x ey.
@@ -782,13 +807,12 @@ __global__ void k_to_float_tab(const double* in, float* out, long long count) {
 }
 
 // T's scaled difference split the same way: FP64 first order + FP32 rest
-__global__ void k_temperature_fast(const PointParams P, double2* Tw) {
-  if (P.gate && *P.gate) return;
+__device__ __forceinline__ void temperature_fast_body(const PointParams& P, double2* Tw, unsigned bidx, unsigned nb) {
   const int D = P.nz > 1 ? 3 : 2;
   const double e = *P.eps;
   const float ef = (float)e;
   const pw::ClosureK C = P.phys.C;
-  for (long long pt = (long long)blockIdx.x * blockDim.x + threadIdx.x; pt < P.npts; pt += (long long)gridDim.x * blockDim.x) {
+  for (long long pt = (long long)bidx * blockDim.x + threadIdx.x; pt < P.npts; pt += (long long)nb * blockDim.x) {
     const int j = row_of(P, pt);
     const double ip0 = P.btab[pw::bt_extra(D, pw::X_IP) * P.nbase + j];
     const double T0 = P.btab[pw::bt_val(D, D + 2) * P.nbase + j];
@@ -809,6 +833,11 @@ __global__ void k_temperature_fast(const PointParams P, double2* Tw) {
     }
     Tw[pt] = make_double2(t[0], t[1]);
   }
+}
+
+__global__ void k_temperature_fast(const PointParams P, double2* Tw) {
+  if (P.gate && *P.gate) return;
+  temperature_fast_body(P, Tw, blockIdx.x, gridDim.x);
 }
 
 // base state as complex fields + base temperature (imaginary parts zero)
@@ -881,6 +910,105 @@ __global__ void k_pack_base(const PackParams P) {
       }
     }
   }
+}
+
+// ---------------------------------------------------------------------------
+// Batched J v: one launch per phase runs the work items (instance, block) of
+// several problems of uneven size.  Item i owns the flat blocks
+// [start[i], start[i+1]); a CTA finds its item by binary search, copies the
+// item's parameters to shared memory and runs the single-problem body with
+// its local block index, so every instance computes exactly what its own
+// launch would.
+// ---------------------------------------------------------------------------
+struct NormItem {
+  const double2* v;
+  long long n;
+  double* partial;
+  unsigned* counter;
+  double* out;
+  double q0norm, fixed_eps;
+  int mode, pad;
+};
+struct TempItem {
+  PointParams P;
+  double2* Tw;
+};
+struct PointItem {
+  PointParams P;
+  const ffn* coefp;
+  const float* btab_f;
+};
+static_assert(sizeof(PassParams) % 8 == 0 && sizeof(TempItem) % 8 == 0 && sizeof(PointItem) % 8 == 0,
+              "items are copied to shared memory in 8-byte words");
+
+// largest i with start[i] <= b (start[0] = 0, increasing)
+__device__ __forceinline__ int batch_item(const int* __restrict__ start, int count, unsigned b) {
+  int lo = 0, hi = count - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if ((unsigned)__ldg(start + mid) <= b) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ void copy_to_shared(void* dst, const void* src, size_t bytes) {
+  const unsigned long long* s8 = (const unsigned long long*)src;
+  unsigned long long* d8 = (unsigned long long*)dst;
+  for (size_t k = threadIdx.x; k < bytes / 8; k += blockDim.x) d8[k] = __ldg(s8 + k);
+}
+
+__global__ void k_norm2_batch(const NormItem* __restrict__ items, const int* __restrict__ start, int count) {
+  const int i = batch_item(start, count, blockIdx.x);
+  const NormItem it = items[i];
+  const unsigned nb = (unsigned)(__ldg(start + i + 1) - __ldg(start + i));
+  norm2_body(it.v, it.n, it.partial, it.counter, it.out, it.mode, it.q0norm, it.fixed_eps,
+             blockIdx.x - (unsigned)__ldg(start + i), nb);
+}
+
+__global__ void k_temperature_fast_batch(const TempItem* __restrict__ items, const int* __restrict__ start, int count) {
+  __shared__ TempItem sI;
+  const int i = batch_item(start, count, blockIdx.x);
+  copy_to_shared(&sI, items + i, sizeof(TempItem));
+  __syncthreads();
+  const unsigned s0 = (unsigned)__ldg(start + i);
+  temperature_fast_body(sI.P, sI.Tw, blockIdx.x - s0, (unsigned)__ldg(start + i + 1) - s0);
+}
+
+template <int D>
+__global__ void __launch_bounds__(128, D == 2 ? 4 : 3)
+    k_point_fast_batch(const PointItem* __restrict__ items, const int* __restrict__ start, int count) {
+  __shared__ PointItem sI;
+  const int i = batch_item(start, count, blockIdx.x);
+  copy_to_shared(&sI, items + i, sizeof(PointItem));
+  __syncthreads();
+  const unsigned s0 = (unsigned)__ldg(start + i);
+  point_fast_body<D>(sI.P, sI.coefp, sI.btab_f, blockIdx.x - s0, (unsigned)__ldg(start + i + 1) - s0);
+}
+
+// line passes: item = (instance, axis, chunk of at most STAB_MAX_JOBS jobs);
+// its blocks are (line block, job) with the line block fastest
+template <bool FF>
+__global__ void k_line_pass_batch(const PassParams* __restrict__ items, const int* __restrict__ start, int count) {
+  __shared__ PassParams sP;
+  const int i = batch_item(start, count, blockIdx.x);
+  copy_to_shared(&sP, items + i, sizeof(PassParams));
+  __syncthreads();
+  const unsigned local = blockIdx.x - (unsigned)__ldg(start + i);
+  const unsigned nbx = (unsigned)((sP.nlines + sP.L - 1) / sP.L);
+  line_pass_body<FF>(sP, local % nbx, local / nbx);
+}
+
+template <bool FF>
+__global__ void __launch_bounds__(kCompactMaxThreads)
+    k_line_pass_compact_batch(const PassParams* __restrict__ items, const int* __restrict__ start, int count) {
+  __shared__ PassParams sP;
+  const int i = batch_item(start, count, blockIdx.x);
+  copy_to_shared(&sP, items + i, sizeof(PassParams));
+  __syncthreads();
+  const unsigned local = blockIdx.x - (unsigned)__ldg(start + i);
+  const unsigned nbx = (unsigned)((sP.nlines + sP.L - 1) / sP.L);
+  line_pass_compact_body<FF>(sP, local % nbx, local / nbx);
 }
 
 }  // namespace
@@ -964,10 +1092,11 @@ static void make_slots(StabHandle* h) {
   S.count = c;
 }
 
-static cudaError_t run_pass(StabHandle* h, int axis, const PassParams& base_params, const std::vector<LineJob>& jobs,
-                            long long contiguous_lines = -1) {
-  if (jobs.empty()) return cudaSuccess;
-  PassParams P = base_params;
+// Parameters and launch shape of one axis's line pass for njobs jobs (the job
+// list itself is filled by the caller, STAB_MAX_JOBS per launch).
+static cudaError_t pass_shape(StabHandle* h, int axis, const PassParams& base_params, size_t njobs,
+                              long long contiguous_lines, PassParams& P, int& threads, size_t& smem) {
+  P = base_params;
   const AxisTables& A = h->ax[axis];
   P.axis = axis;
   P.n = A.n;
@@ -1024,7 +1153,7 @@ static cudaError_t run_pass(StabHandle* h, int axis, const PassParams& base_para
   const long long LS = P.LS;
   // default kinds at once: both when two CTAs of 32 lines' worth of work fit
   // (short lines, small grids: latency matters), else one after the other
-  const long long fill = (P.nlines * (long long)jobs.size() + 2 * 152 - 1) / (2 * 152);
+  const long long fill = (P.nlines * (long long)njobs + 2 * 152 - 1) / (2 * 152);
   P.KP = cfg.kp > 0 ? cfg.kp : (fill <= 4 ? 2 : 1);
   if (P.KP == 3 && P.C > 16) return cudaErrorInvalidValue;  // the compact kernel keeps a chunk in registers
   const int tpl = (P.KP == 2 ? 4 : 2) * P.nchunks;  // threads per line
@@ -1046,9 +1175,21 @@ static cudaError_t run_pass(StabHandle* h, int axis, const PassParams& base_para
   P.divn = make_fastdiv((unsigned)n);
   P.divL = make_fastdiv((unsigned)L);
   P.divnx = make_fastdiv((unsigned)P.nx);
-  int threads = tpl * L;
+  threads = tpl * L;
   threads = ((threads + 31) / 32) * 32;
-  size_t smem = (size_t)smem_line * L + kLineSmemExtra;
+  smem = (size_t)smem_line * L + kLineSmemExtra;
+  return cudaSuccess;
+}
+
+static cudaError_t run_pass(StabHandle* h, int axis, const PassParams& base_params, const std::vector<LineJob>& jobs,
+                            long long contiguous_lines = -1) {
+  if (jobs.empty()) return cudaSuccess;
+  PassParams P;
+  int threads = 0;
+  size_t smem = 0;
+  const cudaError_t e = pass_shape(h, axis, base_params, jobs.size(), contiguous_lines, P, threads, smem);
+  if (e != cudaSuccess) return e;
+  const int L = P.L;
   for (size_t j0 = 0; j0 < jobs.size(); j0 += STAB_MAX_JOBS) {
     P.njobs = (int)std::min<size_t>(STAB_MAX_JOBS, jobs.size() - j0);
     for (int q = 0; q < P.njobs; ++q) P.job[q] = jobs[j0 + q];
@@ -1549,4 +1690,274 @@ cudaError_t launch_norm2_stream(cudaStream_t st, const double2* v, long long n, 
   k_norm2_partial<<<nb, 256, 0, st>>>(v, n, partial, nullptr);
   k_norm2_final<<<1, 32, 0, st>>>(partial, nb, d_out, 1, 0.0, 0.0, nullptr);
   return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Batched J v over several handles (uneven grids): the per-instance items of
+// every phase are built on the host, copied to device memory in one transfer
+// (from a pinned staging buffer guarded by an event), and each phase is one
+// launch per kernel variant for all instances.
+// ---------------------------------------------------------------------------
+struct stab_jv_batch_s {
+  std::vector<StabHandle*> hs;
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  void* d_buf = nullptr;
+  size_t d_cap = 0;
+  void* h_buf = nullptr;  // pinned
+  size_t h_cap = 0;
+  cudaEvent_t copied = nullptr;  // the last transfer out of h_buf has completed
+  std::string err;
+};
+
+namespace {
+
+struct Section {
+  size_t items = 0, start = 0;  // byte offsets in the image
+  int count = 0, blocks = 0, threads = 0;
+  size_t smem = 0;
+};
+
+// image builder: items of one type followed by their block offsets
+struct Image {
+  std::vector<unsigned char> bytes;
+  size_t put(const void* p, size_t n) {
+    size_t off = (bytes.size() + 15) & ~(size_t)15;
+    bytes.resize(off + n);
+    std::memcpy(bytes.data() + off, p, n);
+    return off;
+  }
+  template <class T>
+  Section section(const std::vector<T>& items, const std::vector<int>& blocks, int threads, size_t smem) {
+    Section s;
+    s.count = (int)items.size();
+    if (!s.count) return s;
+    std::vector<int> start(items.size() + 1, 0);
+    for (size_t i = 0; i < items.size(); ++i) start[i + 1] = start[i] + blocks[i];
+    s.items = put(items.data(), items.size() * sizeof(T));
+    s.start = put(start.data(), start.size() * sizeof(int));
+    s.blocks = start.back();
+    s.threads = threads;
+    s.smem = smem;
+    return s;
+  }
+};
+
+}  // namespace
+
+static cudaError_t jv_batch_attributes() {
+  const void* ks[4] = {(const void*)k_line_pass_batch<false>, (const void*)k_line_pass_batch<true>,
+                       (const void*)k_line_pass_compact_batch<false>, (const void*)k_line_pass_compact_batch<true>};
+  for (const void* k : ks) {
+    const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLineSmemMax);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+static cudaError_t jv_batch_apply(stab_jv_batch_s* B, const double2* const* v, double2* const* out, const double* shifts) {
+  const int count = (int)B->hs.size();
+  Image im;
+  // 1. epsilon: one norm item per epsilon-quotient instance
+  std::vector<NormItem> norms;
+  std::vector<int> norm_blocks;
+  // 2. temperature differences (viscous instances)
+  std::vector<TempItem> temps;
+  std::vector<int> temp_blocks;
+  // 4. pointwise assembly, per dimension
+  std::vector<PointItem> points[2];
+  std::vector<int> point_blocks[2];
+  for (int i = 0; i < count; ++i) {
+    StabHandle* h = B->hs[i];
+    if (h->opts.eps_mode != 2) {
+      long long nb = (h->n + 1023) / 1024;
+      nb = std::max<long long>(1, std::min<long long>(nb, h->red_blocks));
+      NormItem it{};
+      it.v = v[i];
+      it.n = h->n;
+      it.partial = h->d_red;
+      it.counter = (unsigned*)(h->d_red + h->red_blocks + 8);
+      it.out = h->d_eps;
+      it.q0norm = h->q0norm;
+      it.fixed_eps = h->opts.eps;
+      it.mode = 2;
+      norms.push_back(it);
+      norm_blocks.push_back((int)nb);
+    }
+    PointParams P = point_params(h, v[i]);
+    P.gate = nullptr;
+    P.out = out[i];
+    P.shift = shifts ? make_double2(shifts[2 * i], shifts[2 * i + 1]) : make_double2(0.0, 0.0);
+    double2* Tw = h->d_scratch + (long long)h->slots.Tw * h->npts;
+    if (h->visc) {
+      temps.push_back(TempItem{P, Tw});
+      temp_blocks.push_back(grid_for(h->npts, 128));
+    }
+    points[h->dim - 2].push_back(PointItem{P, h->d_coef_p, h->d_btab_f});
+    point_blocks[h->dim - 2].push_back(grid_for(h->npts, 128));
+  }
+  const Section s_norm = im.section(norms, norm_blocks, 256, 0);
+  const Section s_temp = im.section(temps, temp_blocks, 128, 0);
+  // 3. line passes y, z, x; per axis one section per kernel variant (main /
+  // compact, FP64 / pair right-hand sides)
+  Section s_line[3][4];
+  static const int order[3] = {1, 2, 0};
+  for (int q = 0; q < 3; ++q) {
+    const int ax = order[q];
+    std::vector<PassParams> items[4];
+    std::vector<int> blocks[4];
+    int threads[4] = {0, 0, 0, 0};
+    size_t smem[4] = {0, 0, 0, 0};
+    for (int i = 0; i < count; ++i) {
+      StabHandle* h = B->hs[i];
+      if (ax >= h->dim) continue;
+      const int D = h->dim;
+      const double2* src[6];
+      for (int f = 0; f < D + 2; ++f) src[f] = v[i] + (long long)f * h->npts;
+      src[D + 2] = h->d_scratch + (long long)h->slots.Tw * h->npts;
+      std::vector<LineJob> jobs;
+      axis_jobs(h, ax, src, jobs);
+      if (jobs.empty()) continue;
+      PassParams base{};
+      base.ff = h->stencil_ff;
+      PassParams P;
+      int thr = 0;
+      size_t sm = 0;
+      const cudaError_t e = pass_shape(h, ax, base, jobs.size(), -1, P, thr, sm);
+      if (e != cudaSuccess) return e;
+      const int var = (P.KP == 3 ? 2 : 0) + (P.ff ? 1 : 0);
+      const long long nbx = (P.nlines + P.L - 1) / P.L;
+      for (size_t j0 = 0; j0 < jobs.size(); j0 += STAB_MAX_JOBS) {
+        P.njobs = (int)std::min<size_t>(STAB_MAX_JOBS, jobs.size() - j0);
+        for (int k = 0; k < P.njobs; ++k) P.job[k] = jobs[j0 + k];
+        items[var].push_back(P);
+        blocks[var].push_back((int)(nbx * P.njobs));
+      }
+      threads[var] = std::max(threads[var], thr);
+      smem[var] = std::max(smem[var], sm);
+    }
+    for (int k = 0; k < 4; ++k) s_line[q][k] = im.section(items[k], blocks[k], threads[k], smem[k]);
+  }
+  Section s_point[2];
+  for (int d = 0; d < 2; ++d) s_point[d] = im.section(points[d], point_blocks[d], 128, 0);
+
+  // transfer: staging buffer (after the previous transfer out of it), device buffer
+  const size_t bytes = im.bytes.size();
+  cudaError_t e;
+  if ((e = cudaEventSynchronize(B->copied)) != cudaSuccess) return e;
+  if (bytes > B->h_cap) {
+    if (B->h_buf) cudaFreeHost(B->h_buf);
+    B->h_buf = nullptr;
+    B->h_cap = 0;
+    if ((e = cudaHostAlloc(&B->h_buf, bytes, cudaHostAllocDefault)) != cudaSuccess) return e;
+    B->h_cap = bytes;
+  }
+  if (bytes > B->d_cap) {
+    if (B->d_buf) cudaFreeAsync(B->d_buf, B->stream);
+    B->d_buf = nullptr;
+    B->d_cap = 0;
+    if ((e = dev_alloc_stream(B->device, B->stream, &B->d_buf, bytes)) != cudaSuccess) return e;
+    B->d_cap = bytes;
+  }
+  std::memcpy(B->h_buf, im.bytes.data(), bytes);
+  if ((e = cudaMemcpyAsync(B->d_buf, B->h_buf, bytes, cudaMemcpyHostToDevice, B->stream)) != cudaSuccess) return e;
+  if ((e = cudaEventRecord(B->copied, B->stream)) != cudaSuccess) return e;
+  const unsigned char* d = (const unsigned char*)B->d_buf;
+  auto items_of = [&](const Section& s) { return (const void*)(d + s.items); };
+  auto start_of = [&](const Section& s) { return (const int*)(d + s.start); };
+
+  // exact tangent: epsilon is zero
+  for (StabHandle* h : B->hs)
+    if (h->opts.eps_mode == 2 && h->last_eps_mode != 2) k_set_scalar<<<1, 1, 0, B->stream>>>(h->d_eps, 0.0);
+  cudaStream_t st = B->stream;
+  if (s_norm.count)
+    k_norm2_batch<<<s_norm.blocks, 256, 0, st>>>((const NormItem*)items_of(s_norm), start_of(s_norm), s_norm.count);
+  if (s_temp.count)
+    k_temperature_fast_batch<<<s_temp.blocks, 128, 0, st>>>((const TempItem*)items_of(s_temp), start_of(s_temp),
+                                                            s_temp.count);
+  for (int q = 0; q < 3; ++q)
+    for (int k = 0; k < 4; ++k) {
+      const Section& s = s_line[q][k];
+      if (!s.count) continue;
+      const PassParams* it = (const PassParams*)items_of(s);
+      if (k == 0) k_line_pass_batch<false><<<s.blocks, s.threads, s.smem, st>>>(it, start_of(s), s.count);
+      else if (k == 1) k_line_pass_batch<true><<<s.blocks, s.threads, s.smem, st>>>(it, start_of(s), s.count);
+      else if (k == 2) k_line_pass_compact_batch<false><<<s.blocks, s.threads, s.smem, st>>>(it, start_of(s), s.count);
+      else k_line_pass_compact_batch<true><<<s.blocks, s.threads, s.smem, st>>>(it, start_of(s), s.count);
+    }
+  if (s_point[0].count)
+    k_point_fast_batch<2><<<s_point[0].blocks, 128, 0, st>>>((const PointItem*)items_of(s_point[0]),
+                                                            start_of(s_point[0]), s_point[0].count);
+  if (s_point[1].count)
+    k_point_fast_batch<3><<<s_point[1].blocks, 128, 0, st>>>((const PointItem*)items_of(s_point[1]),
+                                                            start_of(s_point[1]), s_point[1].count);
+  for (StabHandle* h : B->hs) {
+    h->last_eps_mode = h->opts.eps_mode;
+    h->stats.jv_calls++;
+  }
+  return cudaGetLastError();
+}
+
+extern "C" stab_status stab_jv_batch_create(stab_jv_batch* out, const stab_handle* handles, int count, void* cuda_stream) {
+  if (!out) return STAB_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!handles || count < 1 || count > 4096) return STAB_ERR_INVALID_ARG;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return STAB_ERR_CUDA;
+  std::vector<StabHandle*> hs((size_t)count);
+  for (int i = 0; i < count; ++i) hs[i] = (StabHandle*)handles[i];  // the handle type derives from StabHandle
+  for (int i = 0; i < count; ++i) {
+    StabHandle* h = hs[i];
+    if (!h || h->device != dev) return STAB_ERR_INVALID_ARG;
+    for (int k = 0; k < i; ++k)
+      if (hs[k] == h) return STAB_ERR_INVALID_ARG;  // one derivative scratch per handle
+    if (!(h->homog && h->d_coef && !h->force_dn_path)) return STAB_ERR_UNSUPPORTED;
+  }
+  stab_jv_batch_s* B = new (std::nothrow) stab_jv_batch_s();
+  if (!B) return STAB_ERR_OOM;
+  B->hs = hs;
+  B->device = dev;
+  B->stream = (cudaStream_t)cuda_stream;
+  if (jv_batch_attributes() != cudaSuccess ||
+      cudaEventCreateWithFlags(&B->copied, cudaEventDisableTiming) != cudaSuccess) {
+    delete B;
+    return STAB_ERR_CUDA;
+  }
+  *out = B;
+  return STAB_OK;
+}
+
+extern "C" stab_status stab_jv_batch_apply(stab_jv_batch B, const void* const* v, void* const* Jv, const double* shifts) {
+  if (!B) return STAB_ERR_INVALID_ARG;
+  if (!v || !Jv) {
+    B->err = "stab_jv_batch_apply: null vector list";
+    return STAB_ERR_INVALID_ARG;
+  }
+  const int count = (int)B->hs.size();
+  for (int i = 0; i < count; ++i) {
+    const char* a = (const char*)v[i];
+    const char* b = (const char*)Jv[i];
+    const long long bytes = B->hs[i]->n * (long long)sizeof(double2);
+    if (!a || !b || (a < b + bytes && b < a + bytes)) {
+      B->err = "stab_jv_batch_apply: null or overlapping v / Jv of instance " + std::to_string(i);
+      return STAB_ERR_INVALID_ARG;
+    }
+  }
+  const cudaError_t e = jv_batch_apply(B, (const double2* const*)v, (double2* const*)Jv, shifts);
+  if (e != cudaSuccess) {
+    B->err = std::string("stab_jv_batch_apply: ") + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? STAB_ERR_OOM : STAB_ERR_CUDA;
+  }
+  return STAB_OK;
+}
+
+extern "C" const char* stab_jv_batch_last_error(stab_jv_batch B) { return B ? B->err.c_str() : ""; }
+
+extern "C" void stab_jv_batch_destroy(stab_jv_batch B) {
+  if (!B) return;
+  cudaEventSynchronize(B->copied);
+  if (B->d_buf) cudaFreeAsync(B->d_buf, B->stream);
+  if (B->h_buf) cudaFreeHost(B->h_buf);
+  cudaEventDestroy(B->copied);
+  delete B;
 }

@@ -1,0 +1,88 @@
+"""Batched J v (stab_jv_batch_*): one launch per phase for several problems of
+uneven size.  Each instance's result must equal its handle's own stab_apply_J
+bit for bit (same kernels, same per-instance launch shapes and summation
+order); the single-handle path is the one the parity tests check against the
+oracle."""
+import numpy as np
+import pytest
+
+import stab_inputs as si
+
+pytestmark = pytest.mark.gpu
+
+
+def _instances():
+    from paper_1502_03701_gb300 import Stab
+    specs = [
+        (si.mixing_layer_2d(32, 64), {}),
+        (si.mixing_layer_2d(64, 128, Ma=0.6), dict(eps_mode=2)),
+        ((si.Grid(2, 48, 40, 1, si.LX_04, -15, 15), si.Flow(0.3, 500.0)), dict(stencil_prec=48)),
+        ((si.Grid(2, 70, 67, 1, si.LX_04, -15, 15, 1.0, 1.7), si.Flow(0.6, 500.0)), {}),   # stretched, ragged
+        ((si.Grid(2, 24, 40, 1, si.LX_04, -15, 15), si.Flow(0.9, 0.0)), {}),                 # inviscid
+        ((si.Grid(3, 12, 16, 8, si.LX_04, -15, 15, si.LX_04), si.Flow(0.5, 800.0)), {}),     # 3-D
+        ((si.Grid(3, 16, 20, 6, si.LX_04, -15, 15, si.LX_04), si.Flow(0.4, 300.0)), dict(eps_mode=2, stencil_prec=48)),
+    ]
+    out = []
+    for (g, f), opts in specs:
+        S = Stab(si.tanh_base_flow(g, f), g, f.Ma, f.Re, f.Pr, **opts)
+        out.append((S, g))
+    # launch shapes: one instance in the compact mode, one side by side, one tuned
+    out[0][0].set_line_config(1, 16, 4, 3)
+    out[0][0].set_line_config(0, 16, 2, 2)
+    out[3][0].autotune()
+    out[5][0].set_line_config(2, 16, 2, 3)
+    out[2][0].set_line_config(1, 16, 2, 3)  # compact mode with pair right-hand sides
+    return out
+
+
+def test_batch_equals_each_handle_bit_for_bit():
+    import torch
+    from paper_1502_03701_gb300 import JvBatch
+    inst = _instances()
+    vs = [torch.from_numpy(si.random_complex(500 + i, S.n)).cuda() for i, (S, g) in enumerate(inst)]
+    shifts = [0.0, -1 + 0.2j, 0.5j, 0.0, 2.0, -0.25, 1 - 1j]
+    ref, eps_ref = [], []
+    for (S, g), v, z in zip(inst, vs, shifts):
+        o = torch.empty_like(v)
+        S.apply_J(v, o, z)
+        ref.append(o)
+        eps_ref.append(S.last_eps())
+    B = JvBatch([S for S, g in inst])
+    for rep in range(3):  # repeated calls reuse the staging and parameter buffers
+        outs = [torch.full_like(v, float("nan")) for v in vs]
+        B.apply(vs, outs, shifts)
+        torch.cuda.synchronize()
+        for i, (o, r) in enumerate(zip(outs, ref)):
+            assert torch.equal(o, r), (rep, i, float((o - r).abs().max() / r.abs().max()))
+        assert [S.last_eps() for S, g in inst] == eps_ref
+    # without shifts: J v itself
+    outs = [torch.empty_like(v) for v in vs]
+    B.apply(vs, outs)
+    for (S, g), v, o in zip(inst, vs, outs):
+        r = torch.empty_like(v)
+        S.apply_J(v, r)
+        assert torch.equal(o, r)
+    B.close()
+    for S, g in inst:
+        S.close()
+
+
+def test_batch_rejects_bad_handles_and_vectors():
+    import torch
+    from paper_1502_03701_gb300 import JvBatch, Stab, StabError
+    g, f = si.mixing_layer_2d(16, 32)
+    S = Stab(si.tanh_base_flow(g, f), g, f.Ma, f.Re, f.Pr)
+    G = Stab(si.perturbed_base_flow(g, f, seed=3), g, f.Ma, f.Re, f.Pr)   # base varies in x: not batched
+    with pytest.raises(StabError, match="INVALID_ARG"):
+        JvBatch([S, S])
+    with pytest.raises(StabError, match="UNSUPPORTED"):
+        JvBatch([S, G])
+    B = JvBatch([S])
+    v = torch.zeros(S.n, dtype=torch.complex128, device="cuda")
+    with pytest.raises(StabError, match="overlapping"):
+        B.apply([v], [v])
+    with pytest.raises(ValueError):
+        B.apply([v, v], [v])
+    B.close()
+    S.close()
+    G.close()
