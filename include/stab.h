@@ -250,8 +250,8 @@ stab_status stab_timing_read(stab_handle h, double* ms, long long* count, long l
 /* Autotuner of the compact-derivative line pass (performance only; the paper
  * has no counterpart).  For every axis of h, times each admissible launch
  * shape (C = 16, 32 or 64 points per sweep chunk; L = 1..32 lines per CTA;
- * the first and second derivatives side by side or one after the other, in
- * 4 or 2 planes of shared memory per line)
+ * the first and second derivatives side by side in 6 planes of shared memory
+ * per line, or one after the other in 4 or 2)
  * with CUDA events on the handle's stream and keeps the fastest, in h and in a
  * process-wide cache keyed by device, line length, line count, job count and
  * boundary type; stab_create applies cached shapes to new handles.  force = 0
@@ -267,10 +267,10 @@ stab_status stab_autotune(stab_handle h, int force, int* cfg, double* ms);
  * sweep chunk (16, 32 or 64), L lines per CTA (1..32), kinds = 2 to sweep the
  * first and second derivatives side by side, 1 to do them one after the
  * other with 4 instead of 6 planes of shared memory per line, 3 one after the
- * other with 2 planes (the input reloaded per kind; C = 16 only); all zero
- * restores the built-in default.
- * INVALID_ARG when the shape does not fit the line (more than 1024 threads or
- * the shared-memory limit). */
+ * other with 2 planes (the input reloaded per kind and turned into right-hand
+ * sides in place); all zero restores the built-in default.
+ * INVALID_ARG when the shape does not fit the line (more than 1024 threads,
+ * 512 with kinds 3, or the shared-memory limit). */
 stab_status stab_set_line_config(stab_handle h, int axis, int C, int L, int kinds);
 
 /* Handles take device memory from a library-owned, stream-ordered pool (one

@@ -312,10 +312,10 @@ extern "C" stab_status stab_set_line_config(stab_handle h, int axis, int C, int 
   const long long LS = n + (n >> 5) + 1;
   const int nch = (C > 0) ? (n + C - 1) / C : 0;
   const int tpl = (kinds == 2 ? 4 : 2) * nch, planes = kinds == 3 ? 2 : 2 + 2 * kinds;
-  if ((C != 16 && C != 32 && C != 64) || L < 1 || L > 32 || kinds < 1 || kinds > 3 || (kinds == 3 && C > 16) ||
-      tpl * L > (kinds == 3 ? 512 : 1024) || planes * 8 * LS * L > 200 * 1024) {
-    h->err = "stab_set_line_config: C must be 16, 32 or 64 (16 with kinds 3), L in 1..32 and kinds 1, 2 or 3, "
-             "within 1024 threads and 200 KB";
+  if ((C != 16 && C != 32 && C != 64) || L < 1 || L > 32 || kinds < 1 || kinds > 3 ||
+      tpl * L > (kinds == 3 ? 512 : 1024) || planes * 8 * LS * L + 16 > 200 * 1024) {
+    h->err = "stab_set_line_config: C must be 16, 32 or 64, L in 1..32 and kinds 1, 2 or 3, within 1024 threads "
+             "(512 with kinds 3) and 200 KB";
     return STAB_ERR_INVALID_ARG;
   }
   h->line_cfg[axis] = LineCfg{C, L, kinds};

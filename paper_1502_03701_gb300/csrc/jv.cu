@@ -17,6 +17,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <type_traits>
 #include <map>
 #include <mutex>
 
@@ -132,15 +133,30 @@ __device__ __forceinline__ void stencil_idx(const PassParams& P, int t, int& tm2
   }
 }
 
+// interior right-hand side from the five values f_{t-2} .. f_{t+2} (f_t is
+// only read by the second derivative)
+__device__ __forceinline__ double interior_rhs(const PassParams& P, int kind, double fm2, double fm1, double f0,
+                                               double fp1, double fp2) {
+  if (kind == 0) return fma(P.c1[0], fp1 - fm1, P.c2[0] * (fp2 - fm2));
+  return fma(P.c1[1], fp1 - 2.0 * f0 + fm1, P.c2[1] * (fp2 - 2.0 * f0 + fm2));
+}
+
 // right-hand side (B f)_t of the compact scheme for one real component
 __device__ __forceinline__ double stencil_rhs(const PassParams& P, const double* fl, int t, int kind) {
   auto f = [&](int q) { return fl[sidx(q)]; };
   if (!P.periodic && (t < 2 || t > P.n - 3)) return closure_rhs(P, f, t, kind);
   int tm2, tm1, tp1, tp2;
   stencil_idx(P, t, tm2, tm1, tp1, tp2);
-  if (kind == 0) return fma(P.c1[0], f(tp1) - f(tm1), P.c2[0] * (f(tp2) - f(tm2)));
-  const double f0 = f(t);
-  return fma(P.c1[1], f(tp1) - 2.0 * f0 + f(tm1), P.c2[1] * (f(tp2) - 2.0 * f0 + f(tm2)));
+  return interior_rhs(P, kind, f(tm2), f(tm1), kind ? f(t) : 0.0, f(tp1), f(tp2));
+}
+
+// interior right-hand side in pair arithmetic (values f * 2^-sh)
+__device__ __forceinline__ ffn interior_rhs_ff(const PassParams& P, int kind, ffn fm2, ffn fm1, ffn f0, ffn fp1,
+                                               ffn fp2) {
+  const ffn c1{P.c1h[kind], P.c1l[kind]}, c2{P.c2h[kind], P.c2l[kind]};
+  if (kind == 0) return ff_add(ff_prod(c1, ff_sub(fp1, fm1)), ff_prod(c2, ff_sub(fp2, fm2)));
+  const ffn m2{-2.0f * f0.hi, -2.0f * f0.lo};
+  return ff_add(ff_prod(c1, ff_add(ff_add(fp1, fm1), m2)), ff_prod(c2, ff_add(ff_add(fp2, fm2), m2)));
 }
 
 // The same right-hand side from a line of FP32 pairs holding f * 2^-sh: the
@@ -154,16 +170,7 @@ __device__ __forceinline__ double stencil_rhs_ff(const PassParams& P, const floa
   }
   int tm2, tm1, tp1, tp2;
   stencil_idx(P, t, tm2, tm1, tp1, tp2);
-  const ffn c1{P.c1h[kind], P.c1l[kind]}, c2{P.c2h[kind], P.c2l[kind]};
-  ffn r;
-  if (kind == 0) {
-    r = ff_add(ff_prod(c1, ff_sub(f(tp1), f(tm1))), ff_prod(c2, ff_sub(f(tp2), f(tm2))));
-  } else {
-    const ffn f0 = f(t);
-    const ffn m2{-2.0f * f0.hi, -2.0f * f0.lo};
-    r = ff_add(ff_prod(c1, ff_add(ff_add(f(tp1), f(tm1)), m2)), ff_prod(c2, ff_add(ff_add(f(tp2), f(tm2)), m2)));
-  }
-  return ff_to_d_scaled(r, sh);
+  return ff_to_d_scaled(interior_rhs_ff(P, kind, f(tm2), f(tm1), kind ? f(t) : ffn{0.0f, 0.0f}, f(tp1), f(tp2)), sh);
 }
 
 // biased exponent of |d| (0 for zero and subnormals)
@@ -368,10 +375,22 @@ __global__ void k_line_pass(const PassParams P) {
 }
 
 // Compact variant (KP = 3): kinds in turn, the input reloaded per kind into
-// the only plane of each component; each thread's chunk of right-hand sides
-// (C <= 16) passes through registers so that it can replace the input in
-// place.  Half the shared memory of the kinds-in-turn layout.
+// the only plane of each component, half the shared memory of the
+// kinds-in-turn layout.  Each thread turns its own chunk of input into
+// right-hand sides in place, left to right, with the five stencil values in
+// registers: the two values on each side of the chunk (which neighbouring
+// threads overwrite) and the closure rows of a bounded line are taken before
+// a barrier.  The arithmetic is that of the other layouts, so the results
+// are the same.
 constexpr int kCompactMaxThreads = 512;
+
+// the value (input of one component) at line index q of this thread's chunk
+// [t0, t1) or of its halo (two points on each side, read before the barrier)
+template <class V>
+struct Window {
+  V m2, m1, p0, p1;  // f(t0 - 2), f(t0 - 1), f(t1), f(t1 + 1)
+};
+
 template <bool FF>
 __device__ __forceinline__ void line_pass_compact_body(const PassParams& P, const unsigned bx, const unsigned by) {
   if (P.gate && *P.gate) return;
@@ -391,6 +410,16 @@ __device__ __forceinline__ void line_pass_compact_body(const PassParams& P, cons
   const bool active = threadIdx.x < 2 * per && (l0 + lt) < P.nlines;
   const long long base = active ? line_base(P, l0 + lt) : 0;
   double* Wc = sm + (size_t)comp * plane + (size_t)lt * LS;
+  using V = typename std::conditional<FF, ffn, double>::type;
+  auto at = [&](int q) -> V {  // staged value at line index q (wrapped on periodic lines)
+    if (P.periodic) q = wrap_small(q, n);
+    if constexpr (FF) {
+      const float2 v = ((const float2*)Wc)[sidx(q)];
+      return ffn{v.x, v.y};
+    } else {
+      return Wc[sidx(q)];
+    }
+  };
   if (FF && threadIdx.x == 0) *sE = 0;
   int sh = 0;
   for (int kind = 0; kind < nk; ++kind) {
@@ -421,22 +450,58 @@ __device__ __forceinline__ void line_pass_compact_body(const PassParams& P, cons
       }
     }
     __syncthreads();
-    double rr[16];
-    const int len = t1 - t0;
+    // halo values and the closure rows of this chunk, before any overwrite
+    Window<V> w{};
+    double cl[4] = {0.0, 0.0, 0.0, 0.0};  // rows 0, 1, n - 2, n - 1 (bounded lines)
+    const bool bounded = !P.periodic;
     if (active) {
+      if (P.periodic || t0 >= 2) w.m2 = at(t0 - 2);
+      if (P.periodic || t0 >= 1) w.m1 = at(t0 - 1);
+      if (P.periodic || t1 < n) w.p0 = at(t1);
+      if (P.periodic || t1 + 1 < n) w.p1 = at(t1 + 1);
+      if (bounded) {
+        const int rows[4] = {0, 1, n - 2, n - 1};
 #pragma unroll
-      for (int q = 0; q < 16; ++q)
-        if (q < len) {
-          double r = FF ? stencil_rhs_ff(P, (const float2*)Wc, t0 + q, kind, sh) : stencil_rhs(P, Wc, t0 + q, kind);
-          if (!P.periodic) r *= __ldg(P.tab[kind] + n + t0 + q);
-          rr[q] = r;
-        }
+        for (int k = 0; k < 4; ++k)
+          if (rows[k] >= t0 && rows[k] < t1) {
+            double r;
+            if constexpr (FF) {
+              auto fd = [&](int q) { return ff_to_d_scaled(at(q), sh); };
+              r = closure_rhs(P, fd, rows[k], kind);
+            } else {
+              auto fd = [&](int q) { return at(q); };
+              r = closure_rhs(P, fd, rows[k], kind);
+            }
+            cl[k] = r * __ldg(P.tab[kind] + n + rows[k]);
+          }
+      }
     }
     __syncthreads();
     if (active) {
-#pragma unroll
-      for (int q = 0; q < 16; ++q)
-        if (q < len) Wc[sidx(t0 + q)] = rr[q];
+      // value at q for q in [t0 - 2, t1 + 2): own chunk from shared memory
+      // (positions >= the current row are not yet overwritten), else the halo
+      auto get = [&](int q) -> V {
+        if (q >= t0 && q < t1) return at(q);
+        return q == t0 - 2 ? w.m2 : q == t0 - 1 ? w.m1 : q == t1 ? w.p0 : w.p1;
+      };
+      V fm2 = w.m2, fm1 = w.m1, f0 = get(t0), fp1 = get(t0 + 1), fp2 = get(t0 + 2);
+      for (int t = t0; t < t1; ++t) {
+        double r;
+        if (bounded && (t < 2 || t > n - 3)) {
+          r = t == 0 ? cl[0] : t == 1 ? cl[1] : t == n - 2 ? cl[2] : cl[3];
+        } else {
+          if constexpr (FF) r = ff_to_d_scaled(interior_rhs_ff(P, kind, fm2, fm1, f0, fp1, fp2), sh);
+          else r = interior_rhs(P, kind, fm2, fm1, f0, fp1, fp2);
+          if (bounded) r *= __ldg(P.tab[kind] + n + t);
+        }
+        const V next = (t + 3 < t1 + 2) ? get(t + 3) : fp2;  // f(t + 3) for the next row
+        Wc[sidx(t)] = r;
+        fm2 = fm1;
+        fm1 = f0;
+        f0 = fp1;
+        fp1 = fp2;
+        fp2 = next;
+      }
     }
     __syncthreads();
     line_sweeps(P, Wc, kind, active, t0, t1, base, comp, kind == 0 ? J.out1 : J.out2);
@@ -1155,7 +1220,6 @@ static cudaError_t pass_shape(StabHandle* h, int axis, const PassParams& base_pa
   // (short lines, small grids: latency matters), else one after the other
   const long long fill = (P.nlines * (long long)njobs + 2 * 152 - 1) / (2 * 152);
   P.KP = cfg.kp > 0 ? cfg.kp : (fill <= 4 ? 2 : 1);
-  if (P.KP == 3 && P.C > 16) return cudaErrorInvalidValue;  // the compact kernel keeps a chunk in registers
   const int tpl = (P.KP == 2 ? 4 : 2) * P.nchunks;  // threads per line
   const int max_threads = P.KP == 3 ? kCompactMaxThreads : 1024;
   if (tpl > max_threads) return cudaErrorInvalidValue;
@@ -1332,7 +1396,6 @@ cudaError_t jv_autotune(StabHandle* h, int force, double* ms_out) {
     for (int kp : {1, 2, 3}) {
       for (int C : {16, 32, 64}) {
         if (C > 16 && C >= 2 * n) continue;
-        if (kp == 3 && C > 16) continue;
         for (int L : {1, 2, 4, 8, 16, 32}) {
           const int nch = (n + C - 1) / C;
           const long long LS = n + (n >> 5) + 1;
@@ -1408,7 +1471,7 @@ int jv_tune_load(const char* path) {
     const int got = std::sscanf(line, "%d %lld %d %d %d %d %d %d", &k.n, &k.nlines, &k.njobs, &k.periodic, &c.C, &c.L,
                                 &c.kp, &k.ff);
     if (got < 7) continue;
-    if (c.C < 1 || c.L < 1 || c.kp < 1 || c.kp > 3 || (c.kp == 3 && c.C > 16) || k.n < 1 || (k.ff != 0 && k.ff != 1))
+    if (c.C < 1 || c.L < 1 || c.kp < 1 || c.kp > 3 || k.n < 1 || (k.ff != 0 && k.ff != 1))
       continue;
     k.dev = dev;
     g_tune[k] = c;

@@ -13,6 +13,8 @@ TOL = 1e-10
 CASES = [
     ("ragged2d_stretched", si.Grid(2, 70, 67, 1, si.LX_04, -15, 15, 1.0, 1.7), si.Flow(0.6, 500.0)),
     ("small3d", si.Grid(3, 12, 16, 8, si.LX_04, -15, 15, si.LX_04), si.Flow(0.5, 800.0)),
+    # 33 points in y: chunks of 16 and 32 end one point before the wall (t1 = n - 1)
+    ("ragged_y33", si.Grid(2, 20, 33, 1, si.LX_04, -15, 15), si.Flow(0.4, 700.0)),
 ]
 
 
@@ -51,7 +53,7 @@ def test_every_line_shape_matches_oracle(orc, name, g, f, stencil_prec):
     with pytest.raises(StabError):
         S.set_line_config(0, 32, 1, 4)
     with pytest.raises(StabError):
-        S.set_line_config(0, 32, 1, 3)
+        S.set_line_config(0, 16, 33, 3)
     S.close()
 
 
