@@ -315,9 +315,9 @@ def gmres_throughput(args, Stab, torch, q0, g, f):
 LINE_FLOP_D1, LINE_FLOP_D2 = 10, 14
 FP64_PEAK_GFLOPS = 1250.0  # GB300 FP64 (non-tensor) nominal; 1.2 TFLOP/s measured by an FMA microbenchmark
 # DRAM bytes per launch of the line pass from ncu (dram__bytes_read.sum + dram__bytes_write.sum) on the
-# 512 x 1024 layer (tuned shapes, FP64 right-hand sides): y pass 42.2 + 12.0 MB, x pass 58.8 + 24.3 MB;
-# scaled by grid points.
-LINE_TRAFFIC_512x1024 = {"line_y": (42.208512 + 12.032000) * 1e6, "line_x": (58.796800 + 24.282112) * 1e6}
+# 512 x 1024 layer (tuned shapes: the compact layout on both axes, FP64 right-hand sides): y pass
+# 42.1 + 11.8 MB, x pass 58.9 + 25.7 MB; scaled by grid points.
+LINE_TRAFFIC_512x1024 = {"line_y": (42.108416 + 11.777024) * 1e6, "line_x": (58.887680 + 25.734144) * 1e6}
 
 
 def line_pass_flops(g, visc: bool) -> dict:
@@ -354,7 +354,8 @@ def jv_roofline(g, f, phases: dict, step_s: float, hbm, tangent_s: float) -> dic
     op_achieved = g.n * JV_BYTES_PER_DOF / step_s / 1e9
     return {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
             "frac": achieved / FP64_PEAK_GFLOPS, "traffic": traffic,
-            "kernel": "k_line_pass (compact-derivative line sweeps; y and x launches per J v)",
+            "kernel": "k_line_pass / k_line_pass_compact (compact-derivative line sweeps in the tuned layout; "
+                      "y and x launches per J v)",
             "flop_per_launch": line_flops / launches, "launch_ms": avg_s * 1e3, "launches": launches,
             "peak_source": "FP64 nominal 1.25 TFLOP/s (recipe table); FMA microbenchmark measures 1.2",
             "traffic_source": "ncu dram bytes of the 512x1024 launches scaled by grid points" if traffic else None,
@@ -519,8 +520,11 @@ def pair_stencil_jv(args, Stab, torch, q0, g, f, v, out, flush, stream, bytes_jv
     """The same J v with the compact-scheme right-hand sides in FP32 pair arithmetic
     (stencil_prec 48; sweeps, closures and the pointwise map unchanged), timed like
     the main step, with its largest difference to the FP64-stencil result."""
+    from paper_1502_03701_gb300 import binding
     S = Stab(q0, g, f.Ma, f.Re, f.Pr, stencil_prec=48)
     tuned = S.autotune()
+    if args.tune_cache:
+        binding.autotune_save(args.tune_cache)
     o2 = torch.empty_like(v)
     for _ in range(3):
         S.apply_J(v, o2)

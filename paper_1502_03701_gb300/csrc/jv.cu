@@ -1207,19 +1207,19 @@ static cudaError_t pass_shape(StabHandle* h, int axis, const PassParams& base_pa
   const int n = A.n;
   if (n > 2048) return cudaErrorInvalidValue;
   // launch shape: C points per sweep chunk, L lines per CTA, KP kinds at
-  // once.  Either tuned (stab_autotune) or by default chunks of 16 (32 on
-  // lines of 512 points or more), at most two lines per CTA, fewer on small
-  // grids so that the CTAs cover the SMs (but at least a warp of threads).
+  // once.  Either tuned (stab_autotune) or by default: on small grids
+  // (latency matters) both kinds side by side in chunks of 16, at most two
+  // lines per CTA and fewer so that the CTAs cover the SMs (but at least a
+  // warp of threads); on larger grids the compact layout in chunks of 32 with
+  // up to four lines per CTA (shared memory bounds occupancy there).
   const LineCfg cfg = contiguous_lines >= 0 ? LineCfg{} : h->line_cfg[axis];
-  // default chunk: 16 points (more sweep threads) unless lines are long
-  P.C = cfg.C > 0 ? cfg.C : (n >= 512 ? 32 : 16);
+  const long long fill = (P.nlines * (long long)njobs + 2 * 152 - 1) / (2 * 152);
+  const bool small = fill <= 4;
+  P.C = cfg.C > 0 ? cfg.C : (small || n < 64 ? 16 : 32);
   P.nchunks = (n + P.C - 1) / P.C;
   P.LS = n + (n >> 5) + 1;
   const long long LS = P.LS;
-  // default kinds at once: both when two CTAs of 32 lines' worth of work fit
-  // (short lines, small grids: latency matters), else one after the other
-  const long long fill = (P.nlines * (long long)njobs + 2 * 152 - 1) / (2 * 152);
-  P.KP = cfg.kp > 0 ? cfg.kp : (fill <= 4 ? 2 : 1);
+  P.KP = cfg.kp > 0 ? cfg.kp : (small ? 2 : 3);
   const int tpl = (P.KP == 2 ? 4 : 2) * P.nchunks;  // threads per line
   const int max_threads = P.KP == 3 ? kCompactMaxThreads : 1024;
   if (tpl > max_threads) return cudaErrorInvalidValue;
@@ -1230,7 +1230,9 @@ static cudaError_t pass_shape(StabHandle* h, int axis, const PassParams& base_pa
   if (cfg.L > 0) {
     L = std::min(cfg.L, maxL);
   } else {
-    L = std::min<long long>(std::min<long long>(maxL, 98304 / smem_line), 2);
+    // compact layout: at least four lines and a CTA of about 128 threads (short lines)
+    const int Lc = std::max(4, (128 + tpl - 1) / tpl);
+    L = std::min<long long>(std::min<long long>(maxL, 98304 / smem_line), P.KP == 3 ? Lc : 2);
     const int Lwarp = (32 + tpl - 1) / tpl;
     if (L > fill) L = (int)std::min<long long>(maxL, std::max<long long>(fill, Lwarp));
   }
