@@ -16,8 +16,8 @@ traffic (32 B per complex unknown).  Also reported, measured in the same run:
     256 x 512 layer (block-Jacobi over 8 x 8-point tiles, FP32 inverses; also
     BF16 inverses, and BF16 inverses with an FP32 Krylov basis);
   * "jv_3d": the same J v on the 3-D 128 x 256 x 64 layer (10.5 M unknowns);
-  * "jv_batch_64": J v of the 64 uneven instances of the batch configuration as one
-    batched call (one launch per phase) against 64 single-problem calls;
+  * "jv_batch_64": J v and block-Jacobi apply of the 64 uneven instances of the batch
+    configuration as one batched call (one launch per phase) against 64 single-problem calls;
   * "many_small": uneven small layers solved one at a time on the plain FP64
     path, as one mixed-precision batch (stab_eigs_batch), and as a Poisson
     stream through the continuous-batching server (p50 / p99 latency).
@@ -391,7 +391,7 @@ def jv_batch_64(args, torch) -> dict:
     hs = []
     for p in insts:
         g, f, q0 = _fleet_problem(p)
-        S = Stab(q0, g, f.Ma, f.Re, f.Pr)
+        S = Stab(q0, g, f.Ma, f.Re, f.Pr, precond=1, tile=(8, 8), precond_prec=32)
         S.autotune()
         hs.append(S)
     vs = [torch.from_numpy(si.random_complex(900 + i, S.n)).cuda() for i, S in enumerate(hs)]
@@ -421,6 +421,18 @@ def jv_batch_64(args, torch) -> dict:
     t_batch = timed(lambda: B.apply(vs, outs))
     same = all(torch.equal(o, r) for o, r in zip(outs, refs))
     n_total = sum(S.n for S in hs)
+    # block-Jacobi apply (8 x 8 tiles, FP32 inverses), batched against one call per instance
+    for S in hs:
+        S.precond_build(1.0)
+
+    def plain_pc():
+        for S, v, o in zip(hs, vs, refs):
+            S.precond_apply(v, o)
+
+    t_pc_plain = timed(plain_pc)
+    t_pc_batch = timed(lambda: B.precond_apply(vs, outs))
+    same_pc = all(torch.equal(o, r) for o, r in zip(outs, refs))
+    inv_bytes = sum(S.n * 256 * 8 for S in hs)  # one 256-entry FP32 complex row per unknown
     B.close()
     for S in hs:
         S.close()
@@ -429,7 +441,11 @@ def jv_batch_64(args, torch) -> dict:
                         "GB_per_s": n_total * JV_BYTES_PER_DOF / t_batch / 1e9, "launches_per_step": "5 to 9"},
             "plain_one_at_a_time": {"value": 64 / t_plain, "unit": "instance J v/s", "ms_per_step": t_plain * 1e3,
                                     "GB_per_s": n_total * JV_BYTES_PER_DOF / t_plain / 1e9},
-            "speedup": t_plain / t_batch, "bitwise_equal_to_plain": same}
+            "speedup": t_plain / t_batch, "bitwise_equal_to_plain": same,
+            "precond_apply": {"batched_ms": t_pc_batch * 1e3, "plain_ms": t_pc_plain * 1e3,
+                              "batched_GB_per_s": inv_bytes / t_pc_batch / 1e9, "speedup": t_pc_plain / t_pc_batch,
+                              "bitwise_equal_to_plain": same_pc,
+                              "note": "block-Jacobi over 8 x 8 tiles, FP32 inverses (stored bytes per step)"}}
 
 
 def fleet(args, torch) -> dict:

@@ -148,6 +148,13 @@ stab_status stab_apply_J(stab_handle h, const void* v, void* Jv, double shift_re
 typedef struct stab_jv_batch_s* stab_jv_batch;
 stab_status stab_jv_batch_create(stab_jv_batch* b, const stab_handle* handles, int count, void* cuda_stream);
 stab_status stab_jv_batch_apply(stab_jv_batch b, const void* const* v, void* const* Jv, const double* shifts);
+/* z[i] = M_i^-1 q[i] for every handle of the batch (block-Jacobi inverses of
+ * each handle's last stab_precond_build): one launch per inverse storage
+ * layout for all instances; each result equals its handle's own
+ * stab_precond_apply bit for bit.  q[i], z[i]: device complex128 vectors
+ * of handle i's size, not overlapping.  INVALID_ARG when a handle has no
+ * preconditioner built. */
+stab_status stab_jv_batch_precond_apply(stab_jv_batch b, const void* const* q, void* const* z);
 const char* stab_jv_batch_last_error(stab_jv_batch b);
 void stab_jv_batch_destroy(stab_jv_batch b);
 

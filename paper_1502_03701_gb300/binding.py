@@ -27,7 +27,7 @@ SYMBOLS = ["stab_default_opts", "stab_create", "stab_destroy", "stab_last_error"
            "stab_set_line_config", "stab_trim_memory", "stab_estimate_bytes", "stab_eigs_batch",
            "stab_server_create", "stab_server_submit", "stab_server_wait", "stab_server_result",
            "stab_server_stats", "stab_server_destroy", "stab_jv_batch_create", "stab_jv_batch_apply",
-           "stab_jv_batch_last_error", "stab_jv_batch_destroy"]
+           "stab_jv_batch_last_error", "stab_jv_batch_destroy", "stab_jv_batch_precond_apply"]
 
 # stab_phase, in enum order
 PHASES = ["eps", "temperature", "line_y", "line_z", "line_x", "pointwise", "cgs2", "precond_apply"]
@@ -137,6 +137,7 @@ def load():
     L.stab_timing_read.argtypes = [vp, dp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]
     L.stab_jv_batch_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(vp), i, vp]
     L.stab_jv_batch_apply.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), dp]
+    L.stab_jv_batch_precond_apply.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp)]
     L.stab_jv_batch_last_error.argtypes = [vp]
     L.stab_jv_batch_last_error.restype = ctypes.c_char_p
     L.stab_jv_batch_destroy.argtypes = [vp]
@@ -372,7 +373,7 @@ def eigs_batch(handles, args, concurrency: int = 0):
 
 
 class JvBatch:
-    """stab_jv_batch_*: J v of several problems (uneven grids) with one launch per phase."""
+    """stab_jv_batch_*: J v and block-Jacobi apply of several problems (uneven grids), one launch per phase."""
 
     def __init__(self, handles, stream=None):
         import torch
@@ -404,6 +405,18 @@ class JvBatch:
         if st != 0:
             raise StabError(st, self._L.stab_jv_batch_last_error(self._b).decode())
         return outs
+
+    def precond_apply(self, qs, zs):
+        """zs[i] = M_i^-1 qs[i] with each handle's block-Jacobi inverses (built by precond_build)."""
+        count = len(self.handles)
+        if len(qs) != count or len(zs) != count:
+            raise ValueError("one input and one output vector per handle")
+        q = (ctypes.c_void_p * count)(*[_ptr(x) for x in qs])
+        z = (ctypes.c_void_p * count)(*[_ptr(x) for x in zs])
+        st = self._L.stab_jv_batch_precond_apply(self._b, q, z)
+        if st != 0:
+            raise StabError(st, self._L.stab_jv_batch_last_error(self._b).decode())
+        return zs
 
     def close(self):
         if getattr(self, "_b", None) is not None and self._b.value:

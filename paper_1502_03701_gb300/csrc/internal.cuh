@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <cstring>
 #include <string>
 #include <vector>
 
@@ -201,3 +202,55 @@ cudaError_t pc_build(StabHandle* h, double2 sigma);
 cudaError_t pc_apply(StabHandle* h, const double2* q, double2* z, const float2* q32 = nullptr);
 cudaError_t pc_block(StabHandle* h, double2 sigma, long long t, double2* d_out);
 
+
+// ---------------------------------------------------------------------------
+// Batches of handles (stab_jv_batch_*): per-call parameter images of the
+// batched kernels.  An image holds, per launch, the instances' items followed
+// by the block offsets start[0..count] (item i owns blocks [start[i],
+// start[i+1])), each section 16-byte aligned; batch_stage copies it to the
+// batch's device buffer through a pinned staging buffer.
+// ---------------------------------------------------------------------------
+struct stab_jv_batch_s {
+  std::vector<StabHandle*> hs;
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  void* d_buf = nullptr;
+  size_t d_cap = 0;
+  void* h_buf = nullptr;  // pinned
+  size_t h_cap = 0;
+  cudaEvent_t copied = nullptr;  // the last transfer out of h_buf has completed
+  std::string err;
+};
+
+struct BatchSection {
+  size_t items = 0, start = 0;  // byte offsets in the image
+  int count = 0, blocks = 0, threads = 0;
+  size_t smem = 0;
+};
+
+struct BatchImage {
+  std::vector<unsigned char> bytes;
+  size_t put(const void* p, size_t n) {
+    const size_t off = (bytes.size() + 15) & ~(size_t)15;
+    bytes.resize(off + n);
+    if (n) std::memcpy(bytes.data() + off, p, n);
+    return off;
+  }
+  template <class T>
+  BatchSection section(const std::vector<T>& items, const std::vector<int>& blocks, int threads, size_t smem) {
+    BatchSection s;
+    s.count = (int)items.size();
+    if (!s.count) return s;
+    std::vector<int> start(items.size() + 1, 0);
+    for (size_t i = 0; i < items.size(); ++i) start[i + 1] = start[i] + blocks[i];
+    s.items = put(items.data(), items.size() * sizeof(T));
+    s.start = put(start.data(), start.size() * sizeof(int));
+    s.blocks = start.back();
+    s.threads = threads;
+    s.smem = smem;
+    return s;
+  }
+};
+
+cudaError_t batch_stage(stab_jv_batch_s* B, const BatchImage& im);
+cudaError_t pc_apply_batch(stab_jv_batch_s* B, const double2* const* q, double2* const* z);

@@ -1763,52 +1763,30 @@ cudaError_t launch_norm2_stream(cudaStream_t st, const double2* v, long long n, 
 // (from a pinned staging buffer guarded by an event), and each phase is one
 // launch per kernel variant for all instances.
 // ---------------------------------------------------------------------------
-struct stab_jv_batch_s {
-  std::vector<StabHandle*> hs;
-  int device = 0;
-  cudaStream_t stream = nullptr;
-  void* d_buf = nullptr;
-  size_t d_cap = 0;
-  void* h_buf = nullptr;  // pinned
-  size_t h_cap = 0;
-  cudaEvent_t copied = nullptr;  // the last transfer out of h_buf has completed
-  std::string err;
-};
-
-namespace {
-
-struct Section {
-  size_t items = 0, start = 0;  // byte offsets in the image
-  int count = 0, blocks = 0, threads = 0;
-  size_t smem = 0;
-};
-
-// image builder: items of one type followed by their block offsets
-struct Image {
-  std::vector<unsigned char> bytes;
-  size_t put(const void* p, size_t n) {
-    size_t off = (bytes.size() + 15) & ~(size_t)15;
-    bytes.resize(off + n);
-    std::memcpy(bytes.data() + off, p, n);
-    return off;
+// Copy a parameter image to the batch's device buffer: through the pinned
+// staging buffer, once the previous transfer out of it has completed.
+cudaError_t batch_stage(stab_jv_batch_s* B, const BatchImage& im) {
+  const size_t bytes = im.bytes.size();
+  cudaError_t e;
+  if ((e = cudaEventSynchronize(B->copied)) != cudaSuccess) return e;
+  if (bytes > B->h_cap) {
+    if (B->h_buf) cudaFreeHost(B->h_buf);
+    B->h_buf = nullptr;
+    B->h_cap = 0;
+    if ((e = cudaHostAlloc(&B->h_buf, bytes, cudaHostAllocDefault)) != cudaSuccess) return e;
+    B->h_cap = bytes;
   }
-  template <class T>
-  Section section(const std::vector<T>& items, const std::vector<int>& blocks, int threads, size_t smem) {
-    Section s;
-    s.count = (int)items.size();
-    if (!s.count) return s;
-    std::vector<int> start(items.size() + 1, 0);
-    for (size_t i = 0; i < items.size(); ++i) start[i + 1] = start[i] + blocks[i];
-    s.items = put(items.data(), items.size() * sizeof(T));
-    s.start = put(start.data(), start.size() * sizeof(int));
-    s.blocks = start.back();
-    s.threads = threads;
-    s.smem = smem;
-    return s;
+  if (bytes > B->d_cap) {
+    if (B->d_buf) cudaFreeAsync(B->d_buf, B->stream);
+    B->d_buf = nullptr;
+    B->d_cap = 0;
+    if ((e = dev_alloc_stream(B->device, B->stream, &B->d_buf, bytes)) != cudaSuccess) return e;
+    B->d_cap = bytes;
   }
-};
-
-}  // namespace
+  std::memcpy(B->h_buf, im.bytes.data(), bytes);
+  if ((e = cudaMemcpyAsync(B->d_buf, B->h_buf, bytes, cudaMemcpyHostToDevice, B->stream)) != cudaSuccess) return e;
+  return cudaEventRecord(B->copied, B->stream);
+}
 
 static cudaError_t jv_batch_attributes() {
   const void* ks[4] = {(const void*)k_line_pass_batch<false>, (const void*)k_line_pass_batch<true>,
@@ -1822,7 +1800,7 @@ static cudaError_t jv_batch_attributes() {
 
 static cudaError_t jv_batch_apply(stab_jv_batch_s* B, const double2* const* v, double2* const* out, const double* shifts) {
   const int count = (int)B->hs.size();
-  Image im;
+  BatchImage im;
   // 1. epsilon: one norm item per epsilon-quotient instance
   std::vector<NormItem> norms;
   std::vector<int> norm_blocks;
@@ -1861,11 +1839,11 @@ static cudaError_t jv_batch_apply(stab_jv_batch_s* B, const double2* const* v, d
     points[h->dim - 2].push_back(PointItem{P, h->d_coef_p, h->d_btab_f});
     point_blocks[h->dim - 2].push_back(grid_for(h->npts, 128));
   }
-  const Section s_norm = im.section(norms, norm_blocks, 256, 0);
-  const Section s_temp = im.section(temps, temp_blocks, 128, 0);
+  const BatchSection s_norm = im.section(norms, norm_blocks, 256, 0);
+  const BatchSection s_temp = im.section(temps, temp_blocks, 128, 0);
   // 3. line passes y, z, x; per axis one section per kernel variant (main /
   // compact, FP64 / pair right-hand sides)
-  Section s_line[3][4];
+  BatchSection s_line[3][4];
   static const int order[3] = {1, 2, 0};
   for (int q = 0; q < 3; ++q) {
     const int ax = order[q];
@@ -1903,33 +1881,14 @@ static cudaError_t jv_batch_apply(stab_jv_batch_s* B, const double2* const* v, d
     }
     for (int k = 0; k < 4; ++k) s_line[q][k] = im.section(items[k], blocks[k], threads[k], smem[k]);
   }
-  Section s_point[2];
+  BatchSection s_point[2];
   for (int d = 0; d < 2; ++d) s_point[d] = im.section(points[d], point_blocks[d], 128, 0);
 
-  // transfer: staging buffer (after the previous transfer out of it), device buffer
-  const size_t bytes = im.bytes.size();
   cudaError_t e;
-  if ((e = cudaEventSynchronize(B->copied)) != cudaSuccess) return e;
-  if (bytes > B->h_cap) {
-    if (B->h_buf) cudaFreeHost(B->h_buf);
-    B->h_buf = nullptr;
-    B->h_cap = 0;
-    if ((e = cudaHostAlloc(&B->h_buf, bytes, cudaHostAllocDefault)) != cudaSuccess) return e;
-    B->h_cap = bytes;
-  }
-  if (bytes > B->d_cap) {
-    if (B->d_buf) cudaFreeAsync(B->d_buf, B->stream);
-    B->d_buf = nullptr;
-    B->d_cap = 0;
-    if ((e = dev_alloc_stream(B->device, B->stream, &B->d_buf, bytes)) != cudaSuccess) return e;
-    B->d_cap = bytes;
-  }
-  std::memcpy(B->h_buf, im.bytes.data(), bytes);
-  if ((e = cudaMemcpyAsync(B->d_buf, B->h_buf, bytes, cudaMemcpyHostToDevice, B->stream)) != cudaSuccess) return e;
-  if ((e = cudaEventRecord(B->copied, B->stream)) != cudaSuccess) return e;
+  if ((e = batch_stage(B, im)) != cudaSuccess) return e;
   const unsigned char* d = (const unsigned char*)B->d_buf;
-  auto items_of = [&](const Section& s) { return (const void*)(d + s.items); };
-  auto start_of = [&](const Section& s) { return (const int*)(d + s.start); };
+  auto items_of = [&](const BatchSection& s) { return (const void*)(d + s.items); };
+  auto start_of = [&](const BatchSection& s) { return (const int*)(d + s.start); };
 
   // exact tangent: epsilon is zero
   for (StabHandle* h : B->hs)
@@ -1942,7 +1901,7 @@ static cudaError_t jv_batch_apply(stab_jv_batch_s* B, const double2* const* v, d
                                                             s_temp.count);
   for (int q = 0; q < 3; ++q)
     for (int k = 0; k < 4; ++k) {
-      const Section& s = s_line[q][k];
+      const BatchSection& s = s_line[q][k];
       if (!s.count) continue;
       const PassParams* it = (const PassParams*)items_of(s);
       if (k == 0) k_line_pass_batch<false><<<s.blocks, s.threads, s.smem, st>>>(it, start_of(s), s.count);

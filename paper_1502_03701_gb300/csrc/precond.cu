@@ -266,15 +266,14 @@ __device__ __forceinline__ void load_c<__nv_bfloat162, float>(const __nv_bfloat1
   y = v.y;
 }
 
+// one CTA: row slice `slice` of `nslices` of tile `tile`
 template <class S, class R, bool Q32>
-__global__ void k_apply_cols(const ApplyParams P) {
-  if (P.gate && *P.gate) return;
+__device__ __forceinline__ void apply_cols_body(const ApplyParams& P, long long tile, unsigned slice, unsigned nslices) {
   extern __shared__ unsigned char smraw[];
   C2<R>* qs = (C2<R>*)smraw;
-  const long long tile = blockIdx.x;
   const int b = P.bsz;
-  const int rb0 = (int)((long long)b * blockIdx.y / gridDim.y);
-  const int rb1 = (int)((long long)b * (blockIdx.y + 1) / gridDim.y);
+  const int rb0 = (int)((long long)b * slice / nslices);
+  const int rb1 = (int)((long long)b * (slice + 1) / nslices);
   const S* Mt = (const S*)P.inv + (long long)tile * b * b;
   for (int r = threadIdx.x; r < b; r += blockDim.x) {
     const long long d = tile_dof(P, tile, r);
@@ -302,18 +301,22 @@ __global__ void k_apply_cols(const ApplyParams P) {
   }
 }
 
+template <class S, class R, bool Q32>
+__global__ void k_apply_cols(const ApplyParams P) {
+  if (P.gate && *P.gate) return;
+  apply_cols_body<S, R, Q32>(P, blockIdx.x, blockIdx.y, gridDim.y);
+}
+
 // The same product for blocks of a multiple of four rows: each thread forms
 // four consecutive rows from one 16-byte load per column (four BF16 complex
 // entries), so a warp moves 512 bytes per load instruction.
 template <bool Q32>
-__global__ void k_apply_cols4(const ApplyParams P) {
-  if (P.gate && *P.gate) return;
+__device__ __forceinline__ void apply_cols4_body(const ApplyParams& P, long long tile, unsigned slice, unsigned nslices) {
   extern __shared__ unsigned char smraw[];
   float2* qs = (float2*)smraw;
-  const long long tile = blockIdx.x;
   const int b = P.bsz, b4 = P.bsz >> 2;
-  const int q0 = (int)((long long)b4 * blockIdx.y / gridDim.y);
-  const int q1 = (int)((long long)b4 * (blockIdx.y + 1) / gridDim.y);
+  const int q0 = (int)((long long)b4 * slice / nslices);
+  const int q1 = (int)((long long)b4 * (slice + 1) / nslices);
   const uint4* Mt = (const uint4*)((const __nv_bfloat162*)P.inv + (long long)tile * b * b);
   for (int r = threadIdx.x; r < b; r += blockDim.x) {
     const long long d = tile_dof(P, tile, r);
@@ -347,17 +350,21 @@ __global__ void k_apply_cols4(const ApplyParams P) {
   }
 }
 
+template <bool Q32>
+__global__ void k_apply_cols4(const ApplyParams P) {
+  if (P.gate && *P.gate) return;
+  apply_cols4_body<Q32>(P, blockIdx.x, blockIdx.y, gridDim.y);
+}
+
 // z_tile = Minv_tile q_tile with the inverse stored row-major (FP64 or FP32):
 // one warp per row at a time, FP32 rows of even length read two entries per
 // 16-byte load; grid (tiles, row slices) as above.
 template <class R, bool Q32>
-__global__ void k_apply_rows(const ApplyParams P) {
-  if (P.gate && *P.gate) return;
+__device__ __forceinline__ void apply_rows_body(const ApplyParams& P, long long tile, unsigned slice, unsigned nslices) {
   extern __shared__ unsigned char smraw[];
   C2<R>* qs = (C2<R>*)smraw;
-  const long long tile = blockIdx.x;
-  const int rb0 = (int)((long long)P.bsz * blockIdx.y / gridDim.y);
-  const int rb1 = (int)((long long)P.bsz * (blockIdx.y + 1) / gridDim.y);
+  const int rb0 = (int)((long long)P.bsz * slice / nslices);
+  const int rb1 = (int)((long long)P.bsz * (slice + 1) / nslices);
   const C2<R>* M = (const C2<R>*)P.inv + (long long)tile * P.bsz * P.bsz;
   for (int r = threadIdx.x; r < P.bsz; r += blockDim.x) {
     const long long d = tile_dof(P, tile, r);
@@ -398,6 +405,12 @@ __global__ void k_apply_rows(const ApplyParams P) {
   }
 }
 
+template <class R, bool Q32>
+__global__ void k_apply_rows(const ApplyParams P) {
+  if (P.gate && *P.gate) return;
+  apply_rows_body<R, Q32>(P, blockIdx.x, blockIdx.y, gridDim.y);
+}
+
 // FP32 row-major blocks -> BF16 column-major blocks
 __global__ void k_to_bf16_t(const float2* in, __nv_bfloat162* out, int b) {
   const float2* M = in + (long long)blockIdx.x * b * b;
@@ -406,6 +419,39 @@ __global__ void k_to_bf16_t(const float2* in, __nv_bfloat162* out, int b) {
     const int c = (int)(idx / b), r = (int)(idx - (long long)c * b);  // write O[c][r] (coalesced)
     O[idx] = __float22bfloat162_rn(M[(long long)r * b + c]);
   }
+}
+
+// Batched apply over several handles (stab_jv_batch_precond_apply): item i
+// owns the flat blocks [start[i], start[i+1]) = its (tile, row slice) grid
+// with the tile fastest; V selects the storage layout (0 FP64 rows, 1 FP32
+// rows, 2 BF16 four rows per thread, 3 BF16 one row per thread).
+struct ApplyItem {
+  ApplyParams P;
+  long long ntiles;
+};
+static_assert(sizeof(ApplyItem) % 8 == 0, "items are copied to shared memory in 8-byte words");
+
+template <int V>
+__global__ void k_apply_batch(const ApplyItem* __restrict__ items, const int* __restrict__ start, int count) {
+  __shared__ ApplyItem sI;
+  int lo = 0, hi = count - 1;  // largest i with start[i] <= blockIdx.x
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if ((unsigned)__ldg(start + mid) <= blockIdx.x) lo = mid;
+    else hi = mid - 1;
+  }
+  const unsigned long long* src = (const unsigned long long*)(items + lo);
+  for (int k = threadIdx.x; k < (int)(sizeof(ApplyItem) / 8); k += blockDim.x) ((unsigned long long*)&sI)[k] = __ldg(src + k);
+  __syncthreads();
+  const long long local = (long long)blockIdx.x - __ldg(start + lo);
+  const long long nt = sI.ntiles;
+  const unsigned nslices = (unsigned)((__ldg(start + lo + 1) - __ldg(start + lo)) / nt);
+  const long long tile = local % nt;
+  const unsigned slice = (unsigned)(local / nt);
+  if (V == 0) apply_rows_body<double, false>(sI.P, tile, slice, nslices);
+  else if (V == 1) apply_rows_body<float, false>(sI.P, tile, slice, nslices);
+  else if (V == 2) apply_cols4_body<false>(sI.P, tile, slice, nslices);
+  else apply_cols_body<__nv_bfloat162, float, false>(sI.P, tile, slice, nslices);
 }
 
 struct Geo {
@@ -624,5 +670,95 @@ extern "C" stab_status stab_precond_block(stab_handle hh, double sr, double si, 
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   dfree(h, d);
   if (e != cudaSuccess) { h->err = std::string("stab_precond_block: ") + cudaGetErrorString(e); return STAB_ERR_CUDA; }
+  return STAB_OK;
+}
+
+// Batched block apply: one launch per storage layout for all handles of B.
+cudaError_t pc_apply_batch(stab_jv_batch_s* B, const double2* const* q, double2* const* z) {
+  const int count = (int)B->hs.size();
+  std::vector<ApplyItem> items[4];
+  std::vector<int> blocks[4];
+  int threads[4] = {0, 0, 0, 0};
+  size_t smem[4] = {0, 0, 0, 0};
+  for (int i = 0; i < count; ++i) {
+    StabHandle* h = B->hs[i];
+    if (!h->pvalid) return cudaErrorInvalidValue;
+    Geo g;
+    tile_geo(h, g);
+    ApplyItem it{};
+    ApplyParams& P = it.P;
+    P.q = q[i]; P.z = z[i]; P.inv = h->d_pinv; P.q32 = nullptr;
+    P.nx = h->nx; P.ny = h->ny; P.tx = g.tx; P.ty = g.ty; P.tz = g.tz; P.ntx = g.ntx; P.nty = g.nty;
+    P.ntpts = g.ntpts; P.bsz = g.bsz; P.npts = h->npts;
+    P.gate = nullptr;
+    it.ntiles = g.ntiles;
+    // the same slices and threads as the single-handle apply
+    int slices = (int)((2 * 152 + g.ntiles - 1) / g.ntiles);
+    slices = std::max(1, std::min(slices, g.bsz / 32));
+    int var, thr;
+    size_t sm;
+    if (h->pprec == 64) { var = 0; thr = 256; sm = g.bsz * sizeof(double2); }
+    else if (h->pprec == 32) { var = 1; thr = 256; sm = g.bsz * sizeof(float2); }
+    else if (g.bsz % 4 == 0) {
+      var = 2;
+      const int quads = (g.bsz / 4 + slices - 1) / slices;
+      thr = std::min(256, ((quads + 31) / 32) * 32);
+      sm = g.bsz * sizeof(float2);
+    } else {
+      var = 3;
+      const int rows = (g.bsz + slices - 1) / slices;
+      thr = std::min(256, ((rows + 31) / 32) * 32);
+      sm = g.bsz * sizeof(float2);
+    }
+    if (g.ntiles * slices > (1LL << 30)) return cudaErrorInvalidValue;
+    items[var].push_back(it);
+    blocks[var].push_back((int)(g.ntiles * slices));
+    threads[var] = std::max(threads[var], thr);
+    smem[var] = std::max(smem[var], sm);
+  }
+  BatchImage im;
+  BatchSection sec[4];
+  for (int v = 0; v < 4; ++v) sec[v] = im.section(items[v], blocks[v], threads[v], smem[v]);
+  cudaError_t e = batch_stage(B, im);
+  if (e != cudaSuccess) return e;
+  const unsigned char* d = (const unsigned char*)B->d_buf;
+  for (int v = 0; v < 4; ++v) {
+    const BatchSection& S = sec[v];
+    if (!S.count) continue;
+    const ApplyItem* it = (const ApplyItem*)(d + S.items);
+    const int* st = (const int*)(d + S.start);
+    if (v == 0) k_apply_batch<0><<<S.blocks, S.threads, S.smem, B->stream>>>(it, st, S.count);
+    else if (v == 1) k_apply_batch<1><<<S.blocks, S.threads, S.smem, B->stream>>>(it, st, S.count);
+    else if (v == 2) k_apply_batch<2><<<S.blocks, S.threads, S.smem, B->stream>>>(it, st, S.count);
+    else k_apply_batch<3><<<S.blocks, S.threads, S.smem, B->stream>>>(it, st, S.count);
+  }
+  return cudaGetLastError();
+}
+
+extern "C" stab_status stab_jv_batch_precond_apply(stab_jv_batch B, const void* const* q, void* const* z) {
+  if (!B) return STAB_ERR_INVALID_ARG;
+  if (!q || !z) {
+    B->err = "stab_jv_batch_precond_apply: null vector list";
+    return STAB_ERR_INVALID_ARG;
+  }
+  const int count = (int)B->hs.size();
+  for (int i = 0; i < count; ++i) {
+    const char* a = (const char*)q[i];
+    const char* b = (const char*)z[i];
+    const long long bytes = B->hs[i]->n * (long long)sizeof(double2);
+    if (!a || !b || (a < b + bytes && b < a + bytes)) {
+      B->err = "stab_jv_batch_precond_apply: null or overlapping q / z of instance " + std::to_string(i);
+      return STAB_ERR_INVALID_ARG;
+    }
+    if (!B->hs[i]->pvalid) {
+      B->err = "stab_jv_batch_precond_apply: no preconditioner built for instance " + std::to_string(i);
+      return STAB_ERR_INVALID_ARG;
+    }
+  }
+  const cudaError_t e = pc_apply_batch(B, (const double2* const*)q, (double2* const*)z);
+  if (e != cudaSuccess) {
+    B->err = std::string("stab_jv_batch_precond_apply: ") + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? STAB_ERR_OOM : STAB_ERR_CUDA;
+  }
   return STAB_OK;
 }
