@@ -144,7 +144,8 @@ stab_status stab_apply_J(stab_handle h, const void* v, void* Jv, double shift_re
  *           on other streams.
  * A batch is used by one host thread at a time; its messages are in
  * stab_jv_batch_last_error.  destroy waits for the batch's last parameter
- * transfer (not for its kernels) and releases its buffers in stream order. */
+ * transfer (not for its kernels) and releases its buffers in stream order;
+ * destroy a batch before any of its handles. */
 typedef struct stab_jv_batch_s* stab_jv_batch;
 stab_status stab_jv_batch_create(stab_jv_batch* b, const stab_handle* handles, int count, void* cuda_stream);
 stab_status stab_jv_batch_apply(stab_jv_batch b, const void* const* v, void* const* Jv, const double* shifts);

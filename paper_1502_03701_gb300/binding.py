@@ -388,8 +388,13 @@ class JvBatch:
             raise StabError(st, "stab_jv_batch_create: handles must be distinct, on this device, with y-only base flows")
         self._b = b
 
+    def _check_open(self):
+        if getattr(self, "_b", None) is None or any(getattr(h, "_h", None) is None for h in self.handles):
+            raise StabError(1, "JvBatch: the batch or one of its handles is closed")
+
     def apply(self, vs, outs, shifts=None):
         """outs[i] = J_i vs[i] - shifts[i] vs[i] (complex128 device tensors)."""
+        self._check_open()
         count = len(self.handles)
         if len(vs) != count or len(outs) != count:
             raise ValueError("one input and one output vector per handle")
@@ -408,6 +413,7 @@ class JvBatch:
 
     def precond_apply(self, qs, zs):
         """zs[i] = M_i^-1 qs[i] with each handle's block-Jacobi inverses (built by precond_build)."""
+        self._check_open()
         count = len(self.handles)
         if len(qs) != count or len(zs) != count:
             raise ValueError("one input and one output vector per handle")
