@@ -156,6 +156,16 @@ stab_status stab_jv_batch_apply(stab_jv_batch b, const void* const* v, void* con
  * of handle i's size, not overlapping.  INVALID_ARG when a handle has no
  * preconditioner built. */
 stab_status stab_jv_batch_precond_apply(stab_jv_batch b, const void* const* q, void* const* z);
+/* CGS2 (as stab_orthogonalize) of w[i] against the k[i] orthonormal columns
+ * of V[i] for every handle of the batch: one launch per step for all
+ * instances; each result equals its handle's own stab_orthogonalize bit for
+ * bit.  V[i]: device complex128 n_i x k[i]; w[i]: device complex128 n_i,
+ * updated in place; 1 <= k[i] <= 1536.  hcoef (host, may be NULL): the
+ * coefficients of all instances one after the other (k[0] complex, then
+ * k[1], ...); norms (host, may be NULL): ||w[i]|| after.  Uses each handle's
+ * orthogonalisation scratch; synchronises the batch's stream. */
+stab_status stab_jv_batch_orthogonalize(stab_jv_batch b, const void* const* V, const int* k, void* const* w,
+                                        double* hcoef, double* norms);
 const char* stab_jv_batch_last_error(stab_jv_batch b);
 void stab_jv_batch_destroy(stab_jv_batch b);
 

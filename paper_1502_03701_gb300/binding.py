@@ -27,7 +27,8 @@ SYMBOLS = ["stab_default_opts", "stab_create", "stab_destroy", "stab_last_error"
            "stab_set_line_config", "stab_trim_memory", "stab_estimate_bytes", "stab_eigs_batch",
            "stab_server_create", "stab_server_submit", "stab_server_wait", "stab_server_result",
            "stab_server_stats", "stab_server_destroy", "stab_jv_batch_create", "stab_jv_batch_apply",
-           "stab_jv_batch_last_error", "stab_jv_batch_destroy", "stab_jv_batch_precond_apply"]
+           "stab_jv_batch_last_error", "stab_jv_batch_destroy", "stab_jv_batch_precond_apply",
+           "stab_jv_batch_orthogonalize"]
 
 # stab_phase, in enum order
 PHASES = ["eps", "temperature", "line_y", "line_z", "line_x", "pointwise", "cgs2", "precond_apply"]
@@ -138,6 +139,7 @@ def load():
     L.stab_jv_batch_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(vp), i, vp]
     L.stab_jv_batch_apply.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), dp]
     L.stab_jv_batch_precond_apply.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp)]
+    L.stab_jv_batch_orthogonalize.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(i), ctypes.POINTER(vp), dp, dp]
     L.stab_jv_batch_last_error.argtypes = [vp]
     L.stab_jv_batch_last_error.restype = ctypes.c_char_p
     L.stab_jv_batch_destroy.argtypes = [vp]
@@ -423,6 +425,29 @@ class JvBatch:
         if st != 0:
             raise StabError(st, self._L.stab_jv_batch_last_error(self._b).decode())
         return zs
+
+    def orthogonalize(self, Vs, ks, ws):
+        """CGS2 of ws[i] (updated in place) against the ks[i] columns of Vs[i]; returns
+        ([h_i complex coefficients], [||w_i|| after])."""
+        self._check_open()
+        count = len(self.handles)
+        if len(Vs) != count or len(ks) != count or len(ws) != count:
+            raise ValueError("one basis, column count and vector per handle")
+        V = (ctypes.c_void_p * count)(*[_ptr(x) for x in Vs])
+        K = (ctypes.c_int * count)(*[int(x) for x in ks])
+        W = (ctypes.c_void_p * count)(*[_ptr(x) for x in ws])
+        hc = np.zeros(2 * sum(int(x) for x in ks))
+        nr = np.zeros(count)
+        st = self._L.stab_jv_batch_orthogonalize(self._b, V, K, W, hc.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                                 nr.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+        if st != 0:
+            raise StabError(st, self._L.stab_jv_batch_last_error(self._b).decode())
+        hz = hc.view(np.complex128)
+        out, off = [], 0
+        for x in ks:
+            out.append(hz[off:off + int(x)].copy())
+            off += int(x)
+        return out, list(nr)
 
     def close(self):
         if getattr(self, "_b", None) is not None and self._b.value:

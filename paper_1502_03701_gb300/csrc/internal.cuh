@@ -253,4 +253,14 @@ struct BatchImage {
 };
 
 cudaError_t batch_stage(stab_jv_batch_s* B, const BatchImage& im);
+struct CgsJob {  // one instance of a batched CGS2 (scratch as for kry_cgs2)
+  const double2* V;
+  int k;
+  long long n;
+  double2* w;
+  double2* d_h;
+  double* d_norm;
+  double2* partial;
+};
+cudaError_t kry_cgs2_batch(stab_jv_batch_s* B, const std::vector<CgsJob>& jobs);
 cudaError_t pc_apply_batch(stab_jv_batch_s* B, const double2* const* q, double2* const* z);

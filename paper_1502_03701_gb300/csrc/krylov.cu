@@ -211,12 +211,13 @@ __device__ __forceinline__ double2 col_dot(const float2* x, const float2* w, lon
 
 template <class T>
 __device__ __forceinline__ void block_dot_columns(const T* __restrict__ V, int k, long long n, long long r0,
-                                                  long long r1, const T* w, double2* partial_out, double2* red) {
+                                                  long long r1, const T* w, double2* partial_out, double2* red,
+                                                  unsigned bidx) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   if (k >= nw) {
     for (int j = wid; j < k; j += nw) {
       const double2 d = col_dot(V + (long long)j * n, w, r0, r1, j);
-      if (lane == 0) partial_out[(long long)blockIdx.x * k + j] = d;
+      if (lane == 0) partial_out[(long long)bidx * k + j] = d;
     }
     return;
   }
@@ -236,7 +237,7 @@ __device__ __forceinline__ void block_dot_columns(const T* __restrict__ V, int k
       sr += red[j * G + q].x;
       si += red[j * G + q].y;
     }
-    partial_out[(long long)blockIdx.x * k + j] = make_double2(sr, si);
+    partial_out[(long long)bidx * k + j] = make_double2(sr, si);
   }
   __syncthreads();
 }
@@ -265,66 +266,66 @@ __device__ __forceinline__ double2 row_update(const double2* __restrict__ V, int
   return make_double2(wv.x - (ff_to_d(ar) + dr), wv.y - (ff_to_d(ai) + di));
 }
 
-__device__ __forceinline__ void block_rows(long long n, long long& r0, long long& r1) {
-  const long long rows = (n + gridDim.x - 1) / gridDim.x;
-  r0 = (long long)blockIdx.x * rows;
+// rows [r0, r1) of block bidx of nb (equal contiguous ranges)
+__device__ __forceinline__ void block_rows(long long n, long long& r0, long long& r1, unsigned bidx, unsigned nb) {
+  const long long rows = (n + nb - 1) / nb;
+  r0 = (long long)bidx * rows;
   r1 = r0 + rows < n ? r0 + rows : n;
 }
 
-__global__ void __launch_bounds__(kThreads) k_cgs2_a(const double2* __restrict__ V, int k, long long n,
-                                                    const double2* __restrict__ w, double2* partial1,
-                                                    const int* gate) {
-  if (gate && *gate) return;
+// The three CGS2 steps and the final norm for block bidx of nb (one
+// instance's launch, or one item of a batched launch).
+__device__ __forceinline__ void cgs2_a_body(const double2* __restrict__ V, int k, long long n,
+                                            const double2* __restrict__ w, double2* partial1, unsigned bidx,
+                                            unsigned nb) {
   __shared__ double2 red[kThreads / 32];
   long long r0, r1;
-  block_rows(n, r0, r1);
-  block_dot_columns(V, k, n, r0, r1, w, partial1, red);
+  block_rows(n, r0, r1, bidx, nb);
+  block_dot_columns(V, k, n, r0, r1, w, partial1, red, bidx);
 }
 
-__global__ void __launch_bounds__(kThreads) k_cgs2_b(const double2* __restrict__ V, int k, long long n, double2* w,
-                                                    const double2* partial1, double2* partial2, double2* d_h,
-                                                    const int* gate) {
-  if (gate && *gate) return;
+__device__ __forceinline__ void cgs2_b_body(const double2* __restrict__ V, int k, long long n, double2* w,
+                                            const double2* partial1, double2* partial2, double2* d_h, unsigned bidx,
+                                            unsigned nb) {
   extern __shared__ double2 hs[];  // k complex, then 2k pairs
   __shared__ double2 red[kThreads / 32];
   ffn* hre = (ffn*)(hs + k);
   ffn* him = hre + k;
-  reduce_partials(partial1, gridDim.x, k, hs);
+  reduce_partials(partial1, nb, k, hs);
   __syncthreads();
   for (int j = threadIdx.x; j < k; j += blockDim.x) {
     hre[j] = ff_split(hs[j].x);
     him[j] = ff_split(hs[j].y);
-    if (blockIdx.x == 0) d_h[j] = hs[j];
+    if (bidx == 0) d_h[j] = hs[j];
   }
   __syncthreads();
   long long r0, r1;
-  block_rows(n, r0, r1);
+  block_rows(n, r0, r1, bidx, nb);
   for (long long i = r0 + threadIdx.x; i < r1; i += blockDim.x) w[i] = row_update(V, k, n, i, hs, hre, him, w[i]);
   __syncthreads();  // this block's rows of w are final; the dots below read only them
-  block_dot_columns(V, k, n, r0, r1, w, partial2, red);
+  block_dot_columns(V, k, n, r0, r1, w, partial2, red, bidx);
 }
 
-__global__ void __launch_bounds__(kThreads) k_cgs2_c(const double2* __restrict__ V, int k, long long n, double2* w,
-                                                    const double2* partial2, double2* d_h, double* norm_partial,
-                                                    const int* gate) {
-  if (gate && *gate) return;
+__device__ __forceinline__ void cgs2_c_body(const double2* __restrict__ V, int k, long long n, double2* w,
+                                            const double2* partial2, double2* d_h, double* norm_partial,
+                                            unsigned bidx, unsigned nb) {
   extern __shared__ double2 hs[];  // k complex, then 2k pairs
   __shared__ double red[kThreads / 32];
   ffn* hre = (ffn*)(hs + k);
   ffn* him = hre + k;
-  reduce_partials(partial2, gridDim.x, k, hs);
+  reduce_partials(partial2, nb, k, hs);
   __syncthreads();
   for (int j = threadIdx.x; j < k; j += blockDim.x) {
     hre[j] = ff_split(hs[j].x);
     him[j] = ff_split(hs[j].y);
-    if (blockIdx.x == 0) {
+    if (bidx == 0) {
       double2 h1 = d_h[j];
       d_h[j] = make_double2(h1.x + hs[j].x, h1.y + hs[j].y);
     }
   }
   __syncthreads();
   long long r0, r1;
-  block_rows(n, r0, r1);
+  block_rows(n, r0, r1, bidx, nb);
   double s = 0.0;
   for (long long i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
     const double2 r = row_update(V, k, n, i, hs, hre, him, w[i]);
@@ -338,16 +339,97 @@ __global__ void __launch_bounds__(kThreads) k_cgs2_c(const double2* __restrict__
   if (wid == 0) {
     double t = lane < (int)(blockDim.x >> 5) ? red[lane] : 0.0;
     t = warp_sum(t);
-    if (lane == 0) norm_partial[blockIdx.x] = t;
+    if (lane == 0) norm_partial[bidx] = t;
   }
 }
 
-__global__ void k_norm_final(const double* partial, int nb, double* out, const int* gate) {
-  if (gate && *gate) return;
+__device__ __forceinline__ void norm_final_body(const double* partial, int nb, double* out) {
   double s = 0.0;
   for (int i = threadIdx.x; i < nb; i += 32) s += partial[i];
   s = warp_sum(s);
   if (threadIdx.x == 0) *out = sqrt(s);
+}
+
+__global__ void __launch_bounds__(kThreads) k_cgs2_a(const double2* __restrict__ V, int k, long long n,
+                                                    const double2* __restrict__ w, double2* partial1,
+                                                    const int* gate) {
+  if (gate && *gate) return;
+  cgs2_a_body(V, k, n, w, partial1, blockIdx.x, gridDim.x);
+}
+
+__global__ void __launch_bounds__(kThreads) k_cgs2_b(const double2* __restrict__ V, int k, long long n, double2* w,
+                                                    const double2* partial1, double2* partial2, double2* d_h,
+                                                    const int* gate) {
+  if (gate && *gate) return;
+  cgs2_b_body(V, k, n, w, partial1, partial2, d_h, blockIdx.x, gridDim.x);
+}
+
+__global__ void __launch_bounds__(kThreads) k_cgs2_c(const double2* __restrict__ V, int k, long long n, double2* w,
+                                                    const double2* partial2, double2* d_h, double* norm_partial,
+                                                    const int* gate) {
+  if (gate && *gate) return;
+  cgs2_c_body(V, k, n, w, partial2, d_h, norm_partial, blockIdx.x, gridDim.x);
+}
+
+__global__ void k_norm_final(const double* partial, int nb, double* out, const int* gate) {
+  if (gate && *gate) return;
+  norm_final_body(partial, nb, out);
+}
+
+// Batched CGS2 over several handles (stab_jv_batch_orthogonalize): item i
+// owns the flat blocks [start[i], start[i+1]) (its own block count nb, so its
+// row ranges and reduction order are those of its single launch).
+struct CgsItem {
+  const double2* V;
+  double2* w;
+  double2* p1;
+  double2* p2;
+  double2* d_h;
+  double* np;
+  double* d_norm;
+  long long n;
+  int k, nb;
+};
+static_assert(sizeof(CgsItem) % 8 == 0, "items are read as 8-byte words");
+
+__device__ __forceinline__ int cgs_item(const int* __restrict__ start, int count, unsigned b) {
+  int lo = 0, hi = count - 1;  // largest i with start[i] <= b
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if ((unsigned)__ldg(start + mid) <= b) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+__global__ void __launch_bounds__(kThreads) k_cgs2_a_batch(const CgsItem* __restrict__ items,
+                                                          const int* __restrict__ start, int count) {
+  const int i = cgs_item(start, count, blockIdx.x);
+  const CgsItem it = items[i];
+  cgs2_a_body(it.V, it.k, it.n, it.w, it.p1, blockIdx.x - (unsigned)__ldg(start + i), (unsigned)it.nb);
+}
+
+__global__ void __launch_bounds__(kThreads) k_cgs2_b_batch(const CgsItem* __restrict__ items,
+                                                          const int* __restrict__ start, int count) {
+  const int i = cgs_item(start, count, blockIdx.x);
+  const CgsItem it = items[i];
+  cgs2_b_body(it.V, it.k, it.n, it.w, it.p1, it.p2, it.d_h, blockIdx.x - (unsigned)__ldg(start + i),
+              (unsigned)it.nb);
+}
+
+__global__ void __launch_bounds__(kThreads) k_cgs2_c_batch(const CgsItem* __restrict__ items,
+                                                          const int* __restrict__ start, int count) {
+  const int i = cgs_item(start, count, blockIdx.x);
+  const CgsItem it = items[i];
+  cgs2_c_body(it.V, it.k, it.n, it.w, it.p2, it.d_h, it.np, blockIdx.x - (unsigned)__ldg(start + i),
+              (unsigned)it.nb);
+}
+
+// one 32-thread block per item
+__global__ void k_norm_final_batch(const CgsItem* __restrict__ items, int count) {
+  if ((int)blockIdx.x >= count) return;
+  const CgsItem it = items[blockIdx.x];
+  norm_final_body(it.np, it.nb, it.d_norm);
 }
 
 // ---------------------------------------------------------------------------
@@ -387,8 +469,8 @@ __global__ void __launch_bounds__(kThreads) k_dgks_dots(const T* __restrict__ V,
   __shared__ double2 red[kThreads / 32];
   __shared__ double rn[kThreads / 32];
   long long r0, r1;
-  block_rows(n, r0, r1);
-  block_dot_columns(V, k, n, r0, r1, w, partial, red);
+  block_rows(n, r0, r1, blockIdx.x, gridDim.x);
+  block_dot_columns(V, k, n, r0, r1, w, partial, red, blockIdx.x);
   if (norm_partial) {
     const double t = block_norm_partial(w, r0, r1, rn);
     if (threadIdx.x == 0) norm_partial[blockIdx.x] = t;
@@ -422,7 +504,7 @@ __global__ void __launch_bounds__(kThreads) k_dgks_update(const double2* __restr
   }
   __syncthreads();
   long long r0, r1;
-  block_rows(n, r0, r1);
+  block_rows(n, r0, r1, blockIdx.x, gridDim.x);
   for (long long i = r0 + threadIdx.x; i < r1; i += blockDim.x) w[i] = row_update(V, k, n, i, hs, hre, him, w[i]);
   __syncthreads();
   const double t = block_norm_partial(w, r0, r1, red);
@@ -481,7 +563,7 @@ __global__ void __launch_bounds__(kThreads) k_dgks32_update(const float2* __rest
   }
   __syncthreads();
   long long r0, r1;
-  block_rows(n, r0, r1);
+  block_rows(n, r0, r1, blockIdx.x, gridDim.x);
   for (long long i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
     float ar = 0.f, ai = 0.f;
 #pragma unroll 4
@@ -738,4 +820,46 @@ cudaError_t kry_cgs2_stream(cudaStream_t st, const double2* V, int k, long long 
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   return launch_norm2_stream(st, w, n, norm_partial, norm_blocks, d_norm);
+}
+
+// Batched CGS2: w_i <- (I - V_i V_i^H)^2 w_i for every job, one launch per
+// step for all of them on the batch's stream.  Job i uses the same scratch
+// layout and block count as kry_cgs2 (k >= 1), so its results are those of
+// the single call.
+cudaError_t kry_cgs2_batch(stab_jv_batch_s* B, const std::vector<CgsJob>& jobs) {
+  std::vector<CgsItem> items;
+  std::vector<int> blocks, ones;
+  size_t sm = 0;
+  for (const CgsJob& J : jobs) {
+    if (J.k < 1) return cudaErrorInvalidValue;
+    const int nb = cgs_blocks(J.n);
+    CgsItem it{};
+    it.V = J.V;
+    it.w = J.w;
+    it.p1 = J.partial;
+    it.p2 = J.partial + (size_t)nb * J.k;
+    it.np = (double*)(it.p2 + (size_t)nb * J.k);
+    it.d_h = J.d_h;
+    it.d_norm = J.d_norm;
+    it.n = J.n;
+    it.k = J.k;
+    it.nb = nb;
+    items.push_back(it);
+    blocks.push_back(nb);
+    ones.push_back(1);
+    sm = std::max(sm, (size_t)J.k * (sizeof(double2) + 2 * sizeof(ffn)));
+  }
+  BatchImage im;
+  const BatchSection S = im.section(items, blocks, kThreads, sm);
+  const BatchSection N = im.section(items, ones, 32, 0);
+  cudaError_t e = batch_stage(B, im);
+  if (e != cudaSuccess) return e;
+  const unsigned char* d = (const unsigned char*)B->d_buf;
+  const CgsItem* it = (const CgsItem*)(d + S.items);
+  const int* st = (const int*)(d + S.start);
+  k_cgs2_a_batch<<<S.blocks, kThreads, 0, B->stream>>>(it, st, S.count);
+  k_cgs2_b_batch<<<S.blocks, kThreads, sm, B->stream>>>(it, st, S.count);
+  k_cgs2_c_batch<<<S.blocks, kThreads, sm, B->stream>>>(it, st, S.count);
+  k_norm_final_batch<<<N.count, 32, 0, B->stream>>>((const CgsItem*)(d + N.items), N.count);
+  return cudaGetLastError();
 }

@@ -546,6 +546,54 @@ extern "C" stab_status stab_orthogonalize(stab_handle hh, const void* V, int k, 
   }
 }
 
+extern "C" stab_status stab_jv_batch_orthogonalize(stab_jv_batch B, const void* const* V, const int* k, void* const* w,
+                                                   double* hcoef, double* norms) {
+  if (!B) return STAB_ERR_INVALID_ARG;
+  const int count = (int)B->hs.size();
+  if (!V || !k || !w) {
+    B->err = "stab_jv_batch_orthogonalize: null argument list";
+    return STAB_ERR_INVALID_ARG;
+  }
+  for (int i = 0; i < count; ++i)
+    if (!V[i] || !w[i] || k[i] < 1 || k[i] > 1536) {
+      B->err = "stab_jv_batch_orthogonalize: instance " + std::to_string(i) + " needs V, w and 1 <= k <= 1536";
+      return STAB_ERR_INVALID_ARG;
+    }
+  std::vector<CgsJob> jobs;
+  std::vector<const double2*> dhs;
+  std::vector<const double*> dns;
+  for (int i = 0; i < count; ++i) {
+    StabHandle* h = B->hs[i];
+    try {  // the scratch of stab_orthogonalize, allocated on the handle's stream
+      const long long n = h->n;
+      const size_t part = (size_t)kry_partial_elems(n, k[i]);
+      double2* ws = ensure(h, &h->d_ir, &h->ir_elems, part + 2 * (size_t)k[i] + 2);
+      double2* dh = ws + part;
+      double* dn = (double*)(dh + 2 * k[i]);
+      ck(h, cudaStreamSynchronize(h->stream), "sync");  // the allocation is usable on the batch's stream
+      jobs.push_back(CgsJob{(const double2*)V[i], k[i], n, (double2*)w[i], dh, dn, ws});
+      dhs.push_back(dh);
+      dns.push_back(dn);
+    } catch (Fail& f) {
+      B->err = "stab_jv_batch_orthogonalize: instance " + std::to_string(i) + ": " + h->err;
+      return f.st;
+    }
+  }
+  cudaError_t e = kry_cgs2_batch(B, jobs);
+  size_t off = 0;
+  for (int i = 0; i < count && e == cudaSuccess; ++i) {
+    if (hcoef) e = cudaMemcpyAsync(hcoef + 2 * off, dhs[i], sizeof(double2) * k[i], cudaMemcpyDeviceToHost, B->stream);
+    if (norms && e == cudaSuccess) e = cudaMemcpyAsync(norms + i, dns[i], sizeof(double), cudaMemcpyDeviceToHost, B->stream);
+    off += (size_t)k[i];
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(B->stream);
+  if (e != cudaSuccess) {
+    B->err = std::string("stab_jv_batch_orthogonalize: ") + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? STAB_ERR_OOM : STAB_ERR_CUDA;
+  }
+  return STAB_OK;
+}
+
 extern "C" stab_status stab_eigs(stab_handle hh, double sr, double si, double tr, double ti, int nev, int ncv,
                                  double tol, const void* v0, double* lambda, void* vecs, double* resid, int* nconv,
                                  stab_stats* stats) {

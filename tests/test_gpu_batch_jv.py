@@ -135,3 +135,41 @@ def test_batch_precond_apply_equals_each_handle_bit_for_bit():
     B.close()
     for S in hs:
         S.close()
+
+
+def test_batch_orthogonalize_equals_each_handle_bit_for_bit():
+    """Batched CGS2 over uneven problems and column counts (one column: fewer
+    columns than warps; 40: more) against each handle's stab_orthogonalize."""
+    import torch
+    from paper_1502_03701_gb300 import JvBatch, Stab, StabError
+    specs = [si.mixing_layer_2d(32, 64), (si.Grid(2, 48, 40, 1, si.LX_04, -15, 15), si.Flow(0.3, 500.0)),
+             (si.Grid(3, 12, 16, 8, si.LX_04, -15, 15, si.LX_04), si.Flow(0.5, 800.0)), si.mixing_layer_2d(64, 128)]
+    ks = [1, 5, 11, 40]
+    hs = [Stab(si.tanh_base_flow(g, f), g, f.Ma, f.Re, f.Pr) for g, f in specs]
+    Vs, ws = [], []
+    for i, (S, k) in enumerate(zip(hs, ks)):
+        rng = np.random.default_rng(40 + i)
+        A = rng.standard_normal((S.n, k)) + 1j * rng.standard_normal((S.n, k))
+        Q, _ = np.linalg.qr(A)
+        Vs.append(torch.from_numpy(np.ascontiguousarray(Q.T)).cuda())  # column j at V + j n
+        ws.append(torch.from_numpy(si.random_complex(60 + i, S.n)).cuda())
+    single = []
+    for S, V, k, w in zip(hs, Vs, ks, ws):
+        w1 = w.clone()
+        h1, n1 = S.orthogonalize(V, k, w1)
+        single.append((w1, h1, n1))
+    B = JvBatch(hs)
+    w2 = [w.clone() for w in ws]
+    hcs, nrs = B.orthogonalize(Vs, ks, w2)
+    for i, ((w1, h1, n1), w_b, h_b, n_b) in enumerate(zip(single, w2, hcs, nrs)):
+        assert torch.equal(w1, w_b), i
+        assert np.array_equal(h1, h_b), i
+        assert n1 == n_b, i
+    # the result is an orthogonalisation: w is orthogonal to the columns afterwards
+    for V, k, w in zip(Vs, ks, w2):
+        assert float((V.conj() @ w).abs().max()) < 1e-12 * float(w.abs().max())
+    with pytest.raises(StabError, match="1 <= k"):
+        B.orthogonalize(Vs, [0, 5, 11, 40], w2)
+    B.close()
+    for S in hs:
+        S.close()
