@@ -4,6 +4,8 @@ import ctypes
 import os
 import re
 
+import pytest
+
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
@@ -64,3 +66,25 @@ def test_memory_estimate_grows_with_the_problem():
     fixed = 8 << 20                              # tables and alignment allowance
     assert estimate_bytes(g2, 4, 30, precond=0) - fixed > 3.5 * (base - fixed)
     assert estimate_bytes(g, 4, 30, yonly=False, precond=0) > base
+
+
+def test_batch_binding_checks_arguments_before_calling_the_library():
+    """JvBatch refuses mismatched lists and closed handles on the host (no GPU needed)."""
+    from paper_1502_03701_gb300 import JvBatch, StabError
+
+    class FakeHandle:
+        _h = object()
+
+    B = JvBatch.__new__(JvBatch)
+    B.handles = [FakeHandle(), FakeHandle()]
+    B._b = object()
+    with pytest.raises(ValueError):
+        B.apply([1], [1, 2])
+    with pytest.raises(ValueError):
+        B.precond_apply([1, 2], [1])
+    with pytest.raises(ValueError):
+        B.orthogonalize([1, 2], [3], [1, 2])
+    B.handles[1]._h = None
+    with pytest.raises(StabError, match="closed"):
+        B.apply([1, 2], [1, 2])
+    B._b = None
