@@ -140,11 +140,13 @@ stab_status stab_apply_J(stab_handle h, const void* v, void* Jv, double shift_re
  *   apply:  v[i], Jv[i]: device complex128 vectors of handle i's size, not
  *           overlapping each other; shifts: NULL or 2*count doubles
  *           (re, im of each instance's shift).  Returns when the work is
- *           queued.  While it is in flight, the handles must not be used
- *           on other streams.
+ *           queued.  Every batch call is ordered after the work already
+ *           queued on each handle's own stream, and each handle's stream is
+ *           ordered after the batch call's kernels, so single-handle calls
+ *           before and after a batch call never race with it.
  * A batch is used by one host thread at a time; its messages are in
- * stab_jv_batch_last_error.  destroy waits for the batch's last parameter
- * transfer (not for its kernels) and releases its buffers in stream order;
+ * stab_jv_batch_last_error.  destroy waits for all of the batch's work
+ * (its kernels read the handles' memory) and then releases its buffers;
  * destroy a batch before any of its handles. */
 typedef struct stab_jv_batch_s* stab_jv_batch;
 stab_status stab_jv_batch_create(stab_jv_batch* b, const stab_handle* handles, int count, void* cuda_stream);
@@ -233,7 +235,9 @@ stab_status stab_get_stats(stab_handle h, stab_stats* stats);
  * a message in stab_last_error(NULL).  All calls share the scratch array, so
  * calls whose GPU work overlaps race: serialise them.  The first call on a
  * device looks up the array's device address (with that device current);
- * make that first call before any stream capture. */
+ * make that first call before any stream capture.  The address is kept for
+ * the life of the process, so resetting the device (cudaDeviceReset) after
+ * the first call is not supported. */
 stab_status stab_orthogonalize_noalloc(const void* V, int k, long long n, void* w, double* hcoef, double* norm,
                                        void* stream);
 

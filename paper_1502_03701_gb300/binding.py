@@ -172,12 +172,36 @@ def _ptr(t) -> int:
     return int(t)
 
 
+def _vec_ptr(t, count: int, what: str) -> int:
+    """Device address of a complex128 vector of at least ``count`` entries.
+
+    torch tensors are checked (complex128, CUDA, contiguous, long enough)
+    because the library cannot see their sizes; plain integers are taken as
+    raw device addresses on the caller's responsibility."""
+    if t is None:
+        raise ValueError(f"{what}: missing vector")
+    if hasattr(t, "data_ptr"):
+        import torch
+        if t.dtype != torch.complex128:
+            raise ValueError(f"{what}: expected complex128, got {t.dtype}")
+        if not t.is_cuda:
+            raise ValueError(f"{what}: expected a CUDA tensor")
+        if not t.is_contiguous():
+            raise ValueError(f"{what}: expected a contiguous tensor")
+        if t.numel() < count:
+            raise ValueError(f"{what}: {t.numel()} entries, need {count}")
+        return t.data_ptr()
+    return int(t)
+
+
 def orthogonalize_noalloc(V, k: int, n: int, w, stream=None):
     """CGS2 of w against k columns of V without any device allocation (no handle)."""
     L = load()
     hc = np.zeros(2 * max(k, 1))
     nrm = ctypes.c_double()
-    st = L.stab_orthogonalize_noalloc(_ptr(V), k, n, _ptr(w), hc.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+    pV = _vec_ptr(V, k * n, "orthogonalize_noalloc V") if k > 0 else _ptr(V)
+    st = L.stab_orthogonalize_noalloc(pV, k, n, _vec_ptr(w, n, "orthogonalize_noalloc w"),
+                                      hc.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                                       ctypes.byref(nrm), None if stream is None else stream.cuda_stream)
     if st != 0:
         raise StabError(st, L.stab_last_error(None).decode())
@@ -400,8 +424,10 @@ class JvBatch:
         count = len(self.handles)
         if len(vs) != count or len(outs) != count:
             raise ValueError("one input and one output vector per handle")
-        v = (ctypes.c_void_p * count)(*[_ptr(x) for x in vs])
-        o = (ctypes.c_void_p * count)(*[_ptr(x) for x in outs])
+        ns = [h.n for h in self.handles]
+        v = (ctypes.c_void_p * count)(*[_vec_ptr(x, n, f"JvBatch.apply v[{i}]") for i, (x, n) in enumerate(zip(vs, ns))])
+        o = (ctypes.c_void_p * count)(*[_vec_ptr(x, n, f"JvBatch.apply out[{i}]")
+                                        for i, (x, n) in enumerate(zip(outs, ns))])
         sh = None
         if shifts is not None:
             arr = np.zeros(2 * count)
@@ -419,8 +445,11 @@ class JvBatch:
         count = len(self.handles)
         if len(qs) != count or len(zs) != count:
             raise ValueError("one input and one output vector per handle")
-        q = (ctypes.c_void_p * count)(*[_ptr(x) for x in qs])
-        z = (ctypes.c_void_p * count)(*[_ptr(x) for x in zs])
+        ns = [h.n for h in self.handles]
+        q = (ctypes.c_void_p * count)(*[_vec_ptr(x, n, f"JvBatch.precond_apply q[{i}]")
+                                        for i, (x, n) in enumerate(zip(qs, ns))])
+        z = (ctypes.c_void_p * count)(*[_vec_ptr(x, n, f"JvBatch.precond_apply z[{i}]")
+                                        for i, (x, n) in enumerate(zip(zs, ns))])
         st = self._L.stab_jv_batch_precond_apply(self._b, q, z)
         if st != 0:
             raise StabError(st, self._L.stab_jv_batch_last_error(self._b).decode())
@@ -433,9 +462,12 @@ class JvBatch:
         count = len(self.handles)
         if len(Vs) != count or len(ks) != count or len(ws) != count:
             raise ValueError("one basis, column count and vector per handle")
-        V = (ctypes.c_void_p * count)(*[_ptr(x) for x in Vs])
+        ns = [h.n for h in self.handles]
+        V = (ctypes.c_void_p * count)(*[_vec_ptr(x, int(k) * n, f"JvBatch.orthogonalize V[{i}]")
+                                        for i, (x, k, n) in enumerate(zip(Vs, ks, ns))])
         K = (ctypes.c_int * count)(*[int(x) for x in ks])
-        W = (ctypes.c_void_p * count)(*[_ptr(x) for x in ws])
+        W = (ctypes.c_void_p * count)(*[_vec_ptr(x, n, f"JvBatch.orthogonalize w[{i}]")
+                                        for i, (x, n) in enumerate(zip(ws, ns))])
         hc = np.zeros(2 * sum(int(x) for x in ks))
         nr = np.zeros(count)
         st = self._L.stab_jv_batch_orthogonalize(self._b, V, K, W, hc.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),

@@ -219,6 +219,7 @@ struct stab_jv_batch_s {
   void* h_buf = nullptr;  // pinned
   size_t h_cap = 0;
   cudaEvent_t copied = nullptr;  // the last transfer out of h_buf has completed
+  cudaEvent_t order = nullptr;   // orders the batch's stream against its handles' streams
   std::string err;
 };
 
@@ -230,6 +231,7 @@ struct BatchSection {
 
 struct BatchImage {
   std::vector<unsigned char> bytes;
+  bool overflow = false;  // a section's block count does not fit a launch (batch_stage refuses the image)
   size_t put(const void* p, size_t n) {
     const size_t off = (bytes.size() + 15) & ~(size_t)15;
     bytes.resize(off + n);
@@ -242,7 +244,15 @@ struct BatchImage {
     s.count = (int)items.size();
     if (!s.count) return s;
     std::vector<int> start(items.size() + 1, 0);
-    for (size_t i = 0; i < items.size(); ++i) start[i + 1] = start[i] + blocks[i];
+    long long total = 0;
+    for (size_t i = 0; i < items.size(); ++i) {
+      total += blocks[i];
+      if (blocks[i] < 0 || total > 0x7FFFFFFFLL) {  // grid x and the int offsets are limited to 2^31 - 1
+        overflow = true;
+        total = 0;
+      }
+      start[i + 1] = (int)total;
+    }
     s.items = put(items.data(), items.size() * sizeof(T));
     s.start = put(start.data(), start.size() * sizeof(int));
     s.blocks = start.back();
@@ -253,6 +263,12 @@ struct BatchImage {
 };
 
 cudaError_t batch_stage(stab_jv_batch_s* B, const BatchImage& im);
+// Order the batch's stream after the work queued so far on every handle's own
+// stream (begin), and every handle's stream after the batch's launches (end),
+// so that a batch call and single-handle calls on other streams never race on
+// a handle's scratch.
+cudaError_t batch_order_begin(stab_jv_batch_s* B);
+cudaError_t batch_order_end(stab_jv_batch_s* B);
 struct CgsJob {  // one instance of a batched CGS2 (scratch as for kry_cgs2)
   const double2* V;
   int k;

@@ -1766,6 +1766,7 @@ cudaError_t launch_norm2_stream(cudaStream_t st, const double2* v, long long n, 
 // Copy a parameter image to the batch's device buffer: through the pinned
 // staging buffer, once the previous transfer out of it has completed.
 cudaError_t batch_stage(stab_jv_batch_s* B, const BatchImage& im) {
+  if (im.overflow) return cudaErrorInvalidValue;
   const size_t bytes = im.bytes.size();
   cudaError_t e;
   if ((e = cudaEventSynchronize(B->copied)) != cudaSuccess) return e;
@@ -1786,6 +1787,32 @@ cudaError_t batch_stage(stab_jv_batch_s* B, const BatchImage& im) {
   std::memcpy(B->h_buf, im.bytes.data(), bytes);
   if ((e = cudaMemcpyAsync(B->d_buf, B->h_buf, bytes, cudaMemcpyHostToDevice, B->stream)) != cudaSuccess) return e;
   return cudaEventRecord(B->copied, B->stream);
+}
+
+// distinct handle streams other than the batch's own
+static std::vector<cudaStream_t> batch_handle_streams(const stab_jv_batch_s* B) {
+  std::vector<cudaStream_t> out;
+  for (const StabHandle* h : B->hs)
+    if (h->stream != B->stream && std::find(out.begin(), out.end(), h->stream) == out.end()) out.push_back(h->stream);
+  return out;
+}
+
+cudaError_t batch_order_begin(stab_jv_batch_s* B) {
+  for (cudaStream_t s : batch_handle_streams(B)) {
+    cudaError_t e = cudaEventRecord(B->order, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(B->stream, B->order, 0);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t batch_order_end(stab_jv_batch_s* B) {
+  const std::vector<cudaStream_t> ss = batch_handle_streams(B);
+  if (ss.empty()) return cudaSuccess;
+  cudaError_t e = cudaEventRecord(B->order, B->stream);
+  for (cudaStream_t s : ss)
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, B->order, 0);
+  return e;
 }
 
 static cudaError_t jv_batch_attributes() {
@@ -1870,6 +1897,7 @@ static cudaError_t jv_batch_apply(stab_jv_batch_s* B, const double2* const* v, d
       if (e != cudaSuccess) return e;
       const int var = (P.KP == 3 ? 2 : 0) + (P.ff ? 1 : 0);
       const long long nbx = (P.nlines + P.L - 1) / P.L;
+      if (nbx * STAB_MAX_JOBS > 0x7FFFFFFFLL) return cudaErrorInvalidValue;
       for (size_t j0 = 0; j0 < jobs.size(); j0 += STAB_MAX_JOBS) {
         P.njobs = (int)std::min<size_t>(STAB_MAX_JOBS, jobs.size() - j0);
         for (int k = 0; k < P.njobs; ++k) P.job[k] = jobs[j0 + k];
@@ -1886,6 +1914,7 @@ static cudaError_t jv_batch_apply(stab_jv_batch_s* B, const double2* const* v, d
 
   cudaError_t e;
   if ((e = batch_stage(B, im)) != cudaSuccess) return e;
+  if ((e = batch_order_begin(B)) != cudaSuccess) return e;
   const unsigned char* d = (const unsigned char*)B->d_buf;
   auto items_of = [&](const BatchSection& s) { return (const void*)(d + s.items); };
   auto start_of = [&](const BatchSection& s) { return (const int*)(d + s.start); };
@@ -1919,7 +1948,8 @@ static cudaError_t jv_batch_apply(stab_jv_batch_s* B, const double2* const* v, d
     h->last_eps_mode = h->opts.eps_mode;
     h->stats.jv_calls++;
   }
-  return cudaGetLastError();
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  return batch_order_end(B);
 }
 
 extern "C" stab_status stab_jv_batch_create(stab_jv_batch* out, const stab_handle* handles, int count, void* cuda_stream) {
@@ -1944,6 +1974,11 @@ extern "C" stab_status stab_jv_batch_create(stab_jv_batch* out, const stab_handl
   B->stream = (cudaStream_t)cuda_stream;
   if (jv_batch_attributes() != cudaSuccess ||
       cudaEventCreateWithFlags(&B->copied, cudaEventDisableTiming) != cudaSuccess) {
+    delete B;
+    return STAB_ERR_CUDA;
+  }
+  if (cudaEventCreateWithFlags(&B->order, cudaEventDisableTiming) != cudaSuccess) {
+    cudaEventDestroy(B->copied);
     delete B;
     return STAB_ERR_CUDA;
   }
@@ -1979,9 +2014,13 @@ extern "C" const char* stab_jv_batch_last_error(stab_jv_batch B) { return B ? B-
 
 extern "C" void stab_jv_batch_destroy(stab_jv_batch B) {
   if (!B) return;
+  // the batch's kernels read the handles' scratch, tables and inverses: wait
+  // for all of them before the handles may be destroyed
+  cudaStreamSynchronize(B->stream);
   cudaEventSynchronize(B->copied);
   if (B->d_buf) cudaFreeAsync(B->d_buf, B->stream);
   if (B->h_buf) cudaFreeHost(B->h_buf);
   cudaEventDestroy(B->copied);
+  if (B->order) cudaEventDestroy(B->order);
   delete B;
 }

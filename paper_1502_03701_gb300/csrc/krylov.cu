@@ -854,6 +854,7 @@ cudaError_t kry_cgs2_batch(stab_jv_batch_s* B, const std::vector<CgsJob>& jobs) 
   const BatchSection N = im.section(items, ones, 32, 0);
   cudaError_t e = batch_stage(B, im);
   if (e != cudaSuccess) return e;
+  if ((e = batch_order_begin(B)) != cudaSuccess) return e;
   const unsigned char* d = (const unsigned char*)B->d_buf;
   const CgsItem* it = (const CgsItem*)(d + S.items);
   const int* st = (const int*)(d + S.start);
@@ -861,5 +862,6 @@ cudaError_t kry_cgs2_batch(stab_jv_batch_s* B, const std::vector<CgsJob>& jobs) 
   k_cgs2_b_batch<<<S.blocks, kThreads, sm, B->stream>>>(it, st, S.count);
   k_cgs2_c_batch<<<S.blocks, kThreads, sm, B->stream>>>(it, st, S.count);
   k_norm_final_batch<<<N.count, 32, 0, B->stream>>>((const CgsItem*)(d + N.items), N.count);
-  return cudaGetLastError();
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  return batch_order_end(B);
 }

@@ -13,6 +13,8 @@
 // streams, or from two host threads) race on it and must be serialised by the
 // caller.  The first call on a device looks up the array's device address
 // with that device current; make that first call before any stream capture.
+// That address is kept until the process exits, so a device reset
+// (cudaDeviceReset) after the first call is not supported.
 #include <mutex>
 
 #include "internal.cuh"

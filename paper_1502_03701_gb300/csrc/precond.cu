@@ -721,6 +721,7 @@ cudaError_t pc_apply_batch(stab_jv_batch_s* B, const double2* const* q, double2*
   for (int v = 0; v < 4; ++v) sec[v] = im.section(items[v], blocks[v], threads[v], smem[v]);
   cudaError_t e = batch_stage(B, im);
   if (e != cudaSuccess) return e;
+  if ((e = batch_order_begin(B)) != cudaSuccess) return e;
   const unsigned char* d = (const unsigned char*)B->d_buf;
   for (int v = 0; v < 4; ++v) {
     const BatchSection& S = sec[v];
@@ -732,7 +733,8 @@ cudaError_t pc_apply_batch(stab_jv_batch_s* B, const double2* const* q, double2*
     else if (v == 2) k_apply_batch<2><<<S.blocks, S.threads, S.smem, B->stream>>>(it, st, S.count);
     else k_apply_batch<3><<<S.blocks, S.threads, S.smem, B->stream>>>(it, st, S.count);
   }
-  return cudaGetLastError();
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  return batch_order_end(B);
 }
 
 extern "C" stab_status stab_jv_batch_precond_apply(stab_jv_batch B, const void* const* q, void* const* z) {

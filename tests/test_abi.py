@@ -74,6 +74,7 @@ def test_batch_binding_checks_arguments_before_calling_the_library():
 
     class FakeHandle:
         _h = object()
+        n = 8
 
     B = JvBatch.__new__(JvBatch)
     B.handles = [FakeHandle(), FakeHandle()]
@@ -84,6 +85,12 @@ def test_batch_binding_checks_arguments_before_calling_the_library():
         B.precond_apply([1, 2], [1])
     with pytest.raises(ValueError):
         B.orthogonalize([1, 2], [3], [1, 2])
+    import torch
+    ok = torch.zeros(8, dtype=torch.complex128)
+    with pytest.raises(ValueError, match="CUDA"):  # host tensors are refused before any library call
+        B.apply([ok, ok], [ok, ok])
+    with pytest.raises(ValueError, match="complex128"):
+        B.precond_apply([torch.zeros(8), ok], [ok, ok])
     B.handles[1]._h = None
     with pytest.raises(StabError, match="closed"):
         B.apply([1, 2], [1, 2])
