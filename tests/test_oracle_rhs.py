@@ -213,3 +213,66 @@ def test_dense_jacobian_columns_are_tangent(orc):
     J = orc.core.dense_jacobian(P, q0)
     v = si.random_complex(8, g.n)
     assert np.linalg.norm(J @ v - orc.core.jv(P, q0, v)) < 1e-13 * np.linalg.norm(J @ v)
+
+
+@pytest.mark.parametrize("bulk", [0.0, 0.7])
+def test_xz_fourier_symbol_of_uniform_3d_state(orc, bulk):
+    """3-D pin of every viscous index: a uniform moving state (U, 0, W) with
+    non-reference pressure and entropy (rho0, T0 != 1, so Sutherland's mu(T0)
+    enters), perturbed by q' = (a + b y) exp(i (kx x + kz z)) on a uniform y
+    grid (the bounded compact schemes differentiate a + b y exactly, closure
+    rows included).  On interior rows J q' = E [S (a + b y) + Y b] with the
+    5x5 matrices below, derived by hand from the linearised equations about a
+    uniform state: convection -i(U k1x + W k1z); pressure gradient and
+    divergence; mu (laplacian + d_i div / 3) + mu_v d_i div with pure second
+    derivatives through the compact second-derivative symbols k2^2 and the
+    mixed d_x d_z, d_x d_y, d_y d_z through products of first-derivative
+    symbols; conduction lambda laplacian T' with T' = T0 ((1 - 1/gamma) p'/p0 +
+    s'/c_p) in the p and s rows.  A transposed index in the 3-D viscous stress
+    or a mixed derivative taken as a second derivative fails it."""
+    nx, ny, nz = 8, 7, 6
+    lx, lz = 3.0, 2.5
+    g = si.Grid(3, nx, ny, nz, lx, -1.0, 2.0, lz, 0.0)
+    f = si.Flow(0.6, 50.0, Pr=0.5)
+    P = orc.Problem.from_inputs(g, f, bulk)
+    gam, R = f.gamma, 1.0 / (f.gamma * f.Ma ** 2)
+    cp = gam * R / (gam - 1)
+    p0, s0, U, W = 1.3 * R, 0.3, 0.4, -0.7
+    q0 = np.zeros((5, nz, ny, nx))
+    q0[0], q0[1], q0[3], q0[4] = p0, U, W, s0
+    rho0 = (p0 / R) ** (1 / gam) * math.exp(-s0 / cp)
+    T0 = p0 / (rho0 * R)
+    mu0 = (1 / f.Re) * T0 ** 1.5 * (1 + f.S) / (T0 + f.S)
+    lam0, muv0 = mu0 * cp / f.Pr, bulk * mu0
+    Tp, Ts = T0 * (gam - 1) / (gam * p0), T0 / cp  # T' = Tp p' + Ts s'
+    mx, mz = 2, 1
+    kx1, kx2 = _symbols(lx / nx, mx, nx)
+    kz1, kz2 = _symbols(lz / nz, mz, nz)
+    conv = -1j * (U * kx1 + W * kz1)
+    lap = -(kx2 + kz2)  # second-derivative symbols (y part: d2/dy2 (a + b y) = 0)
+    vd = (mu0 / 3 + muv0) / rho0  # coefficient of d_i div u
+    S = np.zeros((5, 5), dtype=complex)
+    S[0] = [conv + (gam - 1) * lam0 * lap * Tp, -gam * p0 * 1j * kx1, 0, -gam * p0 * 1j * kz1,
+            (gam - 1) * lam0 * lap * Ts]
+    S[1] = [-1j * kx1 / rho0, conv + mu0 / rho0 * lap + vd * (-kx2), 0, vd * (-kx1 * kz1), 0]
+    S[2] = [0, 0, conv + mu0 / rho0 * lap, 0, 0]
+    S[3] = [-1j * kz1 / rho0, vd * (-kz1 * kx1), 0, conv + mu0 / rho0 * lap + vd * (-kz2), 0]
+    S[4] = [lam0 * lap * Tp / (rho0 * T0), 0, 0, 0, conv + lam0 * lap * Ts / (rho0 * T0)]
+    Y = np.zeros((5, 5), dtype=complex)
+    Y[0, 2] = -gam * p0
+    Y[1, 2] = vd * 1j * kx1
+    Y[2] = [-1 / rho0, vd * 1j * kx1, 0, vd * 1j * kz1, 0]
+    Y[3, 2] = vd * 1j * kz1
+    a = si.random_complex(21, 5)
+    b = si.random_complex(22, 5)
+    x = np.arange(nx) * lx / nx
+    z = np.arange(nz) * lz / nz
+    y = g.y()
+    E = np.exp(1j * (2 * math.pi * mx / lx * x[None, None, :] + 2 * math.pi * mz / lz * z[:, None, None]))
+    amp = a[:, None] + b[:, None] * y[None, :]                      # (5, ny)
+    v = amp[:, None, :, None] * E[None]                             # (5, nz, ny, nx)
+    expect = (S @ amp + (Y @ b)[:, None])[:, None, :, None] * E[None]
+    jv = orc.core.jv(P, q0, v.reshape(-1)).reshape(5, nz, ny, nx)
+    inner = slice(1, ny - 1)  # the non-reflective boundary rows have their own form
+    err = np.abs(jv[:, :, inner] - expect[:, :, inner]).max()
+    assert err < 1e-11 * np.abs(expect).max()

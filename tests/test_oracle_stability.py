@@ -14,40 +14,124 @@ import stab_inputs as si
 GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "validation_results.json")))
 
 
-def _validation_problem(orc, Ma, Re, nx=16, ny=64):
-    L1 = GOLD["L1"]
-    # 8 L1 in y, sinh stretching giving a minimum spacing of ~0.08 delta (Sec. Model problem)
-    g = si.Grid(2, nx, ny, 1, L1, -4 * L1, 4 * L1, 1.0, 5.65)
-    f = si.Flow(Ma, Re if Re else 0.0)
-    return g, f, orc.Problem.from_inputs(g, f)
+def _beta_for_min_spacing(Ly: float, ny: int, dmin: float) -> float:
+    """Stretching parameter of y(eta) = yc + (Ly/2) sinh(beta (2 eta - 1))/sinh(beta)
+    whose smallest spacing (at the centre) is dmin."""
+    from scipy.optimize import brentq
+    return brentq(lambda b: Ly * b / math.sinh(b) / (ny - 1) - dmin, 1e-3, 40.0)
 
 
-def _growth(orc, Ma, Re):
-    g, f, P = _validation_problem(orc, Ma, Re)
-    J = orc.core.dense_jacobian(P, si.tanh_base_flow(g, f))
+def _fourier_jacobian(orc, P, q0, m: int = 1) -> np.ndarray:
+    """J restricted to the x-Fourier mode exp(2 pi i m x / Lx): the base state
+    does not depend on x, so J commutes with x-shifts and its columns at x = 0
+    give the whole mode, J_m = sum_x J[(., x), (., 0)] exp(-2 pi i m x / nx)."""
+    nx, ny, npts = P.nx, P.ny, P.nx * P.ny
+    cols = np.array([v * npts + j * nx for v in range(4) for j in range(ny)])
+    Jc = orc.core.jacobian_columns(P, q0, cols).reshape(4, ny, nx, 4 * ny)
+    ph = np.exp(-2j * np.pi * m * np.arange(nx) / nx)
+    return np.einsum("vyxc,x->vyc", Jc, ph).reshape(4 * ny, 4 * ny)
+
+
+def _kh_growth(J: np.ndarray) -> float:
+    """Largest real part among the non-propagating eigenvalues (the tanh
+    layer's Kelvin-Helmholtz mode has zero phase speed)."""
     lam = sla.eigvals(J)
-    real = lam[np.abs(lam.imag) < 1e-6].real
-    return np.sort(real)[::-1]
+    return float(lam[np.abs(lam.imag) < 1e-6].real.max())
+
+
+# Reading of Table validation_config's Reynolds number (the paper does not
+# give its reference length): an independent 1-D viscous solve of the same
+# equations gives a maximum growth rate of 0.1396 at Re_delta = 1000 but
+# 0.1269 at Re_delta = 100, where the table prints 0.1273 / 0.1270 and Mack
+# 0.1271; the table's Re = 1000 is read as Re_delta = 100 (a reference length
+# of ten half-thicknesses).
+RE_TABLE_TO_DELTA = 0.1
+
+
+def test_linstab1d_reproduces_literature():
+    """The independent 1-D solver (tests/linstab1d.py) against published
+    inviscid values: Michalke's incompressible tanh layer (maximum growth
+    0.1897 at alpha 0.4446), Mack's compressible values of Table
+    validation_results, and the paper's L1 = 15.83 = 2 pi / alpha_max at
+    M = 0.5 (Sec. Numerical Experiments)."""
+    pytest.importorskip("sympy")
+    import linstab1d as L
+
+    w, _ = L.kh_growth(0.4446, 0.4446, 0.01, None, N=200, Y=120, beta=5.0)
+    assert abs(w - 0.1897) < 5e-4
+    a05, w05 = L.alpha_max(0.5, None, N=160, Y=100, beta=5.0)
+    assert abs(w05 - GOLD["cases"]["V02"]["mack"]) < 2e-3 * w05
+    assert abs(2 * math.pi / a05 - GOLD["L1_numerical_experiments"]) < 2e-3 * GOLD["L1_numerical_experiments"]
+    a09, w09 = L.alpha_max(0.9, None, N=160, Y=200, beta=5.0)
+    assert abs(w09 - GOLD["cases"]["V03"]["mack"]) < 2e-3 * w09
+
+
+@pytest.mark.parametrize("Ma,Re,Pr,bulk,a,Y,ny", [(0.5, None, 0.71, 0.0, 0.4, 50.0, 192),
+                                                    (0.5, 100.0, 0.71, 0.0, 0.4, 50.0, 192),
+                                                    (0.9, 300.0, 0.2, 0.6, 0.22, 150.0, 256)])
+def test_oracle_fourier_mode_matches_independent_1d_solve(orc, Ma, Re, Pr, bulk, a, Y, ny):
+    """Pin of the 2-D oracle's whole linearised operator (inviscid and
+    viscous terms, conduction, bulk viscosity, Sutherland law) against the
+    independent 1-D solver: the Kelvin-Helmholtz eigenvalue of the oracle's J
+    restricted to one x-Fourier mode equals that of the 1-D symbolic
+    linearisation evaluated with the same compact-scheme modified
+    wavenumbers, to the y-discretisation error (< 2e-6 relative)."""
+    pytest.importorskip("sympy")
+    import linstab1d as L
+
+    nx = 16
+    g = si.Grid(2, nx, ny, 1, 2 * math.pi / a, -Y, Y, 1.0, 3.0 if Y < 100 else 4.5)
+    f = si.Flow(Ma, Re if Re else 0.0, Pr=Pr)
+    P = orc.Problem.from_inputs(g, f, bulk)
+    w = _kh_growth(_fourier_jacobian(orc, P, si.tanh_base_flow(g, f)))
+    hx = g.lx / nx
+    w1, _ = L.kh_growth(L.lele_k1(a, hx), L.lele_k2(a, hx), Ma, Re, N=200 if Y < 100 else 240, Y=Y,
+                        beta=4.0 if Y < 100 else 4.5, Pr=Pr, bulk=bulk)
+    assert abs(w - w1) < 2e-6 * w1
 
 
 @pytest.mark.slow
-def test_growth_rates_against_paper_table(orc):
-    """Least-stable stationary mode at alpha = 2 pi / L1: V05 (M 0.1) and V06
-    (M 0.5) within 2 % of the paper's computed and Blumen's values; the mode
-    is a double eigenvalue (the +-alpha Fourier pair); viscosity (Re 1000)
-    lowers the growth rate; compressibility lowers it monotonically."""
-    c = GOLD["cases"]
-    w01 = _growth(orc, 0.1, None)
-    w05 = _growth(orc, 0.5, None)
-    w05v = _growth(orc, 0.5, 1000)
-    w09 = _growth(orc, 0.9, None)
-    assert abs(w01[0] - w01[1]) < 1e-8 * w01[0]  # double eigenvalue
-    assert abs(w01[0] - c["V05"]["blumen"]) < 0.02 * c["V05"]["blumen"]
-    assert abs(w01[0] - c["V05"]["omega"]) < 0.02 * c["V05"]["omega"]
-    assert abs(w05[0] - c["V06"]["blumen"]) < 0.02 * c["V06"]["blumen"]
-    assert abs(w05[0] - c["V06"]["omega"]) < 0.02 * c["V06"]["omega"]
-    assert w05v[0] < w05[0]
-    assert w09[0] < w05[0] < w01[0]
+@pytest.mark.parametrize("case", ["V01", "V02", "V03", "V04", "V05", "V06", "V07", "V08"])
+def test_growth_rates_against_paper_table(orc, case):
+    """Table validation_results, every row: L1 = 2 pi / alpha_max of the
+    least stable mode (alpha_max from the independent 1-D solve), y extent
+    8 L1 stretched to a minimum spacing of 0.08 delta, the table's resolution;
+    the oracle's growth rate (J restricted to the x-Fourier mode of one
+    wavelength) is within 2 % of the paper's computed value and within 0.5 %
+    of Mack's.  Re: see RE_TABLE_TO_DELTA."""
+    pytest.importorskip("sympy")
+    import linstab1d as L
+
+    c = GOLD["cases"][case]
+    Re = c["Re"] * RE_TABLE_TO_DELTA if c["Re"] else None
+    a, w1 = L.alpha_max(c["Ma"], Re, N=160, Y=150.0 if c["Ma"] > 0.8 else 80.0, beta=5.0)
+    L1 = 2 * math.pi / a
+    nx, ny = c["res"]
+    Ly = 8 * L1
+    g = si.Grid(2, nx, ny, 1, L1, -Ly / 2, Ly / 2, 1.0, _beta_for_min_spacing(Ly, ny, GOLD["min_dy"]))
+    f = si.Flow(c["Ma"], Re if Re else 0.0)
+    P = orc.Problem.from_inputs(g, f)
+    w = _kh_growth(_fourier_jacobian(orc, P, si.tanh_base_flow(g, f)))
+    assert abs(w - c["omega"]) < 0.02 * c["omega"]
+    assert abs(w - c["mack"]) < 0.005 * c["mack"]
+    assert abs(w - w1) < 1e-3 * w1
+
+
+def test_double_kh_eigenvalue_and_trends(orc):
+    """On the 2-D grid the +-alpha Fourier pair makes the least stable mode a
+    double eigenvalue of the dense J; viscosity and compressibility lower the
+    growth rate."""
+    def growth(Ma, Re):
+        L1 = GOLD["L1_numerical_experiments"]
+        g = si.Grid(2, 16, 48, 1, L1, -4 * L1, 4 * L1, 1.0, _beta_for_min_spacing(8 * L1, 48, 0.12))
+        f = si.Flow(Ma, Re)
+        P = orc.Problem.from_inputs(g, f)
+        lam = sla.eigvals(orc.core.dense_jacobian(P, si.tanh_base_flow(g, f)))
+        return np.sort(lam[np.abs(lam.imag) < 1e-6].real)[::-1]
+    w05 = growth(0.5, 0.0)
+    assert abs(w05[0] - w05[1]) < 1e-8 * w05[0]
+    assert growth(0.5, 100.0)[0] < w05[0]
+    assert growth(0.9, 0.0)[0] < w05[0] < growth(0.1, 0.0)[0]
 
 
 def _c1_like(orc, nx=8, ny=16):
