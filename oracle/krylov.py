@@ -100,6 +100,80 @@ def fgmres(A, b, M=None, m: int = 30, tol: float = 1e-10, max_restarts: int = 20
     return x, st
 
 
+def lgmres(A, b, M=None, m: int = 30, k: int = 2, tol: float = 1e-10, max_restarts: int = 200,
+           cycle_check=None):
+    """Restarted GMRES with augmented restarts, LGMRES (Baker, Jessup and
+    Manteuffel 2005; the paper's Sec. "Iterative solvers" and Table
+    comparison_overall use it next to GMRES).
+
+    Every cycle spans the same number m of directions as GMRES(m): m - a
+    Krylov directions of the current residual (right-preconditioned, kept in
+    flexible form) followed by the a <= k most recent error approximations
+    z_c = x_{c+1} - x_c of earlier cycles (newest first), each stored with
+    A z_c so that it enters the Arnoldi process without a matrix-vector
+    product.  A z_c is the difference of the true residuals before and after
+    the cycle.  The stored pairs are scaled to unit ||z||.  x0 = 0; stop when
+    ||b - A x|| <= tol ||b||.  With k = 0 this is ``fgmres``.
+    ``cycle_check(W, x_old, x_new)`` is called after every cycle with the
+    cycle's search directions (for the minimisation pin of the tests)."""
+    n = b.size
+    st = GmresStats()
+    x = np.zeros(n, dtype=np.complex128)
+    bnorm = np.linalg.norm(b)
+    if bnorm == 0.0:
+        st.converged = True
+        return x, st
+    r = b.astype(np.complex128).copy()
+    beta = bnorm
+    aug = []  # (z, A z) pairs, newest first
+    for cycle in range(max_restarts):
+        nkry = m - len(aug)
+        V = np.zeros((n, m + 1), dtype=np.complex128)
+        Z = np.zeros((n, m), dtype=np.complex128)
+        H = np.zeros((m + 1, m), dtype=np.complex128)
+        V[:, 0] = r / beta
+        y = None
+        jend = 0
+        for j in range(m):
+            if j < nkry:
+                Z[:, j] = V[:, j] if M is None else M(V[:, j])
+                w = A(Z[:, j])
+                st.matvecs += 1
+            else:
+                Z[:, j], w = aug[j - nkry]
+                w = w.copy()
+            st.iterations += 1
+            h, w = cgs2(V[:, :j + 1], w)
+            H[:j + 1, j] = h
+            H[j + 1, j] = np.linalg.norm(w)
+            e1 = np.zeros(j + 2, dtype=np.complex128)
+            e1[0] = beta
+            y = np.linalg.lstsq(H[:j + 2, :j + 1], e1, rcond=None)[0]
+            res = np.linalg.norm(e1 - H[:j + 2, :j + 1] @ y)
+            st.history.append(res / bnorm)
+            jend = j + 1
+            if res <= tol * bnorm or H[j + 1, j] == 0.0:
+                break
+            V[:, j + 1] = w / H[j + 1, j]
+        dz = Z[:, :jend] @ y
+        if cycle_check is not None:
+            cycle_check(Z[:, :jend].copy(), x.copy(), x + dz)
+        x = x + dz
+        r_new = b - A(x)
+        st.matvecs += 1
+        dn = np.linalg.norm(dz)
+        if k > 0 and dn > 0.0:
+            aug.insert(0, (dz / dn, (r - r_new) / dn))
+            del aug[k:]
+        r = r_new
+        beta = np.linalg.norm(r)
+        st.restarts = cycle + 1
+        if beta <= tol * bnorm:
+            st.converged = True
+            break
+    return x, st
+
+
 def _wanted_order(theta, sigma, tau):
     """Indices sorted by decreasing |theta|, ties by larger Re lambda, then Im lambda."""
     lam = cayley_lambda(theta, sigma, tau)
