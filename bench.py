@@ -1,21 +1,25 @@
 """Benchmark of the stability hot path on GB300.  Prints one JSON line.
 
-Default (--workload jv): the 256 x 512 compressible tanh mixing layer
-(524,288 complex unknowns, Ma 0.3, Re 1000).  One timed step is one
-application of the matrix-free operator J(q0) v through the C ABI (the
-cancellation-free epsilon-quotient of the paper's Frechet derivative), the
-innermost and most-called step of the method; value = GB/s of algorithmic
-traffic (32 B per complex unknown).  Also reported, measured in the same run:
+Default (--workload jv): the 3-D compressible tanh mixing layer at
+128 x 256 x 64 points (10,485,760 complex unknowns, Ma 0.3, Re 1000), the
+largest single-GPU configuration.  One timed step is one application of the
+matrix-free operator J(q0) v through the C ABI (the cancellation-free
+epsilon-quotient of the paper's Frechet derivative), the innermost and
+most-called step of the method; value = GB/s of algorithmic traffic (32 B per
+complex unknown: read v, write J v; the y-only base tables stay on chip),
+and the roofline compares it with the measured HBM copy bandwidth, with the
+FP64-pipe fraction of the line passes beside it.  Also reported, measured in
+the same run:
+  * "jv_pair_stencil": the same J v with the compact-scheme right-hand sides in
+    FP32 pair arithmetic (stencil_prec 48), and its difference to the main step's;
+  * "jv_2d_256x512": the J v of the 2-D 256 x 512 layer (524,288 unknowns);
   * "eigs": complete Cayley-IRAM solves of the 32 x 64 layer through stab_eigs
     (sigma 1, tau -1, nev 4, ncv 30, block-Jacobi over 16 x 16 tiles, FGMRES(50) to 1e-10,
     exact-tangent J v): converged eigenpairs per second (true residual
     < 1e-8), the p50 / p99 solve latency and the J v count per solve;
-  * "jv_pair_stencil": the same J v with the compact-scheme right-hand sides in
-    FP32 pair arithmetic (stencil_prec 48), and its difference to the main step's;
   * "gmres_256x512": preconditioned FGMRES(50) iterations per second on the
     256 x 512 layer (block-Jacobi over 8 x 8-point tiles, FP32 inverses; also
     BF16 inverses, and BF16 inverses with an FP32 Krylov basis);
-  * "jv_3d": the same J v on the 3-D 128 x 256 x 64 layer (10.5 M unknowns);
   * "jv_batch_64": J v and block-Jacobi apply of the 64 uneven instances of the batch
     configuration as one batched call (one launch per phase) against 64 single-problem calls;
   * "many_small": uneven small layers solved one at a time on the plain FP64
@@ -24,8 +28,7 @@ traffic (32 B per complex unknown).  Also reported, measured in the same run:
 The line-pass launch shapes of the timed grid are autotuned first
 (--tune-cache FILE reuses and stores the tuned shapes).
 
---workload eigs makes the 256 x 512 Cayley-IRAM solve the timed step (slow:
-its inner solves need thousands of preconditioned iterations each).
+--workload eigs makes Cayley-IRAM solves of the 2-D 256 x 512 layer the timed step.
 
 --impl reference times the CPU oracle (plain C++ restatement) on the host
 cores on a bounded sample and scales it to the same metric.
@@ -52,9 +55,14 @@ METRIC = "J·v GB/s (% HBM peak); converged eigenpairs/s; p50/p99 solve latency"
 JV_BYTES_PER_DOF = 32  # read v (16 B) + write J v (16 B); the y-only base tables stay on chip
 L2_FLUSH_BYTES = 512 << 20
 EIG = dict(sigma=0.2j, tau=-1 + 0.2j, nev=10, ncv=60, tol=1e-10)
+EIG_GRID = (256, 512)  # the 2-D layer of the --workload eigs solves
 SOLVER_OPTS = dict(eps_mode=2, precond=1, tile=(8, 8), precond_prec=32, gmres_m=50, gmres_tol=1e-10,
                    gmres_max_restarts=400, max_restarts=60)
 RESID_OK = 1e-8
+
+
+def _jv_workload_name(g) -> str:
+    return f"jv_mixing_layer_{g.nx}x{g.ny}" + (f"x{g.nz}" if g.dim == 3 else "")
 
 
 def _peaks():
@@ -64,9 +72,21 @@ def _peaks():
         return {}
 
 
-def _layer(nx, ny, Ma):
-    g, f = si.mixing_layer_2d(nx, ny, Ma=Ma)
+def _layer(nx, ny, Ma, nz=1):
+    """The tanh mixing layer of the workloads: 2-D for nz = 1, else 3-D (x and z periodic, Lz = Lx)."""
+    if nz > 1:
+        g, f = si.mixing_layer_3d(nx, ny, nz, Ma=Ma)
+    else:
+        g, f = si.mixing_layer_2d(nx, ny, Ma=Ma)
     return g, f, si.tanh_base_flow(g, f)
+
+
+def _jv_sample_grid(g):
+    """Bounded CPU sample of a J v workload: 3-D layers keep their x-y planes and z spacing but only 8
+    z planes (the oracle's cost is linear in the points), 2-D layers run whole."""
+    if g.dim == 3 and g.nz > 8:
+        return si.Grid(3, g.nx, g.ny, 8, g.lx, g.ly0, g.ly1, g.lz * 8 / g.nz, g.stretch)
+    return g
 
 
 class ClockSampler:
@@ -165,11 +185,25 @@ def cpu_baseline_eigs(g, f, q0, jv_calls: float, nconv: float, budget_s: float =
                       f"scaled by the GPU solve's {jv_calls:.0f} J v per solve (lower bound on CPU time)"}
 
 
-def cpu_baseline_jv(g, f, q0, budget_s: float = 12.0) -> dict:
-    dt, count, cores = oracle_jv_seconds(g, f, q0, budget_s, "literal")
-    return {"value": g.n * JV_BYTES_PER_DOF / dt / 1e9, "unit": "GB/s", "cores": cores, "kind": "oracle",
-            "sample": f"{count} literal double epsilon-quotient J v on the full {g.nx}x{g.ny} layer "
-                      f"({dt * 1e3:.1f} ms each)"}
+def _cpu_model() -> str:
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part", "hardware")):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def cpu_baseline_jv(g, f, budget_s: float = 12.0) -> dict:
+    gs = _jv_sample_grid(g)
+    dt, count, cores = oracle_jv_seconds(gs, f, si.tanh_base_flow(gs, f), budget_s, "literal")
+    return {"value": gs.n * JV_BYTES_PER_DOF / dt / 1e9, "unit": "GB/s", "cores": cores, "kind": "oracle",
+            "cpu": _cpu_model(),
+            "sample": f"{count} literal double epsilon-quotient J v of the oracle on a {gs.nx}x{gs.ny}x{gs.nz} "
+                      f"layer ({gs.n} unknowns, {dt * 1e3:.1f} ms each; the workload's x-y planes and spacing), "
+                      f"scaled per unknown to the {g.nx}x{g.ny}x{g.nz} workload"}
 
 
 # ---------------------------------------------------------------------------
@@ -177,25 +211,32 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    g, f, q0 = _layer(args.nx, args.ny, 0.3)
     if args.workload == "jv":
+        g, f, q0 = _layer(args.nx, args.ny, 0.3, args.nz)
         import oracle
         oracle.build()
-        P = oracle.Problem.from_inputs(g, f)
-        v = si.random_complex(11, g.n)
-        eps = oracle.core.knoll_keyes_eps(q0, v)
+        gs = _jv_sample_grid(g)
+        qs = si.tanh_base_flow(gs, f)
+        P = oracle.Problem.from_inputs(gs, f)
+        v = si.random_complex(11, gs.n)
+        eps = oracle.core.knoll_keyes_eps(qs, v)
         for _ in range(max(args.warmup, 1)):
-            oracle.core.jv(P, q0, v, "literal", eps)
+            oracle.core.jv(P, qs, v, "literal", eps)
         t0 = time.perf_counter()
         count = 0
         while count < args.steps and time.perf_counter() - t0 < 60.0:  # K steps, at most a minute
-            oracle.core.jv(P, q0, v, "literal", eps)
+            oracle.core.jv(P, qs, v, "literal", eps)
             count += 1
-        dt = (time.perf_counter() - t0) / count
+        dt = (time.perf_counter() - t0) / count * g.n / gs.n  # per full-size J v
         cores = oracle.core.num_threads()
         val, unit, ms = g.n * JV_BYTES_PER_DOF / dt / 1e9, "GB/s", dt * 1e3
-        sample = f"{count} literal double epsilon-quotient J v on the full {g.nx}x{g.ny} layer (of {args.steps} steps)"
+        sample = (f"{count} literal double epsilon-quotient J v of the oracle on a {gs.nx}x{gs.ny}x{gs.nz} layer "
+                  f"(of {args.steps} steps), scaled per unknown to the {g.nx}x{g.ny}x{g.nz} workload; "
+                  f"CPU {_cpu_model()}")
+        wl = _jv_workload_name(g)
     else:
+        g, f, q0 = _layer(EIG_GRID[0], EIG_GRID[1], 0.3)
+        wl = f"eigs_mixing_layer_{g.nx}x{g.ny}"
         # bounded sample: the oracle's J v time scaled by the J v count of a solve of this workload
         # (recorded by the GPU arm in profiles/; 1 J v per GMRES iteration plus one per restart)
         jv_per_solve = args.ref_jv_per_solve
@@ -207,7 +248,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": unit, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"{args.workload}_mixing_layer_{g.nx}x{g.ny}", "nx": g.nx, "ny": g.ny},
+            "config": {"workload": wl, "nx": g.nx, "ny": g.ny, "nz": g.nz},
             "cpu_baseline": {"value": val, "unit": unit, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": val, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
@@ -251,26 +292,28 @@ def small_layer_eigs(args, Stab, torch, rank):
             "restarts": [r.stats["restarts"] for r in res]}
 
 
-def jv_3d(args, Stab, torch, flush, stream) -> dict:
-    """J v on the 3-D 128 x 256 x 64 layer (10.5 M complex unknowns), autotuned, L2 flushed between steps."""
-    g, f = si.mixing_layer_3d(128, 256, 64, Ma=0.3)
-    q0 = si.tanh_base_flow(g, f)
+def jv_extra(args, Stab, torch, flush, stream, nx, ny, nz=1) -> dict:
+    """J v of another layer (autotuned, L2 flushed between steps) with its own roofline."""
+    g, f, q0 = _layer(nx, ny, 0.3, nz)
     S = Stab(q0, g, f.Ma, f.Re, f.Pr)
     tuned = S.autotune()
+    St = Stab(q0, g, f.Ma, f.Re, f.Pr, eps_mode=2)
     v = torch.from_numpy(si.random_complex(21, g.n)).cuda()
     out = torch.empty_like(v)
     for _ in range(3):
         S.apply_J(v, out)
+        St.apply_J(v, out)
+    tan = _time_jv(St, v, out, 20, flush, stream, torch)
     S.timing(True)
-    steps = _time_jv(S, v, out, args.steps_3d, flush, stream, torch)
+    steps = _time_jv(S, v, out, args.steps_2d, flush, stream, torch)
     ph = S.timing_read()
     S.close()
+    St.close()
     t = statistics.mean(steps)
-    total = sum(x[0] for k, x in ph.items() if k != "dropped")
-    return {"workload": "jv_mixing_layer_128x256x64", "value": g.n * JV_BYTES_PER_DOF / t / 1e9, "unit": "GB/s",
-            "ms_per_step": t * 1e3, "steps": args.steps_3d, "unknowns": g.n,
+    return {"workload": _jv_workload_name(g), "value": g.n * JV_BYTES_PER_DOF / t / 1e9, "unit": "GB/s",
+            "ms_per_step": t * 1e3, "steps": args.steps_2d, "unknowns": g.n,
             "line_pass_shapes": {ax: {"C": c, "L": l, "kinds": k} for ax, (c, l, k, _) in tuned.items()},
-            "phase_share": {k: x[0] / total for k, x in ph.items() if k != "dropped" and x[1]}}
+            "roofline": jv_roofline(g, f, ph, t, _peaks().get("hbm_gbs"), statistics.mean(tan))}
 
 
 def gmres_throughput(args, Stab, torch, q0, g, f):
@@ -313,11 +356,12 @@ def gmres_throughput(args, Stab, torch, q0, g, f):
 #   second derivative : stencil a(f+1 - 2f + f-1) + b(f+2 - 2f + f-2) 9 + tridiagonal solve 5 = 14
 # (solve: forward elimination one FMA, back substitution one FMA and one multiply).
 LINE_FLOP_D1, LINE_FLOP_D2 = 10, 14
-FP64_PEAK_GFLOPS = 1250.0  # GB300 FP64 (non-tensor) nominal; 1.2 TFLOP/s measured by an FMA microbenchmark
-# DRAM bytes per launch of the line pass from ncu (dram__bytes_read.sum + dram__bytes_write.sum) on the
-# 512 x 1024 layer (tuned shapes: the compact layout on both axes, FP64 right-hand sides): y pass
-# 42.1 + 11.8 MB, x pass 58.9 + 25.7 MB; scaled by grid points.
-LINE_TRAFFIC_512x1024 = {"line_y": (42.108416 + 11.777024) * 1e6, "line_x": (58.887680 + 25.734144) * 1e6}
+# FP64 FMA throughput measured on GB300 by the project's microbenchmark (tests/test_gpu_fp_throughput.py,
+# profiles/fp_throughput.md); MEASURED_PEAKS.json carries no FP64 figure.
+FP64_MEASURED_GFLOPS = 1197.0
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of all kernels of one J v, from one ncu capture
+# per layer (see profiles/), keyed by workload; scaled by unknowns when the capture ran on a smaller case.
+JV_TRAFFIC = {}
 
 
 def line_pass_flops(g, visc: bool) -> dict:
@@ -335,7 +379,9 @@ def line_pass_flops(g, visc: bool) -> dict:
 
 
 def jv_roofline(g, f, phases: dict, step_s: float, hbm, tangent_s: float) -> dict:
-    """Roofline of the dominant kernel of the timed J v steps (per-phase CUDA events)."""
+    """Roofline of the timed J v: the operator's algorithmic bytes (32 B per unknown) over its measured
+    step time against the measured HBM copy bandwidth, with the line passes' FP64 rate (the unit that
+    binds on GB300) beside it."""
     ms = {k: v[0] for k, v in phases.items() if k != "dropped"}
     cnt = {k: v[1] for k, v in phases.items() if k != "dropped"}
     total = sum(ms.values())
@@ -345,25 +391,23 @@ def jv_roofline(g, f, phases: dict, step_s: float, hbm, tangent_s: float) -> dic
     flops = line_pass_flops(g, f.Re > 0)
     line_flops = sum(flops[k] * cnt[k] for k in line_keys)
     avg_s = line_ms / 1e3 / launches
-    achieved = line_flops / launches / avg_s / 1e9
-    scale = g.npts / (512 * 1024)
-    traffic = None
-    if g.dim == 2 and f.Re > 0 and LINE_TRAFFIC_512x1024:
-        traffic = sum(LINE_TRAFFIC_512x1024[k] * cnt[k] for k in ("line_y", "line_x")) / launches * scale
+    fp64_achieved = line_flops / launches / avg_s / 1e9
     share = {k: (ms[k] / total if total else None) for k in ms if cnt[k]}
-    op_achieved = g.n * JV_BYTES_PER_DOF / step_s / 1e9
-    return {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
-            "frac": achieved / FP64_PEAK_GFLOPS, "traffic": traffic,
-            "kernel": "k_line_pass / k_line_pass_compact (compact-derivative line sweeps in the tuned layout; "
-                      "y and x launches per J v)",
-            "flop_per_launch": line_flops / launches, "launch_ms": avg_s * 1e3, "launches": launches,
-            "peak_source": "FP64 nominal 1.25 TFLOP/s (recipe table); FMA microbenchmark measures 1.2",
-            "traffic_source": "ncu dram bytes of the 512x1024 launches scaled by grid points" if traffic else None,
+    achieved = g.n * JV_BYTES_PER_DOF / step_s / 1e9
+    tr = JV_TRAFFIC.get(_jv_workload_name(g))
+    return {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+            "frac": (achieved / hbm) if hbm else None,
+            "traffic": tr["bytes"] if tr else None,
+            "kernel": "the J v operator (epsilon norm, temperature differences, y/z/x compact line passes, "
+                      "pointwise assembly: one launch each), timed per step with CUDA events",
+            "bytes_per_step": g.n * JV_BYTES_PER_DOF, "step_ms": step_s * 1e3, "tangent_step_ms": tangent_s * 1e3,
+            "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)",
+            "traffic_source": tr["source"] if tr else "no ncu capture of the current kernels",
             "phase_share": share,
-            "operator": {"bound": "hbm", "achieved": op_achieved, "peak": hbm, "unit": "GB/s",
-                         "frac": (op_achieved / hbm) if hbm else None, "bytes_per_step": g.n * JV_BYTES_PER_DOF,
-                         "step_ms": step_s * 1e3, "tangent_step_ms": tangent_s * 1e3,
-                         "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}}
+            "fp64_pipe": {"kernel": "k_line_pass / k_line_pass_compact (all axes)", "achieved": fp64_achieved,
+                          "peak": FP64_MEASURED_GFLOPS, "unit": "GFLOP/s", "frac": fp64_achieved / FP64_MEASURED_GFLOPS,
+                          "flop_per_launch": line_flops / launches, "launch_ms": avg_s * 1e3, "launches": launches,
+                          "peak_source": "FP64 FMA microbenchmark on GB300 (of measured)"}}
 
 
 # Many small problems (uneven 2-D instances drawn like the 64-instance batch
@@ -591,7 +635,10 @@ def run_ours(args):
 
 
     # J v on the Ma 0.3 layer (both forms)
-    g, f, q0 = _layer(args.nx, args.ny, 0.3)
+    if args.workload == "jv":
+        g, f, q0 = _layer(args.nx, args.ny, 0.3, args.nz)
+    else:
+        g, f, q0 = _layer(EIG_GRID[0], EIG_GRID[1], 0.3)
     n = g.n
     Sj = Stab(q0, g, f.Ma, f.Re, f.Pr)
     if args.tune_cache and os.path.exists(args.tune_cache):
@@ -623,9 +670,11 @@ def run_ours(args):
         unit = "GB/s"
         ms_step = t_max / args.steps * 1e3
         roofline = jv_roofline(g, f, phases, sum(steps_t) / args.steps, hbm, statistics.mean(jv_tan))
-        config = {"workload": f"jv_mixing_layer_{g.nx}x{g.ny}", "nx": g.nx, "ny": g.ny, "Ma": f.Ma, "Re": f.Re,
+        config = {"workload": _jv_workload_name(g), "nx": g.nx, "ny": g.ny, "nz": g.nz, "unknowns": g.n,
+                  "Ma": f.Ma, "Re": f.Re,
                   "line_pass_shapes": {ax: {"C": c, "L": l, "kinds": k} for ax, (c, l, k, _) in tuned.items()},
-                  "eps_mode": "cancellation-free epsilon-quotient", "l2": "flushed between timed steps",
+                  "eps_mode": "cancellation-free epsilon-quotient",
+                  "l2": "flushed between timed steps (512 MB written)",
                   "parallelism": f"replicas{world}"}
         # end to end through the public API: every step copies its input from pinned host memory and
         # its result back; copies run on a second stream, double-buffered, so that step i+1's input
@@ -681,8 +730,9 @@ def run_ours(args):
         call_s = statistics.mean(a.elapsed_time(b) / 1e3 for a, b in evs)
         e2e = {"value": e2e_val, "unit": "GB/s", "h2d_bytes_per_step": n * 16, "d2h_bytes_per_step": n * 16,
                "overlap": "copies double-buffered on a second stream",
-               "l2": "not flushed in this loop: every step's input is new data copied from the host; the "
-                     "operator's scratch and tables stay in L2 between calls as in any stream of calls",
+               "l2": "not flushed in this loop: every step's input is new data copied from the host"
+                     + ("; the operator's derivative scratch (%.0f MB) exceeds L2" % (g.npts * 16 * 37 / 1e6)
+                        if g.dim == 3 else "; the operator's scratch and tables stay in L2 between calls"),
                "single_call": {"value": bytes_jv / call_s / 1e9, "unit": "GB/s", "ms": call_s * 1e3,
                                "l2": "flushed before each call, copies and J v not overlapped"}}
         # every timed phase is one kernel launch of the library (k_norm2, k_temperature_fast,
@@ -692,13 +742,14 @@ def run_ours(args):
         extra["jv_pair_stencil"] = pair_stencil_jv(args, Stab, torch, q0, g, f, v, out, flush, stream, bytes_jv)
         if args.eig_steps > 0:
             extra["eigs"] = small_layer_eigs(args, Stab, torch, rank)
+        if args.steps_2d > 0:
+            extra["jv_2d_256x512"] = jv_extra(args, Stab, torch, flush, stream, 256, 512)
         if args.gmres_restarts > 0:
-            extra["gmres_256x512"] = gmres_throughput(args, Stab, torch, q0, g, f)
+            g2, f2, q2 = _layer(256, 512, 0.3)
+            extra["gmres_256x512"] = gmres_throughput(args, Stab, torch, q2, g2, f2)
         if args.fleet > 0 and world == 1:
             extra["jv_batch_64"] = jv_batch_64(args, torch)
             extra["many_small"] = fleet(args, torch)
-        if args.steps_3d > 0:
-            extra["jv_3d"] = jv_3d(args, Stab, torch, flush, stream)
     else:
         # roofline of the J v kernels from a short phase-timed sample (the solves below are host-driven)
         Sj.timing(True)
@@ -708,7 +759,7 @@ def run_ours(args):
         sweep = (0.3, 0.6, 0.9)
         handles = []
         for Ma in sweep:
-            gg, ff, qq = _layer(args.nx, args.ny, Ma)
+            gg, ff, qq = _layer(EIG_GRID[0], EIG_GRID[1], Ma)
             handles.append(Stab(qq, gg, ff.Ma, ff.Re, ff.Pr, seed=0x5EED + rank, **SOLVER_OPTS))
         vecs = torch.empty((EIG["nev"], n), dtype=torch.complex128, device="cuda")
         v0h = torch.from_numpy(si.start_vector(0x5EED + rank, n)).pin_memory()
@@ -792,7 +843,7 @@ def run_ours(args):
             "e2e": e2e}
     line.update(extra)
     if args.workload == "jv" and rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline_jv(g, f, q0)
+        line["cpu_baseline"] = cpu_baseline_jv(g, f)
     if rank == 0:
         print(json.dumps(line))
     Sj.close()
@@ -811,14 +862,15 @@ def main():
     ap.add_argument("--eig-steps", type=int, default=2)
     ap.add_argument("--gmres-restarts", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--nx", type=int, default=256)
-    ap.add_argument("--ny", type=int, default=512)
+    ap.add_argument("--nx", type=int, default=128)
+    ap.add_argument("--ny", type=int, default=256)
+    ap.add_argument("--nz", type=int, default=64, help="z points of the J v layer (1: 2-D)")
     ap.add_argument("--ref-jv-per-solve", type=int, default=20000)
     ap.add_argument("--fleet", type=int, default=8, help="instances of the many-small-problems section (0: skip)")
     ap.add_argument("--rate", type=float, default=50.0, help="Poisson arrival rate of the served stream (1/s)")
     ap.add_argument("--slots", type=int, default=8)
     ap.add_argument("--budget-gb", type=int, default=64)
-    ap.add_argument("--steps-3d", type=int, default=50, help="timed J v steps on the 128 x 256 x 64 layer (0: skip)")
+    ap.add_argument("--steps-2d", type=int, default=500, help="timed J v steps on the 2-D 256 x 512 layer (0: skip)")
     ap.add_argument("--tune-cache", default="", help="line-pass tuning cache file to load before and save after tuning")
     args = ap.parse_args()
     if args.impl == "reference":

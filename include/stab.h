@@ -81,6 +81,12 @@ typedef struct {
                              48 (interior rows in FP32 pair arithmetic on exactly power-of-two-scaled
                              inputs, ~2^-47 relative; the Thomas sweeps, the closure rows and the set-up
                              stay FP64) */
+  int lgmres_k;           /* inner solver: 0 = GMRES(gmres_m) (default); k in [1, min(8, gmres_m - 1)] =
+                             LGMRES (Sec. "Iterative solvers", after Baker, Jessup and Manteuffel): every
+                             cycle spans gmres_m directions, gmres_m - k Krylov directions of the residual
+                             followed by the k latest error approximations x_{c+1} - x_c of earlier cycles,
+                             which enter without a J v (their products are the residual differences).
+                             Needs gmres_basis_prec = 64 (else STAB_ERR_UNSUPPORTED) */
 } stab_opts;
 
 typedef struct {
@@ -333,6 +339,35 @@ typedef struct {
   stab_stats stats;   /* out */
 } stab_eig_job;
 
+/* Solver-level batching: GMRES of every instance of the batch in lockstep,
+ * (J_i - sigma_i I) x_i = rhs_i (Sec. "Iterative solvers", each handle's
+ * options: restart length, tolerance, block-Jacobi preconditioner, built for
+ * sigma_i on first use).  Each phase of a GMRES cycle (block apply, J v,
+ * CGS2, Givens update, scaling, solution update, true residual) is one
+ * launch for all instances; an instance that converges is skipped by the
+ * following launches through a device-side flag, and the host reads one
+ * report per cycle for all instances.  The orthogonalisation is CGS2 at
+ * every size (stab_solve switches to selective reorthogonalisation from
+ * 16,384 unknowns), so below that size each x_i equals stab_solve's bit for
+ * bit.  sigmas: 2*count doubles (re, im); rhs[i], x[i]: device complex128 of
+ * handle i's size; iters (host, count, may be NULL): iterations per instance.
+ * Handles with gmres_basis_prec = 32 or lgmres_k > 0: STAB_ERR_UNSUPPORTED.
+ * NOT_CONVERGED when an instance reached its restart limit (its x holds the
+ * last iterate).  Synchronises the batch's stream. */
+stab_status stab_jv_batch_solve(stab_jv_batch b, const double* sigmas, const void* const* rhs, void* const* x,
+                                int* iters);
+/* Cayley-IRAM (Algorithm iram) of every instance of the batch in lockstep:
+ * jobs[i] holds the arguments and receives the outputs of a stab_eigs call on
+ * handle i (vecs: device).  The Arnoldi steps of all unfinished instances run
+ * as one launch per phase (J v - tau v, the lockstep GMRES above, CGS2, the
+ * Hessenberg entries) and the implicit restarts as one launch with one CTA
+ * per instance; instances finish independently.  Eigenvalues agree with a
+ * lone stab_eigs to rounding (bit for bit below 16,384 unknowns).  Returns
+ * STAB_OK, NOT_CONVERGED when a job reached its restart limit, or the first
+ * error; each job's own status is in jobs[i].status.  Same restrictions as
+ * stab_jv_batch_solve. */
+stab_status stab_jv_batch_eigs(stab_jv_batch b, stab_eig_job* jobs);
+
 /* Run stab_eigs(handles[i], jobs[i]) for i < count side by side: up to
  * `concurrency` host threads (<= 0: count), each handle on a private stream
  * for the duration (ordered after the handle's stream; the handle's stream is
@@ -374,6 +409,15 @@ typedef struct {
 } stab_request_info;
 
 stab_status stab_server_create(stab_server* server, int slots, long long mem_budget_bytes, int autotune);
+
+/* Lockstep cohorts (default 1): a free worker takes the queue's head and up to
+ * cohort - 1 requests queued behind it whose memory fits, and solves those
+ * that can be batched (base flow varying in y only, FP64 GMRES basis, no
+ * LGMRES) together with stab_jv_batch_eigs, every phase one launch for the
+ * cohort; the others run one after the other on the worker.  Each request of
+ * a cohort finishes when the cohort does.  Applies to cohorts formed after the
+ * call. */
+stab_status stab_server_set_cohort(stab_server server, int cohort);
 
 /* Queue a request; *id identifies it.  OOM if its estimate exceeds the whole budget. */
 stab_status stab_server_submit(stab_server server, const stab_request* request, long long* id);

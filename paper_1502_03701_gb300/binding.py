@@ -28,7 +28,7 @@ SYMBOLS = ["stab_default_opts", "stab_create", "stab_destroy", "stab_last_error"
            "stab_server_create", "stab_server_submit", "stab_server_wait", "stab_server_result",
            "stab_server_stats", "stab_server_destroy", "stab_jv_batch_create", "stab_jv_batch_apply",
            "stab_jv_batch_last_error", "stab_jv_batch_destroy", "stab_jv_batch_precond_apply",
-           "stab_jv_batch_orthogonalize"]
+           "stab_jv_batch_orthogonalize", "stab_jv_batch_solve", "stab_jv_batch_eigs", "stab_server_set_cohort"]
 
 # stab_phase, in enum order
 PHASES = ["eps", "temperature", "line_y", "line_z", "line_x", "pointwise", "cgs2", "precond_apply"]
@@ -52,7 +52,7 @@ class Opts(ctypes.Structure):
                 ("gmres_max_restarts", ctypes.c_int), ("gmres_tol", ctypes.c_double), ("precond", ctypes.c_int),
                 ("tile", ctypes.c_int * 3), ("precond_prec", ctypes.c_int), ("max_restarts", ctypes.c_int),
                 ("seed", ctypes.c_ulonglong), ("gmres_basis_prec", ctypes.c_int),
-                ("stencil_prec", ctypes.c_int)]
+                ("stencil_prec", ctypes.c_int), ("lgmres_k", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -140,6 +140,9 @@ def load():
     L.stab_jv_batch_apply.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), dp]
     L.stab_jv_batch_precond_apply.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp)]
     L.stab_jv_batch_orthogonalize.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(i), ctypes.POINTER(vp), dp, dp]
+    L.stab_server_set_cohort.argtypes = [vp, i]
+    L.stab_jv_batch_solve.argtypes = [vp, dp, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(i)]
+    L.stab_jv_batch_eigs.argtypes = [vp, ctypes.POINTER(EigJob)]
     L.stab_jv_batch_last_error.argtypes = [vp]
     L.stab_jv_batch_last_error.restype = ctypes.c_char_p
     L.stab_jv_batch_destroy.argtypes = [vp]
@@ -199,8 +202,12 @@ def orthogonalize_noalloc(V, k: int, n: int, w, stream=None):
     L = load()
     hc = np.zeros(2 * max(k, 1))
     nrm = ctypes.c_double()
-    pV = _vec_ptr(V, k * n, "orthogonalize_noalloc V") if k > 0 else _ptr(V)
-    st = L.stab_orthogonalize_noalloc(pV, k, n, _vec_ptr(w, n, "orthogonalize_noalloc w"),
+    if 0 <= k <= 128 and 1 <= n <= (1 << 28):  # sizes the library takes: check the tensors against them
+        pV = _vec_ptr(V, k * n, "orthogonalize_noalloc V") if k > 0 else _ptr(V)
+        pw = _vec_ptr(w, n, "orthogonalize_noalloc w")
+    else:  # the library refuses these sizes before touching memory
+        pV, pw = _ptr(V), _ptr(w)
+    st = L.stab_orthogonalize_noalloc(pV, k, n, pw,
                                       hc.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                                       ctypes.byref(nrm), None if stream is None else stream.cuda_stream)
     if st != 0:
@@ -481,6 +488,55 @@ class JvBatch:
             off += int(x)
         return out, list(nr)
 
+    def solve(self, sigmas, rhs, xs):
+        """Lockstep GMRES: xs[i] = (J_i - sigmas[i] I)^-1 rhs[i]; returns (status, [iterations])."""
+        self._check_open()
+        count = len(self.handles)
+        if len(sigmas) != count or len(rhs) != count or len(xs) != count:
+            raise ValueError("one shift, right-hand side and solution vector per handle")
+        ns = [h.n for h in self.handles]
+        sg = np.zeros(2 * count)
+        for i, z in enumerate(sigmas):
+            sg[2 * i], sg[2 * i + 1] = complex(z).real, complex(z).imag
+        b = (ctypes.c_void_p * count)(*[_vec_ptr(x, n, f"JvBatch.solve rhs[{i}]") for i, (x, n) in enumerate(zip(rhs, ns))])
+        x = (ctypes.c_void_p * count)(*[_vec_ptr(v, n, f"JvBatch.solve x[{i}]") for i, (v, n) in enumerate(zip(xs, ns))])
+        it = (ctypes.c_int * count)()
+        st = self._L.stab_jv_batch_solve(self._b, sg.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), b, x, it)
+        if st not in (0, 4):
+            raise StabError(st, self._L.stab_jv_batch_last_error(self._b).decode())
+        return st, list(it)
+
+    def eigs(self, args, vecs=None):
+        """Lockstep Cayley-IRAM: args[i] = (sigma, tau, nev, ncv, tol[, v0]) for handle i; vecs: None or a
+        list of device tensors (nev x n) or None per instance.  Returns [EigResult]."""
+        self._check_open()
+        count = len(self.handles)
+        if len(args) != count:
+            raise ValueError("one job per handle")
+        jobs = (EigJob * count)()
+        keep = []
+        for i, a in enumerate(args):
+            sigma, tau, nev, ncv, tol = a[:5]
+            v0 = a[5] if len(a) > 5 else None
+            lam = np.zeros(2 * nev)
+            res = np.zeros(nev)
+            keep.append((lam, res))
+            J = jobs[i]
+            J.sigma_re, J.sigma_im = complex(sigma).real, complex(sigma).imag
+            J.tau_re, J.tau_im = complex(tau).real, complex(tau).imag
+            J.nev, J.ncv, J.tol = nev, ncv, tol
+            J.v0 = None if v0 is None else _vec_ptr(v0, self.handles[i].n, f"JvBatch.eigs v0[{i}]")
+            J.lambda_ = lam.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+            J.resid = res.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+            if vecs is not None and vecs[i] is not None:
+                J.vecs = _vec_ptr(vecs[i], nev * self.handles[i].n, f"JvBatch.eigs vecs[{i}]")
+        st = self._L.stab_jv_batch_eigs(self._b, jobs)
+        out = [EigResult(lam.view(np.complex128), res, jobs[i].nconv, jobs[i].status, jobs[i].stats.as_dict())
+               for i, (lam, res) in enumerate(keep)]
+        if st not in (0, 4):
+            raise StabError(st, self._L.stab_jv_batch_last_error(self._b).decode())
+        return out
+
     def close(self):
         if getattr(self, "_b", None) is not None and self._b.value:
             self._L.stab_jv_batch_destroy(self._b)
@@ -496,13 +552,17 @@ class JvBatch:
 class Server:
     """Continuous-batching stability server (stab_server_*) on the current CUDA device."""
 
-    def __init__(self, slots: int, mem_budget_bytes: int, autotune: bool = False):
+    def __init__(self, slots: int, mem_budget_bytes: int, autotune: bool = False, cohort: int = 1):
         self._L = load()
         self._s = ctypes.c_void_p()
         st = self._L.stab_server_create(ctypes.byref(self._s), slots, int(mem_budget_bytes), int(autotune))
         if st != 0:
             raise StabError(st, "stab_server_create failed")
         self._nev = {}
+        if cohort != 1:
+            st = self._L.stab_server_set_cohort(self._s, int(cohort))
+            if st != 0:
+                raise StabError(st, "stab_server_set_cohort: cohort must be in [1, 4096]")
 
     def submit(self, base_flow, grid, Ma: float, Re: float, Pr: float, sigma: complex, tau: complex, nev: int,
                ncv: int, tol: float, vectors: bool = False, **opts) -> int:

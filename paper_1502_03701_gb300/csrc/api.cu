@@ -42,6 +42,7 @@ extern "C" void stab_default_opts(stab_opts* o) {
   o->seed = 0x5EEDULL;
   o->gmres_basis_prec = 64;
   o->stencil_prec = 64;
+  o->lgmres_k = 0;
 }
 
 static void free_handle(stab_handle h) {
@@ -66,7 +67,8 @@ static void free_handle(stab_handle h) {
     dfree(h, h->d_dmat[a]);
   }
   for (cudaEvent_t e : h->timer.ev) cudaEventDestroy(e);
-  if (h->gm_exec) cudaGraphExecDestroy(h->gm_exec);
+  for (cudaGraphExec_t e : h->gm_exec)
+    if (e) cudaGraphExecDestroy(e);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   delete h;
 }
@@ -103,6 +105,14 @@ extern "C" stab_status stab_create(stab_handle* out, const double* base_flow, in
       (o.gmres_basis_prec != 32 && o.gmres_basis_prec != 64) || (o.stencil_prec != 48 && o.stencil_prec != 64)) {
     g_create_err = "stab_create: invalid option value";
     return STAB_ERR_INVALID_ARG;
+  }
+  if (o.lgmres_k < 0 || o.lgmres_k > STAB_MAX_LGMRES_K || (o.lgmres_k > 0 && o.lgmres_k >= o.gmres_m)) {
+    g_create_err = "stab_create: lgmres_k must be in [0, min(8, gmres_m - 1)]";
+    return STAB_ERR_INVALID_ARG;
+  }
+  if (o.lgmres_k > 0 && o.gmres_basis_prec != 64) {
+    g_create_err = "stab_create: LGMRES (lgmres_k > 0) needs the FP64 GMRES basis";
+    return STAB_ERR_UNSUPPORTED;
   }
   stab_handle h = new (std::nothrow) stab_handle_s();
   if (!h) return STAB_ERR_OOM;

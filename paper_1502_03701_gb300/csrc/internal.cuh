@@ -11,6 +11,7 @@
 
 #define STAB_MAX_DIM 3
 #define STAB_MAX_JOBS 16
+#define STAB_MAX_LGMRES_K 8
 
 // ---------------------------------------------------------------------------
 // Compact-scheme line solve tables for one axis (device pointers).
@@ -53,14 +54,14 @@ struct Slots {
 struct GmGraphKey {
   bool valid = false;
   double sigma_re = 0, sigma_im = 0;
-  int eps_mode = -1, m = 0, pc = 0, pprec = 0, basis = 64;
+  int eps_mode = -1, m = 0, pc = 0, pprec = 0, basis = 64, lgk = 0, naug = 0;
   const void* ws = nullptr;
   const void* pinv = nullptr;
   long long n = 0;
   bool operator==(const GmGraphKey& o) const {
     return valid && o.valid && sigma_re == o.sigma_re && sigma_im == o.sigma_im && eps_mode == o.eps_mode &&
            m == o.m && pc == o.pc && pprec == o.pprec && ws == o.ws && pinv == o.pinv && n == o.n &&
-           basis == o.basis;
+           basis == o.basis && lgk == o.lgk && naug == o.naug;
   }
 };
 
@@ -137,8 +138,8 @@ struct StabHandle {
   const int* gate = nullptr;
   bool capturing = false;
   cudaStream_t cap_stream = nullptr;
-  cudaGraphExec_t gm_exec = nullptr;
-  GmGraphKey gm_key;
+  cudaGraphExec_t gm_exec[STAB_MAX_LGMRES_K + 1] = {};  // per number of augmentation vectors (LGMRES)
+  GmGraphKey gm_key[STAB_MAX_LGMRES_K + 1];
   std::string err;
 };
 
@@ -263,6 +264,38 @@ struct BatchImage {
 };
 
 cudaError_t batch_stage(stab_jv_batch_s* B, const BatchImage& im);
+
+// Planned batched phases: the sections of a parameter image (built once,
+// copied to the device once) and the launches that read them.  gates[i]
+// (nullable) skips instance i's work while *gates[i] != 0.
+struct JvBatchPlan {
+  BatchSection norm, temp, line[3][4], point[2];
+  std::vector<double*> zero_eps;  // epsilon slots of the exact-tangent instances
+};
+cudaError_t jv_batch_plan(const std::vector<StabHandle*>& hs, const double2* const* v, double2* const* out,
+                          const double2* shifts, const int* const* gates, BatchImage& im, JvBatchPlan& plan);
+cudaError_t jv_batch_launch(const JvBatchPlan& plan, const unsigned char* d, cudaStream_t st);
+cudaError_t jv_batch_zero_eps(const JvBatchPlan& plan, cudaStream_t st);
+struct NormJob {  // ||v|| into *out with the reduction scratch of handle h
+  StabHandle* h;
+  const double2* v;
+  long long n;
+  double* out;
+  int mode;  // 0: sum of squares, 1: norm
+  const int* gate;
+};
+cudaError_t norm_batch_plan(const std::vector<NormJob>& jobs, BatchImage& im, BatchSection& sec);
+cudaError_t norm_batch_launch(const BatchSection& sec, const unsigned char* d, cudaStream_t st);
+struct PcBatchPlan {
+  BatchSection sec[4];
+};
+cudaError_t pc_batch_plan(const std::vector<StabHandle*>& hs, const double2* const* q, double2* const* z,
+                          const int* const* gates, BatchImage& im, PcBatchPlan& plan);
+cudaError_t pc_batch_launch(const PcBatchPlan& plan, const unsigned char* d, cudaStream_t st);
+struct CgsBatchPlan {
+  BatchSection S, N;
+  size_t sm = 0;
+};
 // Order the batch's stream after the work queued so far on every handle's own
 // stream (begin), and every handle's stream after the batch's launches (end),
 // so that a batch call and single-handle calls on other streams never race on
@@ -277,6 +310,9 @@ struct CgsJob {  // one instance of a batched CGS2 (scratch as for kry_cgs2)
   double2* d_h;
   double* d_norm;
   double2* partial;
+  const int* gate = nullptr;
 };
 cudaError_t kry_cgs2_batch(stab_jv_batch_s* B, const std::vector<CgsJob>& jobs);
+cudaError_t cgs2_batch_plan(const std::vector<CgsJob>& jobs, BatchImage& im, CgsBatchPlan& plan);
+cudaError_t cgs2_batch_launch(const CgsBatchPlan& plan, const unsigned char* d, cudaStream_t st);
 cudaError_t pc_apply_batch(stab_jv_batch_s* B, const double2* const* q, double2* const* z);

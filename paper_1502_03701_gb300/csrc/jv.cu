@@ -992,6 +992,7 @@ struct NormItem {
   unsigned* counter;
   double* out;
   double q0norm, fixed_eps;
+  const int* gate;  // per-instance gate of a batched solver (nullable)
   int mode, pad;
 };
 struct TempItem {
@@ -1026,6 +1027,7 @@ __device__ __forceinline__ void copy_to_shared(void* dst, const void* src, size_
 __global__ void k_norm2_batch(const NormItem* __restrict__ items, const int* __restrict__ start, int count) {
   const int i = batch_item(start, count, blockIdx.x);
   const NormItem it = items[i];
+  if (it.gate && *it.gate) return;
   const unsigned nb = (unsigned)(__ldg(start + i + 1) - __ldg(start + i));
   norm2_body(it.v, it.n, it.partial, it.counter, it.out, it.mode, it.q0norm, it.fixed_eps,
              blockIdx.x - (unsigned)__ldg(start + i), nb);
@@ -1036,6 +1038,7 @@ __global__ void k_temperature_fast_batch(const TempItem* __restrict__ items, con
   const int i = batch_item(start, count, blockIdx.x);
   copy_to_shared(&sI, items + i, sizeof(TempItem));
   __syncthreads();
+  if (sI.P.gate && *sI.P.gate) return;
   const unsigned s0 = (unsigned)__ldg(start + i);
   temperature_fast_body(sI.P, sI.Tw, blockIdx.x - s0, (unsigned)__ldg(start + i + 1) - s0);
 }
@@ -1047,6 +1050,7 @@ __global__ void __launch_bounds__(128, D == 2 ? 4 : 3)
   const int i = batch_item(start, count, blockIdx.x);
   copy_to_shared(&sI, items + i, sizeof(PointItem));
   __syncthreads();
+  if (sI.P.gate && *sI.P.gate) return;
   const unsigned s0 = (unsigned)__ldg(start + i);
   point_fast_body<D>(sI.P, sI.coefp, sI.btab_f, blockIdx.x - s0, (unsigned)__ldg(start + i + 1) - s0);
 }
@@ -1825,9 +1829,13 @@ static cudaError_t jv_batch_attributes() {
   return cudaSuccess;
 }
 
-static cudaError_t jv_batch_apply(stab_jv_batch_s* B, const double2* const* v, double2* const* out, const double* shifts) {
-  const int count = (int)B->hs.size();
-  BatchImage im;
+// Parameter-image sections of one batched J v (every phase, one section per
+// kernel variant) for the instances hs: v[i] -> out[i] = J_i v[i] - shift_i v[i].
+// gates (nullable, or per instance nullable): the instance's work is skipped
+// while *gates[i] != 0 (batched solvers drop converged instances this way).
+cudaError_t jv_batch_plan(const std::vector<StabHandle*>& hs, const double2* const* v, double2* const* out,
+                          const double2* shifts, const int* const* gates, BatchImage& im, JvBatchPlan& plan) {
+  const int count = (int)hs.size();
   // 1. epsilon: one norm item per epsilon-quotient instance
   std::vector<NormItem> norms;
   std::vector<int> norm_blocks;
@@ -1837,8 +1845,10 @@ static cudaError_t jv_batch_apply(stab_jv_batch_s* B, const double2* const* v, d
   // 4. pointwise assembly, per dimension
   std::vector<PointItem> points[2];
   std::vector<int> point_blocks[2];
+  plan.zero_eps.clear();
   for (int i = 0; i < count; ++i) {
-    StabHandle* h = B->hs[i];
+    StabHandle* h = hs[i];
+    const int* gate = gates ? gates[i] : nullptr;
     if (h->opts.eps_mode != 2) {
       long long nb = (h->n + 1023) / 1024;
       nb = std::max<long long>(1, std::min<long long>(nb, h->red_blocks));
@@ -1851,13 +1861,16 @@ static cudaError_t jv_batch_apply(stab_jv_batch_s* B, const double2* const* v, d
       it.q0norm = h->q0norm;
       it.fixed_eps = h->opts.eps;
       it.mode = 2;
+      it.gate = gate;
       norms.push_back(it);
       norm_blocks.push_back((int)nb);
+    } else {
+      plan.zero_eps.push_back(h->d_eps);
     }
     PointParams P = point_params(h, v[i]);
-    P.gate = nullptr;
+    P.gate = gate;
     P.out = out[i];
-    P.shift = shifts ? make_double2(shifts[2 * i], shifts[2 * i + 1]) : make_double2(0.0, 0.0);
+    P.shift = shifts ? shifts[i] : make_double2(0.0, 0.0);
     double2* Tw = h->d_scratch + (long long)h->slots.Tw * h->npts;
     if (h->visc) {
       temps.push_back(TempItem{P, Tw});
@@ -1866,11 +1879,10 @@ static cudaError_t jv_batch_apply(stab_jv_batch_s* B, const double2* const* v, d
     points[h->dim - 2].push_back(PointItem{P, h->d_coef_p, h->d_btab_f});
     point_blocks[h->dim - 2].push_back(grid_for(h->npts, 128));
   }
-  const BatchSection s_norm = im.section(norms, norm_blocks, 256, 0);
-  const BatchSection s_temp = im.section(temps, temp_blocks, 128, 0);
+  plan.norm = im.section(norms, norm_blocks, 256, 0);
+  plan.temp = im.section(temps, temp_blocks, 128, 0);
   // 3. line passes y, z, x; per axis one section per kernel variant (main /
   // compact, FP64 / pair right-hand sides)
-  BatchSection s_line[3][4];
   static const int order[3] = {1, 2, 0};
   for (int q = 0; q < 3; ++q) {
     const int ax = order[q];
@@ -1879,7 +1891,7 @@ static cudaError_t jv_batch_apply(stab_jv_batch_s* B, const double2* const* v, d
     int threads[4] = {0, 0, 0, 0};
     size_t smem[4] = {0, 0, 0, 0};
     for (int i = 0; i < count; ++i) {
-      StabHandle* h = B->hs[i];
+      StabHandle* h = hs[i];
       if (ax >= h->dim) continue;
       const int D = h->dim;
       const double2* src[6];
@@ -1890,6 +1902,7 @@ static cudaError_t jv_batch_apply(stab_jv_batch_s* B, const double2* const* v, d
       if (jobs.empty()) continue;
       PassParams base{};
       base.ff = h->stencil_ff;
+      base.gate = gates ? gates[i] : nullptr;
       PassParams P;
       int thr = 0;
       size_t sm = 0;
@@ -1907,30 +1920,25 @@ static cudaError_t jv_batch_apply(stab_jv_batch_s* B, const double2* const* v, d
       threads[var] = std::max(threads[var], thr);
       smem[var] = std::max(smem[var], sm);
     }
-    for (int k = 0; k < 4; ++k) s_line[q][k] = im.section(items[k], blocks[k], threads[k], smem[k]);
+    for (int k = 0; k < 4; ++k) plan.line[q][k] = im.section(items[k], blocks[k], threads[k], smem[k]);
   }
-  BatchSection s_point[2];
-  for (int d = 0; d < 2; ++d) s_point[d] = im.section(points[d], point_blocks[d], 128, 0);
+  for (int d = 0; d < 2; ++d) plan.point[d] = im.section(points[d], point_blocks[d], 128, 0);
+  return im.overflow ? cudaErrorInvalidValue : cudaSuccess;
+}
 
-  cudaError_t e;
-  if ((e = batch_stage(B, im)) != cudaSuccess) return e;
-  if ((e = batch_order_begin(B)) != cudaSuccess) return e;
-  const unsigned char* d = (const unsigned char*)B->d_buf;
+// The launches of a planned batched J v; d = device copy of the image.
+cudaError_t jv_batch_launch(const JvBatchPlan& plan, const unsigned char* d, cudaStream_t st) {
   auto items_of = [&](const BatchSection& s) { return (const void*)(d + s.items); };
   auto start_of = [&](const BatchSection& s) { return (const int*)(d + s.start); };
-
-  // exact tangent: epsilon is zero
-  for (StabHandle* h : B->hs)
-    if (h->opts.eps_mode == 2 && h->last_eps_mode != 2) k_set_scalar<<<1, 1, 0, B->stream>>>(h->d_eps, 0.0);
-  cudaStream_t st = B->stream;
-  if (s_norm.count)
-    k_norm2_batch<<<s_norm.blocks, 256, 0, st>>>((const NormItem*)items_of(s_norm), start_of(s_norm), s_norm.count);
-  if (s_temp.count)
-    k_temperature_fast_batch<<<s_temp.blocks, 128, 0, st>>>((const TempItem*)items_of(s_temp), start_of(s_temp),
-                                                            s_temp.count);
+  if (plan.norm.count)
+    k_norm2_batch<<<plan.norm.blocks, 256, 0, st>>>((const NormItem*)items_of(plan.norm), start_of(plan.norm),
+                                                    plan.norm.count);
+  if (plan.temp.count)
+    k_temperature_fast_batch<<<plan.temp.blocks, 128, 0, st>>>((const TempItem*)items_of(plan.temp),
+                                                               start_of(plan.temp), plan.temp.count);
   for (int q = 0; q < 3; ++q)
     for (int k = 0; k < 4; ++k) {
-      const BatchSection& s = s_line[q][k];
+      const BatchSection& s = plan.line[q][k];
       if (!s.count) continue;
       const PassParams* it = (const PassParams*)items_of(s);
       if (k == 0) k_line_pass_batch<false><<<s.blocks, s.threads, s.smem, st>>>(it, start_of(s), s.count);
@@ -1938,17 +1946,71 @@ static cudaError_t jv_batch_apply(stab_jv_batch_s* B, const double2* const* v, d
       else if (k == 2) k_line_pass_compact_batch<false><<<s.blocks, s.threads, s.smem, st>>>(it, start_of(s), s.count);
       else k_line_pass_compact_batch<true><<<s.blocks, s.threads, s.smem, st>>>(it, start_of(s), s.count);
     }
-  if (s_point[0].count)
-    k_point_fast_batch<2><<<s_point[0].blocks, 128, 0, st>>>((const PointItem*)items_of(s_point[0]),
-                                                            start_of(s_point[0]), s_point[0].count);
-  if (s_point[1].count)
-    k_point_fast_batch<3><<<s_point[1].blocks, 128, 0, st>>>((const PointItem*)items_of(s_point[1]),
-                                                            start_of(s_point[1]), s_point[1].count);
+  if (plan.point[0].count)
+    k_point_fast_batch<2><<<plan.point[0].blocks, 128, 0, st>>>((const PointItem*)items_of(plan.point[0]),
+                                                               start_of(plan.point[0]), plan.point[0].count);
+  if (plan.point[1].count)
+    k_point_fast_batch<3><<<plan.point[1].blocks, 128, 0, st>>>((const PointItem*)items_of(plan.point[1]),
+                                                               start_of(plan.point[1]), plan.point[1].count);
+  return cudaGetLastError();
+}
+
+// Batched ||v|| (mode 1) or ||v||^2 (mode 0): each job with its handle's
+// reduction partials and block count, so each result equals launch_norm2's.
+cudaError_t norm_batch_plan(const std::vector<NormJob>& jobs, BatchImage& im, BatchSection& sec) {
+  std::vector<NormItem> items;
+  std::vector<int> blocks;
+  for (const NormJob& J : jobs) {
+    StabHandle* h = J.h;
+    long long nb = (J.n + 1023) / 1024;
+    nb = std::max<long long>(1, std::min<long long>(nb, h->red_blocks));
+    NormItem it{};
+    it.v = J.v;
+    it.n = J.n;
+    it.partial = h->d_red;
+    it.counter = (unsigned*)(h->d_red + h->red_blocks + 8);
+    it.out = J.out;
+    it.q0norm = h->q0norm;
+    it.fixed_eps = h->opts.eps;
+    it.mode = J.mode;
+    it.gate = J.gate;
+    items.push_back(it);
+    blocks.push_back((int)nb);
+  }
+  sec = im.section(items, blocks, 256, 0);
+  return im.overflow ? cudaErrorInvalidValue : cudaSuccess;
+}
+
+cudaError_t norm_batch_launch(const BatchSection& sec, const unsigned char* d, cudaStream_t st) {
+  if (!sec.count) return cudaSuccess;
+  k_norm2_batch<<<sec.blocks, 256, 0, st>>>((const NormItem*)(d + sec.items), (const int*)(d + sec.start), sec.count);
+  return cudaGetLastError();
+}
+
+// Epsilon of the exact-tangent instances is zero (set once before their J v).
+cudaError_t jv_batch_zero_eps(const JvBatchPlan& plan, cudaStream_t st) {
+  for (double* e : plan.zero_eps) k_set_scalar<<<1, 1, 0, st>>>(e, 0.0);
+  return cudaGetLastError();
+}
+
+static cudaError_t jv_batch_apply(stab_jv_batch_s* B, const double2* const* v, double2* const* out, const double* shifts) {
+  BatchImage im;
+  JvBatchPlan plan;
+  std::vector<double2> sh;
+  if (shifts)
+    for (size_t i = 0; i < B->hs.size(); ++i) sh.push_back(make_double2(shifts[2 * i], shifts[2 * i + 1]));
+  cudaError_t e = jv_batch_plan(B->hs, v, out, shifts ? sh.data() : nullptr, nullptr, im, plan);
+  if (e != cudaSuccess) return e;
+  if ((e = batch_stage(B, im)) != cudaSuccess) return e;
+  if ((e = batch_order_begin(B)) != cudaSuccess) return e;
+  // exact tangent: epsilon is zero
+  for (StabHandle* h : B->hs)
+    if (h->opts.eps_mode == 2 && h->last_eps_mode != 2) k_set_scalar<<<1, 1, 0, B->stream>>>(h->d_eps, 0.0);
+  if ((e = jv_batch_launch(plan, (const unsigned char*)B->d_buf, B->stream)) != cudaSuccess) return e;
   for (StabHandle* h : B->hs) {
     h->last_eps_mode = h->opts.eps_mode;
     h->stats.jv_calls++;
   }
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
   return batch_order_end(B);
 }
 

@@ -387,6 +387,7 @@ struct CgsItem {
   double2* d_h;
   double* np;
   double* d_norm;
+  const int* gate;  // per-instance gate of a batched solver (nullable)
   long long n;
   int k, nb;
 };
@@ -406,6 +407,7 @@ __global__ void __launch_bounds__(kThreads) k_cgs2_a_batch(const CgsItem* __rest
                                                           const int* __restrict__ start, int count) {
   const int i = cgs_item(start, count, blockIdx.x);
   const CgsItem it = items[i];
+  if (it.gate && *it.gate) return;
   cgs2_a_body(it.V, it.k, it.n, it.w, it.p1, blockIdx.x - (unsigned)__ldg(start + i), (unsigned)it.nb);
 }
 
@@ -413,6 +415,7 @@ __global__ void __launch_bounds__(kThreads) k_cgs2_b_batch(const CgsItem* __rest
                                                           const int* __restrict__ start, int count) {
   const int i = cgs_item(start, count, blockIdx.x);
   const CgsItem it = items[i];
+  if (it.gate && *it.gate) return;
   cgs2_b_body(it.V, it.k, it.n, it.w, it.p1, it.p2, it.d_h, blockIdx.x - (unsigned)__ldg(start + i),
               (unsigned)it.nb);
 }
@@ -421,6 +424,7 @@ __global__ void __launch_bounds__(kThreads) k_cgs2_c_batch(const CgsItem* __rest
                                                           const int* __restrict__ start, int count) {
   const int i = cgs_item(start, count, blockIdx.x);
   const CgsItem it = items[i];
+  if (it.gate && *it.gate) return;
   cgs2_c_body(it.V, it.k, it.n, it.w, it.p2, it.d_h, it.np, blockIdx.x - (unsigned)__ldg(start + i),
               (unsigned)it.nb);
 }
@@ -429,6 +433,7 @@ __global__ void __launch_bounds__(kThreads) k_cgs2_c_batch(const CgsItem* __rest
 __global__ void k_norm_final_batch(const CgsItem* __restrict__ items, int count) {
   if ((int)blockIdx.x >= count) return;
   const CgsItem it = items[blockIdx.x];
+  if (it.gate && *it.gate) return;
   norm_final_body(it.np, it.nb, it.d_norm);
 }
 
@@ -822,11 +827,8 @@ cudaError_t kry_cgs2_stream(cudaStream_t st, const double2* V, int k, long long 
   return launch_norm2_stream(st, w, n, norm_partial, norm_blocks, d_norm);
 }
 
-// Batched CGS2: w_i <- (I - V_i V_i^H)^2 w_i for every job, one launch per
-// step for all of them on the batch's stream.  Job i uses the same scratch
-// layout and block count as kry_cgs2 (k >= 1), so its results are those of
-// the single call.
-cudaError_t kry_cgs2_batch(stab_jv_batch_s* B, const std::vector<CgsJob>& jobs) {
+// Parameter image of a batched CGS2 (job i gated by J.gate) and its launches.
+cudaError_t cgs2_batch_plan(const std::vector<CgsJob>& jobs, BatchImage& im, CgsBatchPlan& plan) {
   std::vector<CgsItem> items;
   std::vector<int> blocks, ones;
   size_t sm = 0;
@@ -841,6 +843,7 @@ cudaError_t kry_cgs2_batch(stab_jv_batch_s* B, const std::vector<CgsJob>& jobs) 
     it.np = (double*)(it.p2 + (size_t)nb * J.k);
     it.d_h = J.d_h;
     it.d_norm = J.d_norm;
+    it.gate = J.gate;
     it.n = J.n;
     it.k = J.k;
     it.nb = nb;
@@ -849,19 +852,34 @@ cudaError_t kry_cgs2_batch(stab_jv_batch_s* B, const std::vector<CgsJob>& jobs) 
     ones.push_back(1);
     sm = std::max(sm, (size_t)J.k * (sizeof(double2) + 2 * sizeof(ffn)));
   }
+  plan.S = im.section(items, blocks, kThreads, sm);
+  plan.N = im.section(items, ones, 32, 0);
+  plan.sm = sm;
+  return im.overflow ? cudaErrorInvalidValue : cudaSuccess;
+}
+
+cudaError_t cgs2_batch_launch(const CgsBatchPlan& plan, const unsigned char* d, cudaStream_t st) {
+  if (!plan.S.count) return cudaSuccess;
+  const CgsItem* it = (const CgsItem*)(d + plan.S.items);
+  const int* sp = (const int*)(d + plan.S.start);
+  k_cgs2_a_batch<<<plan.S.blocks, kThreads, 0, st>>>(it, sp, plan.S.count);
+  k_cgs2_b_batch<<<plan.S.blocks, kThreads, plan.sm, st>>>(it, sp, plan.S.count);
+  k_cgs2_c_batch<<<plan.S.blocks, kThreads, plan.sm, st>>>(it, sp, plan.S.count);
+  k_norm_final_batch<<<plan.N.count, 32, 0, st>>>((const CgsItem*)(d + plan.N.items), plan.N.count);
+  return cudaGetLastError();
+}
+
+// Batched CGS2: w_i <- (I - V_i V_i^H)^2 w_i for every job, one launch per
+// step for all of them on the batch's stream.  Job i uses the same scratch
+// layout and block count as kry_cgs2 (k >= 1), so its results are those of
+// the single call.
+cudaError_t kry_cgs2_batch(stab_jv_batch_s* B, const std::vector<CgsJob>& jobs) {
   BatchImage im;
-  const BatchSection S = im.section(items, blocks, kThreads, sm);
-  const BatchSection N = im.section(items, ones, 32, 0);
-  cudaError_t e = batch_stage(B, im);
+  CgsBatchPlan plan;
+  cudaError_t e = cgs2_batch_plan(jobs, im, plan);
   if (e != cudaSuccess) return e;
+  if ((e = batch_stage(B, im)) != cudaSuccess) return e;
   if ((e = batch_order_begin(B)) != cudaSuccess) return e;
-  const unsigned char* d = (const unsigned char*)B->d_buf;
-  const CgsItem* it = (const CgsItem*)(d + S.items);
-  const int* st = (const int*)(d + S.start);
-  k_cgs2_a_batch<<<S.blocks, kThreads, 0, B->stream>>>(it, st, S.count);
-  k_cgs2_b_batch<<<S.blocks, kThreads, sm, B->stream>>>(it, st, S.count);
-  k_cgs2_c_batch<<<S.blocks, kThreads, sm, B->stream>>>(it, st, S.count);
-  k_norm_final_batch<<<N.count, 32, 0, B->stream>>>((const CgsItem*)(d + N.items), N.count);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if ((e = cgs2_batch_launch(plan, (const unsigned char*)B->d_buf, B->stream)) != cudaSuccess) return e;
   return batch_order_end(B);
 }

@@ -443,6 +443,7 @@ __global__ void k_apply_batch(const ApplyItem* __restrict__ items, const int* __
   const unsigned long long* src = (const unsigned long long*)(items + lo);
   for (int k = threadIdx.x; k < (int)(sizeof(ApplyItem) / 8); k += blockDim.x) ((unsigned long long*)&sI)[k] = __ldg(src + k);
   __syncthreads();
+  if (sI.P.gate && *sI.P.gate) return;
   const long long local = (long long)blockIdx.x - __ldg(start + lo);
   const long long nt = sI.ntiles;
   const unsigned nslices = (unsigned)((__ldg(start + lo + 1) - __ldg(start + lo)) / nt);
@@ -673,15 +674,16 @@ extern "C" stab_status stab_precond_block(stab_handle hh, double sr, double si, 
   return STAB_OK;
 }
 
-// Batched block apply: one launch per storage layout for all handles of B.
-cudaError_t pc_apply_batch(stab_jv_batch_s* B, const double2* const* q, double2* const* z) {
-  const int count = (int)B->hs.size();
+// Batched block apply: one launch per storage layout for all instances.
+cudaError_t pc_batch_plan(const std::vector<StabHandle*>& hs, const double2* const* q, double2* const* z,
+                          const int* const* gates, BatchImage& im, PcBatchPlan& plan) {
+  const int count = (int)hs.size();
   std::vector<ApplyItem> items[4];
   std::vector<int> blocks[4];
   int threads[4] = {0, 0, 0, 0};
   size_t smem[4] = {0, 0, 0, 0};
   for (int i = 0; i < count; ++i) {
-    StabHandle* h = B->hs[i];
+    StabHandle* h = hs[i];
     if (!h->pvalid) return cudaErrorInvalidValue;
     Geo g;
     tile_geo(h, g);
@@ -690,7 +692,7 @@ cudaError_t pc_apply_batch(stab_jv_batch_s* B, const double2* const* q, double2*
     P.q = q[i]; P.z = z[i]; P.inv = h->d_pinv; P.q32 = nullptr;
     P.nx = h->nx; P.ny = h->ny; P.tx = g.tx; P.ty = g.ty; P.tz = g.tz; P.ntx = g.ntx; P.nty = g.nty;
     P.ntpts = g.ntpts; P.bsz = g.bsz; P.npts = h->npts;
-    P.gate = nullptr;
+    P.gate = gates ? gates[i] : nullptr;
     it.ntiles = g.ntiles;
     // the same slices and threads as the single-handle apply
     int slices = (int)((2 * 152 + g.ntiles - 1) / g.ntiles);
@@ -716,24 +718,32 @@ cudaError_t pc_apply_batch(stab_jv_batch_s* B, const double2* const* q, double2*
     threads[var] = std::max(threads[var], thr);
     smem[var] = std::max(smem[var], sm);
   }
-  BatchImage im;
-  BatchSection sec[4];
-  for (int v = 0; v < 4; ++v) sec[v] = im.section(items[v], blocks[v], threads[v], smem[v]);
-  cudaError_t e = batch_stage(B, im);
-  if (e != cudaSuccess) return e;
-  if ((e = batch_order_begin(B)) != cudaSuccess) return e;
-  const unsigned char* d = (const unsigned char*)B->d_buf;
+  for (int v = 0; v < 4; ++v) plan.sec[v] = im.section(items[v], blocks[v], threads[v], smem[v]);
+  return im.overflow ? cudaErrorInvalidValue : cudaSuccess;
+}
+
+cudaError_t pc_batch_launch(const PcBatchPlan& plan, const unsigned char* d, cudaStream_t st) {
   for (int v = 0; v < 4; ++v) {
-    const BatchSection& S = sec[v];
+    const BatchSection& S = plan.sec[v];
     if (!S.count) continue;
     const ApplyItem* it = (const ApplyItem*)(d + S.items);
-    const int* st = (const int*)(d + S.start);
-    if (v == 0) k_apply_batch<0><<<S.blocks, S.threads, S.smem, B->stream>>>(it, st, S.count);
-    else if (v == 1) k_apply_batch<1><<<S.blocks, S.threads, S.smem, B->stream>>>(it, st, S.count);
-    else if (v == 2) k_apply_batch<2><<<S.blocks, S.threads, S.smem, B->stream>>>(it, st, S.count);
-    else k_apply_batch<3><<<S.blocks, S.threads, S.smem, B->stream>>>(it, st, S.count);
+    const int* sp = (const int*)(d + S.start);
+    if (v == 0) k_apply_batch<0><<<S.blocks, S.threads, S.smem, st>>>(it, sp, S.count);
+    else if (v == 1) k_apply_batch<1><<<S.blocks, S.threads, S.smem, st>>>(it, sp, S.count);
+    else if (v == 2) k_apply_batch<2><<<S.blocks, S.threads, S.smem, st>>>(it, sp, S.count);
+    else k_apply_batch<3><<<S.blocks, S.threads, S.smem, st>>>(it, sp, S.count);
   }
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+cudaError_t pc_apply_batch(stab_jv_batch_s* B, const double2* const* q, double2* const* z) {
+  BatchImage im;
+  PcBatchPlan plan;
+  cudaError_t e = pc_batch_plan(B->hs, q, z, nullptr, im, plan);
+  if (e != cudaSuccess) return e;
+  if ((e = batch_stage(B, im)) != cudaSuccess) return e;
+  if ((e = batch_order_begin(B)) != cudaSuccess) return e;
+  if ((e = pc_batch_launch(plan, (const unsigned char*)B->d_buf, B->stream)) != cudaSuccess) return e;
   return batch_order_end(B);
 }
 

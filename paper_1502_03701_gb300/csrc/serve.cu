@@ -54,6 +54,8 @@ extern "C" long long stab_estimate_bytes(const stab_grid* g, const stab_opts* op
   b += (nv + 1) * npts * 16;                               // set-up temporary
   const long long m = o.gmres_m, pc = o.precond == 1;
   if (o.gmres_basis_prec == 32) b += (m + 1) * n * 8 + 6 * n * 16;  // FP32 basis; r, b, x, w, z, t
+  else if (o.lgmres_k > 0) b += ((m + 1) + m + 3 + 2 * (long long)o.lgmres_k + 1) * n * 16;  // LGMRES: V, Z, r, b,
+                                                                                       // x, (z, A z) pairs, dz
   else b += ((m + 1) + pc * m + 3) * n * 16;               // GMRES basis, Z, r, b, x
   b += 2 * 608 * (m + 2) * 16;                             // CGS2 partial sums
   b += ((long long)ncv + 2 + nev + 1) * n * 16;            // Arnoldi basis, f, x, restart temporary
@@ -159,6 +161,7 @@ struct ServerReq {
 struct stab_server_s {
   int device = 0;
   int slots = 1;
+  int cohort = 1;  // requests a worker takes at once and solves in lockstep (stab_jv_batch_eigs)
   long long budget = 0;
   int autotune = 0;
   std::mutex mu;
@@ -219,32 +222,129 @@ void serve_one(stab_server_s* S, ServerReq* R, cudaStream_t st) {
   stab_destroy(h);
 }
 
+// A cohort of requests taken at once by one worker: those whose handles can
+// be batched (base flow varying in y only, FP64 GMRES basis, no LGMRES) are
+// solved together by stab_jv_batch_eigs (every phase one launch for the
+// cohort), the others one after the other.
+void serve_cohort(stab_server_s* S, std::vector<ServerReq*>& C, cudaStream_t st) {
+  if (C.size() == 1) {
+    serve_one(S, C[0], st);
+    return;
+  }
+  std::vector<stab_handle> hs(C.size(), nullptr);
+  std::vector<void*> dvecs(C.size(), nullptr);
+  std::vector<size_t> vbytes(C.size(), 0);
+  std::vector<int> batched;
+  for (size_t i = 0; i < C.size(); ++i) {
+    ServerReq* R = C[i];
+    R->lambda.assign(2 * (size_t)R->nev, 0.0);
+    R->resid.assign(R->nev, 0.0);
+    stab_status s = stab_create(&hs[i], R->q0.data(), 0, &R->grid, R->Ma, R->Re, R->Pr, &R->opts, st);
+    if (s != STAB_OK) {
+      R->status = s;
+      R->err = stab_last_error(nullptr);
+      hs[i] = nullptr;
+      continue;
+    }
+    if (S->autotune) stab_autotune(hs[i], 0, nullptr, nullptr);
+    vbytes[i] = (size_t)R->nev * stab_size(hs[i]) * 2 * sizeof(double);
+    if (R->vecs_host && cudaMallocAsync(&dvecs[i], vbytes[i], st) != cudaSuccess) {
+      R->status = STAB_ERR_OOM;
+      R->err = "eigenvector buffer";
+      dvecs[i] = nullptr;
+      stab_destroy(hs[i]);
+      hs[i] = nullptr;
+      continue;
+    }
+    const StabHandle* h = (const StabHandle*)hs[i];
+    if (h->homog && h->d_coef && !h->force_dn_path && h->opts.gmres_basis_prec == 64 && h->opts.lgmres_k == 0)
+      batched.push_back((int)i);
+  }
+  if (batched.size() >= 2) {
+    std::vector<stab_handle> bh;
+    std::vector<stab_eig_job> jobs(batched.size());
+    for (size_t q = 0; q < batched.size(); ++q) {
+      const int i = batched[q];
+      ServerReq* R = C[i];
+      bh.push_back(hs[i]);
+      stab_eig_job& J = jobs[q];
+      std::memset(&J, 0, sizeof(J));
+      J.sigma_re = R->sr; J.sigma_im = R->si; J.tau_re = R->tr; J.tau_im = R->ti;
+      J.nev = R->nev; J.ncv = R->ncv; J.tol = R->tol;
+      J.lambda = R->lambda.data();
+      J.resid = R->resid.data();
+      J.vecs = dvecs[i];
+    }
+    stab_jv_batch B = nullptr;
+    stab_status s = stab_jv_batch_create(&B, bh.data(), (int)bh.size(), st);
+    if (s == STAB_OK) {
+      stab_jv_batch_eigs(B, jobs.data());
+      const std::string msg = stab_jv_batch_last_error(B);
+      stab_jv_batch_destroy(B);
+      for (size_t q = 0; q < batched.size(); ++q) {
+        ServerReq* R = C[batched[q]];
+        R->status = jobs[q].status;
+        R->nconv = jobs[q].nconv;
+        R->stats = jobs[q].stats;
+        if (R->status != STAB_OK) R->err = msg;
+      }
+    } else {
+      batched.clear();  // solved one by one below
+    }
+  } else {
+    batched.clear();
+  }
+  for (size_t i = 0; i < C.size(); ++i) {
+    ServerReq* R = C[i];
+    if (!hs[i]) continue;
+    if (std::find(batched.begin(), batched.end(), (int)i) == batched.end()) {
+      R->status = stab_eigs(hs[i], R->sr, R->si, R->tr, R->ti, R->nev, R->ncv, R->tol, nullptr, R->lambda.data(),
+                            dvecs[i], R->resid.data(), &R->nconv, &R->stats);
+      if (R->status != STAB_OK) R->err = stab_last_error(hs[i]);
+    }
+    if (dvecs[i]) {
+      if (R->status == STAB_OK || R->status == STAB_ERR_NOT_CONVERGED)
+        cudaMemcpyAsync(R->vecs_host, dvecs[i], vbytes[i], cudaMemcpyDeviceToHost, st);
+      cudaFreeAsync(dvecs[i], st);
+    }
+  }
+  cudaStreamSynchronize(st);
+  for (stab_handle h : hs)
+    if (h) stab_destroy(h);
+}
+
 void worker_main(stab_server_s* S) {
   cudaSetDevice(S->device);
   cudaStream_t st = nullptr;
   cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
   for (;;) {
-    ServerReq* R = nullptr;
+    std::vector<ServerReq*> C;
     {
       std::unique_lock<std::mutex> lk(S->mu);
-      // admission: first come, first served; the head waits until its memory fits
+      // admission: first come, first served; the head waits until its memory fits, then (cohort > 1)
+      // the requests queued behind it join while their memory fits
       S->cv.wait(lk, [&] { return S->stop || (!S->queue.empty() && S->in_use + S->queue.front()->est <= S->budget); });
       if (S->stop) break;  // stab_server_destroy has emptied the queue
-      R = S->queue.front();
-      S->queue.pop_front();
-      S->in_use += R->est;
+      do {
+        ServerReq* R = S->queue.front();
+        S->queue.pop_front();
+        S->in_use += R->est;
+        S->running++;
+        R->t_start = Clock::now();
+        C.push_back(R);
+      } while ((int)C.size() < S->cohort && !S->queue.empty() && S->in_use + S->queue.front()->est <= S->budget);
       S->peak_in_use = std::max(S->peak_in_use, S->in_use);
-      S->running++;
       S->peak_running = std::max(S->peak_running, S->running);
-      R->t_start = Clock::now();
     }
-    serve_one(S, R, st);
+    serve_cohort(S, C, st);
     {
       std::lock_guard<std::mutex> lk(S->mu);
-      R->t_end = Clock::now();
-      R->done = true;
-      S->in_use -= R->est;
-      S->running--;
+      for (ServerReq* R : C) {
+        R->t_end = Clock::now();
+        R->done = true;
+        S->in_use -= R->est;
+        S->running--;
+      }
     }
     S->cv.notify_all();
     S->done_cv.notify_all();
@@ -270,6 +370,13 @@ extern "C" stab_status stab_server_create(stab_server* out, int slots, long long
   S->autotune = autotune;
   for (int i = 0; i < slots; ++i) S->workers.emplace_back(worker_main, S);
   *out = S;
+  return STAB_OK;
+}
+
+extern "C" stab_status stab_server_set_cohort(stab_server S, int cohort) {
+  if (!S || cohort < 1 || cohort > 4096) return STAB_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(S->mu);
+  S->cohort = cohort;
   return STAB_OK;
 }
 

@@ -189,3 +189,68 @@ def test_fp32_basis_preconditioned_gmres_and_eigs(orc):
         assert np.abs(r.lam - l).min() < 1e-8 * abs(l)
     assert r.resid.max() < 1e-8
     S.close()
+
+
+@pytest.mark.parametrize("sigma,k", [(0.25, 2), (0.1 + 0.3j, 4)])
+def test_lgmres_solution_against_dense_solve_and_oracle(orc, sigma, k):
+    """LGMRES (augmented restarts, Sec. Iterative solvers) on the 8 x 16
+    layer: the solution meets the tolerance against the dense operator,
+    equals the dense solve, and takes the oracle LGMRES's number of J v
+    products (the augmentation steps take none)."""
+    import torch
+    m = 12
+    S, g, f, q0 = _stab(8, 16, eps_mode=2, gmres_m=m, lgmres_k=k, gmres_tol=1e-12, gmres_max_restarts=2000)
+    J = orc.core.dense_jacobian(orc.Problem.from_inputs(g, f), q0)
+    A = J - sigma * np.eye(g.n)
+    b = si.random_complex(78, g.n)
+    x = torch.zeros(g.n, dtype=torch.complex128, device="cuda")
+    before = S.stats()["jv_calls"]
+    st, iters = S.solve(sigma, torch.from_numpy(b).cuda(), x)
+    jv = S.stats()["jv_calls"] - before
+    S.close()
+    assert st == 0 and iters > 0
+    xh = x.cpu().numpy()
+    assert np.linalg.norm(b - A @ xh) <= 1.05e-12 * np.linalg.norm(b)
+    assert rel_err(xh, sla.solve(A, b)) < 1e-7
+    xo, so = orc.krylov.lgmres(lambda z: A @ z, b, None, m=m, k=k, tol=1e-12, max_restarts=2000)
+    assert so.converged
+    assert abs(jv - so.matvecs) <= max(m, so.matvecs // 20), (jv, so.matvecs)
+
+
+def test_lgmres_preconditioned_above_16k_and_eigs(orc):
+    """LGMRES with block-Jacobi on 64 x 64 (16,384 unknowns, selective
+    reorthogonalisation): the true residual, measured with the oracle's
+    tangent J v, meets the tolerance; Cayley-IRAM with LGMRES inner solves
+    finds the dense LAPACK eigenvalues of the 8 x 16 layer."""
+    import torch
+    g, f = si.mixing_layer_2d(64, 64)
+    from paper_1502_03701_gb300 import Stab
+    q0 = si.tanh_base_flow(g, f)
+    S = Stab(q0, g, f.Ma, f.Re, f.Pr, eps_mode=2, precond=1, tile=(8, 8), gmres_m=40, lgmres_k=3,
+             gmres_tol=1e-10, gmres_max_restarts=400)
+    b = si.random_complex(92, g.n)
+    x = torch.zeros(g.n, dtype=torch.complex128, device="cuda")
+    st, iters = S.solve(0.5 + 0.2j, torch.from_numpy(b).cuda(), x)
+    S.close()
+    assert st == 0
+    xh = x.cpu().numpy()
+    P = orc.Problem.from_inputs(g, f)
+    r = b - (orc.core.jv(P, q0, xh, "tangent") - (0.5 + 0.2j) * xh)
+    assert np.linalg.norm(r) <= 1.1e-10 * np.linalg.norm(b)
+    S, g, f, q0 = _stab(8, 16, eps_mode=2, gmres_m=20, lgmres_k=2, gmres_tol=1e-12, gmres_max_restarts=400)
+    J = orc.core.dense_jacobian(orc.Problem.from_inputs(g, f), q0)
+    ref, _ = orc.stability.dense_reference(J, 0.25, -1.0, 2)
+    res = S.eigs(0.25, -1.0, nev=2, ncv=12, tol=1e-11)
+    S.close()
+    assert res.status == 0 and res.nconv == 2
+    for l in ref:
+        assert np.abs(res.lam - l).min() < 1e-8 * abs(l)
+    assert res.resid.max() < 1e-8
+
+
+def test_lgmres_option_checks():
+    from paper_1502_03701_gb300 import StabError
+    with pytest.raises(StabError, match="INVALID_ARG"):
+        _stab(8, 16, gmres_m=4, lgmres_k=4)
+    with pytest.raises(StabError, match="UNSUPPORTED"):
+        _stab(8, 16, gmres_m=10, lgmres_k=2, gmres_basis_prec=32)

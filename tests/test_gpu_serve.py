@@ -120,3 +120,25 @@ def test_server_admits_by_memory(alone):
     with pytest.raises(StabError):
         srv.wait(12345, 0.0)
     srv.close()
+
+
+def test_server_lockstep_cohort_same_as_alone(alone):
+    """With lockstep cohorts, one worker takes all four queued requests and
+    solves them together (stab_jv_batch_eigs: every phase one launch for the
+    cohort); each result equals the request's lone solve to 1e-12."""
+    from paper_1502_03701_gb300 import Server
+    srv = Server(slots=1, mem_budget_bytes=8 << 30, cohort=4)
+    ids = []
+    for i, p in enumerate(PROBLEMS):
+        g, f, q0 = _problem(*p)
+        ids.append(srv.submit(q0, g, f.Ma, f.Re, f.Pr, *EIG, vectors=(i == 1), **OPTS))
+    for rid, ref, p in zip(ids, alone, PROBLEMS):
+        assert srv.wait(rid, 600.0)
+        got, res, info = srv.result(rid)
+        assert info["status"] == 0 and info["nconv"] == EIG[2], p
+        assert _same(got, res, ref), (p, got, ref)
+        if "vecs" in info:
+            assert np.allclose(np.linalg.norm(info["vecs"], axis=1), 1.0, atol=1e-12)
+    st = srv.stats()
+    assert st["peak_running"] >= 2  # the cohort's requests ran together on the one worker
+    srv.close()
