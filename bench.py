@@ -186,6 +186,13 @@ def cpu_baseline_eigs(g, f, q0, jv_calls: float, nconv: float, budget_s: float =
 
 
 def _cpu_model() -> str:
+    try:  # lscpu names Arm cores (Neoverse-...); /proc/cpuinfo only carries part numbers there
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
     try:
         for line in open("/proc/cpuinfo"):
             if line.lower().startswith(("model name", "cpu part", "hardware")):
@@ -349,6 +356,32 @@ def gmres_throughput(args, Stab, torch, q0, g, f):
     r.update({"sigma": sigma, "tile": [8, 8], "block": 256, "precond": "FP32 inverses", "bf16": out["bf16_inverses"],
               "bf16_fp32_basis": out["bf16_inverses_fp32_basis"]})
     return r
+
+
+def precond_build_256x512(args, Stab, torch) -> dict:
+    """Block-Jacobi build on the 256 x 512 layer (assembly + inversion of every tile block, FP32
+    inverses): Gauss-Jordan on the CUDA cores against the blocked sweep with tensor-core GEMMs
+    (BF16x9-emulated FP32 and TF32), for 8 x 8 tiles (2,048 blocks of 256) and 16 x 16 tiles (512 of
+    1,024).  Inversion work: b^3 complex multiply-adds per block = 8 b^3 real flops."""
+    g, f, q0 = _layer(256, 512, 0.3)
+    out = {}
+    for tile in ((8, 8), (16, 16)):
+        b = 4 * tile[0] * tile[1]
+        nblk = g.npts // (tile[0] * tile[1])
+        flops = 8.0 * b ** 3 * nblk
+        row = {"block": b, "blocks": nblk, "inversion_flop": flops}
+        for fac, key in ((0, "cuda_cores"), (1, "tensor_bf16x9"), (2, "tensor_tf32")):
+            S = Stab(q0, g, f.Ma, f.Re, f.Pr, eps_mode=2, precond=1, tile=tile, precond_prec=32, precond_factor=fac)
+            S.precond_build(1.0)  # warm (cuBLAS handle, workspaces)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            S.precond_build(1.0 + 1e-3j)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            S.close()
+            row[key] = {"seconds": dt, "TFLOP_per_s": flops / dt / 1e12}
+        out[f"{tile[0]}x{tile[1]}"] = row
+    return out
 
 
 # Algorithmic FP64 flops of the compact line pass per real output value (FMA = 2):
@@ -747,6 +780,7 @@ def run_ours(args):
         if args.gmres_restarts > 0:
             g2, f2, q2 = _layer(256, 512, 0.3)
             extra["gmres_256x512"] = gmres_throughput(args, Stab, torch, q2, g2, f2)
+            extra["precond_build_256x512"] = precond_build_256x512(args, Stab, torch)
         if args.fleet > 0 and world == 1:
             extra["jv_batch_64"] = jv_batch_64(args, torch)
             extra["many_small"] = fleet(args, torch)

@@ -87,6 +87,12 @@ typedef struct {
                              followed by the k latest error approximations x_{c+1} - x_c of earlier cycles,
                              which enter without a J v (their products are the residual differences).
                              Needs gmres_basis_prec = 64 (else STAB_ERR_UNSUPPORTED) */
+  int precond_factor;     /* inversion of the FP32 block-Jacobi blocks (precond_prec 32 or 16): 0 = Gauss-Jordan
+                             with partial pivoting on the CUDA cores (default); 1 = the same elimination blocked
+                             in panels of 32 (64 from 512 rows) columns, every panel's update of the other
+                             columns one batched complex GEMM on the tensor cores with FP32 inputs emulated in
+                             BF16 (FP32 accuracy); 2 = the same with TF32 inputs (about 1e-3 relative).
+                             precond_prec 64 always uses the CUDA cores */
 } stab_opts;
 
 typedef struct {

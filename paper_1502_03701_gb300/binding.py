@@ -52,7 +52,8 @@ class Opts(ctypes.Structure):
                 ("gmres_max_restarts", ctypes.c_int), ("gmres_tol", ctypes.c_double), ("precond", ctypes.c_int),
                 ("tile", ctypes.c_int * 3), ("precond_prec", ctypes.c_int), ("max_restarts", ctypes.c_int),
                 ("seed", ctypes.c_ulonglong), ("gmres_basis_prec", ctypes.c_int),
-                ("stencil_prec", ctypes.c_int), ("lgmres_k", ctypes.c_int)]
+                ("stencil_prec", ctypes.c_int), ("lgmres_k", ctypes.c_int),
+                ("precond_factor", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):

@@ -7,6 +7,8 @@
 #include <mutex>
 #include <new>
 
+#include <cublas_v2.h>
+
 #include "internal.cuh"
 
 struct stab_handle_s : StabHandle {};
@@ -43,6 +45,7 @@ extern "C" void stab_default_opts(stab_opts* o) {
   o->gmres_basis_prec = 64;
   o->stencil_prec = 64;
   o->lgmres_k = 0;
+  o->precond_factor = 0;
 }
 
 static void free_handle(stab_handle h) {
@@ -69,6 +72,7 @@ static void free_handle(stab_handle h) {
   for (cudaEvent_t e : h->timer.ev) cudaEventDestroy(e);
   for (cudaGraphExec_t e : h->gm_exec)
     if (e) cudaGraphExecDestroy(e);
+  if (h->cublas) cublasDestroy((cublasHandle_t)h->cublas);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   delete h;
 }
@@ -104,6 +108,10 @@ extern "C" stab_status stab_create(stab_handle* out, const double* base_flow, in
       (o.precond_prec != 16 && o.precond_prec != 32 && o.precond_prec != 64) || (o.precond != 0 && o.precond != 1) ||
       (o.gmres_basis_prec != 32 && o.gmres_basis_prec != 64) || (o.stencil_prec != 48 && o.stencil_prec != 64)) {
     g_create_err = "stab_create: invalid option value";
+    return STAB_ERR_INVALID_ARG;
+  }
+  if (o.precond_factor < 0 || o.precond_factor > 2) {
+    g_create_err = "stab_create: precond_factor must be 0, 1 or 2";
     return STAB_ERR_INVALID_ARG;
   }
   if (o.lgmres_k < 0 || o.lgmres_k > STAB_MAX_LGMRES_K || (o.lgmres_k > 0 && o.lgmres_k >= o.gmres_m)) {

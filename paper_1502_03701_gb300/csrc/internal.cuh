@@ -128,6 +128,7 @@ struct StabHandle {
   struct ffn* d_coef_p;  // d_coef_f as FP32 pairs (hi, lo), read by the pointwise kernel
   float* d_btab_f;       // FP32 copy of the base tables (for the O(eps) remainder)
   bool force_dn_path;    // use the full FP64 difference-number pointwise kernel
+  void* cublas = nullptr;  // cuBLAS handle of the tensor-core block factorisation (created on first use)
   // statistics
   stab_stats stats;
   PhaseTimer timer;

@@ -9,6 +9,7 @@
 // elimination with partial pivoting (first row of maximum modulus) and
 // applied as a batched block matrix-vector product.
 // Local unknown order inside a tile: [var][lz][ly][lx], lx fastest.
+#include <cublas_v2.h>
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -512,6 +513,139 @@ AsmParams asm_params(StabHandle* h, const Geo& g, double2 sigma) {
   return P;
 }
 
+// ---------------------------------------------------------------------------
+// Blocked Gauss-Jordan inversion with partial pivoting whose trailing updates
+// are batched complex GEMMs on the tensor cores (cuBLAS), FP32 blocks.
+// Panel K = [k0, k0 + w): the w elimination steps on the panel columns only
+// (pivot rows searched in all rows >= k, the in-place trick storing the
+// transform's columns), which leaves the columns W = E_K[:, K] of the panel's
+// block transform E_K = I + (W - I_K) e_K^T; the row interchanges are then
+// applied to the other columns C and every other column is updated at once:
+// A[:, C] <- E_K A[:, C] = A[:, C] + (W - I_K) A[K, C], i.e. with R = A[K, C]
+// saved and A[K, C] set to zero, A[:, C] += W R (one GEMM per side of K).
+// The column interchanges are undone at the end, as in the unblocked sweep.
+// ---------------------------------------------------------------------------
+constexpr int kPanelThreads = 256;
+
+// The panel's w steps in place in global memory (one CTA per block; the panel
+// of b x w entries stays in L2).  piv[k] receives the pivot row of step k.
+__global__ void __launch_bounds__(kPanelThreads) k_gj_panel(float2* A, int b, int k0, int w, int* piv, int* info) {
+  __shared__ double rv[kPanelThreads / 32];
+  __shared__ int ri[kPanelThreads / 32];
+  __shared__ int s_piv;
+  __shared__ float2 s_row[64];
+  __shared__ float2 s_f[1024];  // column k before the step (the multipliers), b <= 1024
+  __shared__ float2 s_inv;
+  float2* M = A + (long long)blockIdx.x * b * b;
+  int* pv = piv + (long long)blockIdx.x * b;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int bad = 0;
+  for (int kk = 0; kk < w; ++kk) {
+    const int k = k0 + kk;
+    double best = -1.0;
+    int bi = b;
+    for (int i = k + threadIdx.x; i < b; i += blockDim.x) {
+      const float2 v = M[(long long)i * b + k];
+      const double m = (double)v.x * v.x + (double)v.y * v.y;
+      if (m > best) { best = m; bi = i; }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+    }
+    if (lane == 0) { rv[wid] = best; ri[wid] = bi; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double bb = -1.0;
+      int bbi = b;
+      for (int q = 0; q < (int)(blockDim.x >> 5); ++q)
+        if (rv[q] > bb || (rv[q] == bb && ri[q] < bbi)) { bb = rv[q]; bbi = ri[q]; }
+      if (!(bb > 0.0)) { bad = k + 1; bbi = k; }
+      s_piv = bbi;
+      pv[k] = bbi;
+    }
+    __syncthreads();
+    const int p = s_piv;
+    // swap rows k and p within the panel; the pivot row, scaled, to shared memory
+    if (threadIdx.x < w) {
+      const int c = k0 + threadIdx.x;
+      const float2 a = M[(long long)k * b + c], d = M[(long long)p * b + c];
+      if (p != k) M[(long long)p * b + c] = a;
+      s_row[threadIdx.x] = d;  // row k after the interchange
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const float2 q = s_row[kk];
+      float den = q.x * q.x + q.y * q.y;
+      if (!(den > 0.0f)) den = 1.0f;
+      s_inv = make_float2(q.x / den, -q.y / den);
+    }
+    __syncthreads();
+    const float2 inv = s_inv;
+    if (threadIdx.x < w) {  // row k: divided by the pivot, the pivot position becomes 1 / pivot
+      const float2 q = threadIdx.x == kk ? make_float2(1.0f, 0.0f) : s_row[threadIdx.x];
+      const float2 r = make_float2(q.x * inv.x - q.y * inv.y, q.x * inv.y + q.y * inv.x);
+      s_row[threadIdx.x] = r;
+    }
+    __syncthreads();
+    if (threadIdx.x < w) M[(long long)k * b + k0 + threadIdx.x] = s_row[threadIdx.x];
+    for (int i = threadIdx.x; i < b; i += blockDim.x) s_f[i] = M[(long long)i * b + k];
+    __syncthreads();
+    // the other rows: a_ic -= a_ik r_c, with a_ik taken as zero in the pivot column (in-place trick)
+    for (int idx = threadIdx.x; idx < b * w; idx += blockDim.x) {
+      const int i = idx / w, c = idx - i * w;
+      if (i == k) continue;
+      float2* row = M + (long long)i * b + k0;
+      const float2 f = s_f[i];
+      const float2 r = s_row[c];
+      const float2 a = c == kk ? make_float2(0.0f, 0.0f) : row[c];
+      row[c] = make_float2(a.x - (f.x * r.x - f.y * r.y), a.y - (f.x * r.y + f.y * r.x));
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0 && bad) atomicMax(info, 1);
+}
+
+// The panel's row interchanges on the columns outside K, then T = A[K, :]
+// (w x b, saved) and A[K, C] = 0.  Thread j owns column j.
+__global__ void k_gj_swap_copy(float2* A, int b, int k0, int w, const int* piv, float2* T) {
+  float2* M = A + (long long)blockIdx.x * b * b;
+  const int* pv = piv + (long long)blockIdx.x * b;
+  float2* Tb = T + (long long)blockIdx.x * w * b;
+  for (int j = threadIdx.x; j < b; j += blockDim.x) {
+    const bool inK = j >= k0 && j < k0 + w;
+    if (!inK)
+      for (int kk = 0; kk < w; ++kk) {
+        const int k = k0 + kk, p = pv[k];
+        if (p != k) {
+          const float2 a = M[(long long)k * b + j];
+          M[(long long)k * b + j] = M[(long long)p * b + j];
+          M[(long long)p * b + j] = a;
+        }
+      }
+    for (int kk = 0; kk < w; ++kk) {
+      Tb[(long long)kk * b + j] = M[(long long)(k0 + kk) * b + j];
+      if (!inK) M[(long long)(k0 + kk) * b + j] = make_float2(0.0f, 0.0f);
+    }
+  }
+}
+
+// Undo the row interchanges: swap columns in reverse order (thread i owns row i).
+__global__ void k_gj_unpermute(float2* A, int b, const int* piv) {
+  float2* M = A + (long long)blockIdx.x * b * b;
+  const int* pv = piv + (long long)blockIdx.x * b;
+  for (int i = threadIdx.x; i < b; i += blockDim.x)
+    for (int k = b - 1; k >= 0; --k) {
+      const int p = pv[k];
+      if (p != k) {
+        const float2 t = M[(long long)i * b + k];
+        M[(long long)i * b + k] = M[(long long)i * b + p];
+        M[(long long)i * b + p] = t;
+      }
+    }
+}
+
 int gj_threads(int b) {
   int t = b < 512 ? b : 512;
   return ((t + 31) / 32) * 32;  // whole warps: the pivot search reduces with full-warp shuffles
@@ -520,6 +654,46 @@ int gj_threads(int b) {
 cudaError_t launch_assemble(StabHandle* h, AsmParams& P, long long ntile_batch) {
   if (h->dim == 2) k_assemble<2><<<(unsigned)ntile_batch, 128, 0, h->stream>>>(P);
   else k_assemble<3><<<(unsigned)ntile_batch, 128, 0, h->stream>>>(P);
+  return cudaGetLastError();
+}
+
+// In-place inversion of nb FP32 blocks (b x b, row-major) by the blocked
+// Gauss-Jordan sweep above; mode 1: GEMMs with FP32 inputs emulated on the
+// BF16 tensor cores (BF16x9, FP32 accuracy), mode 2: TF32 tensor cores.
+cudaError_t gj_blocked(StabHandle* h, float2* A, int b, long long nb, int* piv, float2* T, int* d_info, int mode) {
+  if (!h->cublas) {
+    cublasHandle_t c;
+    if (cublasCreate(&c) != CUBLAS_STATUS_SUCCESS) return cudaErrorUnknown;
+    h->cublas = c;
+  }
+  cublasHandle_t cb = (cublasHandle_t)h->cublas;
+  if (cublasSetStream(cb, h->stream) != CUBLAS_STATUS_SUCCESS) return cudaErrorUnknown;
+  cublasComputeType_t ct = CUBLAS_COMPUTE_32F_FAST_TF32;
+  if (mode == 1) {
+    ct = CUBLAS_COMPUTE_32F_EMULATED_16BFX9;
+    cublasSetEmulationStrategy(cb, CUBLAS_EMULATION_STRATEGY_EAGER);
+  }
+  const int W = b >= 512 ? 64 : 32;
+  const cuComplex one = make_cuComplex(1.0f, 0.0f);
+  for (int k0 = 0; k0 < b; k0 += W) {
+    const int w = std::min(W, b - k0);
+    k_gj_panel<<<(unsigned)nb, kPanelThreads, 0, h->stream>>>(A, b, k0, w, piv, d_info);
+    k_gj_swap_copy<<<(unsigned)nb, 256, 0, h->stream>>>(A, b, k0, w, piv, T);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    // column-major view X = A^T (ld b): X[C, :] += T^T[C, :] X[K, :], for C left and right of K
+    const int right = b - (k0 + w);
+    for (int side = 0; side < 2; ++side) {
+      const int m = side == 0 ? k0 : right;
+      const int off = side == 0 ? 0 : k0 + w;
+      if (m <= 0) continue;
+      const cublasStatus_t st = cublasGemmStridedBatchedEx(
+          cb, CUBLAS_OP_N, CUBLAS_OP_N, m, b, w, &one, T + off, CUDA_C_32F, b, (long long)w * b, A + k0, CUDA_C_32F, b,
+          (long long)b * b, &one, A + off, CUDA_C_32F, b, (long long)b * b, (int)nb, ct, CUBLAS_GEMM_DEFAULT);
+      if (st != CUBLAS_STATUS_SUCCESS) return st == CUBLAS_STATUS_NOT_SUPPORTED ? cudaErrorNotSupported : cudaErrorUnknown;
+    }
+  }
+  k_gj_unpermute<<<(unsigned)nb, 256, 0, h->stream>>>(A, b, piv);
   return cudaGetLastError();
 }
 
@@ -562,6 +736,13 @@ cudaError_t pc_build(StabHandle* h, double2 sigma) {
   }
   float2* f32 = nullptr;  // BF16 storage: FP32 inversion in a batch-sized buffer, then rounding
   if (prec == 16 && (e = dalloc(h, &f32, bb * batch * sizeof(float2))) != cudaSuccess) return e;
+  const int fac = h->opts.precond_factor;  // 1, 2: blocked sweep with tensor-core GEMMs (FP32 inversion only)
+  int* piv = nullptr;
+  float2* T = nullptr;
+  if (fac && prec != 64) {
+    if ((e = dalloc(h, &piv, (size_t)batch * g.bsz * sizeof(int))) != cudaSuccess) return e;
+    if ((e = dalloc(h, &T, (size_t)batch * 64 * g.bsz * sizeof(float2))) != cudaSuccess) return e;
+  }
   int* d_info;
   if ((e = dalloc(h, &d_info, sizeof(int))) != cudaSuccess) return e;
   cudaMemsetAsync(d_info, 0, sizeof(int), h->stream);
@@ -580,7 +761,11 @@ cudaError_t pc_build(StabHandle* h, double2 sigma) {
       if ((e = launch_assemble(h, P, nb)) != cudaSuccess) break;
       float2* dst = prec == 32 ? (float2*)h->d_pinv + bb * t0 : f32;
       k_to_float<<<1024, 256, 0, h->stream>>>(h->d_pblk, dst, (long long)(bb * nb));
-      k_gauss_jordan<float><<<(unsigned)nb, gj_threads(g.bsz), smem, h->stream>>>((C2<float>*)dst, g.bsz, d_info);
+      if (fac) {
+        if ((e = gj_blocked(h, dst, g.bsz, nb, piv, T, d_info, fac)) != cudaSuccess) break;
+      } else {
+        k_gauss_jordan<float><<<(unsigned)nb, gj_threads(g.bsz), smem, h->stream>>>((C2<float>*)dst, g.bsz, d_info);
+      }
       if (prec == 16)
         k_to_bf16_t<<<(unsigned)nb, 256, 0, h->stream>>>(f32, (__nv_bfloat162*)h->d_pinv + bb * t0, g.bsz);
     }
@@ -591,6 +776,8 @@ cudaError_t pc_build(StabHandle* h, double2 sigma) {
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   dfree(h, d_info);
   dfree(h, f32);
+  dfree(h, piv);
+  dfree(h, T);
   if (e != cudaSuccess) return e;
   if (info) return cudaErrorInvalidValue;  // a singular block
   h->pvalid = true;
