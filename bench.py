@@ -54,10 +54,13 @@ import stab_inputs as si  # noqa: E402
 METRIC = "J·v GB/s (% HBM peak); converged eigenpairs/s; p50/p99 solve latency"
 JV_BYTES_PER_DOF = 32  # read v (16 B) + write J v (16 B); the y-only base tables stay on chip
 L2_FLUSH_BYTES = 512 << 20
-EIG = dict(sigma=0.2j, tau=-1 + 0.2j, nev=10, ncv=60, tol=1e-10)
+# 256 x 512 solves: the pole right of the spectrum (sigma 1, tau -1: the least stable modes have the largest
+# |theta|); block-Jacobi over 8 x 32-point tiles (1,024 unknowns), the tile shape whose inner solves reach
+# 1e-10 (measured: 3,776 FGMRES(50) iterations, against no convergence for 8 x 8 tiles)
+EIG = dict(sigma=1.0, tau=-1.0, nev=10, ncv=60, tol=1e-10)
 EIG_GRID = (256, 512)  # the 2-D layer of the --workload eigs solves
-SOLVER_OPTS = dict(eps_mode=2, precond=1, tile=(8, 8), precond_prec=32, gmres_m=50, gmres_tol=1e-10,
-                   gmres_max_restarts=400, max_restarts=60)
+SOLVER_OPTS = dict(eps_mode=2, precond=1, tile=(8, 32), precond_prec=32, precond_factor=1, gmres_m=50,
+                   gmres_tol=1e-10, gmres_max_restarts=400, max_restarts=40)
 RESID_OK = 1e-8
 
 
@@ -525,6 +528,56 @@ def jv_batch_64(args, torch) -> dict:
                               "note": "block-Jacobi over 8 x 8 tiles, FP32 inverses (stored bytes per step)"}}
 
 
+def gmres_batch_64(args, torch) -> dict:
+    """Solver-level batching at the batch configuration's full sizes: two FGMRES(30) cycles (60 iterations)
+    of (J - sigma I) x = b for each of the 64 uneven instances (block-Jacobi over 8 x 8 tiles, FP32 inverses),
+    in lockstep (stab_jv_batch_solve: every phase one launch for all instances) against one instance at a
+    time (stab_solve: one captured graph per cycle).  Instance iterations per second; the lockstep iterates
+    equal the lone ones bit for bit below 16,384 unknowns (above, the lone solve reorthogonalises
+    selectively), and agree to the solves' progress above."""
+    from paper_1502_03701_gb300 import JvBatch, Stab
+    insts = si.batched_instances(64, 1234)
+    hs = []
+    for p in insts:
+        g, f, q0 = _fleet_problem(p)
+        S = Stab(q0, g, f.Ma, f.Re, f.Pr, eps_mode=2, precond=1, tile=(8, 8), precond_prec=32, precond_factor=1,
+                 gmres_m=30, gmres_tol=1e-10, gmres_max_restarts=2)
+        S.autotune()
+        S.precond_build(1.0)
+        hs.append(S)
+    bs = [torch.from_numpy(si.random_complex(950 + i, S.n)).cuda() for i, S in enumerate(hs)]
+    xs_plain = [torch.zeros_like(b) for b in bs]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    it_plain = [S.solve(1.0, b, x)[1] for S, b, x in zip(hs, bs, xs_plain)]
+    torch.cuda.synchronize()
+    t_plain = time.perf_counter() - t0
+    B = JvBatch(hs)
+    xs = [torch.zeros_like(b) for b in bs]
+    B.solve([1.0] * len(hs), bs, xs)  # warm (parameter images, workspaces)
+    xs = [torch.zeros_like(b) for b in bs]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    st, it_lock = B.solve([1.0] * len(hs), bs, xs)
+    torch.cuda.synchronize()
+    t_lock = time.perf_counter() - t0
+    B.close()
+    small = [i for i, S in enumerate(hs) if S.n < 16384]
+    same_small = all(torch.equal(xs[i], xs_plain[i]) for i in small)
+    diff = max(float((x - y).norm() / y.norm()) for x, y in zip(xs, xs_plain))
+    n_total = sum(S.n for S in hs)
+    for S in hs:
+        S.close()
+    return {"workload": "gmres_batch_64_uneven_2d", "instances": 64, "unknowns": n_total,
+            "iterations": {"lockstep": int(sum(it_lock)), "plain": int(sum(it_plain))},
+            "lockstep": {"value": sum(it_lock) / t_lock, "unit": "instance iterations/s", "seconds": t_lock},
+            "plain_one_at_a_time": {"value": sum(it_plain) / t_plain, "unit": "instance iterations/s",
+                                    "seconds": t_plain},
+            "speedup": (sum(it_lock) / t_lock) / (sum(it_plain) / t_plain),
+            "bitwise_equal_below_16k": same_small, "instances_below_16k": len(small),
+            "max_rel_diff_of_iterates": diff}
+
+
 def fleet(args, torch) -> dict:
     """Plain one-at-a-time FP64 path vs batched mixed-precision path vs served Poisson stream."""
     from paper_1502_03701_gb300 import Server, Stab, eigs_batch
@@ -558,6 +611,21 @@ def fleet(args, torch) -> dict:
     t_batch = time.perf_counter() - t0
     n_batch = sum(good((r.lam, r.resid)) for r in res if r.nconv == nev)
     err = [float(np.max(np.abs(r.lam - p[0]) / np.abs(p[0]))) for r, p in zip(res, plain)]
+    # lockstep: every phase of all instances' GMRES cycles and Arnoldi steps one launch (stab_jv_batch_eigs),
+    # FP32 inverses factorised on the tensor cores
+    from paper_1502_03701_gb300 import JvBatch
+    t0 = time.perf_counter()
+    hs = [Stab(q0, g, f.Ma, f.Re, f.Pr, precond_prec=32, precond_factor=1, **FLEET_OPTS) for g, f, q0 in probs]
+    for h in hs:
+        h.autotune()
+    B = JvBatch(hs)
+    res_l = B.eigs([FLEET_EIG] * len(hs))
+    B.close()
+    for h in hs:
+        h.close()
+    t_lock = time.perf_counter() - t0
+    n_lock = sum(good((r.lam, r.resid)) for r in res_l if r.nconv == nev)
+    err_l = [float(np.max(np.abs(r.lam - p[0]) / np.abs(p[0]))) for r, p in zip(res_l, plain)]
     # served: Poisson arrivals, continuous batching
     arrivals = si.poisson_arrivals(len(probs), args.rate, 4321)
     srv = Server(slots=args.slots, mem_budget_bytes=args.budget_gb << 30, autotune=True)
@@ -585,11 +653,91 @@ def fleet(args, torch) -> dict:
             "plain_fp64_one_at_a_time": {"value": n_plain / t_plain, "unit": "eigenpairs/s", "seconds": t_plain},
             "batched_mixed": {"value": n_batch / t_batch, "unit": "eigenpairs/s", "seconds": t_batch,
                               "speedup_vs_plain": (n_batch / t_batch) / (n_plain / t_plain) if n_plain else None,
-                              "max_rel_diff_vs_plain_fp64": max(err)},
+                              "max_rel_diff_vs_plain_fp64": max(err),
+                              "how": "stab_eigs_batch: host threads, one stream per instance"},
+            "lockstep_mixed": {"value": n_lock / t_lock, "unit": "eigenpairs/s", "seconds": t_lock,
+                               "speedup_vs_plain": (n_lock / t_lock) / (n_plain / t_plain) if n_plain else None,
+                               "max_rel_diff_vs_plain_fp64": max(err_l),
+                               "how": "stab_jv_batch_eigs: one launch per phase for all instances, FP32 inverses "
+                                      "factorised with tensor-core GEMMs"},
             "served": {"value": n_srv / t_srv, "unit": "eigenpairs/s", "seconds": t_srv,
                        "arrivals_per_s": args.rate, "slots": args.slots,
                        "latency_ms": {"p50": lat[len(lat) // 2] * 1e3, "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))] * 1e3},
                        "peak_running": st["peak_running"], "peak_bytes": st["peak_bytes"]}}
+
+
+# Served stream shaped like the serving configuration: Poisson arrivals (50/s, seed 4321); 95 % 2-D layers
+# drawn like the 64-instance batch configuration with sizes scaled by a quarter per axis, 5 % 3-D layers
+# scaled from 64 x 128 x 32; Cayley-IRAM sigma 1, tau -1, 2 of 12, FGMRES(30) with block-Jacobi.
+SERVE_SIZES = dict(nxs=(16, 32, 64), nys=(32, 64, 128))
+SERVE_3D = (16, 32, 8)
+
+
+def serve_stream(args, torch) -> dict:
+    """Continuous batching under a Poisson load: p50 / p99 latency and eigenpairs/s of the served stream
+    (lockstep cohorts), the plain one-at-a-time FP64 path on the first requests, and each of those
+    requests' eigenvalues alone against in the mix (1e-8)."""
+    from paper_1502_03701_gb300 import Server, Stab
+    count = args.requests
+    insts = si.batched_instances(count, 1234, **SERVE_SIZES)
+    u = si.splitmix64_uniform(777, count) + 0.5
+    probs = []
+    for i, p in enumerate(insts):
+        if u[i] < 0.05:
+            g, f = si.mixing_layer_3d(*SERVE_3D, Ma=float(p["Ma"]))
+            f = si.Flow(float(p["Ma"]), float(p["Re"]))
+            opts = dict(FLEET_OPTS, tile=(4, 4, 4))
+        else:
+            g, f, _ = _fleet_problem(p)
+            opts = dict(FLEET_OPTS, tile=(min(16, p["nx"]), 16))
+        probs.append((g, f, si.tanh_base_flow(g, f), opts))
+    nev = FLEET_EIG[2]
+    arrivals = si.poisson_arrivals(count, args.rate, 4321)
+    srv = Server(slots=args.slots, mem_budget_bytes=args.budget_gb << 30, autotune=True, cohort=args.cohort)
+    t0 = time.perf_counter()
+    ids = []
+    for (g, f, q0, opts), ta in zip(probs, arrivals):
+        dt = t0 + ta - time.perf_counter()
+        if dt > 0:
+            time.sleep(dt)
+        ids.append(srv.submit(q0, g, f.Ma, f.Re, f.Pr, *FLEET_EIG, precond_prec=32, precond_factor=1, **opts))
+    lat, served, n_srv = [], [], 0
+    for rid in ids:
+        srv.wait(rid)
+        lam, resid, info = srv.result(rid)
+        lat.append(info["latency_s"])
+        served.append(lam)
+        n_srv += int(np.sum(resid < RESID_OK)) if info["nconv"] == nev else 0
+    t_srv = time.perf_counter() - t0
+    st = srv.stats()
+    srv.close()
+    # the plain FP64 path, one request at a time, on the first requests
+    k = min(args.plain_requests, count)
+    torch.cuda.synchronize()
+    tp = time.perf_counter()
+    n_plain, diff = 0, []
+    for (g, f, q0, opts), lam_s in zip(probs[:k], served[:k]):
+        S = Stab(q0, g, f.Ma, f.Re, f.Pr, precond_prec=64, **opts)
+        S.autotune()
+        r = S.eigs(*FLEET_EIG)
+        S.close()
+        n_plain += int(np.sum(r.resid < RESID_OK)) if r.nconv == nev else 0
+        diff.append(float(np.max(np.abs(np.sort_complex(lam_s) - np.sort_complex(r.lam)) / np.abs(r.lam))))
+    t_plain = time.perf_counter() - tp
+    lat.sort()
+    return {"workload": f"served stream of {count} requests: 95% 2-D layers Nx in {SERVE_SIZES['nxs']}, Ny in "
+                        f"{SERVE_SIZES['nys']} (the batch configuration's sizes scaled by 1/4 per axis), 5% 3-D "
+                        f"{SERVE_3D[0]}x{SERVE_3D[1]}x{SERVE_3D[2]}; Ma U[0.1,0.9], Re log-U[500,5000]",
+            "arrivals_per_s": args.rate, "requests": count, "slots": args.slots, "cohort": args.cohort,
+            "eig": {"sigma": 1.0, "tau": -1.0, "nev": nev, "ncv": FLEET_EIG[3], "tol": FLEET_EIG[4],
+                    "gmres": "FGMRES(30) to 1e-10, block-Jacobi 16x16 (3-D 4x4x4), FP32 inverses on tensor cores"},
+            "served": {"value": n_srv / t_srv, "unit": "eigenpairs/s", "seconds": t_srv,
+                       "latency_ms": {"p50": lat[len(lat) // 2] * 1e3,
+                                      "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))] * 1e3},
+                       "peak_running": st["peak_running"], "peak_bytes": st["peak_bytes"]},
+            "plain_fp64_one_at_a_time": {"value": n_plain / t_plain, "unit": "eigenpairs/s", "seconds": t_plain,
+                                         "requests": k},
+            "alone_vs_in_mix_max_rel_diff": max(diff) if diff else None}
 
 
 def reduce_over_ranks(x: float, op: str, device: str) -> float:
@@ -783,6 +931,7 @@ def run_ours(args):
             extra["precond_build_256x512"] = precond_build_256x512(args, Stab, torch)
         if args.fleet > 0 and world == 1:
             extra["jv_batch_64"] = jv_batch_64(args, torch)
+            extra["gmres_batch_64"] = gmres_batch_64(args, torch)
             extra["many_small"] = fleet(args, torch)
     else:
         # roofline of the J v kernels from a short phase-timed sample (the solves below are host-driven)
@@ -810,8 +959,13 @@ def run_ours(args):
                 vecs_h.copy_(vecs, non_blocking=True)
             return r
 
-        for s in range(args.warmup):
-            solve(handles[s % 3], False)
+        # warm-up (a full solve takes minutes): per handle the line-pass tuning, a preconditioner build and
+        # one inner solve
+        for S in handles[:max(1, min(args.warmup, 3))]:
+            S.autotune()
+            S.precond_build(EIG["sigma"])
+            bw = torch.from_numpy(si.random_complex(3, n)).cuda()
+            S.solve(EIG["sigma"], bw, torch.zeros_like(bw))
         barrier()
         sampler = ClockSampler(local)
         step_t, results = [], []
@@ -849,9 +1003,10 @@ def run_ours(args):
         st = [r.stats for r in results]
         jv_per_solve = statistics.mean(s_["jv_calls"] for s_ in st)
         config = {"workload": f"eigs_mixing_layer_{g.nx}x{g.ny}", "nx": g.nx, "ny": g.ny, "Re": f.Re,
-                  "Ma_sweep": list(sweep), "sigma": [0.0, 0.2], "tau": [-1.0, 0.2], "nev": EIG["nev"],
+                  "Ma_sweep": list(sweep), "sigma": [1.0, 0.0], "tau": [-1.0, 0.0], "nev": EIG["nev"],
                   "ncv": EIG["ncv"], "tol": EIG["tol"], "gmres": "flexible GMRES(50) to 1e-10",
-                  "precond": "block-Jacobi 8x8 tiles, FP32 inverses", "jv": "exact tangent (FP64)",
+                  "precond": "block-Jacobi 8x32 tiles, FP32 inverses factorised with tensor-core GEMMs",
+                  "jv": "exact tangent (FP64)", "warmup": "per handle: tuning, preconditioner build, one inner solve",
                   "l2": "flushed before each timed solve", "parallelism": f"replicas{world}"}
         extra = {"latency_ms": {"p50": statistics.median(lat) * 1e3, "p99": lat[min(len(lat) - 1,
                                                                                       int(0.99 * len(lat)))] * 1e3},
@@ -886,13 +1041,35 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_serve(args):
+    """--workload serve: the served stream as the bench line (eigenpairs/s of the stream; p50/p99 beside)."""
+    import torch
+    from paper_1502_03701_gb300 import build
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    build.build()
+    sampler = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    with sampler:
+        sampler.wait_first_sample()
+        r = serve_stream(args, torch)
+    line = {"metric": METRIC, "value": r["served"]["value"], "unit": "eigenpairs/s", "n_gpus": 1,
+            "steps": r["requests"], "warmup": 0, "ms_per_step": r["served"]["seconds"] / r["requests"] * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64 (FP32 inverses)",
+            "data": "synthetic (analytic tanh mixing layers)",
+            "config": {"workload": "served_stream", "requests": r["requests"], "rate": args.rate},
+            "clocks": sampler.summary(), "serve": r}
+    print(json.dumps(line))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="jv", choices=["eigs", "jv"])
+    ap.add_argument("--workload", default="jv", choices=["eigs", "jv", "serve"])
+    ap.add_argument("--requests", type=int, default=200, help="served stream length (--workload serve)")
+    ap.add_argument("--plain-requests", type=int, default=16, help="requests also solved one at a time (serve)")
+    ap.add_argument("--cohort", type=int, default=16, help="lockstep cohort size of the server (serve)")
     ap.add_argument("--eig-steps", type=int, default=2)
     ap.add_argument("--gmres-restarts", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -909,6 +1086,8 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "serve":
+        run_serve(args)
     else:
         run_ours(args)
 

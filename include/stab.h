@@ -89,10 +89,17 @@ typedef struct {
                              Needs gmres_basis_prec = 64 (else STAB_ERR_UNSUPPORTED) */
   int precond_factor;     /* inversion of the FP32 block-Jacobi blocks (precond_prec 32 or 16): 0 = Gauss-Jordan
                              with partial pivoting on the CUDA cores (default); 1 = the same elimination blocked
-                             in panels of 32 (64 from 512 rows) columns, every panel's update of the other
+                             in panels of 32 columns (16 above 640 rows) staged in shared memory, every panel's update of the other
                              columns one batched complex GEMM on the tensor cores with FP32 inputs emulated in
                              BF16 (FP32 accuracy); 2 = the same with TF32 inputs (about 1e-3 relative).
                              precond_prec 64 always uses the CUDA cores */
+  int gmres_inner_m;      /* nested inner solver (mixed precision): 0 = none (default); k in [1, 100] = every
+                             step of the FP64 flexible GMRES(gmres_m) takes as its direction z_j an inner
+                             GMRES(k) approximation of (J - sigma I)^{-1} v_j with an FP32 Krylov basis and FP32
+                             orthogonalisation, right preconditioned with the block-Jacobi inverses (opts.precond),
+                             run until its residual is below gmres_inner_tol ||v_j|| or k steps; J v stays FP64.
+                             Needs gmres_basis_prec = 64 and lgmres_k = 0 (else STAB_ERR_UNSUPPORTED) */
+  double gmres_inner_tol; /* relative tolerance of each inner solve, default 1e-3 */
 } stab_opts;
 
 typedef struct {
@@ -357,7 +364,7 @@ typedef struct {
  * 16,384 unknowns), so below that size each x_i equals stab_solve's bit for
  * bit.  sigmas: 2*count doubles (re, im); rhs[i], x[i]: device complex128 of
  * handle i's size; iters (host, count, may be NULL): iterations per instance.
- * Handles with gmres_basis_prec = 32 or lgmres_k > 0: STAB_ERR_UNSUPPORTED.
+ * Handles with gmres_basis_prec = 32, lgmres_k > 0 or gmres_inner_m > 0: STAB_ERR_UNSUPPORTED.
  * NOT_CONVERGED when an instance reached its restart limit (its x holds the
  * last iterate).  Synchronises the batch's stream. */
 stab_status stab_jv_batch_solve(stab_jv_batch b, const double* sigmas, const void* const* rhs, void* const* x,

@@ -53,7 +53,8 @@ class Opts(ctypes.Structure):
                 ("tile", ctypes.c_int * 3), ("precond_prec", ctypes.c_int), ("max_restarts", ctypes.c_int),
                 ("seed", ctypes.c_ulonglong), ("gmres_basis_prec", ctypes.c_int),
                 ("stencil_prec", ctypes.c_int), ("lgmres_k", ctypes.c_int),
-                ("precond_factor", ctypes.c_int)]
+                ("precond_factor", ctypes.c_int), ("gmres_inner_m", ctypes.c_int),
+                ("gmres_inner_tol", ctypes.c_double)]
 
 
 class Stats(ctypes.Structure):

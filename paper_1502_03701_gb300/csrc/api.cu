@@ -46,6 +46,8 @@ extern "C" void stab_default_opts(stab_opts* o) {
   o->stencil_prec = 64;
   o->lgmres_k = 0;
   o->precond_factor = 0;
+  o->gmres_inner_m = 0;
+  o->gmres_inner_tol = 1e-3;
 }
 
 static void free_handle(stab_handle h) {
@@ -109,6 +111,14 @@ extern "C" stab_status stab_create(stab_handle* out, const double* base_flow, in
       (o.gmres_basis_prec != 32 && o.gmres_basis_prec != 64) || (o.stencil_prec != 48 && o.stencil_prec != 64)) {
     g_create_err = "stab_create: invalid option value";
     return STAB_ERR_INVALID_ARG;
+  }
+  if (o.gmres_inner_m < 0 || o.gmres_inner_m > 100 || !(o.gmres_inner_tol >= 0.0 && o.gmres_inner_tol < 1.0)) {
+    g_create_err = "stab_create: gmres_inner_m must be in [0, 100] and gmres_inner_tol in [0, 1)";
+    return STAB_ERR_INVALID_ARG;
+  }
+  if (o.gmres_inner_m > 0 && (o.gmres_basis_prec != 64 || o.lgmres_k > 0)) {
+    g_create_err = "stab_create: the nested inner solver needs the FP64 outer basis and no LGMRES";
+    return STAB_ERR_UNSUPPORTED;
   }
   if (o.precond_factor < 0 || o.precond_factor > 2) {
     g_create_err = "stab_create: precond_factor must be 0, 1 or 2";

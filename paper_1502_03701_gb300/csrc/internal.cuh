@@ -54,14 +54,14 @@ struct Slots {
 struct GmGraphKey {
   bool valid = false;
   double sigma_re = 0, sigma_im = 0;
-  int eps_mode = -1, m = 0, pc = 0, pprec = 0, basis = 64, lgk = 0, naug = 0;
+  int eps_mode = -1, m = 0, pc = 0, pprec = 0, basis = 64, lgk = 0, naug = 0, mi = 0;
   const void* ws = nullptr;
   const void* pinv = nullptr;
   long long n = 0;
   bool operator==(const GmGraphKey& o) const {
     return valid && o.valid && sigma_re == o.sigma_re && sigma_im == o.sigma_im && eps_mode == o.eps_mode &&
            m == o.m && pc == o.pc && pprec == o.pprec && ws == o.ws && pinv == o.pinv && n == o.n &&
-           basis == o.basis && lgk == o.lgk && naug == o.naug;
+           basis == o.basis && lgk == o.lgk && naug == o.naug && mi == o.mi;
   }
 };
 

@@ -527,25 +527,33 @@ AsmParams asm_params(StabHandle* h, const Geo& g, double2 sigma) {
 // ---------------------------------------------------------------------------
 constexpr int kPanelThreads = 256;
 
-// The panel's w steps in place in global memory (one CTA per block; the panel
-// of b x w entries stays in L2).  piv[k] receives the pivot row of step k.
+// The panel's w steps on a copy of the b x w panel in shared memory (one CTA
+// per block; row stride w + 1 complex so that column sweeps spread over the
+// banks), written back at the end.  piv[k] receives the pivot row of step k.
+template <int W>
 __global__ void __launch_bounds__(kPanelThreads) k_gj_panel(float2* A, int b, int k0, int w, int* piv, int* info) {
+  extern __shared__ float2 Ps[];  // [b][W + 1]
   __shared__ double rv[kPanelThreads / 32];
   __shared__ int ri[kPanelThreads / 32];
   __shared__ int s_piv;
-  __shared__ float2 s_row[64];
-  __shared__ float2 s_f[1024];  // column k before the step (the multipliers), b <= 1024
+  __shared__ float2 s_row[W];
   __shared__ float2 s_inv;
+  constexpr int LD = W + 1;
   float2* M = A + (long long)blockIdx.x * b * b;
   int* pv = piv + (long long)blockIdx.x * b;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int idx = threadIdx.x; idx < b * w; idx += blockDim.x) {
+    const int i = idx / w, c = idx - i * w;
+    Ps[i * LD + c] = M[(long long)i * b + k0 + c];
+  }
+  __syncthreads();
   int bad = 0;
   for (int kk = 0; kk < w; ++kk) {
     const int k = k0 + kk;
     double best = -1.0;
     int bi = b;
     for (int i = k + threadIdx.x; i < b; i += blockDim.x) {
-      const float2 v = M[(long long)i * b + k];
+      const float2 v = Ps[i * LD + kk];
       const double m = (double)v.x * v.x + (double)v.y * v.y;
       if (m > best) { best = m; bi = i; }
     }
@@ -567,12 +575,11 @@ __global__ void __launch_bounds__(kPanelThreads) k_gj_panel(float2* A, int b, in
     }
     __syncthreads();
     const int p = s_piv;
-    // swap rows k and p within the panel; the pivot row, scaled, to shared memory
+    // swap rows k and p of the panel; row k (after the interchange) to s_row
     if (threadIdx.x < w) {
-      const int c = k0 + threadIdx.x;
-      const float2 a = M[(long long)k * b + c], d = M[(long long)p * b + c];
-      if (p != k) M[(long long)p * b + c] = a;
-      s_row[threadIdx.x] = d;  // row k after the interchange
+      const float2 a = Ps[k * LD + threadIdx.x], d = Ps[p * LD + threadIdx.x];
+      if (p != k) Ps[p * LD + threadIdx.x] = a;
+      s_row[threadIdx.x] = d;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -587,22 +594,31 @@ __global__ void __launch_bounds__(kPanelThreads) k_gj_panel(float2* A, int b, in
       const float2 q = threadIdx.x == kk ? make_float2(1.0f, 0.0f) : s_row[threadIdx.x];
       const float2 r = make_float2(q.x * inv.x - q.y * inv.y, q.x * inv.y + q.y * inv.x);
       s_row[threadIdx.x] = r;
+      Ps[k * LD + threadIdx.x] = r;
     }
     __syncthreads();
-    if (threadIdx.x < w) M[(long long)k * b + k0 + threadIdx.x] = s_row[threadIdx.x];
-    for (int i = threadIdx.x; i < b; i += blockDim.x) s_f[i] = M[(long long)i * b + k];
-    __syncthreads();
-    // the other rows: a_ic -= a_ik r_c, with a_ik taken as zero in the pivot column (in-place trick)
+    // the other rows: a_ic -= a_ik r_c, a_ik taken as zero in the pivot column (in-place trick); the
+    // thread of (i, kk) owns the multiplier a_ik, so every row's threads read it before it changes
     for (int idx = threadIdx.x; idx < b * w; idx += blockDim.x) {
       const int i = idx / w, c = idx - i * w;
-      if (i == k) continue;
-      float2* row = M + (long long)i * b + k0;
-      const float2 f = s_f[i];
+      if (i == k || c == kk) continue;
+      const float2 f = Ps[i * LD + kk];
       const float2 r = s_row[c];
-      const float2 a = c == kk ? make_float2(0.0f, 0.0f) : row[c];
-      row[c] = make_float2(a.x - (f.x * r.x - f.y * r.y), a.y - (f.x * r.y + f.y * r.x));
+      float2& a = Ps[i * LD + c];
+      a = make_float2(a.x - (f.x * r.x - f.y * r.y), a.y - (f.x * r.y + f.y * r.x));
     }
     __syncthreads();
+    for (int i = threadIdx.x; i < b; i += blockDim.x) {
+      if (i == k) continue;
+      const float2 f = Ps[i * LD + kk];
+      const float2 r = s_row[kk];
+      Ps[i * LD + kk] = make_float2(-(f.x * r.x - f.y * r.y), -(f.x * r.y + f.y * r.x));
+    }
+    __syncthreads();
+  }
+  for (int idx = threadIdx.x; idx < b * w; idx += blockDim.x) {
+    const int i = idx / w, c = idx - i * w;
+    M[(long long)i * b + k0 + c] = Ps[i * LD + c];
   }
   if (threadIdx.x == 0 && bad) atomicMax(info, 1);
 }
@@ -673,11 +689,17 @@ cudaError_t gj_blocked(StabHandle* h, float2* A, int b, long long nb, int* piv, 
     ct = CUBLAS_COMPUTE_32F_EMULATED_16BFX9;
     cublasSetEmulationStrategy(cb, CUBLAS_EMULATION_STRATEGY_EAGER);
   }
-  const int W = b >= 512 ? 64 : 32;
+  // panels of 32 columns while the b x 33 panel fits in shared memory (b <= 640), else 16
+  const int W = b <= 640 ? 32 : 16;
+  const size_t psm = (size_t)b * (W + 1) * sizeof(float2);
+  cudaError_t ea = cudaFuncSetAttribute(W == 32 ? (const void*)k_gj_panel<32> : (const void*)k_gj_panel<16>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psm);
+  if (ea != cudaSuccess) return ea;
   const cuComplex one = make_cuComplex(1.0f, 0.0f);
   for (int k0 = 0; k0 < b; k0 += W) {
     const int w = std::min(W, b - k0);
-    k_gj_panel<<<(unsigned)nb, kPanelThreads, 0, h->stream>>>(A, b, k0, w, piv, d_info);
+    if (W == 32) k_gj_panel<32><<<(unsigned)nb, kPanelThreads, psm, h->stream>>>(A, b, k0, w, piv, d_info);
+    else k_gj_panel<16><<<(unsigned)nb, kPanelThreads, psm, h->stream>>>(A, b, k0, w, piv, d_info);
     k_gj_swap_copy<<<(unsigned)nb, 256, 0, h->stream>>>(A, b, k0, w, piv, T);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -741,7 +763,7 @@ cudaError_t pc_build(StabHandle* h, double2 sigma) {
   float2* T = nullptr;
   if (fac && prec != 64) {
     if ((e = dalloc(h, &piv, (size_t)batch * g.bsz * sizeof(int))) != cudaSuccess) return e;
-    if ((e = dalloc(h, &T, (size_t)batch * 64 * g.bsz * sizeof(float2))) != cudaSuccess) return e;
+    if ((e = dalloc(h, &T, (size_t)batch * 32 * g.bsz * sizeof(float2))) != cudaSuccess) return e;
   }
   int* d_info;
   if ((e = dalloc(h, &d_info, sizeof(int))) != cudaSuccess) return e;

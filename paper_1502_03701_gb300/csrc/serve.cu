@@ -54,6 +54,8 @@ extern "C" long long stab_estimate_bytes(const stab_grid* g, const stab_opts* op
   b += (nv + 1) * npts * 16;                               // set-up temporary
   const long long m = o.gmres_m, pc = o.precond == 1;
   if (o.gmres_basis_prec == 32) b += (m + 1) * n * 8 + 6 * n * 16;  // FP32 basis; r, b, x, w, z, t
+  else if (o.gmres_inner_m > 0)                            // nested: V, Z, r, b, x; inner FP32 basis, w, zt, t
+    b += ((m + 1) + m + 3) * n * 16 + ((long long)o.gmres_inner_m + 1) * n * 8 + 3 * n * 16;
   else if (o.lgmres_k > 0) b += ((m + 1) + m + 3 + 2 * (long long)o.lgmres_k + 1) * n * 16;  // LGMRES: V, Z, r, b,
                                                                                        // x, (z, A z) pairs, dz
   else b += ((m + 1) + pc * m + 3) * n * 16;               // GMRES basis, Z, r, b, x

@@ -51,16 +51,6 @@ double2* ensure(StabHandle* h, double2** p, size_t* have, size_t need) {
   return *p;
 }
 
-// GMRES workspace layout (complex elements).  FP64 basis: V, Z (flexible).
-// FP32 basis: V32, and FP64 work vectors w (J z), zt (preconditioned
-// direction or correction) and t (V32 y).
-struct GmresWs {
-  double2 *V, *Z, *r, *b, *x, *partial, *dh, *y;
-  double* dnorm;
-  float2* V32;
-  double2 *w, *zt, *t;
-  double2 *AZ, *AAZ, *dz;  // LGMRES: augmentation vectors z_a and A z_a (newest first), the cycle's correction
-};
 
 constexpr int kMaxGmresM = 200;  // stab_create rejects larger gmres_m
 constexpr long long kSelectiveMinN = 16384;  // unknowns from which GMRES uses selective reorthogonalisation
@@ -80,9 +70,25 @@ struct GmDev {
   int m;
 };
 
+// GMRES workspace layout (complex elements).  FP64 basis: V, Z (flexible).
+// FP32 basis: V32, and FP64 work vectors w (J z), zt (preconditioned
+// direction or correction) and t (V32 y).  Nested inner solver (FP64 outer
+// flexible GMRES): the inner FP32 basis V32 with w, zt, t, and the inner
+// cycle's least-squares state Din.
+struct GmresWs {
+  double2 *V, *Z, *r, *b, *x, *partial, *dh, *y;
+  double* dnorm;
+  float2* V32;
+  double2 *w, *zt, *t;
+  double2 *AZ, *AAZ, *dz;  // LGMRES: augmentation vectors z_a and A z_a (newest first), the cycle's correction
+  GmDev Din;               // nested inner GMRES (gmres_inner_m > 0)
+  int mi = 0;
+};
+
 struct GmReport {  // read by the host once per cycle
   double beta;     // ||b - A x|| after the cycle
   double znorm;    // LGMRES: ||x_new - x_old|| of the cycle (0: no augmentation vector stored)
+  double inner;    // nested inner solver: inner iterations (J v products) of the cycle
   int jend;        // iterations performed in the cycle
   int status;      // 0, or 1 when a Krylov quantity was not finite
 };
@@ -93,12 +99,17 @@ GmresWs gmres_ws(StabHandle* h, GmDev* D, GmReport** rep) {
   const bool pc = h->opts.precond == 1;
   const bool b32 = h->opts.gmres_basis_prec == 32;
   const int lgk = b32 ? 0 : h->opts.lgmres_k;
-  const bool flex = pc || lgk > 0;  // the directions Z_j are stored
-  const size_t part = (size_t)std::max(kry_partial_elems(n, m + 1), kry_dgks_partial_elems(n, m + 1));
+  const int mi = b32 ? 0 : h->opts.gmres_inner_m;
+  const bool flex = pc || lgk > 0 || mi > 0;  // the directions Z_j are stored
+  const int mp = std::max(m, mi);
+  const size_t part = (size_t)std::max(kry_partial_elems(n, mp + 1), kry_dgks_partial_elems(n, mp + 1));
   const size_t small = (size_t)m * m + (m + 1) + m + (m + 1) / 2 + 1 + 4 + 4;
+  const size_t small_in = mi > 0 ? (size_t)mi * mi + (mi + 1) + mi + (mi + 1) / 2 + 1 + 4 + 2 * (mi + 1) + (mi + 1) + 4
+                                 : 0;
   const size_t basis = b32 ? ((size_t)(m + 1) * n + 1) / 2 : (size_t)(m + 1) * n + (flex ? (size_t)m * n : 0);
-  const size_t work = b32 ? 6 * (size_t)n : 3 * (size_t)n + (lgk > 0 ? (2 * (size_t)lgk + 1) * n : 0);
-  size_t need = basis + work + part + 2 * (m + 1) + (m + 1) + 4 + small;
+  const size_t inner = mi > 0 ? ((size_t)(mi + 1) * n + 1) / 2 + 3 * (size_t)n : 0;
+  const size_t work = (b32 ? 6 * (size_t)n : 3 * (size_t)n + (lgk > 0 ? (2 * (size_t)lgk + 1) * n : 0)) + inner;
+  size_t need = basis + work + part + 2 * (m + 1) + (m + 1) + 4 + small + small_in;
   double2* base = ensure(h, &h->d_gm, &h->gm_elems, need);
   GmresWs w{};
   if (b32) {
@@ -123,6 +134,13 @@ GmresWs gmres_ws(StabHandle* h, GmDev* D, GmReport** rep) {
     w.dz = q + 2 * (size_t)lgk * n;
     q += (2 * (size_t)lgk + 1) * n;
   }
+  if (mi > 0) {
+    w.w = q;
+    w.zt = q + n;
+    w.t = q + 2 * n;
+    w.V32 = (float2*)(q + 3 * n);
+    q += 3 * (size_t)n + ((size_t)(mi + 1) * n + 1) / 2;
+  }
   w.partial = q;
   w.dh = w.partial + part;
   w.y = w.dh + 2 * (m + 1);
@@ -139,6 +157,20 @@ GmresWs gmres_ws(StabHandle* h, GmDev* D, GmReport** rep) {
   D->dnorm = w.dnorm;
   D->y = w.y;
   D->m = m;
+  if (mi > 0) {  // the inner cycle's own least-squares state, coefficients, norm and solution
+    GmDev& I = w.Din;
+    I.R = (hd::zc*)p; p += (size_t)mi * mi;
+    I.g = (hd::zc*)p; p += mi + 1;
+    I.sn = (hd::zc*)p; p += mi;
+    I.cs = (double*)p; p += (mi + 1) / 2 + 1;
+    I.flags = (int*)p; p += 1;
+    I.sc = (double*)p; p += 2;
+    I.dh = p; p += 2 * (mi + 1);
+    I.y = p; p += mi + 1;
+    I.dnorm = (double*)p; p += 2;
+    I.m = mi;
+    w.mi = mi;
+  }
   return w;
 }
 
@@ -240,12 +272,31 @@ __device__ __forceinline__ void gm_solve_body(const GmDev& d) {
 
 __global__ void k_gm_solve(GmDev d) { gm_solve_body(d); }
 
-__global__ void k_gm_report(GmDev d, GmReport* rep) {
+__global__ void k_gm_report(GmDev d, GmReport* rep, const double* inner_tally) {
   rep->beta = *d.dnorm;
   rep->znorm = d.sc[3];
+  rep->inner = inner_tally ? *inner_tally : 0.0;
   rep->jend = d.flags[1];
   rep->status = d.flags[2];
 }
+
+// Nested inner GMRES of one outer step: (J - sigma I) z = v_j from z = 0 with
+// ||v_j|| = 1, gated by the outer cycle (an outer cycle that has converged
+// skips its remaining inner solves); tol_in relative to ||v_j||.
+__global__ void k_gm_inner_init(GmDev in, const int* outer_flags, double tol_in) {
+  if (threadIdx.x == 0) {
+    in.flags[0] = outer_flags[0];
+    in.flags[1] = 0;
+    in.flags[2] = 0;
+    *const_cast<double*>(in.dnorm) = 1.0;
+    in.sc[0] = tol_in;
+  }
+  for (int i = threadIdx.x; i <= in.m; i += blockDim.x) in.g[i] = hd::mk(i == 0 ? 1.0 : 0.0);
+}
+
+// the inner iterations of a cycle, tallied in the inner state's sc[3]
+__global__ void k_gm_inner_reset(GmDev in) { in.sc[3] = 0.0; }
+__global__ void k_gm_inner_tally(GmDev in) { in.sc[3] += in.flags[1]; }
 
 // LGMRES: the newest augmentation pair from the cycle's correction dz and the
 // residuals before (beta_0 V_0) and after (r) it: z = dz / ||dz||,
@@ -290,6 +341,7 @@ cudaGraphExec_t gm_graph(StabHandle* h, cd sigma, int eps_mode, const GmresWs& W
   key.basis = h->opts.gmres_basis_prec;
   key.lgk = lgk;
   key.naug = naug;
+  key.mi = W.mi;
   cudaGraphExec_t& slot = h->gm_exec[naug];
   GmGraphKey& slot_key = h->gm_key[naug];
   if (slot && key == slot_key) return slot;
@@ -338,16 +390,49 @@ cudaGraphExec_t gm_graph(StabHandle* h, cd sigma, int eps_mode, const GmresWs& W
   } else if (err == cudaSuccess) {
     // LGMRES: the last naug of the m steps take the stored augmentation pairs (z_a, A z_a) instead of
     // a preconditioned Krylov direction and its J v
-    const bool flex = pc || lgk > 0;
+    const int mi = W.mi;
+    const bool flex = pc || lgk > 0 || mi > 0;
     const int nkry = m - naug;
     k_gm_cycle_init<<<1, 64, 0, h->stream>>>(D);
+    if (mi > 0) k_gm_inner_reset<<<1, 1, 0, h->stream>>>(W.Din);
     step(kry_scale(h, W.r, n, W.dnorm, W.V));
     for (int j = 0; j < m && err == cudaSuccess; ++j) {
       double2* Vj = W.V + (size_t)j * n;
       double2* Vn = W.V + (size_t)(j + 1) * n;
       double2* zj = flex ? W.Z + (size_t)j * n : Vj;
       h->gate = D.flags;
-      if (j < nkry) {
+      if (mi > 0) {
+        // nested: z_j = the inner FP32-basis GMRES(mi) approximation of (J - sigma I)^{-1} v_j (right
+        // preconditioned with the block inverses), the same steps as the FP32-basis cycle below
+        const GmDev& I = W.Din;
+        h->gate = nullptr;
+        k_gm_inner_init<<<1, 64, 0, h->stream>>>(I, D.flags, h->opts.gmres_inner_tol);
+        h->gate = I.flags;
+        step(kry_to_f32(h, Vj, n, nullptr, W.V32));
+        for (int i = 0; i < mi && err == cudaSuccess; ++i) {
+          const float2* Vi = W.V32 + (size_t)i * n;
+          float2* Vi1 = W.V32 + (size_t)(i + 1) * n;
+          h->gate = I.flags;
+          if (pc) step(pc_apply(h, nullptr, W.zt, Vi));
+          else step(kry_to_f64(h, Vi, n, W.zt));
+          step(jv_apply(h, W.zt, W.w, d2(sigma), eps_mode));
+          step(kry_to_f32(h, W.w, n, nullptr, Vi1));
+          step(kry_dgks32(h, W.V32, i + 1, n, Vi1, const_cast<double2*>(I.dh), const_cast<double*>(I.dnorm),
+                          W.partial));
+          h->gate = nullptr;
+          k_gm_step<<<1, 32, 0, h->stream>>>(I, i);
+          h->gate = I.flags;
+          step(kry_scale32(h, Vi1, n, I.dnorm));
+        }
+        h->gate = nullptr;
+        k_gm_solve<<<1, 64, 0, h->stream>>>(I);
+        k_gm_inner_tally<<<1, 1, 0, h->stream>>>(I);
+        step(kry_gemv32(h, W.V32, mi, I.flags + 1, n, I.y, W.t));
+        h->gate = D.flags;
+        if (pc) step(pc_apply(h, W.t, zj));
+        else step(kry_copy(h, W.t, zj, n));
+        step(jv_apply(h, zj, Vn, d2(sigma), eps_mode));
+      } else if (j < nkry) {
         if (pc) step(pc_apply(h, Vj, zj));
         else if (flex) step(kry_copy(h, Vj, zj, n));
         step(jv_apply(h, zj, Vn, d2(sigma), eps_mode));
@@ -385,14 +470,14 @@ cudaGraphExec_t gm_graph(StabHandle* h, cd sigma, int eps_mode, const GmresWs& W
       k_lg_store<<<(unsigned)nb, thr, 0, h->stream>>>(W.AZ, W.AAZ, W.dz, W.V, W.r, D.sc, n);
       step(cudaGetLastError());
     } else {
-      step(kry_gemv_add(h, pc ? W.Z : W.V, m, n, W.y, W.x, D.flags + 1));
+      step(kry_gemv_add(h, flex ? W.Z : W.V, m, n, W.y, W.x, D.flags + 1));
       step(jv_apply(h, W.x, W.r, d2(sigma), eps_mode));
       step(kry_axpby(h, make_double2(1.0, 0.0), W.b, make_double2(-1.0, 0.0), W.r, n));
     }
     step(launch_norm2(h, W.r, n, W.dnorm, 1));
   }
   if (began) {
-    if (err == cudaSuccess) k_gm_report<<<1, 1, 0, h->stream>>>(D, rep);
+    if (err == cudaSuccess) k_gm_report<<<1, 1, 0, h->stream>>>(D, rep, W.mi > 0 ? W.Din.sc + 3 : nullptr);
     step(cudaGetLastError());
     const cudaError_t e2 = cudaStreamEndCapture(h->cap_stream, &graph);
     if (err == cudaSuccess) err = e2;
@@ -442,7 +527,8 @@ int gmres(StabHandle* h, cd sigma, const double2* b, double2* x, int eps_mode, b
     ck(h, cudaMemcpyAsync(&rep, d_rep, sizeof(GmReport), cudaMemcpyDeviceToHost, h->stream), "report");
     ck(h, cudaStreamSynchronize(h->stream), "sync");
     total += rep.jend;
-    h->stats.jv_calls += std::min(rep.jend, m - naug) + 1;  // augmentation steps take no J v
+    h->stats.jv_calls += std::min(rep.jend, m - naug) + 1 + (long long)rep.inner;  // augmentation steps take
+                                                                                     // no J v; inner steps one
     if (lgk > 0) naug = rep.znorm > 0.0 ? std::min(naug + 1, lgk) : 0;
     if (rep.status) fail(h, STAB_ERR_NUMERIC, "GMRES: non-finite Krylov vector");
     if (!(rep.beta < INFINITY)) fail(h, STAB_ERR_NUMERIC, "GMRES: non-finite residual");
@@ -1294,7 +1380,9 @@ struct StreamSwap {
   }
 };
 
-bool batchable_solver(const StabHandle* h) { return h->opts.gmres_basis_prec == 64 && h->opts.lgmres_k == 0; }
+bool batchable_solver(const StabHandle* h) {
+  return h->opts.gmres_basis_prec == 64 && h->opts.lgmres_k == 0 && h->opts.gmres_inner_m == 0;
+}
 
 }  // namespace
 
@@ -1312,7 +1400,7 @@ extern "C" stab_status stab_jv_batch_solve(stab_jv_batch B, const double* sigmas
       return STAB_ERR_INVALID_ARG;
     }
     if (!batchable_solver(B->hs[i])) {
-      B->err = "stab_jv_batch_solve: instance " + std::to_string(i) + " uses an FP32 basis or LGMRES";
+      B->err = "stab_jv_batch_solve: instance " + std::to_string(i) + " uses an FP32 basis, LGMRES or a nested inner solver";
       return STAB_ERR_UNSUPPORTED;
     }
   }
@@ -1365,7 +1453,7 @@ extern "C" stab_status stab_jv_batch_eigs(stab_jv_batch B, stab_eig_job* jobs) {
       return STAB_ERR_INVALID_ARG;
     }
     if (!batchable_solver(h)) {
-      B->err = "stab_jv_batch_eigs: instance " + std::to_string(i) + " uses an FP32 basis or LGMRES";
+      B->err = "stab_jv_batch_eigs: instance " + std::to_string(i) + " uses an FP32 basis, LGMRES or a nested inner solver";
       return STAB_ERR_UNSUPPORTED;
     }
   }

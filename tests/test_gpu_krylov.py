@@ -254,3 +254,42 @@ def test_lgmres_option_checks():
         _stab(8, 16, gmres_m=4, lgmres_k=4)
     with pytest.raises(StabError, match="UNSUPPORTED"):
         _stab(8, 16, gmres_m=10, lgmres_k=2, gmres_basis_prec=32)
+
+
+def test_nested_fp32_inner_gmres_under_fp64_fgmres(orc):
+    """Mixed precision by nesting: FP64 flexible GMRES whose directions are
+    FP32-basis inner GMRES(10) solves (block-Jacobi inside, FP32 inverses):
+    the solution still meets the FP64 tolerance against the oracle's exact
+    tangent and equals the flat FGMRES solution; Cayley-IRAM with the nested
+    inner solver finds the dense LAPACK eigenvalues of the 8 x 16 layer."""
+    import torch
+    common = dict(eps_mode=2, precond=1, tile=(8, 8), precond_prec=32, gmres_tol=1e-10, gmres_max_restarts=400)
+    S0, g, f, q0 = _stab(32, 64, gmres_m=50, **common)
+    S1, _, _, _ = _stab(32, 64, gmres_m=20, gmres_inner_m=10, gmres_inner_tol=1e-3, **common)
+    b = torch.from_numpy(si.random_complex(5, g.n)).cuda()
+    x0, x1 = torch.zeros_like(b), torch.zeros_like(b)
+    st0, it0 = S0.solve(1.0, b, x0)
+    jv_before = S1.stats()["jv_calls"]
+    st1, it1 = S1.solve(1.0, b, x1)
+    jv1 = S1.stats()["jv_calls"] - jv_before
+    assert st0 == 0 and st1 == 0
+    assert jv1 > it1  # the inner solves' J v products are counted
+    assert rel_err(x1.cpu().numpy(), x0.cpu().numpy()) < 1e-8
+    xh, bh = x1.cpu().numpy(), b.cpu().numpy()
+    P = orc.Problem.from_inputs(g, f)
+    r = bh - (orc.core.jv(P, q0, xh, "tangent") - 1.0 * xh)
+    assert np.linalg.norm(r) <= 1.05e-10 * np.linalg.norm(bh)
+    S0.close()
+    S1.close()
+    S, g, f, q0 = _stab(8, 16, eps_mode=2, gmres_m=12, gmres_inner_m=8, gmres_tol=1e-12, gmres_max_restarts=400)
+    J = orc.core.dense_jacobian(orc.Problem.from_inputs(g, f), q0)
+    ref, _ = orc.stability.dense_reference(J, 0.25, -1.0, 2)
+    res = S.eigs(0.25, -1.0, nev=2, ncv=12, tol=1e-11)
+    S.close()
+    assert res.status == 0 and res.nconv == 2
+    for l in ref:
+        assert np.abs(res.lam - l).min() < 1e-8 * abs(l)
+    assert res.resid.max() < 1e-8
+    from paper_1502_03701_gb300 import StabError
+    with pytest.raises(StabError, match="UNSUPPORTED"):
+        _stab(8, 16, gmres_inner_m=4, gmres_basis_prec=32)
