@@ -1041,6 +1041,38 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_precond(args):
+    """--workload precond: block-Jacobi builds (assembly + inversion of every tile block, FP32 inverses) of
+    the --nx x --ny layer with --tile tiles, by the factorisation --factor (0 CUDA cores, 1 tensor cores
+    BF16x9, 2 tensor cores TF32); --steps timed builds after --warmup builds."""
+    import torch
+    from paper_1502_03701_gb300 import Stab, build
+    build.build()
+    g, f, q0 = _layer(args.nx, args.ny, 0.3)
+    tile = tuple(args.tile)
+    S = Stab(q0, g, f.Ma, f.Re, f.Pr, eps_mode=2, precond=1, tile=tile, precond_prec=32,
+             precond_factor=args.factor)
+    for i in range(args.warmup):
+        S.precond_build(1.0 + 1e-3 * i)
+    times = []
+    for i in range(args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        S.precond_build(2.0 + 1e-3 * i)
+        torch.cuda.synchronize()
+        times.append(time.perf_counter() - t0)
+    S.close()
+    b = 4 * tile[0] * tile[1]
+    nblk = g.npts // (tile[0] * tile[1])
+    flops = 8.0 * b ** 3 * nblk
+    t = statistics.median(times)
+    print(json.dumps({"metric": "block-Jacobi build", "value": flops / t / 1e12, "unit": "TFLOP/s",
+                      "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3,
+                      "higher_is_better": True, "dtype": "f32",
+                      "config": {"workload": f"precond_build_{g.nx}x{g.ny}", "tile": list(tile), "block": b,
+                                 "blocks": nblk, "factor": args.factor}}))
+
+
 def run_serve(args):
     """--workload serve: the served stream as the bench line (eigenpairs/s of the stream; p50/p99 beside)."""
     import torch
@@ -1066,7 +1098,9 @@ def main():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="jv", choices=["eigs", "jv", "serve"])
+    ap.add_argument("--workload", default="jv", choices=["eigs", "jv", "serve", "precond"])
+    ap.add_argument("--tile", type=int, nargs=2, default=[16, 16], help="block-Jacobi tile (--workload precond)")
+    ap.add_argument("--factor", type=int, default=1, help="precond_factor (--workload precond)")
     ap.add_argument("--requests", type=int, default=200, help="served stream length (--workload serve)")
     ap.add_argument("--plain-requests", type=int, default=16, help="requests also solved one at a time (serve)")
     ap.add_argument("--cohort", type=int, default=16, help="lockstep cohort size of the server (serve)")
@@ -1088,6 +1122,8 @@ def main():
         run_reference(args)
     elif args.workload == "serve":
         run_serve(args)
+    elif args.workload == "precond":
+        run_precond(args)
     else:
         run_ours(args)
 
