@@ -38,12 +38,15 @@ class _Prob(ctypes.Structure):
                 ("lx", ctypes.c_double), ("ly0", ctypes.c_double), ("ly1", ctypes.c_double),
                 ("lz", ctypes.c_double), ("stretch", ctypes.c_double),
                 ("gamma", ctypes.c_double), ("Ma", ctypes.c_double), ("Re", ctypes.c_double),
-                ("Pr", ctypes.c_double), ("S", ctypes.c_double), ("bulk", ctypes.c_double)]
+                ("Pr", ctypes.c_double), ("S", ctypes.c_double), ("bulk", ctypes.c_double),
+                ("low_order", ctypes.c_int)]
 
 
 @dataclass(frozen=True)
 class Problem:
-    """Grid + flow parameters (nondimensional; Re <= 0 means inviscid)."""
+    """Grid + flow parameters (nondimensional; Re <= 0 means inviscid).
+    low_order = 1 selects the reduced operator: every derivative by
+    second-order explicit differences instead of the compact schemes."""
     dim: int
     nx: int
     ny: int
@@ -59,11 +62,12 @@ class Problem:
     Pr: float
     S: float
     bulk: float = 0.0
+    low_order: int = 0
 
     @staticmethod
-    def from_inputs(grid, flow, bulk: float = 0.0) -> "Problem":
+    def from_inputs(grid, flow, bulk: float = 0.0, low_order: int = 0) -> "Problem":
         return Problem(grid.dim, grid.nx, grid.ny, grid.nz, grid.lx, grid.ly0, grid.ly1, grid.lz,
-                       grid.stretch, flow.gamma, flow.Ma, flow.Re, flow.Pr, flow.S, bulk)
+                       grid.stretch, flow.gamma, flow.Ma, flow.Re, flow.Pr, flow.S, bulk, low_order)
 
     @property
     def npts(self) -> int:
@@ -75,7 +79,7 @@ class Problem:
 
     def c(self) -> _Prob:
         return _Prob(self.dim, self.nx, self.ny, self.nz, self.lx, self.ly0, self.ly1, self.lz,
-                     self.stretch, self.gamma, self.Ma, self.Re, self.Pr, self.S, self.bulk)
+                     self.stretch, self.gamma, self.Ma, self.Re, self.Pr, self.S, self.bulk, self.low_order)
 
 
 def lib():
@@ -86,6 +90,7 @@ def lib():
         dp = ctypes.POINTER(ctypes.c_double)
         pp = ctypes.POINTER(_Prob)
         L.orc_deriv_line.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, dp, dp]
+        L.orc_deriv_line_low.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, dp, dp]
         L.orc_deriv_field.argtypes = [pp, dp, ctypes.c_int, ctypes.c_int, dp]
         for name in ("orc_rhs", "orc_rhs_quad"):
             getattr(L, name).argtypes = [pp, dp, dp, dp]
@@ -115,10 +120,11 @@ def num_threads() -> int:
     return int(lib().orc_num_threads())
 
 
-def deriv_line(f, h: float, order: int = 1, periodic: bool = True) -> np.ndarray:
+def deriv_line(f, h: float, order: int = 1, periodic: bool = True, low: bool = False) -> np.ndarray:
+    """Compact derivative of one line, or (low) the reduced operator's second-order explicit one."""
     f = _f64(f)
     out = np.empty_like(f)
-    lib().orc_deriv_line(order, int(periodic), f.size, h, _dp(f), _dp(out))
+    (lib().orc_deriv_line_low if low else lib().orc_deriv_line)(order, int(periodic), f.size, h, _dp(f), _dp(out))
     return out
 
 

@@ -69,6 +69,7 @@ struct OrcProblem {
   int dim, nx, ny, nz;
   double lx, ly0, ly1, lz, stretch;
   double gamma, Ma, Re, Pr, S, bulk;
+  int low_order;  // 1: the reduced operator (second-order explicit differences)
 };
 }
 
@@ -201,18 +202,48 @@ static void d2_bounded(const std::vector<T>& f, std::vector<T>& out, double h) {
 }
 
 // ---------------------------------------------------------------------------
+// Reduced operator (Sec. "Numerical experiments", the proposed preconditioner
+// operator: a non-compact, lower-order discretisation of N).  Second-order
+// explicit central differences, f'_i = (f_{i+1} - f_{i-1})/(2h) and
+// f''_i = (f_{i+1} - 2 f_i + f_{i-1})/h^2; on a bounded line the end rows use
+// the second-order one-sided forms f'_0 = (-3 f_0 + 4 f_1 - f_2)/(2h) and
+// f''_0 = (2 f_0 - 5 f_1 + 4 f_2 - f_3)/h^2 (mirrored, the first with a sign
+// change, at the far end).
+// ---------------------------------------------------------------------------
+template <class T>
+static void low_line(const std::vector<T>& f, std::vector<T>& out, double h, int order, bool periodic) {
+  const int n = (int)f.size();
+  out.assign(n, T(0));
+  for (int i = 0; i < n; ++i) {
+    int ip = i + 1, im = i - 1;
+    if (periodic) { ip %= n; im = (im + n) % n; }
+    else if (i == 0 || i == n - 1) continue;
+    out[i] = order == 1 ? (f[ip] - f[im]) / (2.0 * h) : (f[ip] - 2.0 * f[i] + f[im]) / (h * h);
+  }
+  if (periodic) return;
+  const int e = n - 1;
+  if (order == 1) {
+    out[0] = (-3.0 * f[0] + 4.0 * f[1] - f[2]) / (2.0 * h);
+    out[e] = (3.0 * f[e] - 4.0 * f[e - 1] + f[e - 2]) / (2.0 * h);
+  } else {
+    out[0] = (2.0 * f[0] - 5.0 * f[1] + 4.0 * f[2] - f[3]) / (h * h);
+    out[e] = (2.0 * f[e] - 5.0 * f[e - 1] + 4.0 * f[e - 2] - f[e - 3]) / (h * h);
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Grid fields and derivatives along an axis (0 = x, 1 = y, 2 = z).
 // Arrays are [z][y][x], x fastest.
 // ---------------------------------------------------------------------------
 struct Geo {
-  int nx, ny, nz, dim;
+  int nx, ny, nz, dim, low;
   double hx, hz, heta;
   std::vector<double> yp, ypp;  // dy/deta, d2y/deta2 per y row
 };
 
 static Geo make_geo(const OrcProblem& P) {
   Geo g;
-  g.nx = P.nx; g.ny = P.ny; g.nz = P.nz; g.dim = P.dim;
+  g.nx = P.nx; g.ny = P.ny; g.nz = P.nz; g.dim = P.dim; g.low = P.low_order;
   g.hx = P.lx / P.nx;
   g.hz = P.dim == 3 ? P.lz / P.nz : 1.0;
   g.heta = 1.0 / (P.ny - 1);
@@ -254,14 +285,15 @@ static std::vector<T> deriv(const Geo& g, const std::vector<T>& f, int axis, int
     for (int k = 0; k < len; ++k) line[k] = f[idx(k)];
     if (axis == 0 || axis == 2) {
       double h = axis == 0 ? g.hx : g.hz;
-      if (order == 1) d1_periodic(line, d1, h); else d2_periodic(line, d1, h);
+      if (g.low) low_line(line, d1, h, order, true);
+      else if (order == 1) d1_periodic(line, d1, h); else d2_periodic(line, d1, h);
       for (int k = 0; k < len; ++k) out[idx(k)] = d1[k];
     } else {
-      d1_bounded(line, d1, g.heta);
+      if (g.low) low_line(line, d1, g.heta, 1, false); else d1_bounded(line, d1, g.heta);
       if (order == 1) {
         for (int k = 0; k < len; ++k) out[idx(k)] = d1[k] / g.yp[k];
       } else {
-        d2_bounded(line, d2, g.heta);
+        if (g.low) low_line(line, d2, g.heta, 2, false); else d2_bounded(line, d2, g.heta);
         for (int k = 0; k < len; ++k)
           out[idx(k)] = d2[k] / (g.yp[k] * g.yp[k]) - g.ypp[k] * d1[k] / (g.yp[k] * g.yp[k] * g.yp[k]);
       }
@@ -433,6 +465,13 @@ void orc_deriv_line(int order, int periodic, int n, double h, const double* f, d
   std::vector<double> line(f, f + n), d;
   if (periodic) { if (order == 1) d1_periodic(line, d, h); else d2_periodic(line, d, h); }
   else { if (order == 1) d1_bounded(line, d, h); else d2_bounded(line, d, h); }
+  std::memcpy(out, d.data(), sizeof(double) * n);
+}
+
+// One second-order explicit derivative of a single line (the reduced operator).
+void orc_deriv_line_low(int order, int periodic, int n, double h, const double* f, double* out) {
+  std::vector<double> line(f, f + n), d;
+  low_line(line, d, h, order, periodic != 0);
   std::memcpy(out, d.data(), sizeof(double) * n);
 }
 

@@ -65,8 +65,6 @@ static void free_handle(stab_handle h) {
   dfree(h, h->d_coef);
   dfree(h, h->d_coef_f);
   dfree(h, h->d_coef_p);
-  dfree(h, h->d_coef_sp);
-  dfree(h, h->d_sp_idx);
   dfree(h, h->d_btab_f);
   for (int a = 0; a < 3; ++a) {
     dfree(h, h->ax[a].tab[0]);

@@ -127,13 +127,6 @@ struct StabHandle {
   double* d_coef_f;      // the same with the y metric folded in (inputs: eta-derivatives)
   struct ffn* d_coef_p;  // d_coef_f as FP32 pairs (hi, lo), read by the pointwise kernel
   float* d_btab_f;       // FP32 copy of the base tables (for the O(eps) remainder)
-  // the per-row coefficients that are nonzero in some row (compact pointwise map): sp_q[k] = input of
-  // entry k, entries of output a in [sp_start[a], sp_start[a + 1]); d_coef_sp = [ny][sp_nnz] pairs
-  struct ffn* d_coef_sp = nullptr;
-  int* d_sp_idx = nullptr;  // device copy: sp_start[D + 3], then sp_q[sp_nnz]
-  int sp_nnz = 0;
-  unsigned char sp_q[5 * 45];
-  short sp_start[6];
   bool force_dn_path;    // use the full FP64 difference-number pointwise kernel
   void* cublas = nullptr;  // cuBLAS handle of the tensor-core block factorisation (created on first use)
   // statistics

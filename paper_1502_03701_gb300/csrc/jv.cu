@@ -835,113 +835,6 @@ __global__ void __launch_bounds__(128, D == 2 ? 4 : 3) k_point_fast(const PointP
   point_fast_body<D>(P, coefp, btab_f, blockIdx.x, gridDim.x);
 }
 
-// The same map with only the coefficients that are nonzero in some row: entry
-// k of a row is (output of its range, input q[k]); the row's pairs are stored
-// back to back.  The inputs of a point, split into pairs, are staged in
-// shared memory (one column per thread), so the products loop over the entries
-// at run time.  Exact-zero coefficients add nothing to a pair sum, and the
-// remaining products are accumulated in the same order, so the results equal
-// k_point_fast's bit for bit.
-constexpr int kSparseThreads = 128;
-
-// idx: start[D + 3] (output ranges) then q[nnz] (inputs), in device memory
-template <int D>
-__global__ void __launch_bounds__(kSparseThreads, D == 2 ? 4 : 3)
-    k_point_sparse(const PointParams P, const ffn* __restrict__ coefs, int nnz, const int* __restrict__ idx,
-                   const float* __restrict__ btab_f) {
-  if (P.gate && *P.gate) return;
-  const int* __restrict__ qi = idx + D + 3;
-  constexpr int NW = pw::nw_inputs(D);
-  constexpr int o2 = (D + 3) + D * (D + 3), om = o2 + D * (D + 1);
-  extern __shared__ float2 sw[];  // [NW][kSparseThreads]
-  const int tid = threadIdx.x;
-  const double e = *P.eps;
-  const bool visc = P.phys.visc;
-  for (long long pt = (long long)blockIdx.x * blockDim.x + tid; pt < P.npts; pt += (long long)gridDim.x * blockDim.x) {
-    const int j = row_of(P, pt);
-    const bool bc_row = (j == 0 || j == P.ny - 1);
-    const unsigned fl = bc_row ? P.bcflags[(j == P.ny - 1 ? (long long)P.nx * P.nz : 0)] : 0u;
-    const float2* Cp = (const float2*)(coefs + (long long)j * nnz);
-    auto S = [&](int slot) { return P.scratch[(long long)slot * P.npts + pt]; };
-#pragma unroll 1
-    for (int part = 0; part < 2; ++part) {
-      auto pick = [&](double2 z) { return part ? z.y : z.x; };
-      auto put = [&](int q, double v) {
-        const ffn f = ff_split(v);
-        sw[q * kSparseThreads + tid] = make_float2(f.hi, f.lo);
-      };
-#pragma unroll
-      for (int f = 0; f < D + 2; ++f) put(f, pick(P.v[(long long)f * P.npts + pt]));
-      put(D + 2, visc ? pick(S(P.s_Tw)) : 0.0);
-#pragma unroll
-      for (int ax = 0; ax < D; ++ax)
-#pragma unroll
-        for (int f = 0; f < D + 3; ++f)
-          put(D + 3 + ax * (D + 3) + f, (f < D + 2 || visc) ? pick(S(P.s_d1[ax][f])) : 0.0);
-#pragma unroll
-      for (int ax = 0; ax < D; ++ax)
-#pragma unroll
-        for (int g = 0; g < D + 1; ++g) put(o2 + ax * (D + 1) + g, visc ? pick(S(P.s_d2[ax][g])) : 0.0);
-#pragma unroll
-      for (int a = 0; a < D; ++a)
-#pragma unroll
-        for (int c = 0; c < D; ++c) put(om + a * D + c, (visc && a != c) ? pick(S(P.s_mix[a][c])) : 0.0);
-      double res[D + 2];
-#pragma unroll
-      for (int a = 0; a < D + 2; ++a) {
-        ffn acc{0.0f, 0.0f};
-        const int k1 = __ldg(idx + a + 1);
-        for (int k = __ldg(idx + a); k < k1; ++k) {
-          const float2 c = __ldg(Cp + k);
-          const float2 w = sw[__ldg(qi + k) * kSparseThreads + tid];
-          ff_acc_prod(acc, ffn{c.x, c.y}, ffn{w.x, w.y});
-        }
-        res[a] = ff_to_d(acc);
-      }
-      if (e != 0.0) {  // O(eps) remainder, as in k_point_fast
-        const float ey = ff_split(P.eta_y[j]).hi, eyy = ff_split(P.eta_yy[j]).hi;
-        pw::WIn<D, float> Wf;
-#pragma unroll
-        for (int q = 0; q < NW; ++q) set_input<D, float>(Wf, q, sw[q * kSparseThreads + tid].x);
-#pragma unroll
-        for (int f = 0; f < D + 3; ++f) Wf.d1[1][f] *= ey;
-#pragma unroll
-        for (int g = 0; g < D + 1; ++g)
-          Wf.d2[1][g] = fmaf(Wf.d2[1][g], ey * ey,
-                             sw[(D + 3 + (D + 3) + (g < D ? 1 + g : D + 2)) * kSparseThreads + tid].x * eyy);
-#pragma unroll
-        for (int a = 0; a < D; ++a)
-#pragma unroll
-          for (int c = 0; c < D; ++c)
-            if (a == 1 || c == 1) Wf.mix[a][c] *= ey;
-        auto Bf = [&](int slot) { return btab_f[(long long)slot * P.nbase + j]; };
-        pw::DN3 o[D + 2];
-        pw::rhs_num<D, pw::DN3>(P.phys, Bf, Wf, e, bc_row, fl, o);
-#pragma unroll
-        for (int a = 0; a < D + 2; ++a) res[a] += f2d_exact(o[a].w2);
-      }
-#pragma unroll
-      for (int a = 0; a < D + 2; ++a) {
-        const long long o = (long long)a * P.npts + pt;
-        double2 vv = P.v[o];
-        double sv = part ? (P.shift.x * vv.y + P.shift.y * vv.x) : (P.shift.x * vv.x - P.shift.y * vv.y);
-        double r = res[a] - sv;
-        if (part) P.out[o].y = r; else P.out[o].x = r;
-      }
-    }
-  }
-}
-
-__global__ void k_gather_pairs(const ffn* __restrict__ dense, int row_len, const short* __restrict__ idx, int nnz,
-                               int rows, ffn* out) {
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < (long long)rows * nnz;
-       i += (long long)gridDim.x * blockDim.x) {
-    const long long r = i / nnz;
-    const int k = (int)(i - r * nnz);
-    out[i] = dense[r * row_len + idx[k]];
-  }
-}
-
 // Fold the y metric into the per-row coefficients so that the pointwise kernel
 // can use the line passes' eta-derivatives directly:
 //   f_y = f_eta ey,  f_yy = f_etaeta ey^2 + f_eta eyy,  mixed with y: x ey.
@@ -1663,9 +1556,6 @@ cudaError_t jv_setup(StabHandle* h, const double* q0_host) {
   for (const void* k : line_kernels)
     if ((err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLineSmemMax)) != cudaSuccess)
       return err;
-  const int sp_sm = pw::nw_inputs(3) * kSparseThreads * (int)sizeof(float2);  // 46 KB for the 3-D inputs
-  if ((err = cudaFuncSetAttribute((const void*)k_point_sparse<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  sp_sm)) != cudaSuccess) return err;
   make_slots(h);
   // axis tables: x (0) periodic, y (1) bounded in eta, z (2) periodic
   const int lens[3] = {h->nx, h->ny, h->nz};
@@ -1802,46 +1692,6 @@ cudaError_t jv_setup(StabHandle* h, const double* q0_host) {
     if ((err = dalloc(h, &h->d_btab_f, nbt * sizeof(float))) != cudaSuccess) return err;
     k_to_float_tab<<<64, 256, 0, h->stream>>>(h->d_btab, h->d_btab_f, nbt);
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
-    // the coefficients that are nonzero in some row, for the compact pointwise kernel
-    std::vector<double> cf((size_t)ncf);
-    if ((err = cudaMemcpyAsync(cf.data(), h->d_coef_f, ncf * sizeof(double), cudaMemcpyDeviceToHost, h->stream)) !=
-        cudaSuccess) return err;
-    if ((err = cudaStreamSynchronize(h->stream)) != cudaSuccess) return err;
-    const int rl = (D + 2) * nw;
-    std::vector<short> idx;
-    int k = 0;
-    for (int a = 0; a < D + 2; ++a) {
-      h->sp_start[a] = (short)k;
-      for (int q = 0; q < nw; ++q) {
-        bool nz = false;
-        for (int j = 0; j < h->ny && !nz; ++j) nz = cf[(size_t)j * rl + a * nw + q] != 0.0;
-        if (nz) {
-          h->sp_q[k++] = (unsigned char)q;
-          idx.push_back((short)(a * nw + q));
-        }
-      }
-    }
-    h->sp_start[D + 2] = (short)k;
-    h->sp_nnz = k;
-    if (k > 0 && k < rl) {  // worth it only when some coefficient is zero everywhere
-      short* didx;
-      if ((err = dalloc(h, &didx, idx.size() * sizeof(short))) != cudaSuccess) return err;
-      if ((err = cudaMemcpyAsync(didx, idx.data(), idx.size() * sizeof(short), cudaMemcpyHostToDevice, h->stream)) !=
-          cudaSuccess) return err;
-      if ((err = dalloc(h, &h->d_coef_sp, (size_t)h->ny * k * sizeof(ffn))) != cudaSuccess) return err;
-      k_gather_pairs<<<64, 256, 0, h->stream>>>(h->d_coef_p, rl, didx, k, h->ny, h->d_coef_sp);
-      if ((err = cudaGetLastError()) != cudaSuccess) return err;
-      std::vector<int> si(D + 3 + k);
-      for (int a = 0; a <= D + 2; ++a) si[a] = h->sp_start[a];
-      for (int q = 0; q < k; ++q) si[D + 3 + q] = h->sp_q[q];
-      if ((err = dalloc(h, &h->d_sp_idx, si.size() * sizeof(int))) != cudaSuccess) return err;
-      if ((err = cudaMemcpyAsync(h->d_sp_idx, si.data(), si.size() * sizeof(int), cudaMemcpyHostToDevice,
-                                 h->stream)) != cudaSuccess) return err;
-      if ((err = cudaStreamSynchronize(h->stream)) != cudaSuccess) return err;
-      dfree(h, didx);
-    } else {
-      h->sp_nnz = 0;
-    }
   }
   if ((err = cudaStreamSynchronize(h->stream)) != cudaSuccess) return err;
   dfree(h, bv);
@@ -1891,14 +1741,7 @@ cudaError_t jv_apply(StabHandle* h, const double2* v, double2* out, double2 shif
   src[D + 2] = Tw;
   if ((err = run_derivatives(h, src, h->stencil_ff)) != cudaSuccess) return err;
   const int tp = phase_begin(h, STAB_PHASE_POINTWISE);
-  if (fast && h->sp_nnz > 0) {
-    const size_t sm = (size_t)pw::nw_inputs(D) * kSparseThreads * sizeof(float2);
-    const int nb = grid_for(h->npts, kSparseThreads);
-    if (D == 2)
-      k_point_sparse<2><<<nb, kSparseThreads, sm, h->stream>>>(P, h->d_coef_sp, h->sp_nnz, h->d_sp_idx, h->d_btab_f);
-    else
-      k_point_sparse<3><<<nb, kSparseThreads, sm, h->stream>>>(P, h->d_coef_sp, h->sp_nnz, h->d_sp_idx, h->d_btab_f);
-  } else if (fast) {
+  if (fast) {
     if (D == 2) k_point_fast<2><<<grid_for(h->npts, thr), thr, 0, h->stream>>>(P, h->d_coef_p, h->d_btab_f);
     else k_point_fast<3><<<grid_for(h->npts, thr), thr, 0, h->stream>>>(P, h->d_coef_p, h->d_btab_f);
   } else {

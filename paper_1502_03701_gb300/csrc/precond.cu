@@ -523,7 +523,12 @@ AsmParams asm_params(StabHandle* h, const Geo& g, double2 sigma) {
 // applied to the other columns C and every other column is updated at once:
 // A[:, C] <- E_K A[:, C] = A[:, C] + (W - I_K) A[K, C], i.e. with R = A[K, C]
 // saved and A[K, C] set to zero, A[:, C] += W R (one GEMM per side of K).
-// The column interchanges are undone at the end, as in the unblocked sweep.
+// Two levels: the panels of an outer block of PB columns update only the
+// columns of that outer block (GEMMs with K = one panel); the outer block's
+// transform, accumulated in its PB columns in the same in-place form, then
+// updates every other column (GEMMs with K = PB).  Both levels are the same
+// identity applied to nested column sets, so the result is the unblocked
+// sweep's up to rounding.  The column interchanges are undone at the end.
 // ---------------------------------------------------------------------------
 constexpr int kPanelThreads = 256;
 
@@ -623,26 +628,27 @@ __global__ void __launch_bounds__(kPanelThreads) k_gj_panel(float2* A, int b, in
   if (threadIdx.x == 0 && bad) atomicMax(info, 1);
 }
 
-// The panel's row interchanges on the columns outside K, then T = A[K, :]
-// (w x b, saved) and A[K, C] = 0.  Thread j owns column j.
-__global__ void k_gj_swap_copy(float2* A, int b, int k0, int w, const int* piv, float2* T) {
+// The row interchanges of steps [r0, r0 + rw) on the columns C = [lo, hi)
+// outside K = [r0, r0 + rw), then T[kk][j] = A[r0 + kk][j] for j in C (saved,
+// row length b) and A[K, C] = 0.  Thread j owns column j.
+__global__ void k_gj_swap_copy(float2* A, int b, int r0, int rw, int lo, int hi, const int* piv, float2* T,
+                               long long tstride) {
   float2* M = A + (long long)blockIdx.x * b * b;
   const int* pv = piv + (long long)blockIdx.x * b;
-  float2* Tb = T + (long long)blockIdx.x * w * b;
-  for (int j = threadIdx.x; j < b; j += blockDim.x) {
-    const bool inK = j >= k0 && j < k0 + w;
-    if (!inK)
-      for (int kk = 0; kk < w; ++kk) {
-        const int k = k0 + kk, p = pv[k];
-        if (p != k) {
-          const float2 a = M[(long long)k * b + j];
-          M[(long long)k * b + j] = M[(long long)p * b + j];
-          M[(long long)p * b + j] = a;
-        }
+  float2* Tb = T + (long long)blockIdx.x * tstride;
+  for (int j = lo + threadIdx.x; j < hi; j += blockDim.x) {
+    if (j >= r0 && j < r0 + rw) continue;
+    for (int kk = 0; kk < rw; ++kk) {
+      const int k = r0 + kk, p = pv[k];
+      if (p != k) {
+        const float2 a = M[(long long)k * b + j];
+        M[(long long)k * b + j] = M[(long long)p * b + j];
+        M[(long long)p * b + j] = a;
       }
-    for (int kk = 0; kk < w; ++kk) {
-      Tb[(long long)kk * b + j] = M[(long long)(k0 + kk) * b + j];
-      if (!inK) M[(long long)(k0 + kk) * b + j] = make_float2(0.0f, 0.0f);
+    }
+    for (int kk = 0; kk < rw; ++kk) {
+      Tb[(long long)kk * b + j] = M[(long long)(r0 + kk) * b + j];
+      M[(long long)(r0 + kk) * b + j] = make_float2(0.0f, 0.0f);
     }
   }
 }
@@ -673,9 +679,13 @@ cudaError_t launch_assemble(StabHandle* h, AsmParams& P, long long ntile_batch) 
   return cudaGetLastError();
 }
 
+// Outer block width of the two-level sweep (a multiple of both panel widths).
+int gj_outer(int b) { return b <= 512 ? 128 : 256; }
+
 // In-place inversion of nb FP32 blocks (b x b, row-major) by the blocked
 // Gauss-Jordan sweep above; mode 1: GEMMs with FP32 inputs emulated on the
 // BF16 tensor cores (BF16x9, FP32 accuracy), mode 2: TF32 tensor cores.
+// T holds gj_outer(b) x b complex values per block.
 cudaError_t gj_blocked(StabHandle* h, float2* A, int b, long long nb, int* piv, float2* T, int* d_info, int mode) {
   if (!h->cublas) {
     cublasHandle_t c;
@@ -691,28 +701,42 @@ cudaError_t gj_blocked(StabHandle* h, float2* A, int b, long long nb, int* piv, 
   }
   // panels of 32 columns while the b x 33 panel fits in shared memory (b <= 640), else 16
   const int W = b <= 640 ? 32 : 16;
+  const int PB = gj_outer(b);
+  const long long tstride = (long long)PB * b;
   const size_t psm = (size_t)b * (W + 1) * sizeof(float2);
   cudaError_t ea = cudaFuncSetAttribute(W == 32 ? (const void*)k_gj_panel<32> : (const void*)k_gj_panel<16>,
                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psm);
   if (ea != cudaSuccess) return ea;
   const cuComplex one = make_cuComplex(1.0f, 0.0f);
-  for (int k0 = 0; k0 < b; k0 += W) {
-    const int w = std::min(W, b - k0);
-    if (W == 32) k_gj_panel<32><<<(unsigned)nb, kPanelThreads, psm, h->stream>>>(A, b, k0, w, piv, d_info);
-    else k_gj_panel<16><<<(unsigned)nb, kPanelThreads, psm, h->stream>>>(A, b, k0, w, piv, d_info);
-    k_gj_swap_copy<<<(unsigned)nb, 256, 0, h->stream>>>(A, b, k0, w, piv, T);
+  // rows [r0, r0 + rw) eliminated: interchanges, T and zeroing on [lo, hi) outside them, then
+  // (column-major view X = A^T, ld b) X[C, :] += T^T[C, :] X[K, :] for C left and right of K
+  auto update = [&](int r0, int rw, int lo, int hi) -> cudaError_t {
+    k_gj_swap_copy<<<(unsigned)nb, 256, 0, h->stream>>>(A, b, r0, rw, lo, hi, piv, T, tstride);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    // column-major view X = A^T (ld b): X[C, :] += T^T[C, :] X[K, :], for C left and right of K
-    const int right = b - (k0 + w);
     for (int side = 0; side < 2; ++side) {
-      const int m = side == 0 ? k0 : right;
-      const int off = side == 0 ? 0 : k0 + w;
+      const int c0 = side == 0 ? lo : r0 + rw;
+      const int m = side == 0 ? r0 - lo : hi - (r0 + rw);
       if (m <= 0) continue;
       const cublasStatus_t st = cublasGemmStridedBatchedEx(
-          cb, CUBLAS_OP_N, CUBLAS_OP_N, m, b, w, &one, T + off, CUDA_C_32F, b, (long long)w * b, A + k0, CUDA_C_32F, b,
-          (long long)b * b, &one, A + off, CUDA_C_32F, b, (long long)b * b, (int)nb, ct, CUBLAS_GEMM_DEFAULT);
+          cb, CUBLAS_OP_N, CUBLAS_OP_N, m, b, rw, &one, T + c0, CUDA_C_32F, b, tstride, A + r0, CUDA_C_32F, b,
+          (long long)b * b, &one, A + c0, CUDA_C_32F, b, (long long)b * b, (int)nb, ct, CUBLAS_GEMM_DEFAULT);
       if (st != CUBLAS_STATUS_SUCCESS) return st == CUBLAS_STATUS_NOT_SUPPORTED ? cudaErrorNotSupported : cudaErrorUnknown;
+    }
+    return cudaSuccess;
+  };
+  for (int o0 = 0; o0 < b; o0 += PB) {
+    const int ow = std::min(PB, b - o0);
+    for (int k0 = o0; k0 < o0 + ow; k0 += W) {
+      const int w = std::min(W, o0 + ow - k0);
+      if (W == 32) k_gj_panel<32><<<(unsigned)nb, kPanelThreads, psm, h->stream>>>(A, b, k0, w, piv, d_info);
+      else k_gj_panel<16><<<(unsigned)nb, kPanelThreads, psm, h->stream>>>(A, b, k0, w, piv, d_info);
+      cudaError_t e = update(k0, w, o0, o0 + ow);
+      if (e != cudaSuccess) return e;
+    }
+    if (ow < b) {
+      cudaError_t e = update(o0, ow, 0, b);
+      if (e != cudaSuccess) return e;
     }
   }
   k_gj_unpermute<<<(unsigned)nb, 256, 0, h->stream>>>(A, b, piv);
@@ -763,7 +787,7 @@ cudaError_t pc_build(StabHandle* h, double2 sigma) {
   float2* T = nullptr;
   if (fac && prec != 64) {
     if ((e = dalloc(h, &piv, (size_t)batch * g.bsz * sizeof(int))) != cudaSuccess) return e;
-    if ((e = dalloc(h, &T, (size_t)batch * 32 * g.bsz * sizeof(float2))) != cudaSuccess) return e;
+    if ((e = dalloc(h, &T, (size_t)batch * gj_outer(g.bsz) * g.bsz * sizeof(float2))) != cudaSuccess) return e;
   }
   int* d_info;
   if ((e = dalloc(h, &d_info, sizeof(int))) != cudaSuccess) return e;

@@ -67,7 +67,11 @@ extern "C" long long stab_estimate_bytes(const stab_grid* g, const stab_opts* op
     const long long ntiles = npts / std::max<long long>(1, o.tile[0] * o.tile[1] * tz);
     const long long bb = bsz * bsz;
     b += ntiles * bb * (o.precond_prec == 64 ? 16 : o.precond_prec == 32 ? 8 : 4);  // inverses
-    b += std::min<long long>(ntiles, std::max<long long>(1, (1ll << 30) / (bb * 16))) * bb * 16;  // assembly batch
+    const long long batch = std::min<long long>(ntiles, std::max<long long>(1, (1ll << 30) / (bb * 16)));
+    b += batch * bb * 16;                                  // assembly batch
+    if (o.precond_prec == 16) b += batch * bb * 8;         // FP32 inversion before rounding to BF16
+    if (o.precond_factor && o.precond_prec != 64)          // pivots and the saved rows of the blocked sweep
+      b += batch * bsz * (4 + (bsz <= 512 ? 128 : 256) * 8);
     const long long la = std::max<long long>({(long long)g->nx, (long long)g->ny, D == 3 ? g->nz : 1});
     b += (long long)D * 3 * la * la * 16;                  // 1-D derivative matrices
   }
