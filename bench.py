@@ -20,6 +20,11 @@ the same run:
   * "gmres_256x512": preconditioned FGMRES(50) iterations per second on the
     256 x 512 layer (block-Jacobi over 8 x 8-point tiles, FP32 inverses; also
     BF16 inverses, and BF16 inverses with an FP32 Krylov basis);
+  * "precond_build_256x512": the block-Jacobi build on the CUDA cores and with
+    tensor-core GEMMs (BF16x9, TF32), 8 x 8 and 16 x 16 tiles;
+  * "preconditioners_256x512": the inner solve to 1e-10 at sigma = 1 with exact
+    8 x 32 blocks against reduced-operator blocks (block-tridiagonal factors)
+    over taller tiles: iterations, time, build, factor bytes, apply time;
   * "jv_batch_64": J v and block-Jacobi apply of the 64 uneven instances of the batch
     configuration as one batched call (one launch per phase) against 64 single-problem calls;
   * "many_small": uneven small layers solved one at a time on the plain FP64
@@ -384,6 +389,60 @@ def precond_build_256x512(args, Stab, torch) -> dict:
             S.close()
             row[key] = {"seconds": dt, "TFLOP_per_s": flops / dt / 1e12}
         out[f"{tile[0]}x{tile[1]}"] = row
+    return out
+
+
+def preconditioners_256x512(args, Stab, torch) -> dict:
+    """The 256 x 512 inner solve (FGMRES(50) to 1e-10 at sigma = 1) with exact tile blocks (block-Jacobi
+    over 8 x 32 tiles, FP32 inverses factorised with TF32 tensor-core GEMMs) against the reduced-operator
+    blocks (second-order explicit operator, block-tridiagonal FP32 factors) over taller tiles: iterations,
+    solve time, build time, factor bytes and the time of one block apply (CUDA events, 20 applies)."""
+    g, f, q0 = _layer(256, 512, 0.3)
+    sigma = 1.0
+    b = torch.from_numpy(si.random_complex(1, g.n)).cuda()
+    out = {"sigma": sigma, "tol": 1e-10, "gmres": "FGMRES(50)"}
+    variants = (("exact_8x32", dict(precond=1, tile=(8, 32), precond_factor=2)),
+                ("reduced_8x64", dict(precond=2, tile=(8, 64))),
+                ("reduced_8x512", dict(precond=2, tile=(8, 512))),
+                ("reduced_4x512", dict(precond=2, tile=(4, 512))))
+    for key, o in variants:
+        S = Stab(q0, g, f.Ma, f.Re, f.Pr, eps_mode=2, precond_prec=32, gmres_m=50, gmres_tol=1e-10,
+                 gmres_max_restarts=120, **o)
+        S.autotune()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        S.precond_build(sigma)
+        torch.cuda.synchronize()
+        t_build = time.perf_counter() - t0
+        z = torch.empty_like(b)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        S.precond_apply(b, z)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(20):
+            S.precond_apply(b, z)
+        e1.record()
+        torch.cuda.synchronize()
+        apply_ms = e0.elapsed_time(e1) / 20
+        x = torch.zeros_like(b)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st, it = S.solve(sigma, b, x)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        ax = torch.empty_like(b)
+        S.apply_J(x, ax, sigma)
+        res = float(torch.linalg.vector_norm(b - ax) / torch.linalg.vector_norm(b))
+        tile = o["tile"]
+        if o["precond"] == 1:
+            nbytes = g.n * 4 * tile[0] * tile[1] * 8
+        else:
+            m = 4 * 2 * tile[0]
+            nbytes = g.n * 3 * m * 8
+        S.close()
+        out[key] = {"iterations": it, "converged": st == 0, "true_rel_residual": res, "solve_s": dt,
+                    "ms_per_iteration": 1e3 * dt / max(it, 1), "build_s": t_build, "apply_ms": apply_ms,
+                    "factor_bytes": nbytes, "apply_GB_per_s": nbytes / apply_ms / 1e6}
     return out
 
 
@@ -929,6 +988,7 @@ def run_ours(args):
             g2, f2, q2 = _layer(256, 512, 0.3)
             extra["gmres_256x512"] = gmres_throughput(args, Stab, torch, q2, g2, f2)
             extra["precond_build_256x512"] = precond_build_256x512(args, Stab, torch)
+            extra["preconditioners_256x512"] = preconditioners_256x512(args, Stab, torch)
         if args.fleet > 0 and world == 1:
             extra["jv_batch_64"] = jv_batch_64(args, torch)
             extra["gmres_batch_64"] = gmres_batch_64(args, torch)

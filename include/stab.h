@@ -67,7 +67,14 @@ typedef struct {
   int gmres_m;            /* inner GMRES restart length, default 30 */
   int gmres_max_restarts; /* default 200 */
   double gmres_tol;       /* inner relative residual tolerance, default 1e-10 */
-  int precond;            /* 0 none, 1 block-Jacobi */
+  int precond;            /* 0 none, 1 block-Jacobi (exact tile blocks of J), 2 block-Jacobi of the reduced
+                             operator (Sec. "Numerical experiments", Conclusions: the right-hand side
+                             discretised with second-order explicit differences, f' = (f+1 - f-1)/(2h),
+                             f'' = (f+1 - 2f + f-1)/h^2, second-order one-sided at the y boundaries; its tile
+                             blocks are block tridiagonal in levels of two y lines, factorised by block
+                             Thomas elimination and stored as three level blocks per level, so tiles may
+                             span the whole y range: ty even, nv * 2 * tx * tz <= 256 unknowns per level;
+                             precond_prec 64 or 32 (16: STAB_ERR_UNSUPPORTED); single-handle solves only) */
   int tile[3];            /* block-Jacobi tile in grid points (x, y, z), default 8 x 8 x 1 */
   int precond_prec;       /* block-Jacobi inverse storage: 64 (FP64), 32 (FP32, default) or 16 (BF16:
                              inverted in FP32, stored in bfloat16, applied with FP32 accumulation) */
@@ -196,8 +203,8 @@ stab_status stab_last_eps(stab_handle h, double* eps);
 /* Solve (J - sigma I) x = b by restarted, right-preconditioned (flexible)
  * GMRES to ||b - (J - sigma I) x|| <= opts.gmres_tol ||b|| with x0 = 0
  * (Sec. "Iterative solvers").  b, x: device complex128 n.  Uses the
- * block-Jacobi preconditioner when opts.precond = 1 (built on first use for
- * this sigma).  iters (host, may be NULL) receives the iteration count.
+ * block-Jacobi preconditioner when opts.precond = 1 or 2 (built on first use
+ * for this sigma).  iters (host, may be NULL) receives the iteration count.
  * NOT_CONVERGED if the restart limit is reached (x holds the last iterate). */
 stab_status stab_solve(stab_handle h, double sigma_re, double sigma_im, const void* b, void* x, int* iters);
 
@@ -205,14 +212,20 @@ stab_status stab_solve(stab_handle h, double sigma_re, double sigma_im, const vo
  * "Preconditioning"): one dense block per tile of opts.tile grid points with
  * all variables, the principal submatrix of (J_tangent - sigma I) over the
  * tile's unknowns (local order [var][lz][ly][lx]), inverted by LU with partial
- * pivoting and stored in opts.precond_prec precision. */
+ * pivoting and stored in opts.precond_prec precision.  With opts.precond = 2
+ * the blocks are those of the reduced operator's tangent, factorised level by
+ * level (S_l = D_l - L_l S_{l-1}^{-1} U_{l-1}, each S_l inverted with partial
+ * pivoting inside the level).  INVALID_ARG if the tile does not fit the grid
+ * (or, for precond 2, ty is odd or a level exceeds 256 unknowns); NUMERIC if a
+ * block (a level) is singular. */
 stab_status stab_precond_build(stab_handle h, double sigma_re, double sigma_im);
 
 /* z = M^{-1} q with the block-Jacobi preconditioner (built before).  Device complex128 n. */
 stab_status stab_precond_apply(stab_handle h, const void* q, void* z);
 
 /* Copy the assembled (unfactored) block of tile t, b x b complex128 row-major, to host memory
- * `out`; assembles it on demand for sigma (diagnostics and tests). */
+ * `out`; assembles it on demand for sigma (diagnostics and tests).  With opts.precond = 2 the
+ * reduced operator's block (b = nv * tile points, any size the caller can hold). */
 stab_status stab_precond_block(stab_handle h, double sigma_re, double sigma_im, long long t, double* out);
 
 /* Orthogonalise w against the k orthonormal columns of V by classical

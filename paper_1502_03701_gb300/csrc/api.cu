@@ -66,10 +66,12 @@ static void free_handle(stab_handle h) {
   dfree(h, h->d_coef_f);
   dfree(h, h->d_coef_p);
   dfree(h, h->d_btab_f);
+  dfree(h, h->d_btab_low);
   for (int a = 0; a < 3; ++a) {
     dfree(h, h->ax[a].tab[0]);
     dfree(h, h->ax[a].tabf[0]);
     dfree(h, h->d_dmat[a]);
+    dfree(h, h->d_dmat_low[a]);
   }
   for (cudaEvent_t e : h->timer.ev) cudaEventDestroy(e);
   for (cudaGraphExec_t e : h->gm_exec)
@@ -107,7 +109,7 @@ extern "C" stab_status stab_create(stab_handle* out, const double* base_flow, in
   }
   if (o.gmres_m < 1 || o.gmres_m > 200 || !(o.gmres_tol > 0) || o.gmres_max_restarts < 1 || o.eps < 0 ||
       !(o.gamma > 1) || o.sutherland_S < 0 || o.bulk_visc_ratio < 0 || o.max_restarts < 0 ||
-      (o.precond_prec != 16 && o.precond_prec != 32 && o.precond_prec != 64) || (o.precond != 0 && o.precond != 1) ||
+      (o.precond_prec != 16 && o.precond_prec != 32 && o.precond_prec != 64) || (o.precond < 0 || o.precond > 2) ||
       (o.gmres_basis_prec != 32 && o.gmres_basis_prec != 64) || (o.stencil_prec != 48 && o.stencil_prec != 64)) {
     g_create_err = "stab_create: invalid option value";
     return STAB_ERR_INVALID_ARG;
@@ -118,6 +120,10 @@ extern "C" stab_status stab_create(stab_handle* out, const double* base_flow, in
   }
   if (o.gmres_inner_m > 0 && (o.gmres_basis_prec != 64 || o.lgmres_k > 0)) {
     g_create_err = "stab_create: the nested inner solver needs the FP64 outer basis and no LGMRES";
+    return STAB_ERR_UNSUPPORTED;
+  }
+  if (o.precond == 2 && o.precond_prec == 16) {
+    g_create_err = "stab_create: the reduced-operator preconditioner (precond 2) stores FP32 or FP64 factors";
     return STAB_ERR_UNSUPPORTED;
   }
   if (o.precond_factor < 0 || o.precond_factor > 2) {

@@ -123,6 +123,8 @@ struct StabHandle {
   bool pvalid;
   int pprec;
   double* d_dmat[3];     // dense 1-D derivative matrices [kind][n*n] per axis (assembly)
+  double* d_dmat_low[3] = {nullptr, nullptr, nullptr};  // the reduced operator's (second-order explicit)
+  double* d_btab_low = nullptr;  // base tables with the reduced operator's derivatives
   double* d_coef;        // per-row tangent coefficients of the pointwise map (y-only base)
   double* d_coef_f;      // the same with the y metric folded in (inputs: eta-derivatives)
   struct ffn* d_coef_p;  // d_coef_f as FP32 pairs (hi, lo), read by the pointwise kernel
@@ -169,6 +171,8 @@ int jv_tune_save(const char* path);
 int jv_tune_load(const char* path);
 void jv_tune_apply_cached(StabHandle* h);
 cudaError_t jv_derivative_matrices(StabHandle* h, int axis, double2* work, double2* out1, double2* out2);
+// base tables of the reduced operator (second-order explicit derivatives of the base fields) into btab
+cudaError_t jv_reduced_base_table(StabHandle* h, double* btab);
 
 // krylov.cu
 cudaError_t kry_dot(StabHandle* h, const double2* V, int k, long long n, const double2* w, double2* d_h,

@@ -977,6 +977,36 @@ __global__ void k_pack_base(const PackParams P) {
   }
 }
 
+static PackParams pack_params(StabHandle* h, double* btab) {
+  const int D = h->dim;
+  PackParams K{};
+  K.q0 = h->d_q0;
+  K.scratch = h->d_scratch;
+  K.btab = btab;
+  K.npts = h->npts;
+  K.nbase = h->nbase;
+  K.nx = h->nx;
+  K.ny = h->ny;
+  K.D = D;
+  K.homog = h->homog;
+  K.visc = h->visc;
+  K.s_Tw = h->slots.Tw;
+  for (int a = 0; a < 3; ++a) {
+    for (int f = 0; f < 6; ++f) K.s_d1[a][f] = h->slots.d1[a][f];
+    for (int g = 0; g < 4; ++g) K.s_d2[a][g] = h->slots.d2[a][g];
+    for (int c = 0; c < 3; ++c) K.s_mix[a][c] = h->slots.mix[a][c];
+  }
+  K.eta_y = h->d_metric;
+  K.eta_yy = h->d_metric + h->ny;
+  K.pref = h->R;
+  K.igam = 1.0 / h->gamma;
+  K.icp = 1.0 / h->cp;
+  K.R = h->R;
+  K.gam = h->gamma;
+  K.S = h->S;
+  return K;
+}
+
 // ---------------------------------------------------------------------------
 // Batched J v: one launch per phase runs the work items (instance, block) of
 // several problems of uneven size.  Item i owns the flat blocks
@@ -1310,6 +1340,82 @@ static void axis_jobs(StabHandle* h, int ax, const double2* const* src, std::vec
   }
 }
 
+static int grid_for(long long n, int threads) {
+  long long b = (n + threads - 1) / threads;
+  if (b > 152LL * 16) b = 152LL * 16;
+  if (b < 1) b = 1;
+  return (int)b;
+}
+
+// ---------------------------------------------------------------------------
+// The reduced operator's base table: the base fields' derivatives taken with
+// second-order explicit differences (Sec. "Numerical experiments", the
+// non-compact lower-order discretisation proposed for the preconditioner):
+// f'_i = (f_{i+1} - f_{i-1})/(2h), f''_i = (f_{i+1} - 2 f_i + f_{i-1})/h^2,
+// on a bounded line the end rows second-order one-sided,
+// f'_0 = (-3 f_0 + 4 f_1 - f_2)/(2h), f''_0 = (2 f_0 - 5 f_1 + 4 f_2 - f_3)/h^2
+// (mirrored at the far end, the first with a sign change).  Derivatives in the
+// computational coordinate, into the same slots as the compact passes.
+// ---------------------------------------------------------------------------
+__global__ void k_low_deriv(const double2* in, double2* out1, double2* out2, int axis, int n, double hh, int periodic,
+                            int nx, int ny, long long npts) {
+  const long long st = axis == 0 ? 1 : axis == 1 ? nx : (long long)nx * ny;
+  for (long long pt = (long long)blockIdx.x * blockDim.x + threadIdx.x; pt < npts; pt += (long long)gridDim.x * blockDim.x) {
+    const int i = axis == 0 ? (int)(pt % nx) : axis == 1 ? (int)((pt / nx) % ny) : (int)(pt / ((long long)nx * ny));
+    auto f = [&](int k) {
+      if (periodic) k = (k % n + n) % n;
+      return in[pt + (long long)(k - i) * st];
+    };
+    double2 d1, d2;
+    if (periodic || (i > 0 && i < n - 1)) {
+      const double2 fp = f(i + 1), fm = f(i - 1), f0 = f(i);
+      d1 = make_double2((fp.x - fm.x) / (2.0 * hh), (fp.y - fm.y) / (2.0 * hh));
+      d2 = make_double2((fp.x - 2.0 * f0.x + fm.x) / (hh * hh), (fp.y - 2.0 * f0.y + fm.y) / (hh * hh));
+    } else {
+      const int sg = i == 0 ? 1 : -1;  // direction into the line
+      const double2 a0 = f(i), a1 = f(i + sg), a2 = f(i + 2 * sg), a3 = f(i + 3 * sg);
+      const double s1 = sg / (2.0 * hh);
+      d1 = make_double2((-3.0 * a0.x + 4.0 * a1.x - a2.x) * s1, (-3.0 * a0.y + 4.0 * a1.y - a2.y) * s1);
+      d2 = make_double2((2.0 * a0.x - 5.0 * a1.x + 4.0 * a2.x - a3.x) / (hh * hh),
+                        (2.0 * a0.y - 5.0 * a1.y + 4.0 * a2.y - a3.y) / (hh * hh));
+    }
+    if (out1) out1[pt] = d1;
+    if (out2) out2[pt] = d2;
+  }
+}
+
+cudaError_t jv_reduced_base_table(StabHandle* h, double* btab) {
+  const int D = h->dim;
+  cudaError_t err;
+  double2* bv;
+  if ((err = dalloc(h, &bv, (size_t)(h->nv + 1) * h->npts * sizeof(double2))) != cudaSuccess) return err;
+  double2* bT = bv + (long long)h->nv * h->npts;
+  const int thr = 256;
+  k_base_fields<<<grid_for(h->npts, thr), thr, 0, h->stream>>>(h->d_q0, h->npts, h->nv, h->R, 1.0 / h->gamma,
+                                                                1.0 / h->cp, h->R, bv, bT);
+  const double2* src[6];
+  for (int f = 0; f < D + 2; ++f) src[f] = bv + (long long)f * h->npts;
+  src[D + 2] = bT;
+  static const int order[3] = {1, 2, 0};  // y and z first: the mixed derivatives take their outputs
+  for (int q = 0; q < 3 && (err = cudaGetLastError()) == cudaSuccess; ++q) {
+    const int ax = order[q];
+    if (ax >= D) continue;
+    std::vector<LineJob> jobs;
+    axis_jobs(h, ax, src, jobs);
+    for (const LineJob& J : jobs)
+      k_low_deriv<<<grid_for(h->npts, thr), thr, 0, h->stream>>>(J.in, J.out1, J.out2, ax, h->ax[ax].n, h->ax[ax].h,
+                                                                 h->ax[ax].periodic, h->nx, h->ny, h->npts);
+  }
+  if (err == cudaSuccess) {
+    PackParams K = pack_params(h, btab);
+    k_pack_base<<<grid_for(h->nbase, thr), thr, 0, h->stream>>>(K);
+    err = cudaGetLastError();
+  }
+  if (err == cudaSuccess) err = cudaStreamSynchronize(h->stream);
+  dfree(h, bv);
+  return err;
+}
+
 // all derivative passes for field sources src[f] (f = 0..D+2): y, then z,
 // then x (the mixed derivatives need the y and z passes)
 static cudaError_t run_derivatives(StabHandle* h, const double2* const* src, int ff) {
@@ -1530,13 +1636,6 @@ static PointParams point_params(StabHandle* h, const double2* v) {
   return P;
 }
 
-static int grid_for(long long n, int threads) {
-  long long b = (n + threads - 1) / threads;
-  if (b > 152LL * 16) b = 152LL * 16;
-  if (b < 1) b = 1;
-  return (int)b;
-}
-
 cudaError_t launch_norm2(StabHandle* h, const double2* v, long long n, double* d_out, int mode) {
   // block count depends on n only, so the summation order is reproducible
   long long nb = (n + 1023) / 1024;
@@ -1648,31 +1747,7 @@ cudaError_t jv_setup(StabHandle* h, const double* q0_host) {
   for (int f = 0; f < D + 2; ++f) src[f] = bv + (long long)f * h->npts;
   src[D + 2] = bT;
   if ((err = run_derivatives(h, src, 0)) != cudaSuccess) return err;  // base tables: FP64 right-hand sides
-  PackParams K{};
-  K.q0 = h->d_q0;
-  K.scratch = h->d_scratch;
-  K.btab = h->d_btab;
-  K.npts = h->npts;
-  K.nbase = h->nbase;
-  K.nx = h->nx;
-  K.ny = h->ny;
-  K.D = D;
-  K.homog = h->homog;
-  K.visc = h->visc;
-  K.s_Tw = h->slots.Tw;
-  for (int a = 0; a < 3; ++a) {
-    for (int f = 0; f < 6; ++f) K.s_d1[a][f] = h->slots.d1[a][f];
-    for (int g = 0; g < 4; ++g) K.s_d2[a][g] = h->slots.d2[a][g];
-    for (int c = 0; c < 3; ++c) K.s_mix[a][c] = h->slots.mix[a][c];
-  }
-  K.eta_y = h->d_metric;
-  K.eta_yy = h->d_metric + h->ny;
-  K.pref = h->R;
-  K.igam = 1.0 / h->gamma;
-  K.icp = 1.0 / h->cp;
-  K.R = h->R;
-  K.gam = h->gamma;
-  K.S = h->S;
+  PackParams K = pack_params(h, h->d_btab);
   k_pack_base<<<grid_for(h->nbase, thr), thr, 0, h->stream>>>(K);
   if ((err = cudaGetLastError()) != cudaSuccess) return err;
   if (h->homog) {

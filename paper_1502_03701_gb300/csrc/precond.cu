@@ -39,6 +39,71 @@ struct AsmParams {
   double2* out;  // [tile - tile0][row][col]
 };
 
+// Column (beta, q) of the linearised operator at the rows of point p (all
+// variables), for grid points p and q that lie in the same tile: the unit
+// perturbation's derivatives come from the 1-D derivative matrices, the
+// coefficients from the base table.
+template <int D>
+__device__ __forceinline__ void asm_entry(const AsmParams& P, const int gp[3], const int gq[3], int beta,
+                                          double res[D + 2]) {
+  const long long ptp = ((long long)gp[2] * P.ny + gp[1]) * P.nx + gp[0];
+  const long long ptq = ((long long)gq[2] * P.ny + gq[1]) * P.nx + gq[0];
+  const long long bp = P.homog ? gp[1] : ptp, bq = P.homog ? gq[1] : ptq;
+  const double ig = P.phys.C.ig;
+  // field values at q of the unit perturbation (fields 0..D+1 = variables, D+2 = T)
+  double fq[D + 3];
+#pragma unroll
+  for (int f = 0; f < D + 2; ++f) fq[f] = f == beta ? 1.0 : 0.0;
+  {
+    const double T0 = P.btab[(long long)pw::bt_val(D, D + 2) * P.nbase + bq];
+    const double ip0 = P.btab[(long long)pw::bt_extra(D, pw::X_IP) * P.nbase + bq];
+    fq[D + 2] = beta == 0 ? T0 * (1.0 - ig) * ip0 : (beta == D + 1 ? T0 * P.phys.C.icp : 0.0);
+  }
+  const double ey = P.eta_y[gp[1]], eyy = P.eta_yy[gp[1]];
+  bool same[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) same[a] = gp[a] == gq[a];
+  auto d1c = [&](int a) { return P.Dm1[a][(long long)gq[a] * P.nax[a] + gp[a]].x; };  // D[p][q]
+  auto d2c = [&](int a) { return P.Dm2[a][(long long)gq[a] * P.nax[a] + gp[a]].x; };
+  pw::WIn<D> W;
+  const bool at_q = same[0] && same[1] && same[2];
+#pragma unroll
+  for (int f = 0; f < D + 3; ++f) W.v[f] = at_q ? fq[f] : 0.0;
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    bool line = true;  // p and q differ only along axis a
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+      if (c != a && !same[c]) line = false;
+    const double c1 = line ? d1c(a) * (a == 1 ? ey : 1.0) : 0.0;
+    double c2 = 0.0;
+    if (line) c2 = a == 1 ? fma(d2c(a), ey * ey, d1c(a) * eyy) : d2c(a);
+#pragma unroll
+    for (int f = 0; f < D + 3; ++f) W.d1[a][f] = c1 * fq[f];
+#pragma unroll
+    for (int g = 0; g < D + 1; ++g) W.d2[a][g] = c2 * fq[g < D ? 1 + g : D + 2];
+  }
+#pragma unroll
+  for (int a = 0; a < D; ++a)
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      double w = 0.0;
+      if (a != c) {
+        bool plane = true;  // p and q differ only along axes a and c
+#pragma unroll
+        for (int o = 0; o < 3; ++o)
+          if (o != a && o != c && !same[o]) plane = false;
+        if (plane) w = d1c(a) * d1c(c) * ((a == 1 || c == 1) ? ey : 1.0) * fq[1 + c];
+      }
+      W.mix[a][c] = w;
+    }
+  auto B = [&](int slot) { return P.btab[(long long)slot * P.nbase + bp]; };
+  const bool bc_row = gp[1] == 0 || gp[1] == P.ny - 1;
+  const unsigned fl =
+      bc_row ? P.bcflags[(gp[1] == P.ny - 1 ? (long long)P.nx * P.nz : 0) + (long long)gp[2] * P.nx + gp[0]] : 0u;
+  pw::rhs_diff<D>(P.phys, B, W, 0.0, bc_row, fl, res);
+}
+
 template <int D>
 __global__ void __launch_bounds__(128) k_assemble(const AsmParams P) {
   const long long tile = P.tile0 + blockIdx.x;
@@ -48,7 +113,6 @@ __global__ void __launch_bounds__(128) k_assemble(const AsmParams P) {
   const int x0 = tX * P.tx, y0 = tY * P.ty, z0 = tZ * P.tz;
   const int T = P.ntpts, bsz = P.bsz;
   double2* blk = P.out + (long long)blockIdx.x * bsz * bsz;
-  const double ig = P.phys.C.ig;
   for (long long idx = threadIdx.x; idx < (long long)bsz * T; idx += blockDim.x) {
     const int col = (int)(idx / T), pp = (int)(idx % T);
     const int beta = col / T, q = col % T;
@@ -56,68 +120,50 @@ __global__ void __launch_bounds__(128) k_assemble(const AsmParams P) {
     const int px = pp % P.tx, py = (pp / P.tx) % P.ty, pz = pp / (P.tx * P.ty);
     const int gq[3] = {x0 + qx, y0 + qy, z0 + qz};
     const int gp[3] = {x0 + px, y0 + py, z0 + pz};
-    const long long ptp = ((long long)gp[2] * P.ny + gp[1]) * P.nx + gp[0];
-    const long long ptq = ((long long)gq[2] * P.ny + gq[1]) * P.nx + gq[0];
-    const long long bp = P.homog ? gp[1] : ptp, bq = P.homog ? gq[1] : ptq;
-    // field values at q of the unit perturbation (fields 0..D+1 = variables, D+2 = T)
-    double fq[D + 3];
-#pragma unroll
-    for (int f = 0; f < D + 2; ++f) fq[f] = f == beta ? 1.0 : 0.0;
-    {
-      const double T0 = P.btab[(long long)pw::bt_val(D, D + 2) * P.nbase + bq];
-      const double ip0 = P.btab[(long long)pw::bt_extra(D, pw::X_IP) * P.nbase + bq];
-      fq[D + 2] = beta == 0 ? T0 * (1.0 - ig) * ip0 : (beta == D + 1 ? T0 * P.phys.C.icp : 0.0);
-    }
-    const double ey = P.eta_y[gp[1]], eyy = P.eta_yy[gp[1]];
-    bool same[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) same[a] = gp[a] == gq[a];
-    auto d1c = [&](int a) { return P.Dm1[a][(long long)gq[a] * P.nax[a] + gp[a]].x; };  // D[p][q]
-    auto d2c = [&](int a) { return P.Dm2[a][(long long)gq[a] * P.nax[a] + gp[a]].x; };
-    pw::WIn<D> W;
-    const bool at_q = same[0] && same[1] && same[2];
-#pragma unroll
-    for (int f = 0; f < D + 3; ++f) W.v[f] = at_q ? fq[f] : 0.0;
-#pragma unroll
-    for (int a = 0; a < D; ++a) {
-      bool line = true;  // p and q differ only along axis a
-#pragma unroll
-      for (int c = 0; c < 3; ++c)
-        if (c != a && !same[c]) line = false;
-      const double c1 = line ? d1c(a) * (a == 1 ? ey : 1.0) : 0.0;
-      double c2 = 0.0;
-      if (line) c2 = a == 1 ? fma(d2c(a), ey * ey, d1c(a) * eyy) : d2c(a);
-#pragma unroll
-      for (int f = 0; f < D + 3; ++f) W.d1[a][f] = c1 * fq[f];
-#pragma unroll
-      for (int g = 0; g < D + 1; ++g) W.d2[a][g] = c2 * fq[g < D ? 1 + g : D + 2];
-    }
-#pragma unroll
-    for (int a = 0; a < D; ++a)
-#pragma unroll
-      for (int c = 0; c < D; ++c) {
-        double w = 0.0;
-        if (a != c) {
-          bool plane = true;  // p and q differ only along axes a and c
-#pragma unroll
-          for (int o = 0; o < 3; ++o)
-            if (o != a && o != c && !same[o]) plane = false;
-          if (plane) w = d1c(a) * d1c(c) * ((a == 1 || c == 1) ? ey : 1.0) * fq[1 + c];
-        }
-        W.mix[a][c] = w;
-      }
-    auto B = [&](int slot) { return P.btab[(long long)slot * P.nbase + bp]; };
-    const bool bc_row = gp[1] == 0 || gp[1] == P.ny - 1;
-    const unsigned fl =
-        bc_row ? P.bcflags[(gp[1] == P.ny - 1 ? (long long)P.nx * P.nz : 0) + (long long)gp[2] * P.nx + gp[0]] : 0u;
     double res[D + 2];
-    pw::rhs_diff<D>(P.phys, B, W, 0.0, bc_row, fl, res);
+    asm_entry<D>(P, gp, gq, beta, res);
 #pragma unroll
     for (int a = 0; a < D + 2; ++a) {
       const int row = a * T + pp;
       double2 val = make_double2(res[a], 0.0);
       if (row == col) { val.x -= P.sigma.x; val.y -= P.sigma.y; }
       blk[(long long)row * bsz + col] = val;
+    }
+  }
+}
+
+// Reduced-operator tiles in block-tridiagonal form.  A tile's points are
+// grouped in levels of two y lines (level l: local y in {2l, 2l + 1}); with
+// the three-point interior stencils and the end rows reaching three points in,
+// a level couples only to itself and its two neighbours.  Level unknowns are
+// ordered [var][lz][ly][lx] (m = nv * 2 * tx * tz).  Grid (tiles, levels, 3):
+// kind 0 = L_l (columns of level l - 1), 1 = D_l (- sigma on the diagonal),
+// 2 = U_l (columns of level l + 1); out[tile][l][kind] is m x m, row-major.
+template <int D>
+__global__ void __launch_bounds__(128) k_assemble_bt(const AsmParams P, int m, int nlev, double2* out) {
+  const int lev = blockIdx.y, kind = blockIdx.z;
+  const int ql = lev + kind - 1;
+  if (ql < 0 || ql >= nlev) return;
+  const long long tile = P.tile0 + blockIdx.x;
+  const int tX = (int)(tile % P.ntx);
+  const int tY = (int)((tile / P.ntx) % P.nty);
+  const int tZ = (int)(tile / ((long long)P.ntx * P.nty));
+  const int x0 = tX * P.tx, y0 = tY * P.ty, z0 = tZ * P.tz;
+  const int NP = 2 * P.tx * P.tz;
+  double2* blk = out + (((long long)blockIdx.x * nlev + lev) * 3 + kind) * m * m;
+  for (int idx = threadIdx.x; idx < m * NP; idx += blockDim.x) {
+    const int col = idx / NP, pp = idx % NP;
+    const int beta = col / NP, q = col % NP;
+    const int gq[3] = {x0 + q % P.tx, y0 + 2 * ql + (q / P.tx) % 2, z0 + q / (2 * P.tx)};
+    const int gp[3] = {x0 + pp % P.tx, y0 + 2 * lev + (pp / P.tx) % 2, z0 + pp / (2 * P.tx)};
+    double res[D + 2];
+    asm_entry<D>(P, gp, gq, beta, res);
+#pragma unroll
+    for (int a = 0; a < D + 2; ++a) {
+      const int row = a * NP + pp;
+      double2 val = make_double2(res[a], 0.0);
+      if (kind == 1 && row == col) { val.x -= P.sigma.x; val.y -= P.sigma.y; }
+      blk[(long long)row * m + col] = val;
     }
   }
 }
@@ -136,16 +182,14 @@ __global__ void k_to_float(const double2* in, float2* out, long long count) {
 
 // In-place Gauss-Jordan inversion with partial pivoting of one b x b complex
 // block per CTA (row-major).  Threads own columns; rows are swept in order.
+// The sweep of one block M (b x b, row-major) by the calling CTA; prow, pcol:
+// b complex, perm: b ints, in shared memory.  Returns (thread 0) the first
+// step whose pivot column was zero, plus one, else 0.
 template <class R>
-__global__ void k_gauss_jordan(C2<R>* A, int b, int* info) {
-  extern __shared__ unsigned char smraw[];
-  C2<R>* prow = (C2<R>*)smraw;
-  C2<R>* pcol = prow + b;
-  int* perm = (int*)(pcol + b);
+__device__ int gj_sweep(C2<R>* M, int b, C2<R>* prow, C2<R>* pcol, int* perm) {
   __shared__ double rv[32];
   __shared__ int ri[32];
   __shared__ int s_piv;
-  C2<R>* M = A + (long long)blockIdx.x * b * b;
   const int nthr = blockDim.x, lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   int bad = 0;
   for (int k = 0; k < b; ++k) {
@@ -233,7 +277,165 @@ __global__ void k_gauss_jordan(C2<R>* A, int b, int* info) {
       }
     __syncthreads();
   }
+  return bad;
+}
+
+template <class R>
+__global__ void k_gauss_jordan(C2<R>* A, int b, int* info) {
+  extern __shared__ unsigned char smraw[];
+  C2<R>* prow = (C2<R>*)smraw;
+  C2<R>* pcol = prow + b;
+  int* perm = (int*)(pcol + b);
+  const int bad = gj_sweep<R>(A + (long long)blockIdx.x * b * b, b, prow, pcol, perm);
   if (threadIdx.x == 0 && bad) atomicMax(info, 1);
+}
+
+// Block-tridiagonal LU of a reduced-operator tile (one CTA per tile, levels in
+// order; block Thomas elimination): S_0 = D_0, S_l = D_l - L_l X_{l-1},
+// X_l = S_l^{-1} U_l, with S_l inverted by the Gauss-Jordan sweep above
+// (partial pivoting inside the level).  F[tile][l] = {L_l, S_l^{-1}, X_l}.
+template <class R>
+__global__ void k_bt_factor(const double2* asmb, C2<R>* F, int m, int nlev, int* info) {
+  extern __shared__ unsigned char smraw[];
+  C2<R>* prow = (C2<R>*)smraw;
+  C2<R>* pcol = prow + m;
+  int* perm = (int*)(pcol + m);
+  const long long mm = (long long)m * m;
+  const double2* A = asmb + (long long)blockIdx.x * nlev * 3 * mm;
+  C2<R>* Ft = F + (long long)blockIdx.x * nlev * 3 * mm;
+  int bad = 0;
+  for (int l = 0; l < nlev; ++l) {
+    const double2* Al = A + (long long)l * 3 * mm;
+    C2<R>* L = Ft + (long long)l * 3 * mm;
+    C2<R>* S = L + mm;
+    C2<R>* X = S + mm;
+    const C2<R>* Xp = L - mm;  // X_{l-1}
+    for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) {
+      const double2 lv = l > 0 ? Al[idx] : make_double2(0.0, 0.0), dv = Al[mm + idx];
+      C2<R> sv = {(R)dv.x, (R)dv.y};
+      if (l > 0) {
+        const int i = idx / m, c = idx - (idx / m) * m;
+        R ax = 0, ay = 0;
+        for (int k = 0; k < m; ++k) {
+          const double2 a = Al[(long long)i * m + k];
+          const C2<R> x = Xp[(long long)k * m + c];
+          ax += (R)a.x * x.x - (R)a.y * x.y;
+          ay += (R)a.x * x.y + (R)a.y * x.x;
+        }
+        sv.x -= ax;
+        sv.y -= ay;
+      }
+      L[idx] = C2<R>{(R)lv.x, (R)lv.y};
+      S[idx] = sv;
+    }
+    __syncthreads();
+    const int b = gj_sweep<R>(S, m, prow, pcol, perm);
+    if (b && !bad) bad = b;
+    __syncthreads();
+    if (l + 1 < nlev)
+      for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) {
+        const int i = idx / m, c = idx - (idx / m) * m;
+        R ax = 0, ay = 0;
+        for (int k = 0; k < m; ++k) {
+          const C2<R> a = S[(long long)i * m + k];
+          const double2 u = Al[2 * mm + (long long)k * m + c];
+          ax += a.x * (R)u.x - a.y * (R)u.y;
+          ay += a.x * (R)u.y + a.y * (R)u.x;
+        }
+        X[idx] = C2<R>{ax, ay};
+      }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0 && bad) atomicMax(info, 1);
+}
+
+struct BtApplyParams {
+  const double2* q;
+  const float2* q32;  // FP32 input (GMRES with an FP32 basis) instead of q
+  double2* z;
+  const void* F;
+  int m, nlev, tx, ty, tz, ntx, nty, nx, ny;
+  long long npts;
+  const int* gate;
+};
+
+// z = M^{-1} q for the block-tridiagonal tiles (one CTA per tile): forward
+// y_l = S_l^{-1} (q_l - L_l y_{l-1}), backward x_l = y_l - X_l x_{l+1}, the
+// level vectors in shared memory, y kept in z between the sweeps.  Each row's
+// dot product is split over G threads (G a power of two), reduced by shuffles.
+template <class R, bool Q32>
+__global__ void __launch_bounds__(256) k_bt_apply(const BtApplyParams P) {
+  if (P.gate && *P.gate) return;
+  extern __shared__ unsigned char smraw[];
+  C2<R>* va = (C2<R>*)smraw;
+  C2<R>* vb = va + P.m;
+  const int m = P.m, NP = 2 * P.tx * P.tz;
+  const long long mm = (long long)m * m;
+  const long long tile = blockIdx.x;
+  const int tX = (int)(tile % P.ntx), tY = (int)((tile / P.ntx) % P.nty), tZ = (int)(tile / ((long long)P.ntx * P.nty));
+  const C2<R>* Ft = (const C2<R>*)P.F + tile * P.nlev * 3 * mm;
+  int G = 1;
+  while (G < 32 && 2 * G * m <= (int)blockDim.x) G *= 2;
+  const int row = threadIdx.x / G, g = threadIdx.x % G;
+  const bool act = row < m;
+  auto dof = [&](int l, int r) -> long long {
+    const int a = r / NP, pp = r % NP;
+    const int x = tX * P.tx + pp % P.tx, y = tY * P.ty + 2 * l + (pp / P.tx) % 2, z = tZ * P.tz + pp / (2 * P.tx);
+    return (long long)a * P.npts + ((long long)z * P.ny + y) * P.nx + x;
+  };
+  // (M x)_row, complete in every lane of the row's group
+  auto mv = [&](const C2<R>* M, const C2<R>* x) {
+    R sx = 0, sy = 0;
+    if (act)
+      for (int k = g; k < m; k += G) {
+        const C2<R> a = M[(long long)row * m + k], b = x[k];
+        sx += a.x * b.x - a.y * b.y;
+        sy += a.x * b.y + a.y * b.x;
+      }
+    for (int o = G >> 1; o > 0; o >>= 1) {
+      sx += __shfl_xor_sync(0xffffffffu, sx, o);
+      sy += __shfl_xor_sync(0xffffffffu, sy, o);
+    }
+    return C2<R>{sx, sy};
+  };
+  C2<R>* yp = va;  // y_{l-1}
+  C2<R>* t = vb;
+  for (int l = 0; l < P.nlev; ++l) {
+    const C2<R>* L = Ft + (long long)l * 3 * mm;
+    for (int r = threadIdx.x; r < m; r += blockDim.x) {
+      const long long d = dof(l, r);
+      if (Q32) { const float2 v = P.q32[d]; t[r] = C2<R>{(R)v.x, (R)v.y}; }
+      else { const double2 v = P.q[d]; t[r] = C2<R>{(R)v.x, (R)v.y}; }
+    }
+    __syncthreads();
+    if (l > 0) {
+      const C2<R> s = mv(L, yp);
+      __syncthreads();
+      if (act && g == 0) { t[row].x -= s.x; t[row].y -= s.y; }
+      __syncthreads();
+    }
+    const C2<R> y = mv(L + mm, t);
+    __syncthreads();
+    if (act && g == 0) {
+      yp[row] = y;
+      P.z[dof(l, row)] = make_double2((double)y.x, (double)y.y);
+    }
+    __syncthreads();
+  }
+  C2<R>* xn = yp;  // x_{l+1}
+  C2<R>* xc = t;
+  for (int l = P.nlev - 2; l >= 0; --l) {
+    const C2<R> s = mv(Ft + (long long)l * 3 * mm + 2 * mm, xn);
+    if (act && g == 0) {
+      const long long d = dof(l, row);
+      const double2 y = P.z[d];
+      const C2<R> x = {(R)y.x - s.x, (R)y.y - s.y};
+      xc[row] = x;
+      P.z[d] = make_double2((double)x.x, (double)x.y);
+    }
+    __syncthreads();
+    C2<R>* tmp = xn; xn = xc; xc = tmp;
+  }
 }
 
 struct ApplyParams {
@@ -461,6 +663,19 @@ struct Geo {
   long long ntiles;
 };
 
+// Tiles of the reduced-operator preconditioner (precond = 2): any tile that
+// divides the grid with an even number of y points, levels of m = nv * 2 * tx * tz
+// unknowns with m <= kBtMaxLevel.
+constexpr int kBtMaxLevel = 256;
+struct BtGeo {
+  int m, nlev;
+};
+bool bt_geo(StabHandle* h, const Geo& g, BtGeo& b) {
+  b.m = h->nv * 2 * g.tx * g.tz;
+  b.nlev = g.ty / 2;
+  return g.ty % 2 == 0 && b.m <= kBtMaxLevel;
+}
+
 bool tile_geo(StabHandle* h, Geo& g) {
   g.tx = h->opts.tile[0];
   g.ty = h->opts.tile[1];
@@ -472,7 +687,64 @@ bool tile_geo(StabHandle* h, Geo& g) {
   g.ntpts = g.tx * g.ty * g.tz;
   g.bsz = h->nv * g.ntpts;
   g.ntiles = (long long)g.ntx * g.nty * g.ntz;
+  if (h->opts.precond == 2) {
+    BtGeo b;
+    return bt_geo(h, g, b);
+  }
   return g.bsz <= 1024;
+}
+
+// The reduced operator's second-order explicit 1-D derivative matrices (same
+// layout as the compact ones: [l * n + t] = (D e_l)_t) and its base table.
+cudaError_t ensure_reduced(StabHandle* h) {
+  cudaError_t e;
+  for (int a = 0; a < h->dim; ++a) {
+    if (h->d_dmat_low[a]) continue;
+    const int n = h->ax[a].n;
+    const double hh = h->ax[a].h;
+    const bool per = h->ax[a].periodic;
+    std::vector<double2> M((size_t)2 * n * n, make_double2(0.0, 0.0));
+    auto put = [&](int which, int t, int l, double v) {
+      if (per) l = (l % n + n) % n;
+      M[(size_t)which * n * n + (size_t)l * n + t].x += v;
+    };
+    for (int t = 0; t < n; ++t) {
+      if (per || (t > 0 && t < n - 1)) {
+        put(0, t, t + 1, 1.0 / (2.0 * hh));
+        put(0, t, t - 1, -1.0 / (2.0 * hh));
+        put(1, t, t + 1, 1.0 / (hh * hh));
+        put(1, t, t, -2.0 / (hh * hh));
+        put(1, t, t - 1, 1.0 / (hh * hh));
+      } else {
+        const int sg = t == 0 ? 1 : -1;
+        put(0, t, t, -3.0 * sg / (2.0 * hh));
+        put(0, t, t + sg, 4.0 * sg / (2.0 * hh));
+        put(0, t, t + 2 * sg, -1.0 * sg / (2.0 * hh));
+        put(1, t, t, 2.0 / (hh * hh));
+        put(1, t, t + sg, -5.0 / (hh * hh));
+        put(1, t, t + 2 * sg, 4.0 / (hh * hh));
+        put(1, t, t + 3 * sg, -1.0 / (hh * hh));
+      }
+    }
+    double2* buf;
+    if ((e = dalloc(h, &buf, M.size() * sizeof(double2))) != cudaSuccess) return e;
+    if ((e = cudaMemcpyAsync(buf, M.data(), M.size() * sizeof(double2), cudaMemcpyHostToDevice, h->stream)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(h->stream)) != cudaSuccess) {
+      dfree(h, buf);
+      return e;
+    }
+    h->d_dmat_low[a] = (double*)buf;
+  }
+  if (!h->d_btab_low) {
+    double* t;
+    if ((e = dalloc(h, &t, (size_t)pw::bt_count(h->dim) * h->nbase * sizeof(double))) != cudaSuccess) return e;
+    if ((e = jv_reduced_base_table(h, t)) != cudaSuccess) {
+      dfree(h, t);
+      return e;
+    }
+    h->d_btab_low = t;
+  }
+  return cudaSuccess;
 }
 
 cudaError_t ensure_dmats(StabHandle* h) {
@@ -501,11 +773,14 @@ AsmParams asm_params(StabHandle* h, const Geo& g, double2 sigma) {
   P.eta_y = h->d_metric;
   P.eta_yy = h->d_metric + h->ny;
   P.bcflags = h->d_bcflags;
+  const bool red = h->opts.precond == 2;  // the reduced operator's tables
+  if (red) P.btab = h->d_btab_low;
   for (int a = 0; a < 3; ++a) {
     P.nax[a] = h->ax[a].n;
     const int n = h->ax[a].n;
-    P.Dm1[a] = a < h->dim ? (const double2*)h->d_dmat[a] : nullptr;
-    P.Dm2[a] = a < h->dim ? (const double2*)h->d_dmat[a] + (size_t)n * n : nullptr;
+    const double* dm = red ? h->d_dmat_low[a] : h->d_dmat[a];
+    P.Dm1[a] = a < h->dim ? (const double2*)dm : nullptr;
+    P.Dm2[a] = a < h->dim ? (const double2*)dm + (size_t)n * n : nullptr;
   }
   if (h->dim == 2) { P.Dm1[2] = P.Dm1[0]; P.Dm2[2] = P.Dm2[0]; P.nax[2] = 1; }
   P.phys = phys_of(h);
@@ -749,16 +1024,74 @@ cudaError_t pc_block(StabHandle* h, double2 sigma, long long t, double2* d_out) 
   Geo g;
   if (!tile_geo(h, g) || t < 0 || t >= g.ntiles) return cudaErrorInvalidValue;
   cudaError_t e;
-  if ((e = ensure_dmats(h)) != cudaSuccess) return e;
+  if ((e = h->opts.precond == 2 ? ensure_reduced(h) : ensure_dmats(h)) != cudaSuccess) return e;
   AsmParams P = asm_params(h, g, sigma);
   P.tile0 = t;
   P.out = d_out;
   return launch_assemble(h, P, 1);
 }
 
+// Reduced-operator preconditioner: the tiles' level blocks assembled in FP64
+// in batches of at most ~1 GiB, factorised by block Thomas elimination in the
+// storage precision (FP32 or FP64).
+cudaError_t pc_build_reduced(StabHandle* h, const Geo& g, double2 sigma) {
+  BtGeo bg;
+  if (!bt_geo(h, g, bg)) return cudaErrorInvalidValue;
+  cudaError_t e;
+  if ((e = ensure_reduced(h)) != cudaSuccess) return e;
+  const int prec = h->opts.precond_prec == 64 ? 64 : 32;
+  const size_t esz = prec == 64 ? sizeof(double2) : sizeof(float2);
+  const size_t per = (size_t)bg.nlev * 3 * bg.m * bg.m;  // complex values per tile
+  if (!h->d_pinv || h->ntiles != g.ntiles || h->bsize != -(long long)bg.m * bg.nlev || h->pprec != prec) {
+    dfree(h, h->d_pinv);
+    h->d_pinv = nullptr;
+    if ((e = dalloc(h, &h->d_pinv, per * g.ntiles * esz)) != cudaSuccess) return e;
+    h->ntiles = g.ntiles;
+    h->bsize = -(long long)bg.m * bg.nlev;  // negative: block-tridiagonal layout
+    h->pprec = prec;
+  }
+  h->pvalid = false;
+  long long batch = (long long)((1ull << 30) / (per * sizeof(double2)));
+  if (batch < 1) batch = 1;
+  if (batch > g.ntiles) batch = g.ntiles;
+  double2* asmb;
+  if ((e = dalloc(h, &asmb, per * batch * sizeof(double2))) != cudaSuccess) return e;
+  int* d_info;
+  if ((e = dalloc(h, &d_info, sizeof(int))) != cudaSuccess) { dfree(h, asmb); return e; }
+  cudaMemsetAsync(d_info, 0, sizeof(int), h->stream);
+  AsmParams P = asm_params(h, g, sigma);
+  const size_t smem = (size_t)2 * bg.m * esz + (size_t)bg.m * sizeof(int);
+  for (long long t0 = 0; t0 < g.ntiles && e == cudaSuccess; t0 += batch) {
+    const long long nb = std::min(batch, g.ntiles - t0);
+    P.tile0 = t0;
+    const dim3 grid((unsigned)nb, (unsigned)bg.nlev, 3u);
+    if (h->dim == 2) k_assemble_bt<2><<<grid, 128, 0, h->stream>>>(P, bg.m, bg.nlev, asmb);
+    else k_assemble_bt<3><<<grid, 128, 0, h->stream>>>(P, bg.m, bg.nlev, asmb);
+    if (prec == 64)
+      k_bt_factor<double><<<(unsigned)nb, 256, smem, h->stream>>>(asmb, (C2<double>*)h->d_pinv + per * t0, bg.m,
+                                                                    bg.nlev, d_info);
+    else
+      k_bt_factor<float><<<(unsigned)nb, 256, smem, h->stream>>>(asmb, (C2<float>*)h->d_pinv + per * t0, bg.m,
+                                                                   bg.nlev, d_info);
+    e = cudaGetLastError();
+  }
+  int info = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&info, d_info, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  dfree(h, d_info);
+  dfree(h, asmb);
+  if (e != cudaSuccess) return e;
+  if (info) return cudaErrorInvalidValue;
+  h->psigma_re = sigma.x;
+  h->psigma_im = sigma.y;
+  h->pvalid = true;
+  return cudaSuccess;
+}
+
 cudaError_t pc_build(StabHandle* h, double2 sigma) {
   Geo g;
   if (!tile_geo(h, g)) return cudaErrorInvalidValue;
+  if (h->opts.precond == 2) return pc_build_reduced(h, g, sigma);
   cudaError_t e;
   if ((e = ensure_dmats(h)) != cudaSuccess) return e;
   const int prec = h->opts.precond_prec;
@@ -837,6 +1170,27 @@ cudaError_t pc_apply(StabHandle* h, const double2* q, double2* z, const float2* 
   if (!h->pvalid) return cudaErrorInvalidValue;
   Geo g;
   tile_geo(h, g);
+  if (h->opts.precond == 2) {
+    BtGeo bg;
+    bt_geo(h, g, bg);
+    BtApplyParams B{};
+    B.q = q; B.q32 = q32; B.z = z; B.F = h->d_pinv;
+    B.m = bg.m; B.nlev = bg.nlev; B.tx = g.tx; B.ty = g.ty; B.tz = g.tz; B.ntx = g.ntx; B.nty = g.nty;
+    B.nx = h->nx; B.ny = h->ny; B.npts = h->npts; B.gate = h->gate;
+    const int ts = phase_begin(h, STAB_PHASE_PRECOND_APPLY);
+    const unsigned nt = (unsigned)g.ntiles;
+    if (h->pprec == 64) {
+      const size_t sm = 2 * bg.m * sizeof(double2);
+      if (q32) k_bt_apply<double, true><<<nt, 256, sm, h->stream>>>(B);
+      else k_bt_apply<double, false><<<nt, 256, sm, h->stream>>>(B);
+    } else {
+      const size_t sm = 2 * bg.m * sizeof(float2);
+      if (q32) k_bt_apply<float, true><<<nt, 256, sm, h->stream>>>(B);
+      else k_bt_apply<float, false><<<nt, 256, sm, h->stream>>>(B);
+    }
+    phase_end(h, ts);
+    return cudaGetLastError();
+  }
   ApplyParams P{};
   P.q = q; P.z = z; P.inv = h->d_pinv; P.q32 = q32;
   P.nx = h->nx; P.ny = h->ny; P.tx = g.tx; P.ty = g.ty; P.tz = g.tz; P.ntx = g.ntx; P.nty = g.nty;
@@ -875,7 +1229,7 @@ extern "C" stab_status stab_precond_build(stab_handle hh, double sr, double si) 
   StabHandle* h = (StabHandle*)hh;
   if (!h) return STAB_ERR_INVALID_ARG;
   Geo g;
-  if (!tile_geo(h, g)) { h->err = "stab_precond_build: tile must divide the grid and give blocks of at most 1024 unknowns"; return STAB_ERR_INVALID_ARG; }
+  if (!tile_geo(h, g)) { h->err = h->opts.precond == 2 ? "stab_precond_build: tile must divide the grid, with an even ty and levels of at most 256 unknowns (nv * 2 * tx * tz)" : "stab_precond_build: tile must divide the grid and give blocks of at most 1024 unknowns"; return STAB_ERR_INVALID_ARG; }
   cudaError_t e = pc_build(h, make_double2(sr, si));
   if (e == cudaErrorInvalidValue) { h->err = "stab_precond_build: singular block"; return STAB_ERR_NUMERIC; }
   if (e != cudaSuccess) { h->err = std::string("stab_precond_build: ") + cudaGetErrorString(e); return e == cudaErrorMemoryAllocation ? STAB_ERR_OOM : STAB_ERR_CUDA; }
@@ -918,6 +1272,7 @@ cudaError_t pc_batch_plan(const std::vector<StabHandle*>& hs, const double2* con
   for (int i = 0; i < count; ++i) {
     StabHandle* h = hs[i];
     if (!h->pvalid) return cudaErrorInvalidValue;
+    if (h->opts.precond == 2) return cudaErrorNotSupported;  // block-tridiagonal tiles: single-handle apply only
     Geo g;
     tile_geo(h, g);
     ApplyItem it{};
@@ -998,6 +1353,10 @@ extern "C" stab_status stab_jv_batch_precond_apply(stab_jv_batch B, const void* 
     if (!B->hs[i]->pvalid) {
       B->err = "stab_jv_batch_precond_apply: no preconditioner built for instance " + std::to_string(i);
       return STAB_ERR_INVALID_ARG;
+    }
+    if (B->hs[i]->opts.precond == 2) {
+      B->err = "stab_jv_batch_precond_apply: instance " + std::to_string(i) + " uses the reduced-operator preconditioner";
+      return STAB_ERR_UNSUPPORTED;
     }
   }
   const cudaError_t e = pc_apply_batch(B, (const double2* const*)q, (double2* const*)z);

@@ -52,7 +52,7 @@ extern "C" long long stab_estimate_bytes(const stab_grid* g, const stab_opts* op
   b += (long long)pw::bt_count(D) * nbase * (8 + 4);       // base tables, FP64 and FP32
   b += scratch_fields(D, visc) * npts * 16;                // derivative fields
   b += (nv + 1) * npts * 16;                               // set-up temporary
-  const long long m = o.gmres_m, pc = o.precond == 1;
+  const long long m = o.gmres_m, pc = o.precond != 0;
   if (o.gmres_basis_prec == 32) b += (m + 1) * n * 8 + 6 * n * 16;  // FP32 basis; r, b, x, w, z, t
   else if (o.gmres_inner_m > 0)                            // nested: V, Z, r, b, x; inner FP32 basis, w, zt, t
     b += ((m + 1) + m + 3) * n * 16 + ((long long)o.gmres_inner_m + 1) * n * 8 + 3 * n * 16;
@@ -61,7 +61,15 @@ extern "C" long long stab_estimate_bytes(const stab_grid* g, const stab_opts* op
   else b += ((m + 1) + pc * m + 3) * n * 16;               // GMRES basis, Z, r, b, x
   b += 2 * 608 * (m + 2) * 16;                             // CGS2 partial sums
   b += ((long long)ncv + 2 + nev + 1) * n * 16;            // Arnoldi basis, f, x, restart temporary
-  if (pc) {
+  if (pc && o.precond == 2) {  // block-tridiagonal factors: 3 level blocks per level, FP64 assembly batch
+    const long long tz = D == 3 ? o.tile[2] : 1;
+    const long long lm = nv * 2 * o.tile[0] * tz, nlev = std::max(1, o.tile[1] / 2);
+    const long long ntiles = npts / std::max<long long>(1, o.tile[0] * o.tile[1] * tz);
+    const long long per = nlev * 3 * lm * lm;
+    b += ntiles * per * (o.precond_prec == 64 ? 16 : 8);
+    b += std::min<long long>(ntiles, std::max<long long>(1, (1ll << 30) / (per * 16))) * per * 16;
+    b += (long long)(nv + 1) * npts * 16;                // base fields for the reduced table
+  } else if (pc) {
     const long long tz = D == 3 ? o.tile[2] : 1;
     const long long bsz = nv * o.tile[0] * o.tile[1] * tz;
     const long long ntiles = npts / std::max<long long>(1, o.tile[0] * o.tile[1] * tz);
@@ -263,7 +271,8 @@ void serve_cohort(stab_server_s* S, std::vector<ServerReq*>& C, cudaStream_t st)
       continue;
     }
     const StabHandle* h = (const StabHandle*)hs[i];
-    if (h->homog && h->d_coef && !h->force_dn_path && h->opts.gmres_basis_prec == 64 && h->opts.lgmres_k == 0)
+    if (h->homog && h->d_coef && !h->force_dn_path && h->opts.gmres_basis_prec == 64 && h->opts.lgmres_k == 0 &&
+        h->opts.gmres_inner_m == 0 && h->opts.precond != 2)
       batched.push_back((int)i);
   }
   if (batched.size() >= 2) {

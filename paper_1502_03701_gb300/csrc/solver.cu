@@ -96,7 +96,7 @@ struct GmReport {  // read by the host once per cycle
 GmresWs gmres_ws(StabHandle* h, GmDev* D, GmReport** rep) {
   const long long n = h->n;
   const int m = h->opts.gmres_m;
-  const bool pc = h->opts.precond == 1;
+  const bool pc = h->opts.precond != 0;
   const bool b32 = h->opts.gmres_basis_prec == 32;
   const int lgk = b32 ? 0 : h->opts.lgmres_k;
   const int mi = b32 ? 0 : h->opts.gmres_inner_m;
@@ -325,7 +325,7 @@ cudaGraphExec_t gm_graph(StabHandle* h, cd sigma, int eps_mode, const GmresWs& W
                          int naug) {
   const long long n = h->n;
   const int m = h->opts.gmres_m;
-  const bool pc = h->opts.precond == 1;
+  const bool pc = h->opts.precond != 0;
   const int lgk = h->opts.gmres_basis_prec == 32 ? 0 : h->opts.lgmres_k;
   GmGraphKey key;
   key.valid = true;
@@ -677,7 +677,7 @@ extern "C" stab_status stab_solve(stab_handle hh, double sr, double si, const vo
   if (!b || !x) { h->err = "stab_solve: null vector"; return STAB_ERR_INVALID_ARG; }
   try {
     const cd sigma(sr, si);
-    if (h->opts.precond == 1 && !(h->pvalid && h->psigma_re == sr && h->psigma_im == si))
+    if (h->opts.precond != 0 && !(h->pvalid && h->psigma_re == sr && h->psigma_im == si))
       ck(h, pc_build(h, d2(sigma)), "preconditioner build");
     bool conv;
     int it = gmres(h, sigma, (const double2*)b, (double2*)x, h->opts.eps_mode, &conv);
@@ -775,7 +775,7 @@ extern "C" stab_status stab_eigs(stab_handle hh, double sr, double si, double tr
   const long long n = h->n;
   stab_status result = STAB_OK;
   try {
-    if (h->opts.precond == 1 && !(h->pvalid && h->psigma_re == sr && h->psigma_im == si)) {
+    if (h->opts.precond != 0 && !(h->pvalid && h->psigma_re == sr && h->psigma_im == si)) {
       auto tp = std::chrono::steady_clock::now();
       ck(h, pc_build(h, d2(sigma)), "preconditioner build");
       ck(h, cudaStreamSynchronize(h->stream), "sync");
@@ -1155,7 +1155,7 @@ struct BatchGmres {
       B.h = hs[i];
       B.sigma = sig[i];
       B.m = B.h->opts.gmres_m;
-      B.pc = B.h->opts.precond == 1;
+      B.pc = B.h->opts.precond != 0;
       GmReport* unused;
       B.W = gmres_ws(B.h, &B.D, &unused);
       if (B.pc && !(B.h->pvalid && B.h->psigma_re == sig[i].real() && B.h->psigma_im == sig[i].imag()))
@@ -1381,7 +1381,8 @@ struct StreamSwap {
 };
 
 bool batchable_solver(const StabHandle* h) {
-  return h->opts.gmres_basis_prec == 64 && h->opts.lgmres_k == 0 && h->opts.gmres_inner_m == 0;
+  return h->opts.gmres_basis_prec == 64 && h->opts.lgmres_k == 0 && h->opts.gmres_inner_m == 0 &&
+         h->opts.precond != 2;
 }
 
 }  // namespace
@@ -1400,7 +1401,7 @@ extern "C" stab_status stab_jv_batch_solve(stab_jv_batch B, const double* sigmas
       return STAB_ERR_INVALID_ARG;
     }
     if (!batchable_solver(B->hs[i])) {
-      B->err = "stab_jv_batch_solve: instance " + std::to_string(i) + " uses an FP32 basis, LGMRES or a nested inner solver";
+      B->err = "stab_jv_batch_solve: instance " + std::to_string(i) + " uses an FP32 basis, LGMRES, a nested inner solver or the reduced-operator preconditioner";
       return STAB_ERR_UNSUPPORTED;
     }
   }
@@ -1453,7 +1454,7 @@ extern "C" stab_status stab_jv_batch_eigs(stab_jv_batch B, stab_eig_job* jobs) {
       return STAB_ERR_INVALID_ARG;
     }
     if (!batchable_solver(h)) {
-      B->err = "stab_jv_batch_eigs: instance " + std::to_string(i) + " uses an FP32 basis, LGMRES or a nested inner solver";
+      B->err = "stab_jv_batch_eigs: instance " + std::to_string(i) + " uses an FP32 basis, LGMRES, a nested inner solver or the reduced-operator preconditioner";
       return STAB_ERR_UNSUPPORTED;
     }
   }
@@ -1496,7 +1497,7 @@ extern "C" stab_status stab_jv_batch_eigs(stab_jv_batch B, stab_eig_job* jobs) {
       maxm = std::max(maxm, S.m);
       StabHandle* h = S.h;
       const long long n = h->n;
-      if (h->opts.precond == 1 && !(h->pvalid && h->psigma_re == S.sigma.real() && h->psigma_im == S.sigma.imag())) {
+      if (h->opts.precond != 0 && !(h->pvalid && h->psigma_re == S.sigma.real() && h->psigma_im == S.sigma.imag())) {
         auto tp = std::chrono::steady_clock::now();
         ck(h, pc_build(h, d2(S.sigma)), "preconditioner build");
         ck(h, cudaStreamSynchronize(st), "sync");

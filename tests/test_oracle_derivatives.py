@@ -1,7 +1,10 @@
 """Pins of the oracle's compact finite differences (Sec. Governing equations,
 the Lele 1992 schemes): closed-form modified wavenumbers, polynomial
 exactness, exact zero on constants, the tridiagonal solvers against a dense
-library solve, and the convergence order on a stretched grid."""
+library solve, and the convergence order on a stretched grid; the reduced
+operator's second-order explicit differences likewise."""
+import math
+
 import numpy as np
 import pytest
 
@@ -141,3 +144,26 @@ def test_stretched_y_metric_convergence(orc):
         e2.append(np.abs(d2 + np.sin(y / 3) / 9).max())
     assert np.log2(e1[0] / e1[1]) > 2.5 and np.log2(e1[1] / e1[2]) > 2.7
     assert np.log2(e2[0] / e2[1]) > 2.5 and np.log2(e2[1] / e2[2]) > 2.7
+
+
+@pytest.mark.parametrize("n", [16, 33])
+def test_reduced_operator_differences(orc, n):
+    """The reduced operator's second-order explicit differences: periodic
+    modified wavenumbers sin(kh)/h and 2 (1 - cos(kh))/h^2 on every Fourier
+    mode; on a bounded line the first derivative exact for quadratics and the
+    second for cubics, end rows included (second-order one-sided forms)."""
+    h = 2 * math.pi / n
+    x = np.arange(n) * h
+    for k in range(1, n // 2):
+        f = np.cos(k * x)
+        d1 = orc.core.deriv_line(f, h, 1, True, low=True)
+        d2 = orc.core.deriv_line(f, h, 2, True, low=True)
+        assert np.abs(d1 + math.sin(k * h) / h * np.sin(k * x)).max() < 1e-12
+        assert np.abs(d2 + 2 * (1 - math.cos(k * h)) / h ** 2 * f).max() < 1e-11
+    hb = 0.37
+    y = np.arange(n) * hb - 1.3
+    f = 0.4 - 1.1 * y + 0.7 * y ** 2
+    assert np.abs(orc.core.deriv_line(f, hb, 1, False, low=True) - (-1.1 + 1.4 * y)).max() < 1e-11
+    f3 = f + 0.3 * y ** 3
+    assert np.abs(orc.core.deriv_line(f3, hb, 2, False, low=True) - (1.4 + 1.8 * y)).max() < 1e-10
+    assert np.abs(orc.core.deriv_line(np.full(n, 2.5), hb, 1, False, low=True)).max() < 1e-12

@@ -12,10 +12,10 @@ import stab_inputs as si
 GAM = 1.4
 
 
-def _problem(orc, nx=16, ny=24, Ma=0.3, Re=1000.0, stretch=0.0, dim=2, nz=1, bulk=0.0):
+def _problem(orc, nx=16, ny=24, Ma=0.3, Re=1000.0, stretch=0.0, dim=2, nz=1, bulk=0.0, low=0):
     g = si.Grid(dim, nx, ny, nz, 2 * math.pi / 0.4, -15.0, 15.0, 2 * math.pi / 0.4, stretch)
     f = si.Flow(Ma, Re)
-    return g, f, orc.Problem.from_inputs(g, f, bulk)
+    return g, f, orc.Problem.from_inputs(g, f, bulk, low)
 
 
 def _uniform(g, f, U0=0.0, s0=0.0):
@@ -55,21 +55,28 @@ def test_galilean_shift_adds_convection(orc):
     assert np.linalg.norm(j1 - j0 + 0.7 * dx) < 1e-12 * np.linalg.norm(j0)
 
 
-def _symbols(h, k, n):
+def _symbols(h, k, n, low=0):
+    """Modified wavenumbers k' (first derivative) and k''^2 (second) of the
+    compact schemes, or (low) of the reduced operator's second-order explicit
+    differences: sin(kh)/h and 2 (1 - cos(kh))/h^2."""
     kh = 2 * math.pi * k / n
+    if low:
+        return math.sin(kh) / h, 2 * (1 - math.cos(kh)) / h ** 2
     k1 = (14 / 9 * math.sin(kh) + (1 / 18) * math.sin(2 * kh)) / (1 + 2 / 3 * math.cos(kh)) / h
     k2 = (24 / 11 * (1 - math.cos(kh)) + 3 / 22 * (1 - math.cos(2 * kh))) / (1 + 4 / 11 * math.cos(kh)) / h ** 2
     return k1, k2
 
 
+@pytest.mark.parametrize("low", [0, 1])
 @pytest.mark.parametrize("Re", [0.0, 200.0])
 @pytest.mark.parametrize("k", [1, 3])
-def test_x_fourier_modes_of_uniform_state(orc, Re, k):
+def test_x_fourier_modes_of_uniform_state(orc, Re, k, low):
     """On y-independent perturbations exp(i k x) of a uniform state at rest,
     J reduces to the linearised 1-D compressible Navier-Stokes symbol: a 3x3
     (p, u, s) block with the acoustic pair and conduction, and the shear mode
-    lambda = -mu k''^2 / rho for v (derived by hand from the equations)."""
-    g, f, P = _problem(orc, nx=16, ny=12, Re=Re, Ma=0.4)
+    lambda = -mu k''^2 / rho for v (derived by hand from the equations).  The
+    reduced operator (low) has the same symbol with its own wavenumbers."""
+    g, f, P = _problem(orc, nx=16, ny=12, Re=Re, Ma=0.4, low=low)
     q0 = _uniform(g, f)
     R = 1 / (GAM * f.Ma ** 2)
     p0 = R
@@ -78,7 +85,7 @@ def test_x_fourier_modes_of_uniform_state(orc, Re, k):
     lam0 = mu0 * cp / f.Pr
     Tp = (GAM - 1) / (GAM * p0)  # dT/dp at constant s, T0 = 1
     Ts = 1 / cp  # dT/ds at constant p
-    k1, k2 = _symbols(g.lx / g.nx, k, g.nx)
+    k1, k2 = _symbols(g.lx / g.nx, k, g.nx, low)
     M = np.array([[-(GAM - 1) * lam0 * k2 * Tp, -1j * GAM * p0 * k1, -(GAM - 1) * lam0 * k2 * Ts],
                   [-1j * k1, -(4 / 3) * mu0 * k2, 0],
                   [-lam0 * k2 * Tp, 0, -lam0 * k2 * Ts]])
@@ -215,8 +222,9 @@ def test_dense_jacobian_columns_are_tangent(orc):
     assert np.linalg.norm(J @ v - orc.core.jv(P, q0, v)) < 1e-13 * np.linalg.norm(J @ v)
 
 
+@pytest.mark.parametrize("low", [0, 1])
 @pytest.mark.parametrize("bulk", [0.0, 0.7])
-def test_xz_fourier_symbol_of_uniform_3d_state(orc, bulk):
+def test_xz_fourier_symbol_of_uniform_3d_state(orc, bulk, low):
     """3-D pin of every viscous index: a uniform moving state (U, 0, W) with
     non-reference pressure and entropy (rho0, T0 != 1, so Sutherland's mu(T0)
     enters), perturbed by q' = (a + b y) exp(i (kx x + kz z)) on a uniform y
@@ -229,12 +237,15 @@ def test_xz_fourier_symbol_of_uniform_3d_state(orc, bulk):
     mixed d_x d_z, d_x d_y, d_y d_z through products of first-derivative
     symbols; conduction lambda laplacian T' with T' = T0 ((1 - 1/gamma) p'/p0 +
     s'/c_p) in the p and s rows.  A transposed index in the 3-D viscous stress
-    or a mixed derivative taken as a second derivative fails it."""
+    or a mixed derivative taken as a second derivative fails it.  The reduced
+    operator (low: second-order explicit differences, which also differentiate
+    a + b y exactly, end rows included) is pinned by the same symbol with its
+    own modified wavenumbers."""
     nx, ny, nz = 8, 7, 6
     lx, lz = 3.0, 2.5
     g = si.Grid(3, nx, ny, nz, lx, -1.0, 2.0, lz, 0.0)
     f = si.Flow(0.6, 50.0, Pr=0.5)
-    P = orc.Problem.from_inputs(g, f, bulk)
+    P = orc.Problem.from_inputs(g, f, bulk, low)
     gam, R = f.gamma, 1.0 / (f.gamma * f.Ma ** 2)
     cp = gam * R / (gam - 1)
     p0, s0, U, W = 1.3 * R, 0.3, 0.4, -0.7
@@ -246,8 +257,8 @@ def test_xz_fourier_symbol_of_uniform_3d_state(orc, bulk):
     lam0, muv0 = mu0 * cp / f.Pr, bulk * mu0
     Tp, Ts = T0 * (gam - 1) / (gam * p0), T0 / cp  # T' = Tp p' + Ts s'
     mx, mz = 2, 1
-    kx1, kx2 = _symbols(lx / nx, mx, nx)
-    kz1, kz2 = _symbols(lz / nz, mz, nz)
+    kx1, kx2 = _symbols(lx / nx, mx, nx, low)
+    kz1, kz2 = _symbols(lz / nz, mz, nz, low)
     conv = -1j * (U * kx1 + W * kz1)
     lap = -(kx2 + kz2)  # second-derivative symbols (y part: d2/dy2 (a + b y) = 0)
     vd = (mu0 / 3 + muv0) / rho0  # coefficient of d_i div u
