@@ -395,15 +395,18 @@ def precond_build_256x512(args, Stab, torch) -> dict:
 def preconditioners_256x512(args, Stab, torch) -> dict:
     """The 256 x 512 inner solve (FGMRES(50) to 1e-10 at sigma = 1) with exact tile blocks (block-Jacobi
     over 8 x 32 tiles, FP32 inverses factorised with TF32 tensor-core GEMMs) against the reduced-operator
-    blocks (second-order explicit operator, block-tridiagonal FP32 factors) over taller tiles: iterations,
-    solve time, build time, factor bytes and the time of one block apply (CUDA events, 20 applies)."""
+    blocks (second-order explicit operator, block-tridiagonal FP32 factors) over taller tiles, and with
+    LGMRES(50, 4) beside GMRES(50): iterations, J v calls, solve time, build time, factor bytes and the
+    time of one block apply (CUDA events, 20 applies)."""
     g, f, q0 = _layer(256, 512, 0.3)
     sigma = 1.0
     b = torch.from_numpy(si.random_complex(1, g.n)).cuda()
     out = {"sigma": sigma, "tol": 1e-10, "gmres": "FGMRES(50)"}
     variants = (("exact_8x32", dict(precond=1, tile=(8, 32), precond_factor=2)),
+                ("exact_8x32_lgmres4", dict(precond=1, tile=(8, 32), precond_factor=2, lgmres_k=4)),
                 ("reduced_8x64", dict(precond=2, tile=(8, 64))),
                 ("reduced_8x512", dict(precond=2, tile=(8, 512))),
+                ("reduced_8x512_lgmres4", dict(precond=2, tile=(8, 512), lgmres_k=4)),
                 ("reduced_4x512", dict(precond=2, tile=(4, 512))))
     for key, o in variants:
         S = Stab(q0, g, f.Ma, f.Re, f.Pr, eps_mode=2, precond_prec=32, gmres_m=50, gmres_tol=1e-10,
@@ -425,11 +428,13 @@ def preconditioners_256x512(args, Stab, torch) -> dict:
         torch.cuda.synchronize()
         apply_ms = e0.elapsed_time(e1) / 20
         x = torch.zeros_like(b)
+        jv0 = S.stats()["jv_calls"]
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         st, it = S.solve(sigma, b, x)
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
+        jv = S.stats()["jv_calls"] - jv0
         ax = torch.empty_like(b)
         S.apply_J(x, ax, sigma)
         res = float(torch.linalg.vector_norm(b - ax) / torch.linalg.vector_norm(b))
@@ -440,7 +445,7 @@ def preconditioners_256x512(args, Stab, torch) -> dict:
             m = 4 * 2 * tile[0]
             nbytes = g.n * 3 * m * 8
         S.close()
-        out[key] = {"iterations": it, "converged": st == 0, "true_rel_residual": res, "solve_s": dt,
+        out[key] = {"iterations": it, "jv_calls": jv, "converged": st == 0, "true_rel_residual": res, "solve_s": dt,
                     "ms_per_iteration": 1e3 * dt / max(it, 1), "build_s": t_build, "apply_ms": apply_ms,
                     "factor_bytes": nbytes, "apply_GB_per_s": nbytes / apply_ms / 1e6}
     return out
@@ -1000,10 +1005,15 @@ def run_ours(args):
         roofline = jv_roofline(g, f, Sj.timing_read(), statistics.mean(sample_t), hbm, statistics.mean(jv_tan))
         Sj.timing(False)
         sweep = (0.3, 0.6, 0.9)
+        solver_opts = dict(SOLVER_OPTS)
+        if args.eig_precond == 2:  # reduced-operator blocks, block-tridiagonal factors
+            solver_opts.update(precond=2, tile=tuple(args.eig_tile or (8, EIG_GRID[1])))
+        elif args.eig_tile:
+            solver_opts.update(tile=tuple(args.eig_tile))
         handles = []
         for Ma in sweep:
             gg, ff, qq = _layer(EIG_GRID[0], EIG_GRID[1], Ma)
-            handles.append(Stab(qq, gg, ff.Ma, ff.Re, ff.Pr, seed=0x5EED + rank, **SOLVER_OPTS))
+            handles.append(Stab(qq, gg, ff.Ma, ff.Re, ff.Pr, seed=0x5EED + rank, **solver_opts))
         vecs = torch.empty((EIG["nev"], n), dtype=torch.complex128, device="cuda")
         v0h = torch.from_numpy(si.start_vector(0x5EED + rank, n)).pin_memory()
         v0d = torch.empty(n, dtype=torch.complex128, device="cuda")
@@ -1065,7 +1075,10 @@ def run_ours(args):
         config = {"workload": f"eigs_mixing_layer_{g.nx}x{g.ny}", "nx": g.nx, "ny": g.ny, "Re": f.Re,
                   "Ma_sweep": list(sweep), "sigma": [1.0, 0.0], "tau": [-1.0, 0.0], "nev": EIG["nev"],
                   "ncv": EIG["ncv"], "tol": EIG["tol"], "gmres": "flexible GMRES(50) to 1e-10",
-                  "precond": "block-Jacobi 8x32 tiles, FP32 inverses factorised with tensor-core GEMMs",
+                  "precond": (f"block-Jacobi {solver_opts['tile'][0]}x{solver_opts['tile'][1]} tiles, FP32 inverses "
+                              "factorised with tensor-core GEMMs") if solver_opts["precond"] == 1 else
+                             (f"reduced-operator block-Jacobi {solver_opts['tile'][0]}x{solver_opts['tile'][1]} tiles, "
+                              "FP32 block-tridiagonal factors"),
                   "jv": "exact tangent (FP64)", "warmup": "per handle: tuning, preconditioner build, one inner solve",
                   "l2": "flushed before each timed solve", "parallelism": f"replicas{world}"}
         extra = {"latency_ms": {"p50": statistics.median(lat) * 1e3, "p99": lat[min(len(lat) - 1,
@@ -1161,6 +1174,10 @@ def main():
     ap.add_argument("--workload", default="jv", choices=["eigs", "jv", "serve", "precond"])
     ap.add_argument("--tile", type=int, nargs=2, default=[16, 16], help="block-Jacobi tile (--workload precond)")
     ap.add_argument("--factor", type=int, default=1, help="precond_factor (--workload precond)")
+    ap.add_argument("--eig-precond", type=int, default=1, choices=[1, 2],
+                    help="inner preconditioner of --workload eigs: 1 exact tile blocks, 2 reduced-operator blocks")
+    ap.add_argument("--eig-tile", type=int, nargs=2, default=None,
+                    help="tile of --workload eigs (default 8 x 32 exact, 8 x 512 reduced)")
     ap.add_argument("--requests", type=int, default=200, help="served stream length (--workload serve)")
     ap.add_argument("--plain-requests", type=int, default=16, help="requests also solved one at a time (serve)")
     ap.add_argument("--cohort", type=int, default=16, help="lockstep cohort size of the server (serve)")
