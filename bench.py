@@ -1010,6 +1010,8 @@ def run_ours(args):
             solver_opts.update(precond=2, tile=tuple(args.eig_tile or (8, EIG_GRID[1])))
         elif args.eig_tile:
             solver_opts.update(tile=tuple(args.eig_tile))
+        if args.eig_lgmres:
+            solver_opts.update(lgmres_k=args.eig_lgmres)
         handles = []
         for Ma in sweep:
             gg, ff, qq = _layer(EIG_GRID[0], EIG_GRID[1], Ma)
@@ -1061,20 +1063,24 @@ def run_ours(args):
         lat = sorted(step_t)
         # end to end: start vector from pinned host memory in, eigenvectors out, inside the timed region
         barrier()
-        te0 = time.perf_counter()
-        e2e_good = 0
-        for s in range(max(1, min(args.steps, 3))):
-            r = solve(handles[s % 3], True)
-            torch.cuda.synchronize()
-            e2e_good += int(np.sum(r.resid[:r.nconv] < RESID_OK))
-        te = (time.perf_counter() - te0)
-        e2e = {"value": world * e2e_good / te, "unit": "eigenpairs/s", "h2d_bytes_per_step": n * 16,
-               "d2h_bytes_per_step": EIG["nev"] * n * 16 + EIG["nev"] * 24}
+        e2e = None
+        if args.eig_e2e:
+            te0 = time.perf_counter()
+            e2e_good = 0
+            for s in range(max(1, min(args.steps, 3))):
+                r = solve(handles[s % 3], True)
+                torch.cuda.synchronize()
+                e2e_good += int(np.sum(r.resid[:r.nconv] < RESID_OK))
+            te = (time.perf_counter() - te0)
+            e2e = {"value": world * e2e_good / te, "unit": "eigenpairs/s", "h2d_bytes_per_step": n * 16,
+                   "d2h_bytes_per_step": EIG["nev"] * n * 16 + EIG["nev"] * 24}
         st = [r.stats for r in results]
         jv_per_solve = statistics.mean(s_["jv_calls"] for s_ in st)
         config = {"workload": f"eigs_mixing_layer_{g.nx}x{g.ny}", "nx": g.nx, "ny": g.ny, "Re": f.Re,
                   "Ma_sweep": list(sweep), "sigma": [1.0, 0.0], "tau": [-1.0, 0.0], "nev": EIG["nev"],
-                  "ncv": EIG["ncv"], "tol": EIG["tol"], "gmres": "flexible GMRES(50) to 1e-10",
+                  "ncv": EIG["ncv"], "tol": EIG["tol"],
+                  "gmres": ("flexible GMRES(50) to 1e-10" if not args.eig_lgmres else
+                            f"flexible LGMRES(50, {args.eig_lgmres}) to 1e-10"),
                   "precond": (f"block-Jacobi {solver_opts['tile'][0]}x{solver_opts['tile'][1]} tiles, FP32 inverses "
                               "factorised with tensor-core GEMMs") if solver_opts["precond"] == 1 else
                              (f"reduced-operator block-Jacobi {solver_opts['tile'][0]}x{solver_opts['tile'][1]} tiles, "
@@ -1117,13 +1123,14 @@ def run_ours(args):
 def run_precond(args):
     """--workload precond: block-Jacobi builds (assembly + inversion of every tile block, FP32 inverses) of
     the --nx x --ny layer with --tile tiles, by the factorisation --factor (0 CUDA cores, 1 tensor cores
-    BF16x9, 2 tensor cores TF32); --steps timed builds after --warmup builds."""
+    BF16x9, 2 tensor cores TF32), or (--precond 2) of the reduced-operator block-tridiagonal factors;
+    --steps timed builds after --warmup builds, then 20 applies timed with CUDA events."""
     import torch
     from paper_1502_03701_gb300 import Stab, build
     build.build()
     g, f, q0 = _layer(args.nx, args.ny, 0.3)
     tile = tuple(args.tile)
-    S = Stab(q0, g, f.Ma, f.Re, f.Pr, eps_mode=2, precond=1, tile=tile, precond_prec=32,
+    S = Stab(q0, g, f.Ma, f.Re, f.Pr, eps_mode=2, precond=args.precond, tile=tile, precond_prec=32,
              precond_factor=args.factor)
     for i in range(args.warmup):
         S.precond_build(1.0 + 1e-3 * i)
@@ -1134,16 +1141,36 @@ def run_precond(args):
         S.precond_build(2.0 + 1e-3 * i)
         torch.cuda.synchronize()
         times.append(time.perf_counter() - t0)
+    q = torch.from_numpy(si.random_complex(1, g.n)).cuda()
+    z = torch.empty_like(q)
+    S.precond_apply(q, z)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(20):
+        S.precond_apply(q, z)
+    e1.record()
+    torch.cuda.synchronize()
+    apply_ms = e0.elapsed_time(e1) / 20
     S.close()
-    b = 4 * tile[0] * tile[1]
-    nblk = g.npts // (tile[0] * tile[1])
-    flops = 8.0 * b ** 3 * nblk
     t = statistics.median(times)
-    print(json.dumps({"metric": "block-Jacobi build", "value": flops / t / 1e12, "unit": "TFLOP/s",
-                      "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3,
-                      "higher_is_better": True, "dtype": "f32",
-                      "config": {"workload": f"precond_build_{g.nx}x{g.ny}", "tile": list(tile), "block": b,
-                                 "blocks": nblk, "factor": args.factor}}))
+    if args.precond == 2:
+        m = 4 * 2 * tile[0]
+        nbytes = g.n * 3 * m * 8
+        line = {"metric": "reduced-operator block-Jacobi build", "value": 1.0 / t, "unit": "builds/s",
+                "config": {"workload": f"precond_reduced_{g.nx}x{g.ny}", "tile": list(tile), "level": m,
+                           "levels_per_tile": tile[1] // 2}}
+    else:
+        b = 4 * tile[0] * tile[1]
+        nblk = g.npts // (tile[0] * tile[1])
+        nbytes = g.n * b * 8
+        line = {"metric": "block-Jacobi build", "value": 8.0 * b ** 3 * nblk / t / 1e12, "unit": "TFLOP/s",
+                "config": {"workload": f"precond_build_{g.nx}x{g.ny}", "tile": list(tile), "block": b,
+                           "blocks": nblk, "factor": args.factor}}
+    line.update({"n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3,
+                 "higher_is_better": True, "dtype": "f32",
+                 "apply": {"ms": apply_ms, "factor_bytes": nbytes, "GB_per_s": nbytes / apply_ms / 1e6}})
+    print(json.dumps(line))
 
 
 def run_serve(args):
@@ -1174,6 +1201,9 @@ def main():
     ap.add_argument("--workload", default="jv", choices=["eigs", "jv", "serve", "precond"])
     ap.add_argument("--tile", type=int, nargs=2, default=[16, 16], help="block-Jacobi tile (--workload precond)")
     ap.add_argument("--factor", type=int, default=1, help="precond_factor (--workload precond)")
+    ap.add_argument("--precond", type=int, default=1, choices=[1, 2], help="preconditioner (--workload precond)")
+    ap.add_argument("--eig-lgmres", type=int, default=0, help="lgmres_k of the inner solves (--workload eigs)")
+    ap.add_argument("--eig-e2e", type=int, default=1, help="0: skip the end-to-end solves (--workload eigs)")
     ap.add_argument("--eig-precond", type=int, default=1, choices=[1, 2],
                     help="inner preconditioner of --workload eigs: 1 exact tile blocks, 2 reduced-operator blocks")
     ap.add_argument("--eig-tile", type=int, nargs=2, default=None,

@@ -293,7 +293,11 @@ __global__ void k_gauss_jordan(C2<R>* A, int b, int* info) {
 // Block-tridiagonal LU of a reduced-operator tile (one CTA per tile, levels in
 // order; block Thomas elimination): S_0 = D_0, S_l = D_l - L_l X_{l-1},
 // X_l = S_l^{-1} U_l, with S_l inverted by the Gauss-Jordan sweep above
-// (partial pivoting inside the level).  F[tile][l] = {L_l, S_l^{-1}, X_l}.
+// (partial pivoting inside the level).  Stored per level
+// F[tile][l] = {P_l = S_l^{-1} L_l, S_l^{-1}, X_l}: the forward substitution
+// y_l = S_l^{-1} (q_l - L_l y_{l-1}) = S_l^{-1} q_l - P_l y_{l-1} then has one
+// product per level on its dependency chain, and the S_l^{-1} q_l of all
+// levels are independent.
 template <class R>
 __global__ void k_bt_factor(const double2* asmb, C2<R>* F, int m, int nlev, int* info) {
   extern __shared__ unsigned char smraw[];
@@ -306,12 +310,12 @@ __global__ void k_bt_factor(const double2* asmb, C2<R>* F, int m, int nlev, int*
   int bad = 0;
   for (int l = 0; l < nlev; ++l) {
     const double2* Al = A + (long long)l * 3 * mm;
-    C2<R>* L = Ft + (long long)l * 3 * mm;
-    C2<R>* S = L + mm;
+    C2<R>* Pl = Ft + (long long)l * 3 * mm;
+    C2<R>* S = Pl + mm;
     C2<R>* X = S + mm;
-    const C2<R>* Xp = L - mm;  // X_{l-1}
+    const C2<R>* Xp = Pl - mm;  // X_{l-1}
     for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) {
-      const double2 lv = l > 0 ? Al[idx] : make_double2(0.0, 0.0), dv = Al[mm + idx];
+      const double2 dv = Al[mm + idx];
       C2<R> sv = {(R)dv.x, (R)dv.y};
       if (l > 0) {
         const int i = idx / m, c = idx - (idx / m) * m;
@@ -325,25 +329,31 @@ __global__ void k_bt_factor(const double2* asmb, C2<R>* F, int m, int nlev, int*
         sv.x -= ax;
         sv.y -= ay;
       }
-      L[idx] = C2<R>{(R)lv.x, (R)lv.y};
       S[idx] = sv;
     }
     __syncthreads();
     const int b = gj_sweep<R>(S, m, prow, pcol, perm);
     if (b && !bad) bad = b;
     __syncthreads();
-    if (l + 1 < nlev)
-      for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) {
-        const int i = idx / m, c = idx - (idx / m) * m;
-        R ax = 0, ay = 0;
-        for (int k = 0; k < m; ++k) {
-          const C2<R> a = S[(long long)i * m + k];
-          const double2 u = Al[2 * mm + (long long)k * m + c];
-          ax += a.x * (R)u.x - a.y * (R)u.y;
-          ay += a.x * (R)u.y + a.y * (R)u.x;
+    for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) {
+      const int i = idx / m, c = idx - (idx / m) * m;
+      R px = 0, py = 0, xx = 0, xy = 0;
+      for (int k = 0; k < m; ++k) {
+        const C2<R> a = S[(long long)i * m + k];
+        if (l > 0) {
+          const double2 lv = Al[(long long)k * m + c];
+          px += a.x * (R)lv.x - a.y * (R)lv.y;
+          py += a.x * (R)lv.y + a.y * (R)lv.x;
         }
-        X[idx] = C2<R>{ax, ay};
+        if (l + 1 < nlev) {
+          const double2 u = Al[2 * mm + (long long)k * m + c];
+          xx += a.x * (R)u.x - a.y * (R)u.y;
+          xy += a.x * (R)u.y + a.y * (R)u.x;
+        }
       }
+      Pl[idx] = C2<R>{px, py};
+      X[idx] = C2<R>{xx, xy};
+    }
     __syncthreads();
   }
   if (threadIdx.x == 0 && bad) atomicMax(info, 1);
@@ -359,82 +369,153 @@ struct BtApplyParams {
   const int* gate;
 };
 
-// z = M^{-1} q for the block-tridiagonal tiles (one CTA per tile): forward
-// y_l = S_l^{-1} (q_l - L_l y_{l-1}), backward x_l = y_l - X_l x_{l+1}, the
-// level vectors in shared memory, y kept in z between the sweeps.  Each row's
-// dot product is split over G threads (G a power of two), reduced by shuffles.
+__device__ __forceinline__ long long bt_dof(const BtApplyParams& P, long long tile, int l, int r) {
+  const int NP = 2 * P.tx * P.tz;
+  const int tX = (int)(tile % P.ntx), tY = (int)((tile / P.ntx) % P.nty), tZ = (int)(tile / ((long long)P.ntx * P.nty));
+  const int a = r / NP, pp = r % NP;
+  const int x = tX * P.tx + pp % P.tx, y = tY * P.ty + 2 * l + (pp / P.tx) % 2, z = tZ * P.tz + pp / (2 * P.tx);
+  return (long long)a * P.npts + ((long long)z * P.ny + y) * P.nx + x;
+}
+
+// Rows per CTA and threads per row of the level products: G threads (a power
+// of two) share a row, G * m <= blockDim.
+__device__ __forceinline__ int bt_group(int m) {
+  int G = 1;
+  while (G < 32 && 2 * G * m <= (int)blockDim.x) G *= 2;
+  return G;
+}
+
+// w_l = S_l^{-1} q_l for every level of every tile, into z (grid: tiles x levels).
 template <class R, bool Q32>
-__global__ void __launch_bounds__(256) k_bt_apply(const BtApplyParams P) {
+__global__ void __launch_bounds__(256) k_bt_rhs(const BtApplyParams P) {
+  if (P.gate && *P.gate) return;
+  extern __shared__ unsigned char smraw[];
+  C2<R>* t = (C2<R>*)smraw;
+  const int m = P.m, l = blockIdx.y;
+  const long long tile = blockIdx.x, mm = (long long)m * m;
+  const C2<R>* S = (const C2<R>*)P.F + (tile * P.nlev + l) * 3 * mm + mm;
+  for (int r = threadIdx.x; r < m; r += blockDim.x) {
+    const long long d = bt_dof(P, tile, l, r);
+    if (Q32) { const float2 v = P.q32[d]; t[r] = C2<R>{(R)v.x, (R)v.y}; }
+    else { const double2 v = P.q[d]; t[r] = C2<R>{(R)v.x, (R)v.y}; }
+  }
+  __syncthreads();
+  const int G = bt_group(m);
+  const int row = threadIdx.x / G, g = threadIdx.x % G;
+  R sx = 0, sy = 0;
+  if (row < m)
+    for (int k = g; k < m; k += G) {
+      const C2<R> a = S[(long long)row * m + k], b = t[k];
+      sx += a.x * b.x - a.y * b.y;
+      sy += a.x * b.y + a.y * b.x;
+    }
+  for (int o = G >> 1; o > 0; o >>= 1) {
+    sx += __shfl_xor_sync(0xffffffffu, sx, o);
+    sy += __shfl_xor_sync(0xffffffffu, sy, o);
+  }
+  if (row < m && g == 0) P.z[bt_dof(P, tile, l, row)] = make_double2((double)sx, (double)sy);
+}
+
+// The level recurrences of one tile (one CTA per tile), z holding w on entry:
+// forward y_l = w_l - P_l y_{l-1}, backward x_l = y_l - X_l x_{l+1}.  Each row's
+// product is split over G threads; with KP > 0 every thread holds its
+// fragment (at most KP entries) of the next level's matrix and the next w in
+// registers, loaded while the current level is reduced, so the dependency
+// chain carries no global-memory latency.
+template <class R, int KP>
+__global__ void __launch_bounds__(256) k_bt_sweep(const BtApplyParams P) {
   if (P.gate && *P.gate) return;
   extern __shared__ unsigned char smraw[];
   C2<R>* va = (C2<R>*)smraw;
   C2<R>* vb = va + P.m;
-  const int m = P.m, NP = 2 * P.tx * P.tz;
-  const long long mm = (long long)m * m;
-  const long long tile = blockIdx.x;
-  const int tX = (int)(tile % P.ntx), tY = (int)((tile / P.ntx) % P.nty), tZ = (int)(tile / ((long long)P.ntx * P.nty));
-  const C2<R>* Ft = (const C2<R>*)P.F + tile * P.nlev * 3 * mm;
-  int G = 1;
-  while (G < 32 && 2 * G * m <= (int)blockDim.x) G *= 2;
+  const int m = P.m, nlev = P.nlev;
+  const long long tile = blockIdx.x, mm = (long long)m * m;
+  const C2<R>* Ft = (const C2<R>*)P.F + tile * nlev * 3 * mm;
+  const int G = bt_group(m);
   const int row = threadIdx.x / G, g = threadIdx.x % G;
-  const bool act = row < m;
-  auto dof = [&](int l, int r) -> long long {
-    const int a = r / NP, pp = r % NP;
-    const int x = tX * P.tx + pp % P.tx, y = tY * P.ty + 2 * l + (pp / P.tx) % 2, z = tZ * P.tz + pp / (2 * P.tx);
-    return (long long)a * P.npts + ((long long)z * P.ny + y) * P.nx + x;
+  const bool act = row < m, lead = act && g == 0;
+  C2<R> cur[KP > 0 ? KP : 1], nxt[KP > 0 ? KP : 1];
+  auto fetch = [&](C2<R>* frag, const C2<R>* M) {
+#pragma unroll
+    for (int j = 0; j < KP; ++j) {
+      const int k = g + j * G;
+      frag[j] = (act && k < m) ? M[(long long)row * m + k] : C2<R>{0, 0};
+    }
   };
-  // (M x)_row, complete in every lane of the row's group
-  auto mv = [&](const C2<R>* M, const C2<R>* x) {
+  // (M x)_row from registers (KP > 0) or from memory, complete in every lane of the row's group
+  auto mv = [&](const C2<R>* frag, const C2<R>* M, const C2<R>* x) {
     R sx = 0, sy = 0;
-    if (act)
+    if (KP > 0) {
+#pragma unroll
+      for (int j = 0; j < KP; ++j) {
+        const int k = g + j * G;
+        const C2<R> b = k < m ? x[k] : C2<R>{0, 0};
+        sx += frag[j].x * b.x - frag[j].y * b.y;
+        sy += frag[j].x * b.y + frag[j].y * b.x;
+      }
+    } else if (act) {
       for (int k = g; k < m; k += G) {
         const C2<R> a = M[(long long)row * m + k], b = x[k];
         sx += a.x * b.x - a.y * b.y;
         sy += a.x * b.y + a.y * b.x;
       }
+    }
     for (int o = G >> 1; o > 0; o >>= 1) {
       sx += __shfl_xor_sync(0xffffffffu, sx, o);
       sy += __shfl_xor_sync(0xffffffffu, sy, o);
     }
     return C2<R>{sx, sy};
   };
-  C2<R>* yp = va;  // y_{l-1}
-  C2<R>* t = vb;
-  for (int l = 0; l < P.nlev; ++l) {
-    const C2<R>* L = Ft + (long long)l * 3 * mm;
-    for (int r = threadIdx.x; r < m; r += blockDim.x) {
-      const long long d = dof(l, r);
-      if (Q32) { const float2 v = P.q32[d]; t[r] = C2<R>{(R)v.x, (R)v.y}; }
-      else { const double2 v = P.q[d]; t[r] = C2<R>{(R)v.x, (R)v.y}; }
-    }
-    __syncthreads();
-    if (l > 0) {
-      const C2<R> s = mv(L, yp);
-      __syncthreads();
-      if (act && g == 0) { t[row].x -= s.x; t[row].y -= s.y; }
-      __syncthreads();
-    }
-    const C2<R> y = mv(L + mm, t);
-    __syncthreads();
-    if (act && g == 0) {
-      yp[row] = y;
-      P.z[dof(l, row)] = make_double2((double)y.x, (double)y.y);
-    }
-    __syncthreads();
+  // forward: y_0 = w_0
+  C2<R>* yp = va;
+  C2<R>* yc = vb;
+  double2 wn = make_double2(0.0, 0.0);
+  if (lead) {
+    const double2 w = P.z[bt_dof(P, tile, 0, row)];
+    yp[row] = C2<R>{(R)w.x, (R)w.y};
+    if (nlev > 1) wn = P.z[bt_dof(P, tile, 1, row)];
   }
-  C2<R>* xn = yp;  // x_{l+1}
-  C2<R>* xc = t;
-  for (int l = P.nlev - 2; l >= 0; --l) {
-    const C2<R> s = mv(Ft + (long long)l * 3 * mm + 2 * mm, xn);
-    if (act && g == 0) {
-      const long long d = dof(l, row);
-      const double2 y = P.z[d];
-      const C2<R> x = {(R)y.x - s.x, (R)y.y - s.y};
-      xc[row] = x;
-      P.z[d] = make_double2((double)x.x, (double)x.y);
+  if (KP > 0 && nlev > 1) fetch(nxt, Ft + 3 * mm);
+  __syncthreads();
+  for (int l = 1; l < nlev; ++l) {
+    const C2<R>* Pl = Ft + (long long)l * 3 * mm;
+    const double2 w = wn;
+    if (KP > 0) {
+#pragma unroll
+      for (int j = 0; j < KP; ++j) cur[j] = nxt[j];
+      if (l + 1 < nlev) fetch(nxt, Pl + 3 * mm);
+    }
+    if (lead && l + 1 < nlev) wn = P.z[bt_dof(P, tile, l + 1, row)];
+    const C2<R> s = mv(cur, Pl, yp);
+    if (lead) {
+      const C2<R> y = {(R)w.x - s.x, (R)w.y - s.y};
+      yc[row] = y;
+      P.z[bt_dof(P, tile, l, row)] = make_double2((double)y.x, (double)y.y);
     }
     __syncthreads();
-    C2<R>* tmp = xn; xn = xc; xc = tmp;
+    C2<R>* tmp = yp; yp = yc; yc = tmp;
+  }
+  // backward: x_{nlev-1} = y_{nlev-1} (in yp)
+  if (KP > 0 && nlev > 1) fetch(nxt, Ft + (long long)(nlev - 2) * 3 * mm + 2 * mm);
+  double2 yn = make_double2(0.0, 0.0);
+  if (lead && nlev > 1) yn = P.z[bt_dof(P, tile, nlev - 2, row)];
+  for (int l = nlev - 2; l >= 0; --l) {
+    const C2<R>* Xl = Ft + (long long)l * 3 * mm + 2 * mm;
+    const double2 y = yn;
+    if (KP > 0) {
+#pragma unroll
+      for (int j = 0; j < KP; ++j) cur[j] = nxt[j];
+      if (l > 0) fetch(nxt, Xl - 3 * mm);
+    }
+    if (lead && l > 0) yn = P.z[bt_dof(P, tile, l - 1, row)];
+    const C2<R> s = mv(cur, Xl, yp);
+    if (lead) {
+      const C2<R> x = {(R)y.x - s.x, (R)y.y - s.y};
+      yc[row] = x;
+      P.z[bt_dof(P, tile, l, row)] = make_double2((double)x.x, (double)x.y);
+    }
+    __syncthreads();
+    C2<R>* tmp = yp; yp = yc; yc = tmp;
   }
 }
 
@@ -1178,15 +1259,24 @@ cudaError_t pc_apply(StabHandle* h, const double2* q, double2* z, const float2* 
     B.m = bg.m; B.nlev = bg.nlev; B.tx = g.tx; B.ty = g.ty; B.tz = g.tz; B.ntx = g.ntx; B.nty = g.nty;
     B.nx = h->nx; B.ny = h->ny; B.npts = h->npts; B.gate = h->gate;
     const int ts = phase_begin(h, STAB_PHASE_PRECOND_APPLY);
+    const dim3 grid_rhs((unsigned)g.ntiles, (unsigned)bg.nlev);
     const unsigned nt = (unsigned)g.ntiles;
+    // threads per row of the 256-thread products, and the row fragment length
+    int G = 1;
+    while (G < 32 && 2 * G * bg.m <= 256) G *= 2;
+    const int frag = (bg.m + G - 1) / G;
     if (h->pprec == 64) {
       const size_t sm = 2 * bg.m * sizeof(double2);
-      if (q32) k_bt_apply<double, true><<<nt, 256, sm, h->stream>>>(B);
-      else k_bt_apply<double, false><<<nt, 256, sm, h->stream>>>(B);
+      if (q32) k_bt_rhs<double, true><<<grid_rhs, 256, sm, h->stream>>>(B);
+      else k_bt_rhs<double, false><<<grid_rhs, 256, sm, h->stream>>>(B);
+      if (frag <= 8) k_bt_sweep<double, 8><<<nt, 256, sm, h->stream>>>(B);
+      else k_bt_sweep<double, 0><<<nt, 256, sm, h->stream>>>(B);
     } else {
       const size_t sm = 2 * bg.m * sizeof(float2);
-      if (q32) k_bt_apply<float, true><<<nt, 256, sm, h->stream>>>(B);
-      else k_bt_apply<float, false><<<nt, 256, sm, h->stream>>>(B);
+      if (q32) k_bt_rhs<float, true><<<grid_rhs, 256, sm, h->stream>>>(B);
+      else k_bt_rhs<float, false><<<grid_rhs, 256, sm, h->stream>>>(B);
+      if (frag <= 16) k_bt_sweep<float, 16><<<nt, 256, sm, h->stream>>>(B);
+      else k_bt_sweep<float, 0><<<nt, 256, sm, h->stream>>>(B);
     }
     phase_end(h, ts);
     return cudaGetLastError();

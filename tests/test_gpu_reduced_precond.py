@@ -48,7 +48,7 @@ APPLY_CASES = [
     ("2d_tall_tiles", si.mixing_layer_2d(16, 32), (4, 32), 64, 1e-9),
     ("2d_tall_tiles_fp32", si.mixing_layer_2d(16, 32), (4, 32), 32, 1e-3),
     ("2d_square_tiles", si.mixing_layer_2d(16, 32), (8, 8), 64, 1e-9),
-    ("3d", (si.Grid(3, 8, 8, 4, si.LX_04, -15, 15, si.LX_04), si.Flow(0.5, 800.0)), (2, 8, 2), 64, 1e-9),
+    ("3d", (si.Grid(3, 8, 8, 6, si.LX_04, -15, 15, si.LX_04), si.Flow(0.5, 800.0)), (2, 8, 2), 64, 1e-9),
 ]
 
 
