@@ -1012,6 +1012,8 @@ def run_ours(args):
             solver_opts.update(tile=tuple(args.eig_tile))
         if args.eig_lgmres:
             solver_opts.update(lgmres_k=args.eig_lgmres)
+        if args.eig_max_restarts:
+            solver_opts.update(max_restarts=args.eig_max_restarts)
         handles = []
         for Ma in sweep:
             gg, ff, qq = _layer(EIG_GRID[0], EIG_GRID[1], Ma)
@@ -1078,7 +1080,7 @@ def run_ours(args):
         jv_per_solve = statistics.mean(s_["jv_calls"] for s_ in st)
         config = {"workload": f"eigs_mixing_layer_{g.nx}x{g.ny}", "nx": g.nx, "ny": g.ny, "Re": f.Re,
                   "Ma_sweep": list(sweep), "sigma": [1.0, 0.0], "tau": [-1.0, 0.0], "nev": EIG["nev"],
-                  "ncv": EIG["ncv"], "tol": EIG["tol"],
+                  "ncv": EIG["ncv"], "tol": EIG["tol"], "iram_max_restarts": solver_opts["max_restarts"],
                   "gmres": ("flexible GMRES(50) to 1e-10" if not args.eig_lgmres else
                             f"flexible LGMRES(50, {args.eig_lgmres}) to 1e-10"),
                   "precond": (f"block-Jacobi {solver_opts['tile'][0]}x{solver_opts['tile'][1]} tiles, FP32 inverses "
@@ -1204,6 +1206,8 @@ def main():
     ap.add_argument("--precond", type=int, default=1, choices=[1, 2], help="preconditioner (--workload precond)")
     ap.add_argument("--eig-lgmres", type=int, default=0, help="lgmres_k of the inner solves (--workload eigs)")
     ap.add_argument("--eig-e2e", type=int, default=1, help="0: skip the end-to-end solves (--workload eigs)")
+    ap.add_argument("--eig-max-restarts", type=int, default=0,
+                    help="IRAM restart limit of --workload eigs (0: the default 40); a capped solve reports nconv")
     ap.add_argument("--eig-precond", type=int, default=1, choices=[1, 2],
                     help="inner preconditioner of --workload eigs: 1 exact tile blocks, 2 reduced-operator blocks")
     ap.add_argument("--eig-tile", type=int, nargs=2, default=None,

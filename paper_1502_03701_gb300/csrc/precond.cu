@@ -386,7 +386,9 @@ __device__ __forceinline__ int bt_group(int m) {
 }
 
 // w_l = S_l^{-1} q_l for every level of every tile, into z (grid: tiles x levels).
-template <class R, bool Q32>
+// KP > 0: each thread's row fragment (at most KP entries) is loaded in one
+// unrolled batch, so all its loads are in flight together.
+template <class R, bool Q32, int KP>
 __global__ void __launch_bounds__(256) k_bt_rhs(const BtApplyParams P) {
   if (P.gate && *P.gate) return;
   extern __shared__ unsigned char smraw[];
@@ -403,12 +405,27 @@ __global__ void __launch_bounds__(256) k_bt_rhs(const BtApplyParams P) {
   const int G = bt_group(m);
   const int row = threadIdx.x / G, g = threadIdx.x % G;
   R sx = 0, sy = 0;
-  if (row < m)
+  if (KP > 0) {
+    C2<R> a[KP > 0 ? KP : 1];
+#pragma unroll
+    for (int j = 0; j < KP; ++j) {
+      const int k = g + j * G;
+      a[j] = (row < m && k < m) ? S[(long long)row * m + k] : C2<R>{0, 0};
+    }
+#pragma unroll
+    for (int j = 0; j < KP; ++j) {
+      const int k = g + j * G;
+      const C2<R> b = k < m ? t[k] : C2<R>{0, 0};
+      sx += a[j].x * b.x - a[j].y * b.y;
+      sy += a[j].x * b.y + a[j].y * b.x;
+    }
+  } else if (row < m) {
     for (int k = g; k < m; k += G) {
       const C2<R> a = S[(long long)row * m + k], b = t[k];
       sx += a.x * b.x - a.y * b.y;
       sy += a.x * b.y + a.y * b.x;
     }
+  }
   for (int o = G >> 1; o > 0; o >>= 1) {
     sx += __shfl_xor_sync(0xffffffffu, sx, o);
     sy += __shfl_xor_sync(0xffffffffu, sy, o);
@@ -1267,16 +1284,26 @@ cudaError_t pc_apply(StabHandle* h, const double2* q, double2* z, const float2* 
     const int frag = (bg.m + G - 1) / G;
     if (h->pprec == 64) {
       const size_t sm = 2 * bg.m * sizeof(double2);
-      if (q32) k_bt_rhs<double, true><<<grid_rhs, 256, sm, h->stream>>>(B);
-      else k_bt_rhs<double, false><<<grid_rhs, 256, sm, h->stream>>>(B);
-      if (frag <= 8) k_bt_sweep<double, 8><<<nt, 256, sm, h->stream>>>(B);
-      else k_bt_sweep<double, 0><<<nt, 256, sm, h->stream>>>(B);
+      if (frag <= 8) {
+        if (q32) k_bt_rhs<double, true, 8><<<grid_rhs, 256, sm, h->stream>>>(B);
+        else k_bt_rhs<double, false, 8><<<grid_rhs, 256, sm, h->stream>>>(B);
+        k_bt_sweep<double, 8><<<nt, 256, sm, h->stream>>>(B);
+      } else {
+        if (q32) k_bt_rhs<double, true, 0><<<grid_rhs, 256, sm, h->stream>>>(B);
+        else k_bt_rhs<double, false, 0><<<grid_rhs, 256, sm, h->stream>>>(B);
+        k_bt_sweep<double, 0><<<nt, 256, sm, h->stream>>>(B);
+      }
     } else {
       const size_t sm = 2 * bg.m * sizeof(float2);
-      if (q32) k_bt_rhs<float, true><<<grid_rhs, 256, sm, h->stream>>>(B);
-      else k_bt_rhs<float, false><<<grid_rhs, 256, sm, h->stream>>>(B);
-      if (frag <= 16) k_bt_sweep<float, 16><<<nt, 256, sm, h->stream>>>(B);
-      else k_bt_sweep<float, 0><<<nt, 256, sm, h->stream>>>(B);
+      if (frag <= 16) {
+        if (q32) k_bt_rhs<float, true, 16><<<grid_rhs, 256, sm, h->stream>>>(B);
+        else k_bt_rhs<float, false, 16><<<grid_rhs, 256, sm, h->stream>>>(B);
+        k_bt_sweep<float, 16><<<nt, 256, sm, h->stream>>>(B);
+      } else {
+        if (q32) k_bt_rhs<float, true, 0><<<grid_rhs, 256, sm, h->stream>>>(B);
+        else k_bt_rhs<float, false, 0><<<grid_rhs, 256, sm, h->stream>>>(B);
+        k_bt_sweep<float, 0><<<nt, 256, sm, h->stream>>>(B);
+      }
     }
     phase_end(h, ts);
     return cudaGetLastError();
