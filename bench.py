@@ -461,7 +461,14 @@ LINE_FLOP_D1, LINE_FLOP_D2 = 10, 14
 FP64_MEASURED_GFLOPS = 1197.0
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of all kernels of one J v, from one ncu capture
 # per layer (see profiles/), keyed by workload; scaled by unknowns when the capture ran on a smaller case.
-JV_TRAFFIC = {}
+JV_TRAFFIC = {
+    # ncu on the 128x256x16 layer (2,621,440 unknowns: the derivative slots, 310 MB, exceed L2): one
+    # J v with the epsilon norm read 615.1 MB and wrote 155.9 MB; the z planes are independent, so the
+    # 128x256x64 layer moves four times as much (profiles/jv_mixing_layer_128x256x64_launches.md)
+    "jv_mixing_layer_128x256x64": {"bytes": 4 * (615.1e6 + 155.9e6),
+                                   "source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of all kernels of "
+                                             "one J v on the 128x256x16 layer, scaled by 4 (z planes)"},
+}
 
 
 def line_pass_flops(g, visc: bool) -> dict:
