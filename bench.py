@@ -392,25 +392,16 @@ def precond_build_256x512(args, Stab, torch) -> dict:
     return out
 
 
-def preconditioners_256x512(args, Stab, torch) -> dict:
-    """The 256 x 512 inner solve (FGMRES(50) to 1e-10 at sigma = 1) with exact tile blocks (block-Jacobi
-    over 8 x 32 tiles, FP32 inverses factorised with TF32 tensor-core GEMMs) against the reduced-operator
-    blocks (second-order explicit operator, block-tridiagonal FP32 factors) over taller tiles, and with
-    LGMRES(50, 4) beside GMRES(50): iterations, J v calls, solve time, build time, factor bytes and the
-    time of one block apply (CUDA events, 20 applies)."""
-    g, f, q0 = _layer(256, 512, 0.3)
-    sigma = 1.0
+def inner_solves(Stab, torch, g, f, q0, variants, sigma=1.0, max_restarts=120) -> dict:
+    """FGMRES(50) to 1e-10 of (J - sigma I) x = b on one layer per preconditioner variant (name, options):
+    iterations, J v calls, solve time, build time, factor bytes (FP32) and the time of one block apply
+    (CUDA events, 20 applies)."""
     b = torch.from_numpy(si.random_complex(1, g.n)).cuda()
-    out = {"sigma": sigma, "tol": 1e-10, "gmres": "FGMRES(50)"}
-    variants = (("exact_8x32", dict(precond=1, tile=(8, 32), precond_factor=2)),
-                ("exact_8x32_lgmres4", dict(precond=1, tile=(8, 32), precond_factor=2, lgmres_k=4)),
-                ("reduced_8x64", dict(precond=2, tile=(8, 64))),
-                ("reduced_8x512", dict(precond=2, tile=(8, 512))),
-                ("reduced_8x512_lgmres4", dict(precond=2, tile=(8, 512), lgmres_k=4)),
-                ("reduced_4x512", dict(precond=2, tile=(4, 512))))
+    out = {"sigma": sigma, "tol": 1e-10, "gmres": "FGMRES(50)", "unknowns": g.n}
+    nv = g.dim + 2
     for key, o in variants:
         S = Stab(q0, g, f.Ma, f.Re, f.Pr, eps_mode=2, precond_prec=32, gmres_m=50, gmres_tol=1e-10,
-                 gmres_max_restarts=120, **o)
+                 gmres_max_restarts=max_restarts, **o)
         S.autotune()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -439,16 +430,117 @@ def preconditioners_256x512(args, Stab, torch) -> dict:
         S.apply_J(x, ax, sigma)
         res = float(torch.linalg.vector_norm(b - ax) / torch.linalg.vector_norm(b))
         tile = o["tile"]
+        tz = tile[2] if g.dim == 3 else 1
         if o["precond"] == 1:
-            nbytes = g.n * 4 * tile[0] * tile[1] * 8
+            nbytes = g.n * nv * tile[0] * tile[1] * tz * 8
         else:
-            m = 4 * 2 * tile[0]
-            nbytes = g.n * 3 * m * 8
+            nbytes = g.n * 3 * (nv * 2 * tile[0] * tz) * 8
         S.close()
         out[key] = {"iterations": it, "jv_calls": jv, "converged": st == 0, "true_rel_residual": res, "solve_s": dt,
                     "ms_per_iteration": 1e3 * dt / max(it, 1), "build_s": t_build, "apply_ms": apply_ms,
                     "factor_bytes": nbytes, "apply_GB_per_s": nbytes / apply_ms / 1e6}
     return out
+
+
+def preconditioners_256x512(args, Stab, torch) -> dict:
+    """The 256 x 512 inner solve (FGMRES(50) to 1e-10 at sigma = 1) with exact tile blocks (block-Jacobi
+    over 8 x 32 tiles, FP32 inverses factorised with TF32 tensor-core GEMMs) against the reduced-operator
+    blocks (second-order explicit operator, block-tridiagonal FP32 factors) over taller tiles, and with
+    LGMRES(50, 4) beside GMRES(50)."""
+    g, f, q0 = _layer(256, 512, 0.3)
+    variants = (("exact_8x32", dict(precond=1, tile=(8, 32), precond_factor=2)),
+                ("exact_8x32_lgmres4", dict(precond=1, tile=(8, 32), precond_factor=2, lgmres_k=4)),
+                ("reduced_8x64", dict(precond=2, tile=(8, 64))),
+                ("reduced_8x512", dict(precond=2, tile=(8, 512))),
+                ("reduced_8x512_lgmres4", dict(precond=2, tile=(8, 512), lgmres_k=4)),
+                ("reduced_4x512", dict(precond=2, tile=(4, 512))))
+    return inner_solves(Stab, torch, g, f, q0, variants)
+
+
+def _parse_variants(spec: str, dim: int):
+    """'exact:8x8x2,reduced:4x128x2:lg4' -> [(name, Stab options)]."""
+    out = []
+    for item in spec.split(","):
+        parts = item.split(":")
+        tile = tuple(int(t) for t in parts[1].split("x"))
+        if dim == 2:
+            tile = tile[:2]
+        o = dict(precond=1 if parts[0] == "exact" else 2, tile=tile)
+        if parts[0] == "exact":
+            o["precond_factor"] = 2
+        name = f"{parts[0]}_{parts[1]}"
+        for extra in parts[2:]:
+            if extra.startswith("lg"):
+                o["lgmres_k"] = int(extra[2:])
+                name += f"_lgmres{o['lgmres_k']}"
+        out.append((name, o))
+    return out
+
+
+def run_mixed(args):
+    """--workload mixed: Cayley-IRAM (sigma 1, tau -1, nev 4, ncv 20, tol 1e-10, exact-tangent J v) of the
+    --nx x --ny x --nz layer with FP64 block inverses over --tile3 tiles (the plain path) against the
+    mixed-precision variants (FP32 inverses factorised with BF16x9 or TF32 tensor-core GEMMs; BF16
+    inverses with the FP32 Krylov basis; the nested FP32-basis inner GMRES(10); the reduced-operator
+    blocks over --reduced-tile tiles with FP32 factors): per eigenvalue the relative difference to the
+    FP64 path, true residuals, J v counts and times."""
+    import numpy as np
+    import torch
+    from paper_1502_03701_gb300 import Stab, build
+    build.build()
+    g, f, q0 = _layer(args.nx, args.ny, 0.3, nz=args.nz)
+    tile = tuple(args.tile3[:g.dim]) if g.dim == 3 else tuple(args.tile3[:2])
+    rtile = tuple(args.reduced_tile[:g.dim]) if g.dim == 3 else tuple(args.reduced_tile[:2])
+    v0 = torch.from_numpy(si.start_vector(0x5EED, g.n)).cuda()
+    variants = [("fp64_inverses", dict(precond=1, tile=tile, precond_prec=64)),
+                ("fp32_tensor_bf16x9", dict(precond=1, tile=tile, precond_prec=32, precond_factor=1)),
+                ("fp32_tensor_tf32", dict(precond=1, tile=tile, precond_prec=32, precond_factor=2)),
+                ("bf16_inverses_fp32_basis", dict(precond=1, tile=tile, precond_prec=16, precond_factor=1,
+                                                  gmres_basis_prec=32)),
+                ("nested_fp32_inner_gmres10", dict(precond=1, tile=tile, precond_prec=32, precond_factor=1,
+                                                   gmres_inner_m=10, gmres_inner_tol=1e-3)),
+                ("reduced_fp32_factors", dict(precond=2, tile=rtile, precond_prec=32))]
+    ref, rows = None, {}
+    for name, o in variants:
+        gm = 20 if o.get("gmres_inner_m") else 50
+        S = Stab(q0, g, f.Ma, f.Re, f.Pr, eps_mode=2, gmres_m=gm, gmres_tol=1e-10, gmres_max_restarts=200,
+                 max_restarts=30, **o)
+        S.autotune()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = S.eigs(1.0, -1.0, nev=4, ncv=20, tol=1e-10, v0=v0)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        S.close()
+        row = {"status": r.status, "nconv": r.nconv, "seconds": dt, "lam": [[l.real, l.imag] for l in r.lam],
+               "resid": [float(x) for x in r.resid], "jv_calls": r.stats["jv_calls"],
+               "gmres_iterations": r.stats["gmres_iterations"], "tile": list(o["tile"])}
+        if ref is None:
+            ref = r.lam
+        else:
+            row["rel_diff_vs_fp64"] = [float(np.abs(ref - l).min() / abs(l)) for l in r.lam]
+        rows[name] = row
+    worst = max(max(v.get("rel_diff_vs_fp64", [0.0])) for v in rows.values())
+    print(json.dumps({"metric": "largest relative eigenvalue difference to the FP64 path", "value": worst,
+                      "unit": "relative", "n_gpus": 1, "higher_is_better": False, "dtype": "f64",
+                      "config": {"workload": _jv_workload_name(g).replace("jv_", "mixed_"), "sigma": 1.0, "tau": -1.0,
+                                 "nev": 4, "ncv": 20, "tol": 1e-10},
+                      "variants": rows}))
+
+
+def run_inner(args):
+    """--workload inner: the inner solve of the --nx x --ny (x --nz) layer at sigma = 1 for each
+    preconditioner variant of --variants (kind:TXxTYxTZ[:lgK], kind exact or reduced)."""
+    import torch
+    from paper_1502_03701_gb300 import Stab, build
+    build.build()
+    g, f, q0 = _layer(args.nx, args.ny, 0.3, nz=args.nz)
+    r = inner_solves(Stab, torch, g, f, q0, _parse_variants(args.variants, g.dim), max_restarts=args.inner_restarts)
+    best = min((v["solve_s"] for v in r.values() if isinstance(v, dict) and v["converged"]), default=None)
+    print(json.dumps({"metric": "inner solve to 1e-10", "value": (1.0 / best) if best else None, "unit": "solves/s",
+                      "n_gpus": 1, "higher_is_better": True, "dtype": "f64",
+                      "config": {"workload": _jv_workload_name(g).replace("jv_", "inner_"), "variants": args.variants},
+                      "inner": r}))
 
 
 # Algorithmic FP64 flops of the compact line pass per real output value (FMA = 2):
@@ -1207,7 +1299,13 @@ def main():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="jv", choices=["eigs", "jv", "serve", "precond"])
+    ap.add_argument("--workload", default="jv", choices=["eigs", "jv", "serve", "precond", "inner", "mixed"])
+    ap.add_argument("--tile3", type=int, nargs=3, default=[8, 8, 2], help="exact-block tile (--workload mixed)")
+    ap.add_argument("--reduced-tile", type=int, nargs=3, default=[4, 64, 2],
+                    help="reduced-operator tile (--workload mixed)")
+    ap.add_argument("--variants", default="exact:8x8x2,reduced:4x128x2",
+                    help="preconditioner variants of --workload inner: kind:TXxTYxTZ[:lgK], comma separated")
+    ap.add_argument("--inner-restarts", type=int, default=80, help="FGMRES(50) restart limit (--workload inner)")
     ap.add_argument("--tile", type=int, nargs=2, default=[16, 16], help="block-Jacobi tile (--workload precond)")
     ap.add_argument("--factor", type=int, default=1, help="precond_factor (--workload precond)")
     ap.add_argument("--precond", type=int, default=1, choices=[1, 2], help="preconditioner (--workload precond)")
@@ -1242,6 +1340,10 @@ def main():
         run_serve(args)
     elif args.workload == "precond":
         run_precond(args)
+    elif args.workload == "inner":
+        run_inner(args)
+    elif args.workload == "mixed":
+        run_mixed(args)
     else:
         run_ours(args)
 
