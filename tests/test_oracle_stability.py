@@ -210,3 +210,35 @@ def test_block_jacobi_reduces_gmres_iterations(orc):
     _, st0 = orc.krylov.fgmres(lambda z: A @ z, b, None, m=40, tol=1e-8, max_restarts=200)
     _, st1 = orc.krylov.fgmres(lambda z: A @ z, b, M, m=40, tol=1e-8, max_restarts=200)
     assert st1.converged and st1.matvecs < st0.matvecs
+
+
+@pytest.mark.parametrize("dim,shape,tile", [(2, (8, 12, 1), (4, 12)), (2, (16, 16, 1), (8, 8)),
+                                            (3, (8, 8, 6), (4, 8, 2))])
+def test_reduced_operator_tiles_are_block_tridiagonal_in_y_levels(orc, dim, shape, tile):
+    """The structure the reduced-operator preconditioner's factorisation relies on (reading of the
+    reduced operator: three-point stencils, four-point end rows): inside every tile, grouping the points in
+    levels of two y lines, a level of J_low couples only to itself and its two neighbouring levels, the
+    domain's y boundaries included.  The compact operator's tiles are dense along y (its derivatives are
+    global on a line), so the same grouping has nonzero couplings two or more levels apart there."""
+    nx, ny, nz = shape
+    if dim == 2:
+        g, f = si.mixing_layer_2d(nx, ny)
+    else:
+        g = si.Grid(3, nx, ny, nz, si.LX_04, -15, 15, si.LX_04)
+        f = si.Flow(0.5, 800.0)
+    q0 = si.tanh_base_flow(g, f)
+    JL = orc.core.dense_jacobian(orc.Problem.from_inputs(g, f, low_order=1), q0)
+    J = orc.core.dense_jacobian(orc.Problem.from_inputs(g, f), q0)
+    npts = nx * ny * nz
+    tx, ty = tile[0], tile[1]
+    tz = tile[2] if dim == 3 else 1
+    nlev = ty // 2
+    for t, dofs in enumerate(orc.stability.tile_dofs(orc.Problem.from_inputs(g, f), tile[:dim])):
+        pts = dofs % npts
+        ylocal = (pts // nx) % ny % ty
+        lev = ylocal // 2
+        far = np.abs(lev[:, None] - lev[None, :]) > 1
+        blk_low = JL[np.ix_(dofs, dofs)]
+        assert np.all(blk_low[far] == 0.0), t
+        if nlev > 2:
+            assert np.abs(J[np.ix_(dofs, dofs)][far]).max() > 0.0
