@@ -151,3 +151,23 @@ def test_reduced_preconditioner_rejections():
         B.solve([0.5], [q], [torch.zeros_like(q)])
     B.close()
     S.close()
+
+
+@pytest.mark.parametrize("opts", [dict(gmres_basis_prec=32), dict(gmres_inner_m=10, gmres_inner_tol=1e-3),
+                                  dict(lgmres_k=4)], ids=["fp32_basis", "nested_inner", "lgmres"])
+def test_reduced_preconditioner_with_other_inner_solvers(orc, opts):
+    """The reduced-operator preconditioner under the FP32-basis GMRES (FP32 input to the level sweeps),
+    the nested FP32 inner GMRES and LGMRES: each solve meets 1e-10 against the oracle's exact-tangent
+    J v."""
+    import torch
+    g, f = si.mixing_layer_2d(32, 64)
+    S, q0 = _make(g, f, tile=(8, 64), precond_prec=32, eps_mode=2, gmres_m=30 if "gmres_inner_m" in opts else 50,
+                  gmres_tol=1e-10, gmres_max_restarts=200, **opts)
+    b = si.random_complex(6, g.n)
+    x = torch.zeros(g.n, dtype=torch.complex128, device="cuda")
+    st, iters = S.solve(1.0, torch.from_numpy(b).cuda(), x)
+    S.close()
+    assert st == 0 and iters > 0
+    xh = x.cpu().numpy()
+    r = b - (orc.core.jv(orc.Problem.from_inputs(g, f), q0, xh, "tangent") - xh)
+    assert np.linalg.norm(r) <= 1.1e-10 * np.linalg.norm(b)
