@@ -95,3 +95,20 @@ def test_batch_binding_checks_arguments_before_calling_the_library():
     with pytest.raises(StabError, match="closed"):
         B.apply([1, 2], [1, 2])
     B._b = None
+
+
+def test_memory_estimate_of_the_reduced_preconditioner():
+    """The reduced-operator factors take three m x m level blocks per level (m = nv * 2 * tx * tz), so
+    their estimate does not grow with the tile height, while the dense tile inverses grow with its square."""
+    import stab_inputs as si
+    from paper_1502_03701_gb300 import estimate_bytes
+    g, _ = si.mixing_layer_2d(64, 128, Ma=0.3)
+    n = 4 * 64 * 128
+    base = estimate_bytes(g, 4, 30, precond=0)
+    short = estimate_bytes(g, 4, 30, precond=2, tile=(8, 16)) - base
+    tall = estimate_bytes(g, 4, 30, precond=2, tile=(8, 128)) - base
+    m = 4 * 2 * 8
+    assert short >= n * 3 * m * 8 and tall >= n * 3 * m * 8      # FP32 factors: 3 m complex per unknown
+    assert tall < 1.2 * short + (2 << 20)
+    dense = estimate_bytes(g, 4, 30, precond=1, tile=(8, 16)) - base
+    assert dense > n * 4 * 8 * 16 * 8                            # b complex per unknown, b = 512
